@@ -1,0 +1,286 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow, CPU-only FP64 statement of the batched step-and-render (kinematic bicycle,
+OBB collision, off-road, halt; per-camera transform, near/guard clipping, projection,
+1/16-pixel snapping, and the integer + FP32 raster rule).  Only ``tests/``, the smoke
+check and the benchmark's CPU-baseline leg may import this package; the product path
+(the CUDA library and its binding) never does, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, compiled with -ffp-contract=off); this
+module only marshals numpy arrays.  Every function cites the passage it follows in the
+C source.  Parity pins: ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+
+COLLIDED, OFFROAD, HALTED = 1, 2, 4
+
+TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,)),
+                      ("prim", "<u4"), ("sub", "<u4")])
+
+
+class OrCam(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("hfov", ctypes.c_double), ("cam_height", ctypes.c_double),
+                ("near", ctypes.c_double), ("line_z", ctypes.c_double),
+                ("guard", ctypes.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, FP64 geometry, no fused multiply-adds but fmaf).
+
+    ``ORACLE_SO`` in the environment names a prebuilt library to load instead (the
+    mutation test uses it to load deliberately broken copies).
+    """
+    if os.environ.get("ORACLE_SO"):
+        return os.environ["ORACLE_SO"]
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib_handle = None
+P = ctypes.POINTER
+c_f64p, c_f32p, c_u8p = P(ctypes.c_double), P(ctypes.c_float), P(ctypes.c_uint8)
+c_u16p, c_u64p = P(ctypes.c_uint16), P(ctypes.c_uint64)
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(build())
+        lib.or_bicycle.argtypes = [c_f64p, c_f64p, c_f64p, c_f64p] + [ctypes.c_double] * 5
+        lib.or_obb_overlap.argtypes = [c_f64p, c_f64p]
+        lib.or_obb_overlap.restype = ctypes.c_int
+        lib.or_point_in_quad.argtypes = [ctypes.c_double, ctypes.c_double, c_f32p]
+        lib.or_point_in_quad.restype = ctypes.c_int
+        lib.or_step_world.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p, c_u8p,
+                                      c_f32p, ctypes.c_int32, c_f32p, ctypes.c_double,
+                                      ctypes.c_double]
+        lib.or_camera_tris.argtypes = [P(OrCam), ctypes.c_int32, c_f64p, ctypes.c_int32,
+                                       ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
+        lib.or_camera_tris.restype = ctypes.c_int64
+        for fn in (lib.or_raster, lib.or_raster_bruteforce):
+            fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, c_u64p, c_u8p,
+                           c_f32p, c_u16p]
+        lib.or_f32_to_f16.argtypes = [ctypes.c_float]
+        lib.or_f32_to_f16.restype = ctypes.c_uint16
+        lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
+        lib.or_f32_to_bf16.restype = ctypes.c_uint16
+        lib.or_onehot_bf16.argtypes = [c_u8p, ctypes.c_int64, c_f32p, c_f32p, c_u16p]
+        _lib_handle = lib
+    return _lib_handle
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---------------------------------------------------------------------------------------
+# Dynamics
+# ---------------------------------------------------------------------------------------
+
+def bicycle(x, y, yaw, v, L, accel, steer, dt=0.1, vmax=30.0):
+    """One kinematic-bicycle step (App. A "Action Space and Dynamics"); returns x, y, yaw, v."""
+    cx, cy, cyaw, cv = (ctypes.c_double(float(t)) for t in (x, y, yaw, v))
+    _lib().or_bicycle(ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(cyaw), ctypes.byref(cv),
+                      float(L), float(accel), float(steer), float(dt), float(vmax))
+    return cx.value, cy.value, cyaw.value, cv.value
+
+
+def obb_overlap(a: Sequence[float], b: Sequence[float]) -> bool:
+    """Footprint interiors intersect (x, y, yaw, L, W each)."""
+    aa, bb = _c(a[:5], np.float64), _c(b[:5], np.float64)
+    return bool(_lib().or_obb_overlap(_p(aa, c_f64p), _p(bb, c_f64p)))
+
+
+def point_in_quad(px: float, py: float, quad: Sequence[float]) -> bool:
+    q = _c(quad, np.float32)
+    return bool(_lib().or_point_in_quad(float(px), float(py), _p(q, c_f32p)))
+
+
+def step_world(boxes6: np.ndarray, state: np.ndarray, flags: np.ndarray, actions: np.ndarray,
+               road: np.ndarray, dt: float = 0.1, vmax: float = 30.0) -> None:
+    """One step of one world in place (App. A dynamics + infractions + halt).
+
+    boxes6 float64 [n_boxes, 6]; state float64 [n_agents, 4]; flags uint8 [n_agents];
+    actions float32 [n_agents, 2]; road float32 [n_road, 8].
+    """
+    assert boxes6.dtype == np.float64 and boxes6.flags.c_contiguous
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    assert flags.dtype == np.uint8 and flags.flags.c_contiguous
+    act = _c(actions, np.float32)
+    rd = _c(road, np.float32).reshape(-1, 8)
+    _lib().or_step_world(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p), _p(state, c_f64p),
+                         _p(flags, c_u8p), _p(act, c_f32p), rd.shape[0], _p(rd, c_f32p),
+                         float(dt), float(vmax))
+
+
+# ---------------------------------------------------------------------------------------
+# Geometry and raster
+# ---------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class CamConfig:
+    width: int
+    height: int
+    hfov: float = math.pi / 2
+    cam_height: float = 1.5
+    near: float = 0.1
+    line_z: float = 0.02
+    guard: float = 4.0
+
+    def c(self) -> OrCam:
+        return OrCam(self.width, self.height, self.hfov, self.cam_height, self.near,
+                     self.line_z, self.guard)
+
+
+def camera_tris(cam: CamConfig, boxes6: np.ndarray, ego: int, road: np.ndarray,
+                line: np.ndarray, ax: float, ay: float, ayaw: float, cam_yaw: float = 0.0,
+                cap: Optional[int] = None) -> np.ndarray:
+    """FP64 scene triangles of one camera after clipping, snapping and back-face culling."""
+    b = _c(boxes6, np.float64).reshape(-1, 6)
+    rd = _c(road, np.float32).reshape(-1, 8)
+    ln = _c(line, np.float32).reshape(-1, 8)
+    lib = _lib()
+    c = cam.c()
+    if cap is None:
+        cap = 6 * (12 * b.shape[0] + 2 * rd.shape[0] + 2 * ln.shape[0]) + 16
+    out = np.zeros(cap, TRI_DTYPE)
+    n = lib.or_camera_tris(ctypes.byref(c), b.shape[0], _p(b, c_f64p), int(ego), rd.shape[0],
+                           _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), float(ax), float(ay),
+                           float(ayaw), float(cam_yaw), out.ctypes.data, cap)
+    assert n <= cap
+    return out[:n].copy()
+
+
+@dataclasses.dataclass
+class Image:
+    key: np.ndarray      # uint64 [H, W]
+    cls: np.ndarray      # uint8 [H, W]
+    depth: np.ndarray    # float32 [H, W] (FP32 key mode) or uint16 binary16 bits (FP16)
+
+
+def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: int,
+           road_end: int, bruteforce: bool = False) -> Image:
+    """The raster rule on snapped triangles; box_end = 12 n_boxes, road_end = box_end + 2 n_road."""
+    t = _c(tris, TRI_DTYPE)
+    if key_f16 and len(t):
+        assert int(t["prim"].max()) <= 0xFFFE, "FP16 keys hold 16-bit primitive ids"
+    key = np.zeros((height, width), np.uint64)
+    cls = np.zeros((height, width), np.uint8)
+    d32 = np.zeros((height, width), np.float32)
+    d16 = np.zeros((height, width), np.uint16)
+    fn = _lib().or_raster_bruteforce if bruteforce else _lib().or_raster
+    fn(t.ctypes.data, len(t), width, height, int(key_f16), box_end, road_end, _p(key, c_u64p),
+       _p(cls, c_u8p), _p(d32, c_f32p), _p(d16, c_u16p))
+    return Image(key, cls, d16 if key_f16 else d32)
+
+
+def f32_to_f16_bits(x) -> np.ndarray:
+    a = np.asarray(x, np.float32).ravel()
+    lib = _lib()
+    return np.array([lib.or_f32_to_f16(float(v)) for v in a], np.uint16)
+
+
+def f32_to_bf16_bits(x) -> np.ndarray:
+    a = np.asarray(x, np.float32).ravel()
+    lib = _lib()
+    return np.array([lib.or_f32_to_bf16(float(v)) for v in a], np.uint16)
+
+
+def onehot_bf16(cls: np.ndarray, mean=(0.5,) * 4, std=(0.5,) * 4) -> np.ndarray:
+    """bf16 bits [4, *cls.shape] of (onehot - mean) / std, per channel."""
+    c = _c(cls, np.uint8)
+    m, s = _c(mean, np.float32), _c(std, np.float32)
+    out = np.zeros((4,) + c.shape, np.uint16)
+    _lib().or_onehot_bf16(_p(c, c_u8p), c.size, _p(m, c_f32p), _p(s, c_f32p), _p(out, c_u16p))
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Batch driver over worlds (plain loops)
+# ---------------------------------------------------------------------------------------
+
+class Sim:
+    """Oracle simulation of a batch of worlds: FP64 agent state, latched flags."""
+
+    def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0):
+        self.w = worlds
+        self.dt, self.vmax = dt, vmax
+        na = worlds.n_agents
+        self.agent_off = worlds.agent_offsets()
+        self.state = np.zeros((na, 4), np.float64)
+        self.flags = np.zeros(na, np.uint8)
+        for w in range(worlds.n_worlds):
+            b0 = int(worlds.box_off[w])
+            a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
+            bx = worlds.boxes[b0:b0 + (a1 - a0)].astype(np.float64)
+            self.state[a0:a1, 0:3] = bx[:, 0:3]
+            self.state[a0:a1, 3] = bx[:, 6]
+
+    def set_state(self, state, flags) -> None:
+        self.state[:] = np.asarray(state, np.float64)
+        self.flags[:] = np.asarray(flags, np.uint8)
+
+    def boxes6(self, w: int) -> np.ndarray:
+        b0, b1 = int(self.w.box_off[w]), int(self.w.box_off[w + 1])
+        b = self.w.boxes[b0:b1, 0:6].astype(np.float64)
+        a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
+        b[: a1 - a0, 0:3] = self.state[a0:a1, 0:3]
+        return np.ascontiguousarray(b)
+
+    def road(self, w: int) -> np.ndarray:
+        return self.w.road[int(self.w.road_off[w]):int(self.w.road_off[w + 1])]
+
+    def line(self, w: int) -> np.ndarray:
+        return self.w.line[int(self.w.line_off[w]):int(self.w.line_off[w + 1])]
+
+    def step(self, actions: np.ndarray, worlds: Optional[Sequence[int]] = None) -> None:
+        ws = range(self.w.n_worlds) if worlds is None else worlds
+        for w in ws:
+            a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
+            b = self.boxes6(w)
+            st = np.ascontiguousarray(self.state[a0:a1])
+            fl = np.ascontiguousarray(self.flags[a0:a1])
+            step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax)
+            self.state[a0:a1] = st
+            self.flags[a0:a1] = fl
+
+    def camera_tris(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> np.ndarray:
+        a = int(self.agent_off[w]) + agent_local
+        return camera_tris(cam, self.boxes6(w), agent_local, self.road(w), self.line(w),
+                           self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw)
+
+    def prim_ranges(self, w: int):
+        nb = int(self.w.box_off[w + 1] - self.w.box_off[w])
+        nr = int(self.w.road_off[w + 1] - self.w.road_off[w])
+        return 12 * nb, 12 * nb + 2 * nr
+
+    def render(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float,
+               key_f16: bool = False) -> Image:
+        tris = self.camera_tris(cam, w, agent_local, cam_yaw)
+        be, re = self.prim_ranges(w)
+        return raster(tris, cam.width, cam.height, key_f16, be, re)

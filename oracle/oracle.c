@@ -1,0 +1,564 @@
+/*
+ * ORACLE -- test infrastructure only.  A plain, slow, CPU-only FP64 statement of what
+ * the batched step-and-render computes, used by tests/, the smoke check and the CPU
+ * baseline leg of the benchmark.  The product path never calls it; it shares no code,
+ * header, table or constant with the CUDA library.
+ *
+ * What it follows (paper: "Scaling Self-Play for End-to-End Driving", Gigapixel):
+ *   Sec. 3.1 and App. A "High-Throughput Batched Rendering": the world is agent/static
+ *     cuboids plus flat road planes and thin lane-line strips; each agent gets an
+ *     ego-centric perspective image.
+ *   App. A "Action Space and Dynamics": kinematic bicycle, wheelbase 60 % of length,
+ *     simulation step 0.1 s.
+ *   App. A "Reward Functions" and "Other Details": vehicle collisions and leaving the
+ *     drivable area are infractions; an infracting agent is halted in place (velocity
+ *     zeroed) and keeps being observed/rendered.
+ * The paper gives no rasterisation rule; the rule below is this project's reading
+ * (listed as such in the design notes): 1/16-pixel round-half-even snapping, pixel-centre
+ * sampling, top-left fill rule, back-face culling, near plane + 4x guard band clipping
+ * (Sutherland-Hodgman, planes in the order near, left, right, bottom, top), reversed-Z
+ * depth d = n / z_view interpolated by a fixed FP32 plane formula, nearest (largest d)
+ * wins, ties to the smaller primitive id.
+ *
+ * Precision: geometry and dynamics in FP64.  The raster stage applies the rule on
+ * snapped integer vertices and FP32 per-vertex depths; its depth-plane arithmetic is the
+ * fixed IEEE FP32 sequence the rule defines (compile with -ffp-contract=off so no
+ * operation is fused that the rule does not fuse).
+ *
+ * Parity pins: see tests/test_oracle_pins.py (closed forms, symmetry, brute-force ray
+ * casting, watertightness, bicycle closed forms, SAT vs polygon clipping, point-in-quad vs
+ * winding number, half/bfloat16 rounding vs numpy/torch).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------------------
+ * Dynamics (App. A "Action Space and Dynamics"; "Other Details")
+ * ------------------------------------------------------------------------------------ */
+
+enum { OR_COLLIDED = 1, OR_OFFROAD = 2, OR_HALTED = 4 };
+
+static double wrap_pi(double a) {
+    /* to (-pi, pi] */
+    while (a > M_PI) a -= 2.0 * M_PI;
+    while (a <= -M_PI) a += 2.0 * M_PI;
+    return a;
+}
+
+/*
+ * Kinematic bicycle, centre reference point, wheelbase 0.6 L split evenly
+ * (l_r = l_f = 0.3 L): slip angle beta = atan(l_r / (l_f + l_r) * tan(steer)); explicit
+ * Euler with the speed of the start of the step; then v += a dt clipped to [0, v_max].
+ */
+void or_bicycle(double *x, double *y, double *yaw, double *v, double L, double accel,
+                double steer, double dt, double vmax) {
+    double lr = 0.3 * L;
+    double beta = atan(0.5 * tan(steer));
+    double v0 = *v;
+    *x += v0 * cos(*yaw + beta) * dt;
+    *y += v0 * sin(*yaw + beta) * dt;
+    *yaw = wrap_pi(*yaw + (v0 / lr) * sin(beta) * dt);
+    double vn = v0 + accel * dt;
+    if (vn < 0.0) vn = 0.0;
+    if (vn > vmax) vn = vmax;
+    *v = vn;
+}
+
+/* Footprint corners of a box (x, y, yaw, L, W), counter-clockwise from above. */
+static void footprint(double x, double y, double yaw, double L, double W, double c[4][2]) {
+    double cs = cos(yaw), sn = sin(yaw);
+    const double sx[4] = {-0.5, 0.5, 0.5, -0.5};
+    const double sy[4] = {-0.5, -0.5, 0.5, 0.5};
+    for (int k = 0; k < 4; ++k) {
+        double lx = sx[k] * L, ly = sy[k] * W;
+        c[k][0] = x + cs * lx - sn * ly;
+        c[k][1] = y + sn * lx + cs * ly;
+    }
+}
+
+/*
+ * Two footprints collide iff their interiors intersect.  For convex polygons this holds
+ * iff no edge normal separates them (separating-axis theorem): on every one of the four
+ * axes the projected intervals overlap with positive length.  Touching is not a collision.
+ */
+int or_obb_overlap(const double a[5], const double b[5]) {
+    double ca[4][2], cb[4][2];
+    footprint(a[0], a[1], a[2], a[3], a[4], ca);
+    footprint(b[0], b[1], b[2], b[3], b[4], cb);
+    double axes[4][2] = {{cos(a[2]), sin(a[2])}, {-sin(a[2]), cos(a[2])},
+                         {cos(b[2]), sin(b[2])}, {-sin(b[2]), cos(b[2])}};
+    for (int k = 0; k < 4; ++k) {
+        double amin = INFINITY, amax = -INFINITY, bmin = INFINITY, bmax = -INFINITY;
+        for (int i = 0; i < 4; ++i) {
+            double pa = ca[i][0] * axes[k][0] + ca[i][1] * axes[k][1];
+            double pb = cb[i][0] * axes[k][0] + cb[i][1] * axes[k][1];
+            if (pa < amin) amin = pa;
+            if (pa > amax) amax = pa;
+            if (pb < bmin) bmin = pb;
+            if (pb > bmax) bmax = pb;
+        }
+        double lo = amin > bmin ? amin : bmin;
+        double hi = amax < bmax ? amax : bmax;
+        if (!(lo < hi)) return 0;
+    }
+    return 1;
+}
+
+/* Point in a convex quad (corners counter-clockwise from above); boundary counts inside. */
+int or_point_in_quad(double px, double py, const float *q) {
+    for (int k = 0; k < 4; ++k) {
+        double ax = q[2 * k], ay = q[2 * k + 1];
+        double bx = q[2 * ((k + 1) & 3)], by = q[2 * ((k + 1) & 3) + 1];
+        double cr = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+        if (cr < 0.0) return 0;
+    }
+    return 1;
+}
+
+/*
+ * One simulation step of one world, in place.
+ *   boxes  [n_boxes][6]  x, y, yaw, L, W, H  (rows of agents are overwritten from state)
+ *   state  [n_agents][4] x, y, yaw, v        (FP64)
+ *   flags  [n_agents]    bit0 collided, bit1 off-road, bit2 halted (all latched)
+ *   actions[n_agents][2] accel (m/s^2), steer (rad)
+ *   road   [n_road][8]   road-surface quads
+ * Order: move every non-halted agent; then flag collisions among all pairs that contain
+ * an agent; then flag agents with a footprint corner outside every road quad; then halt
+ * every flagged agent (v = 0).  Halted agents stay in place and stay in the scene.
+ */
+void or_step_world(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
+                   uint8_t *flags, const float *actions, int32_t n_road, const float *road,
+                   double dt, double vmax) {
+    for (int32_t i = 0; i < n_agents; ++i) {
+        double *s = state + 4 * i;
+        if (!(flags[i] & OR_HALTED)) {
+            or_bicycle(&s[0], &s[1], &s[2], &s[3], boxes[6 * i + 3], actions[2 * i],
+                       actions[2 * i + 1], dt, vmax);
+        } else {
+            s[3] = 0.0;
+        }
+        boxes[6 * i + 0] = s[0];
+        boxes[6 * i + 1] = s[1];
+        boxes[6 * i + 2] = s[2];
+    }
+    for (int32_t i = 0; i < n_agents; ++i) {
+        for (int32_t j = i + 1; j < n_boxes; ++j) {
+            double a[5] = {boxes[6 * i], boxes[6 * i + 1], boxes[6 * i + 2], boxes[6 * i + 3],
+                           boxes[6 * i + 4]};
+            double b[5] = {boxes[6 * j], boxes[6 * j + 1], boxes[6 * j + 2], boxes[6 * j + 3],
+                           boxes[6 * j + 4]};
+            if (or_obb_overlap(a, b)) {
+                flags[i] |= OR_COLLIDED;
+                if (j < n_agents) flags[j] |= OR_COLLIDED;
+            }
+        }
+    }
+    for (int32_t i = 0; i < n_agents; ++i) {
+        double c[4][2];
+        footprint(boxes[6 * i], boxes[6 * i + 1], boxes[6 * i + 2], boxes[6 * i + 3],
+                  boxes[6 * i + 4], c);
+        for (int k = 0; k < 4; ++k) {
+            int inside = 0;
+            for (int32_t r = 0; r < n_road && !inside; ++r)
+                inside = or_point_in_quad(c[k][0], c[k][1], road + 8 * r);
+            if (!inside) {
+                flags[i] |= OR_OFFROAD;
+                break;
+            }
+        }
+    }
+    for (int32_t i = 0; i < n_agents; ++i) {
+        if (flags[i] & (OR_COLLIDED | OR_OFFROAD)) {
+            flags[i] |= OR_HALTED;
+            state[4 * i + 3] = 0.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Geometry: camera, scene triangles, clipping, projection, snapping (FP64)
+ * ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t X[3], Y[3]; /* snapped positions, 1/16 pixel units, y down */
+    float d[3];         /* per-vertex reversed-Z depth n / z_view, rounded to FP32 */
+    uint32_t prim;      /* primitive id (see below) */
+    uint32_t sub;       /* index of the triangle in the clipped polygon's fan */
+} or_tri;
+
+typedef struct {
+    int32_t width, height;
+    double hfov;        /* horizontal field of view, rad */
+    double cam_height;  /* camera height above ground, m */
+    double near;        /* near plane distance, m */
+    double line_z;      /* lane-line strip height above the road, m */
+    double guard;       /* guard band, in multiples of the viewport half-extent */
+} or_cam;
+
+typedef struct { double x, y, z; } v3;
+
+/* Box corner k: x = +-L/2 (bit 0), y = +-W/2 (bit 1), z = 0 or H (bit 2). */
+static v3 box_corner(const double *b, int k) {
+    double lx = (k & 1) ? 0.5 * b[3] : -0.5 * b[3];
+    double ly = (k & 2) ? 0.5 * b[4] : -0.5 * b[4];
+    double cs = cos(b[2]), sn = sin(b[2]);
+    v3 p = {b[0] + cs * lx - sn * ly, b[1] + sn * lx + cs * ly, (k & 4) ? b[5] : 0.0};
+    return p;
+}
+
+/* Faces as corner quads, counter-clockwise seen from outside, in the order
+ * +x, -x, +y, -y, +z, -z.  Face quad (q0 q1 q2 q3) -> triangles (q0 q1 q2), (q0 q2 q3). */
+static const int BOX_FACES[6][4] = {
+    {1, 3, 7, 5}, {0, 4, 6, 2}, {2, 6, 7, 3}, {0, 1, 5, 4}, {4, 5, 7, 6}, {0, 2, 3, 1}};
+
+typedef struct {
+    double s, c;   /* sin, cos of camera yaw */
+    double px, py, pz;
+    double f;      /* focal length in pixels */
+    double tx, ty; /* viewport half-extent over focal length */
+} camera;
+
+static v3 to_view(const camera *cm, v3 p) {
+    double dx = p.x - cm->px, dy = p.y - cm->py, dz = p.z - cm->pz;
+    v3 v = {dx * cm->s - dy * cm->c, dz, dx * cm->c + dy * cm->s};
+    return v;
+}
+
+/* Signed distance-like value to clip plane k (inside >= 0). */
+static double plane_dist(const or_cam *cfg, const camera *cm, int k, v3 v) {
+    double g = cfg->guard;
+    switch (k) {
+    case 0: return v.z - cfg->near;
+    case 1: return v.x + g * cm->tx * v.z;
+    case 2: return g * cm->tx * v.z - v.x;
+    case 3: return v.y + g * cm->ty * v.z;
+    default: return g * cm->ty * v.z - v.y;
+    }
+}
+
+/* Sutherland-Hodgman against one plane; the crossing point is always interpolated from
+ * the inside vertex towards the outside one. */
+static int clip_plane(const or_cam *cfg, const camera *cm, int k, const v3 *in, int n, v3 *out) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        v3 a = in[i], b = in[(i + 1) % n];
+        double da = plane_dist(cfg, cm, k, a), db = plane_dist(cfg, cm, k, b);
+        int ia = da >= 0.0, ib = db >= 0.0;
+        if (ia) out[m++] = a;
+        if (ia != ib) {
+            v3 vi = ia ? a : b, vo = ia ? b : a;
+            double di = ia ? da : db, dov = ia ? db : da;
+            double t = di / (di - dov);
+            v3 p = {vi.x + t * (vo.x - vi.x), vi.y + t * (vo.y - vi.y), vi.z + t * (vo.z - vi.z)};
+            out[m++] = p;
+        }
+    }
+    return m;
+}
+
+static int64_t emit_triangle(const or_cam *cfg, const camera *cm, v3 a, v3 b, v3 c, uint32_t prim,
+                             or_tri *out, int64_t n, int64_t cap) {
+    v3 poly[16], tmp[16];
+    poly[0] = to_view(cm, a);
+    poly[1] = to_view(cm, b);
+    poly[2] = to_view(cm, c);
+    int m = 3;
+    for (int k = 0; k < 5 && m >= 3; ++k) {
+        m = clip_plane(cfg, cm, k, poly, m, tmp);
+        memcpy(poly, tmp, sizeof(v3) * (size_t)m);
+    }
+    if (m < 3) return n;
+    int32_t X[16], Y[16];
+    float d[16];
+    for (int i = 0; i < m; ++i) {
+        double xs = 0.5 * cfg->width + cm->f * poly[i].x / poly[i].z;
+        double ys = 0.5 * cfg->height - cm->f * poly[i].y / poly[i].z;
+        X[i] = (int32_t)rint(16.0 * xs); /* default rounding mode: round half to even */
+        Y[i] = (int32_t)rint(16.0 * ys);
+        d[i] = (float)(cfg->near / poly[i].z);
+    }
+    for (int k = 1; k + 1 < m; ++k) {
+        int i0 = 0, i1 = k, i2 = k + 1;
+        int64_t area2 = (int64_t)(X[i1] - X[i0]) * (Y[i2] - Y[i0]) -
+                        (int64_t)(X[i2] - X[i0]) * (Y[i1] - Y[i0]);
+        if (area2 >= 0) continue; /* back-facing or degenerate in y-down screen space */
+        if (n < cap) {
+            or_tri *t = out + n;
+            t->X[0] = X[i0]; t->X[1] = X[i1]; t->X[2] = X[i2];
+            t->Y[0] = Y[i0]; t->Y[1] = Y[i1]; t->Y[2] = Y[i2];
+            t->d[0] = d[i0]; t->d[1] = d[i1]; t->d[2] = d[i2];
+            t->prim = prim;
+            t->sub = (uint32_t)(k - 1);
+        }
+        ++n;
+    }
+    return n;
+}
+
+/*
+ * Scene triangles of one camera, FP64 geometry.
+ *   boxes [n_boxes][6] x, y, yaw, L, W, H (current poses); box `ego` is skipped
+ *   road/line quads [n][8]; roads at z = 0, lane lines at z = cfg->line_z
+ *   agent pose (ax, ay, ayaw), camera yaw offset cam_yaw
+ * Primitive ids: box b face-triangle t -> 12 b + t; road quad r triangle t ->
+ * 12 n_boxes + 2 r + t; lane-line quad l triangle t -> 12 n_boxes + 2 n_road + 2 l + t.
+ * Writes at most `cap` triangles; returns the number produced.
+ */
+int64_t or_camera_tris(const or_cam *cfg, int32_t n_boxes, const double *boxes, int32_t ego,
+                       int32_t n_road, const float *road, int32_t n_line, const float *line,
+                       double ax, double ay, double ayaw, double cam_yaw, or_tri *out,
+                       int64_t cap) {
+    camera cm;
+    double yaw = ayaw + cam_yaw;
+    cm.s = sin(yaw);
+    cm.c = cos(yaw);
+    cm.px = ax;
+    cm.py = ay;
+    cm.pz = cfg->cam_height;
+    cm.f = 0.5 * cfg->width / tan(0.5 * cfg->hfov);
+    cm.tx = 0.5 * cfg->width / cm.f;
+    cm.ty = 0.5 * cfg->height / cm.f;
+    int64_t n = 0;
+    for (int32_t b = 0; b < n_boxes; ++b) {
+        if (b == ego) continue;
+        const double *bx = boxes + 6 * b;
+        v3 cn[8];
+        for (int k = 0; k < 8; ++k) cn[k] = box_corner(bx, k);
+        for (int f = 0; f < 6; ++f) {
+            const int *q = BOX_FACES[f];
+            n = emit_triangle(cfg, &cm, cn[q[0]], cn[q[1]], cn[q[2]], (uint32_t)(12 * b + 2 * f),
+                              out, n, cap);
+            n = emit_triangle(cfg, &cm, cn[q[0]], cn[q[2]], cn[q[3]],
+                              (uint32_t)(12 * b + 2 * f + 1), out, n, cap);
+        }
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        int32_t nq = pass ? n_line : n_road;
+        const float *qs = pass ? line : road;
+        double z = pass ? cfg->line_z : 0.0;
+        uint32_t base = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road : 0));
+        for (int32_t i = 0; i < nq; ++i) {
+            const float *q = qs + 8 * i;
+            v3 c[4];
+            for (int k = 0; k < 4; ++k) {
+                c[k].x = q[2 * k];
+                c[k].y = q[2 * k + 1];
+                c[k].z = z;
+            }
+            n = emit_triangle(cfg, &cm, c[0], c[1], c[2], base + 2 * i, out, n, cap);
+            n = emit_triangle(cfg, &cm, c[0], c[2], c[3], base + 2 * i + 1, out, n, cap);
+        }
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Raster rule on snapped triangles (integer coverage + FP32 depth)
+ * ------------------------------------------------------------------------------------ */
+
+/* IEEE binary32 -> binary16, round to nearest even (subnormals, overflow, NaN handled). */
+uint16_t or_f32_to_f16(float f) {
+    uint32_t x;
+    memcpy(&x, &f, 4);
+    uint32_t sign = (x >> 16) & 0x8000u;
+    uint32_t ax = x & 0x7FFFFFFFu;
+    if (ax >= 0x7F800000u) return (uint16_t)(sign | 0x7C00u | (ax > 0x7F800000u ? 0x200u : 0u));
+    if (ax >= 0x477FF000u) return (uint16_t)(sign | 0x7C00u); /* >= 65520 rounds to inf */
+    int32_t e = (int32_t)(ax >> 23);
+    uint32_t mant = ax & 0x7FFFFFu;
+    if (e >= 113) { /* normal half: value >= 2^-14 */
+        uint32_t h = ((uint32_t)(e - 112) << 10) | (mant >> 13);
+        uint32_t rem = mant & 0x1FFFu;
+        if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+        return (uint16_t)(sign | h);
+    }
+    /* subnormal half (or zero): value / 2^-24, rounded */
+    if (e == 0) return (uint16_t)sign; /* float subnormals are far below half's range */
+    uint32_t m24 = mant | 0x800000u;
+    int32_t shift = 126 - e; /* >= 14 */
+    if (shift > 24) return (uint16_t)sign;
+    uint32_t h = m24 >> shift;
+    uint32_t rem = m24 & ((1u << shift) - 1u);
+    uint32_t half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (h & 1u))) ++h;
+    return (uint16_t)(sign | h);
+}
+
+/* IEEE binary32 -> bfloat16, round to nearest even. */
+uint16_t or_f32_to_bf16(float f) {
+    uint32_t x;
+    memcpy(&x, &f, 4);
+    if ((x & 0x7FFFFFFFu) > 0x7F800000u) return (uint16_t)((x >> 16) | 0x40u);
+    x += 0x7FFFu + ((x >> 16) & 1u);
+    return (uint16_t)(x >> 16);
+}
+
+/* Triangle in raster form: positive-area vertex order, edge top-left flags, depth plane. */
+typedef struct {
+    int64_t X[3], Y[3];
+    int tl[3];
+    float d0, a, b;
+    uint32_t prim;
+} rtri;
+
+static int setup_rtri(const or_tri *t, rtri *r) {
+    int64_t area2 = (int64_t)(t->X[1] - t->X[0]) * (t->Y[2] - t->Y[0]) -
+                    (int64_t)(t->X[2] - t->X[0]) * (t->Y[1] - t->Y[0]);
+    if (area2 == 0) return 0;
+    int o[3] = {0, 1, 2};
+    if (area2 < 0) { o[1] = 2; o[2] = 1; area2 = -area2; }
+    float dv[3];
+    for (int k = 0; k < 3; ++k) {
+        r->X[k] = t->X[o[k]];
+        r->Y[k] = t->Y[o[k]];
+        dv[k] = t->d[o[k]];
+    }
+    for (int k = 0; k < 3; ++k) {
+        int64_t dx = r->X[(k + 1) % 3] - r->X[k], dy = r->Y[(k + 1) % 3] - r->Y[k];
+        /* with area2 > 0 in y-down space: top edge = horizontal going +x; left = going up */
+        r->tl[k] = (dy == 0 && dx > 0) || (dy < 0);
+    }
+    /* depth plane d(X, Y) = d0 + a (X - X0) + b (Y - Y0), fixed FP32 sequence */
+    float fx1 = (float)(r->X[1] - r->X[0]), fy1 = (float)(r->Y[1] - r->Y[0]);
+    float fx2 = (float)(r->X[2] - r->X[0]), fy2 = (float)(r->Y[2] - r->Y[0]);
+    float e1 = dv[1] - dv[0], e2 = dv[2] - dv[0];
+    float fa = (float)area2;
+    float na = e1 * fy2;
+    na = na - e2 * fy1;
+    float nb = e2 * fx1;
+    nb = nb - e1 * fx2;
+    r->a = na / fa;
+    r->b = nb / fa;
+    r->d0 = dv[0];
+    r->prim = t->prim;
+    return 1;
+}
+
+static int64_t floor16(int64_t a) { return a >= 0 ? a / 16 : -((-a + 15) / 16); }
+
+/* Coverage of the pixel with centre (Xp, Yp) (1/16 units) by the triangle. */
+static int covers(const rtri *r, int64_t Xp, int64_t Yp) {
+    for (int k = 0; k < 3; ++k) {
+        int64_t xa = r->X[k], ya = r->Y[k], xb = r->X[(k + 1) % 3], yb = r->Y[(k + 1) % 3];
+        int64_t e = (xb - xa) * (Yp - ya) - (yb - ya) * (Xp - xa);
+        if (e < 0 || (e == 0 && !r->tl[k])) return 0;
+    }
+    return 1;
+}
+
+static uint64_t pixel_key(const rtri *r, int64_t Xp, int64_t Yp, int key_f16) {
+    float gx = (float)(Xp - r->X[0]), gy = (float)(Yp - r->Y[0]);
+    float dp = fmaf(r->a, gx, fmaf(r->b, gy, r->d0));
+    if (!(dp > 0.0f)) dp = 0.0f;
+    if (key_f16) {
+        uint16_t h = or_f32_to_f16(dp);
+        return ((uint64_t)h << 16) | (uint64_t)(0xFFFFu - (r->prim & 0xFFFFu));
+    }
+    uint32_t bits;
+    memcpy(&bits, &dp, 4);
+    return ((uint64_t)bits << 32) | (uint64_t)(0xFFFFFFFFu - r->prim);
+}
+
+/* Class of a primitive id: 3 vehicle/box, 1 road, 2 lane line. */
+static uint8_t prim_class(uint32_t prim, uint32_t box_end, uint32_t road_end) {
+    return prim < box_end ? 3 : (prim < road_end ? 1 : 2);
+}
+
+static void resolve(const uint64_t *key, int64_t npx, int key_f16, uint32_t box_end,
+                    uint32_t road_end, uint8_t *cls, float *depth, uint16_t *depth16) {
+    for (int64_t p = 0; p < npx; ++p) {
+        uint64_t k = key[p];
+        uint8_t c = 0;
+        float dv = 0.0f;
+        uint16_t h = 0;
+        if (k) {
+            uint32_t prim = key_f16 ? (0xFFFFu - (uint32_t)(k & 0xFFFFu))
+                                    : (0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+            c = prim_class(prim, box_end, road_end);
+            if (key_f16) h = (uint16_t)(k >> 16);
+            else {
+                uint32_t bits = (uint32_t)(k >> 32);
+                memcpy(&dv, &bits, 4);
+            }
+        }
+        if (cls) cls[p] = c;
+        if (depth) depth[p] = dv;
+        if (depth16) depth16[p] = h;
+    }
+}
+
+/*
+ * Rasterise snapped triangles into W x H.  Pixel (i, j) samples (16 i + 8, 16 j + 8).
+ * Output per pixel: the max key (0 = background), the class (0 background, 1 road,
+ * 2 lane line, 3 box) and the winner's depth (FP32 mode) or its binary16 bits (FP16 mode).
+ * The loop visits each triangle's snapped bounding box; or_raster_bruteforce visits every
+ * pixel for every triangle and must give the same result.
+ */
+void or_raster(const or_tri *tris, int64_t n, int32_t W, int32_t H, int32_t key_f16,
+               uint32_t box_end, uint32_t road_end, uint64_t *key, uint8_t *cls, float *depth,
+               uint16_t *depth16) {
+    memset(key, 0, sizeof(uint64_t) * (size_t)W * (size_t)H);
+    for (int64_t t = 0; t < n; ++t) {
+        rtri r;
+        if (!setup_rtri(tris + t, &r)) continue;
+        int64_t xmin = r.X[0], xmax = r.X[0], ymin = r.Y[0], ymax = r.Y[0];
+        for (int k = 1; k < 3; ++k) {
+            if (r.X[k] < xmin) xmin = r.X[k];
+            if (r.X[k] > xmax) xmax = r.X[k];
+            if (r.Y[k] < ymin) ymin = r.Y[k];
+            if (r.Y[k] > ymax) ymax = r.Y[k];
+        }
+        /* pixel i has centre 16 i + 8: i in [ceil((xmin-8)/16), floor((xmax-8)/16)] */
+        int64_t i0 = -floor16(-(xmin - 8)), i1 = floor16(xmax - 8);
+        int64_t j0 = -floor16(-(ymin - 8)), j1 = floor16(ymax - 8);
+        if (i0 < 0) i0 = 0;
+        if (j0 < 0) j0 = 0;
+        if (i1 > W - 1) i1 = W - 1;
+        if (j1 > H - 1) j1 = H - 1;
+        for (int64_t j = j0; j <= j1; ++j)
+            for (int64_t i = i0; i <= i1; ++i) {
+                int64_t Xp = 16 * i + 8, Yp = 16 * j + 8;
+                if (!covers(&r, Xp, Yp)) continue;
+                uint64_t k = pixel_key(&r, Xp, Yp, key_f16);
+                if (k > key[j * W + i]) key[j * W + i] = k;
+            }
+    }
+    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, cls, depth, depth16);
+}
+
+void or_raster_bruteforce(const or_tri *tris, int64_t n, int32_t W, int32_t H, int32_t key_f16,
+                          uint32_t box_end, uint32_t road_end, uint64_t *key, uint8_t *cls,
+                          float *depth, uint16_t *depth16) {
+    for (int32_t j = 0; j < H; ++j)
+        for (int32_t i = 0; i < W; ++i) {
+            uint64_t best = 0;
+            for (int64_t t = 0; t < n; ++t) {
+                rtri r;
+                if (!setup_rtri(tris + t, &r)) continue;
+                int64_t Xp = 16 * (int64_t)i + 8, Yp = 16 * (int64_t)j + 8;
+                if (!covers(&r, Xp, Yp)) continue;
+                uint64_t k = pixel_key(&r, Xp, Yp, key_f16);
+                if (k > best) best = k;
+            }
+            key[(int64_t)j * W + i] = best;
+        }
+    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, cls, depth, depth16);
+}
+
+/*
+ * Policy-input encoding: 4-channel one-hot of the class image, normalised per channel,
+ * bfloat16, NCHW.  value(c) = bf16((onehot_c - mean_c) / std_c), computed in FP32.
+ *   cls [n] -> out [4][n]
+ */
+void or_onehot_bf16(const uint8_t *cls, int64_t n, const float *mean, const float *std_,
+                    uint16_t *out) {
+    uint16_t val[4][2];
+    for (int c = 0; c < 4; ++c)
+        for (int hot = 0; hot < 2; ++hot) {
+            float t = ((float)hot - mean[c]) / std_[c];
+            val[c][hot] = or_f32_to_bf16(t);
+        }
+    for (int c = 0; c < 4; ++c)
+        for (int64_t p = 0; p < n; ++p) out[(int64_t)c * n + p] = val[c][cls[p] == c];
+}

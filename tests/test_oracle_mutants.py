@@ -1,0 +1,51 @@
+"""Plant one mistake at a time in a copy of the oracle's C source and check that the pins
+in test_oracle_pins.py fail for every one of them (so the pins constrain the oracle)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "near plane sign": ("case 0: return v.z - cfg->near;", "case 0: return cfg->near - v.z;"),
+    "fill rule mirrored": ("r->tl[k] = (dy == 0 && dx > 0) || (dy < 0);",
+                           "r->tl[k] = (dy == 0 && dx < 0) || (dy > 0);"),
+    "no top-left rule": ("if (e < 0 || (e == 0 && !r->tl[k])) return 0;", "if (e <= 0) return 0;"),
+    "screen y not flipped": ("double ys = 0.5 * cfg->height - cm->f",
+                             "double ys = 0.5 * cfg->height + cm->f"),
+    "depth plane operand": ("nb = nb - e1 * fx2;", "nb = nb - e1 * fy2;"),
+    "slip angle factor": ("double beta = atan(0.5 * tan(steer));", "double beta = atan(tan(steer));"),
+    "rear axle distance": ("double lr = 0.3 * L;", "double lr = 0.6 * L;"),
+    "heading with new speed": ("*yaw = wrap_pi(*yaw + (v0 / lr)",
+                               "*yaw = wrap_pi(*yaw + ((v0 + accel * dt) / lr)"),
+    "touching collides": ("if (!(lo < hi)) return 0;", "if (!(lo <= hi)) return 0;"),
+    "road edge outside": ("if (cr < 0.0) return 0;", "if (cr <= 0.0) return 0;"),
+    "ties to larger id": ("| (uint64_t)(0xFFFFFFFFu - r->prim);", "| (uint64_t)(r->prim);"),
+    "zero area kept": ("if (area2 >= 0) continue;", "if (area2 > 0) continue;"),
+    "camera right axis": ("v3 v = {dx * cm->s - dy * cm->c, dz,", "v3 v = {dy * cm->c - dx * cm->s, dz,"),
+    "half not rounded": ("if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;", ""),
+    "halt keeps speed": ("            state[4 * i + 3] = 0.0;\n        }\n    }\n}", "        }\n    }\n}"),
+    "lane lines on road plane": ("double z = pass ? cfg->line_z : 0.0;", "double z = 0.0;"),
+    "ego drawn": ("if (b == ego) continue;", ""),
+    "guard band off": ("double g = cfg->guard;", "double g = 1e9;"),
+    "near clip t flipped": ("double t = di / (di - dov);", "double t = dov / (dov - di);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    a, b = MUTANTS[name]
+    assert a in src, "mutation site not found: " + name
+    c = tmp_path / "mut.c"
+    so = tmp_path / "mut.so"
+    c.write_text(src.replace(a, b, 1))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(c), "-lm"])
+    env = dict(os.environ, ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "pins did not catch mutant %r:\n%s" % (name, r.stdout[-2000:])

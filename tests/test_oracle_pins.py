@@ -1,0 +1,744 @@
+"""Pins for the CPU oracle: closed forms, invariants, brute force and independent methods.
+
+Each test checks the oracle against something other than itself, chosen so that a
+plausible slip in it (a dropped term, a flipped sign or index, a transposed operand, a
+wrong fill rule) fails at least one of them.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import CamConfig
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            vals[k] = [float(t) for t in v]
+    return vals
+
+
+def ego_box(x=0.0, y=0.0, yaw=0.0):
+    return [x, y, yaw, 4.5, 1.9, 1.5]
+
+
+def render_scene(cam, boxes, road=(), line=(), pose=(0.0, 0.0, 0.0), cam_yaw=0.0,
+                 key_f16=False, ego=0):
+    b = np.array(boxes, np.float64).reshape(-1, 6)
+    rd = np.array(road, np.float32).reshape(-1, 8)
+    ln = np.array(line, np.float32).reshape(-1, 8)
+    tris = oracle.camera_tris(cam, b, ego, rd, ln, pose[0], pose[1], pose[2], cam_yaw)
+    img = oracle.raster(tris, cam.width, cam.height, key_f16, 12 * len(b), 12 * len(b) + 2 * len(rd))
+    return img, tris
+
+
+def rect_quad(x0, x1, y0, y1):
+    """Axis-aligned rectangle as a quad, counter-clockwise from above."""
+    return [x0, y0, x1, y0, x1, y1, x0, y1]
+
+
+# ---------------------------------------------------------------------------------------
+# Rendering closed forms
+# ---------------------------------------------------------------------------------------
+
+def test_empty_scene_is_background():
+    cam = CamConfig(32, 24)
+    img, tris = render_scene(cam, [ego_box()])
+    assert len(tris) == 0
+    assert not img.cls.any() and not img.depth.any() and not img.key.any()
+
+
+def _box_face_expectation(W, H, D, hw, bh, cam_h=1.5):
+    f = Fraction(W, 2)  # hfov = 90 deg
+    x_lo, x_hi = Fraction(W, 2) - f * hw / D, Fraction(W, 2) + f * hw / D
+    y_top, y_bot = Fraction(H, 2) - f * (bh - cam_h) / D, Fraction(H, 2) + f * cam_h / D
+    cols = [i for i in range(W) if x_lo < i + Fraction(1, 2) < x_hi]
+    rows = [j for j in range(H) if y_top < j + Fraction(1, 2) < y_bot]
+    # every pixel centre must be >= 1/16 px from an edge, so snapping cannot flip it
+    margin = min(min(abs(i + Fraction(1, 2) - e) for e in (x_lo, x_hi)) for i in range(W))
+    margin = min(margin, min(min(abs(j + Fraction(1, 2) - e) for e in (y_top, y_bot))
+                             for j in range(H)))
+    return cols, rows, margin
+
+
+def test_golden_box_face_rectangle():
+    g = read_golden("box_front_face_64x64.txt")
+    W, H = int(g["width"][0]), int(g["height"][0])
+    D, hw, bh = (Fraction(str(g[k][0])) for k in ("distance", "half_width", "box_height"))
+    cols, rows, margin = _box_face_expectation(W, H, D, hw, bh)
+    # the derivation in the fixture and the exact arithmetic here agree
+    assert (cols[0], cols[-1]) == tuple(int(v) for v in g["cols"])
+    assert (rows[0], rows[-1]) == tuple(int(v) for v in g["rows"])
+    assert margin >= Fraction(1, 16)
+    L = 4.5
+    cam = CamConfig(W, H)
+    img, _ = render_scene(cam, [ego_box(), [float(D) + L / 2, 0.0, 0.0, L, 2 * float(hw), float(bh)]])
+    expect = np.zeros((H, W), bool)
+    expect[rows[0]:rows[-1] + 1, cols[0]:cols[-1] + 1] = True
+    assert np.array_equal(img.cls == 3, expect)
+    assert np.array_equal(img.cls != 0, expect)
+    assert np.all(img.depth[expect] == np.float32(g["depth"][0]))
+    assert np.all(img.depth[~expect] == 0)
+
+
+def _generic_box_cases(n=6):
+    """Seeded (W, H, D, half-width, height) cases with every pixel centre >= 1/8 px from
+    the face's projected edges."""
+    rng = np.random.default_rng(21)
+    out = []
+    while len(out) < n:
+        W, H = [(64, 64), (128, 96), (48, 48), (256, 144), (96, 64), (512, 512)][len(out) % 6]
+        D = Fraction(int(rng.integers(40, 300)), 10)
+        hw = Fraction(int(rng.integers(90, 100)), 100)
+        bh = Fraction(int(rng.integers(140, 170)), 100)
+        if _box_face_expectation(W, H, D, hw, bh)[2] >= Fraction(1, 8):
+            out.append((W, H, D, hw, bh))
+    return out
+
+
+@pytest.mark.parametrize("W,H,D,hw,bh", _generic_box_cases())
+def test_box_face_rectangle_general(W, H, D, hw, bh):
+    cols, rows, margin = _box_face_expectation(W, H, D, hw, bh)
+    assert margin >= Fraction(1, 8) and cols and rows
+    L = 4.2
+    cam = CamConfig(W, H)
+    img, _ = render_scene(cam, [ego_box(), [float(D) + L / 2, 0.0, 0.0, L, 2 * float(hw), float(bh)]])
+    expect = np.zeros((H, W), bool)
+    expect[rows[0]:rows[-1] + 1, cols[0]:cols[-1] + 1] = True
+    assert np.array_equal(img.cls == 3, expect)
+    assert np.all(img.depth[expect] == np.float32(0.1 / float(D)))
+
+
+def test_ground_strip_vanishing_lines_and_row_depth():
+    """A strip |y| < r ahead of the camera: edges are the lines u - W/2 = +-(r/h)(v - H/2)
+    through the vanishing point, and the ground depth in row v is n (v - H/2) / (f h)."""
+    W = H = 64
+    f, h, n, r = 32.0, 1.5, 0.1, 1.3137
+    cam = CamConfig(W, H)
+    img, _ = render_scene(cam, [ego_box()], road=[rect_quad(-5.0, 200.0, -r, r)])
+    u = np.arange(W) + 0.5
+    v = np.arange(H) + 0.5 - H / 2
+    checked = 0
+    for j in range(H):
+        if v[j] <= 0:
+            assert not img.cls[j].any()
+            continue
+        half = r / h * v[j]
+        dist = np.abs(np.abs(u - W / 2) - half)
+        inside = np.abs(u - W / 2) < half
+        sure = dist > 1 / 8
+        assert np.array_equal(img.cls[j][sure] == 1, inside[sure])
+        d_exact = n * v[j] / (f * h)
+        tol = (n / (f * h)) / 16 + 1e-7  # depth gradient per px times 1/16 px of snapping
+        cov = img.cls[j] == 1
+        assert np.all(np.abs(img.depth[j][cov] - d_exact) <= tol)
+        checked += int(sure.sum())
+    assert checked > 1000
+
+
+def test_mirror_symmetry_of_centred_scene():
+    W = H = 64
+    r, lw = 1.7321, 0.15
+    cam = CamConfig(W, H)
+    boxes = [ego_box(), [8.137 + 2.2, 0.0, 0.0, 4.4, 1.8913, 1.6217]]
+    road = [rect_quad(-5.0, 150.0, -r, r)]
+    line = [rect_quad(-5.0, 150.0, r - lw / 2, r + lw / 2),
+            rect_quad(-5.0, 150.0, -r - lw / 2, -r + lw / 2)]
+    img, _ = render_scene(cam, boxes, road, line)
+    assert (img.cls == 3).sum() > 20 and (img.cls == 1).sum() > 100 and (img.cls == 2).sum() > 10
+    assert np.array_equal(img.cls, img.cls[:, ::-1])
+
+
+# ---------------------------------------------------------------------------------------
+# Independent FP64 ray casting on tiny images
+# ---------------------------------------------------------------------------------------
+
+def _quad_contains(q, px, py):
+    q = np.asarray(q, np.float64).reshape(4, 2)
+    ok = np.ones_like(px, bool)
+    for k in range(4):
+        a, b = q[k], q[(k + 1) % 4]
+        cr = (b[0] - a[0]) * (py - a[1]) - (b[1] - a[1]) * (px - a[0])
+        ok &= cr >= 0
+    return ok
+
+
+def raycast(W, H, boxes, ego, road, line, pose, cam_yaw, jx=0.0, jy=0.0,
+            h=1.5, near=0.1, line_z=0.02, hfov=math.pi / 2):
+    """Nearest hit per pixel by slab tests (boxes) and plane hits (ground quads)."""
+    psi = pose[2] + cam_yaw
+    f = (W / 2) / math.tan(hfov / 2)
+    uu = np.arange(W) + 0.5 + jx
+    vv = np.arange(H) + 0.5 + jy
+    xv = ((uu - W / 2) / f)[None, :]
+    yv = (-(vv - H / 2) / f)[:, None]
+    right = np.array([math.sin(psi), -math.cos(psi), 0.0])
+    fwd = np.array([math.cos(psi), math.sin(psi), 0.0])
+    D = xv[..., None] * right + yv[..., None] * np.array([0, 0, 1.0]) + fwd  # [H, W, 3]
+    D = np.broadcast_to(D, (H, W, 3))
+    O = np.array([pose[0], pose[1], h])
+    best_t = np.full((H, W), np.inf)
+    best_cls = np.zeros((H, W), np.uint8)
+    best_obj = np.full((H, W), -1)
+    for bi, b in enumerate(boxes):
+        if bi == ego:
+            continue
+        cs, sn = math.cos(b[2]), math.sin(b[2])
+        # ray in box-local frame
+        ox, oy = O[0] - b[0], O[1] - b[1]
+        lo_o = np.array([cs * ox + sn * oy, -sn * ox + cs * oy, O[2]])
+        ld = np.stack([cs * D[..., 0] + sn * D[..., 1], -sn * D[..., 0] + cs * D[..., 1], D[..., 2]], -1)
+        lo = np.array([-b[3] / 2, -b[4] / 2, 0.0])
+        hi = np.array([b[3] / 2, b[4] / 2, b[5]])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1 = (lo - lo_o) / ld
+            t2 = (hi - lo_o) / ld
+        tmin = np.nanmax(np.minimum(t1, t2), axis=-1)
+        tmax = np.nanmin(np.maximum(t1, t2), axis=-1)
+        hit = (tmin <= tmax) & (tmin >= near) & (tmin < best_t)
+        best_t[hit], best_cls[hit], best_obj[hit] = tmin[hit], 3, bi
+    for cls, quads, z, base in ((1, road, 0.0, 1000), (2, line, line_z, 100000)):
+        for qi, q in enumerate(quads):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t = (z - h) / D[..., 2]
+            px, py = O[0] + t * D[..., 0], O[1] + t * D[..., 1]
+            hit = (D[..., 2] < 0) & (t >= near) & _quad_contains(q, px, py) & (t < best_t)
+            best_t[hit], best_cls[hit], best_obj[hit] = t[hit], cls, base + qi
+    depth = np.where(np.isfinite(best_t), near / best_t, 0.0)
+    return best_cls, depth, best_obj
+
+
+def _random_scene(rng):
+    boxes = [ego_box(0.0, 0.0, 0.0)]
+    want = rng.integers(2, 6)
+    while len(boxes) < want + 1:
+        ang = rng.uniform(-0.7, 0.7)
+        dist = rng.uniform(4.0, 30.0)
+        x, y = dist * math.cos(ang), dist * math.sin(ang)
+        # bounding circles (radius <= 2.7 m) apart: boxes never interpenetrate
+        if all(math.hypot(x - b[0], y - b[1]) > 5.5 for b in boxes):
+            boxes.append([x, y, rng.uniform(-math.pi, math.pi), rng.uniform(4, 5),
+                          rng.uniform(1.8, 2.0), rng.uniform(1.4, 1.7)])
+    road, line = [], []
+    for _ in range(rng.integers(2, 5)):
+        cx, cy = rng.uniform(-10, 40), rng.uniform(-20, 20)
+        hd = rng.uniform(-math.pi, math.pi)
+        L, Wd = rng.uniform(10, 60), rng.uniform(3, 8)
+        c, s = math.cos(hd), math.sin(hd)
+
+        def corner(a, b):
+            return [cx + c * a - s * b, cy + s * a + c * b]
+        road.append(sum([corner(-L / 2, -Wd / 2), corner(L / 2, -Wd / 2), corner(L / 2, Wd / 2),
+                         corner(-L / 2, Wd / 2)], []))
+        for off in (-Wd / 2, 0.0, Wd / 2):
+            line.append(sum([corner(-L / 2, off - 0.075), corner(L / 2, off - 0.075),
+                             corner(L / 2, off + 0.075), corner(-L / 2, off + 0.075)], []))
+    return boxes, road, line
+
+
+def _outline_distance(W, H, boxes, ego, road, line, pose, cam_yaw, h=1.5, near=0.1,
+                      line_z=0.02, hfov=math.pi / 2):
+    """Distance (px) from each pixel centre to the nearest projected outline edge of any
+    box face or ground quad, after cutting each polygon at the near plane."""
+    psi = pose[2] + cam_yaw
+    f = (W / 2) / math.tan(hfov / 2)
+    right = np.array([math.sin(psi), -math.cos(psi), 0.0])
+    fwd = np.array([math.cos(psi), math.sin(psi), 0.0])
+    O = np.array([pose[0], pose[1], h])
+    polys = []
+    for bi, b in enumerate(boxes):
+        if bi == ego:
+            continue
+        c, s = math.cos(b[2]), math.sin(b[2])
+        P = {}
+        for sx in (-1, 1):
+            for sy in (-1, 1):
+                for z in (0.0, b[5]):
+                    lx, ly = sx * b[3] / 2, sy * b[4] / 2
+                    P[(sx, sy, z)] = np.array([b[0] + c * lx - s * ly, b[1] + s * lx + c * ly, z])
+        for axis in range(3):
+            for sign in (0, 1):
+                pts = [k for k in P if (k[axis] > 0 if axis < 2 else k[2] > 0) == bool(sign)]
+                # order the 4 face corners around the face
+                cen = np.mean([P[k] for k in pts], 0)
+                nrm = cen - np.mean(list(P.values()), 0)  # face normal direction
+                u = P[pts[0]] - cen
+                v = np.cross(nrm, u)
+                ang = [math.atan2(np.dot(P[k] - cen, v), np.dot(P[k] - cen, u)) for k in pts]
+                polys.append([P[pts[i]] for i in np.argsort(ang)])
+    for quads, z in ((road, 0.0), (line, line_z)):
+        for q in quads:
+            qq = np.asarray(q, np.float64).reshape(4, 2)
+            polys.append([np.array([x, y, z]) for x, y in qq])
+    cx = (np.arange(W) + 0.5)[None, :]
+    cy = (np.arange(H) + 0.5)[:, None]
+    best = np.full((H, W), np.inf)
+    for poly in polys:
+        vw = [np.array([np.dot(p - O, right), p[2] - O[2], np.dot(p - O, fwd)]) for p in poly]
+        out = []
+        for i in range(len(vw)):  # keep the part with z >= near
+            a, b = vw[i], vw[(i + 1) % len(vw)]
+            if a[2] >= near:
+                out.append(a)
+            if (a[2] >= near) != (b[2] >= near):
+                t = (near - a[2]) / (b[2] - a[2])
+                out.append(a + t * (b - a))
+        if len(out) < 2:
+            continue
+        pts = [(W / 2 + f * p[0] / p[2], H / 2 - f * p[1] / p[2]) for p in out]
+        for i in range(len(pts)):
+            (ax, ay), (bx, by) = pts[i], pts[(i + 1) % len(pts)]
+            dx, dy = bx - ax, by - ay
+            L2 = dx * dx + dy * dy
+            t = np.clip(((cx - ax) * dx + (cy - ay) * dy) / L2, 0, 1) if L2 > 0 else 0.0
+            d = np.hypot(cx - (ax + t * dx), cy - (ay + t * dy))
+            best = np.minimum(best, d)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("W,H", [(16, 16), (32, 32), (40, 24)])
+def test_raycast_agrees_away_from_edges(seed, W, H):
+    """Every pixel whose centre is more than 1/16 px from all projected outlines (snapping
+    moves a vertex by at most 1/32 px per axis) must show the ray-cast class, and the
+    depth must match within the change of depth across 1/16 px."""
+    rng = np.random.default_rng(100 + seed)
+    boxes, road, line = _random_scene(rng)
+    cam_yaw = rng.uniform(-0.3, 0.3)
+    cam = CamConfig(W, H)
+    img, _ = render_scene(cam, boxes, road, line, cam_yaw=cam_yaw)
+    cls0, d0, obj0 = raycast(W, H, boxes, 0, road, line, (0, 0, 0), cam_yaw)
+    sure = _outline_distance(W, H, boxes, 0, road, line, (0, 0, 0), cam_yaw) > 1 / 16
+    dspread = np.zeros((H, W))
+    for jx, jy in ((1 / 16, 0), (-1 / 16, 0), (0, 1 / 16), (0, -1 / 16)):
+        c, d, o = raycast(W, H, boxes, 0, road, line, (0, 0, 0), cam_yaw, jx, jy)
+        assert np.array_equal(o[sure], obj0[sure])  # no outline within 1/16 px
+        dspread = np.maximum(dspread, np.abs(d - d0))
+    assert sure.mean() > 0.5
+    assert np.array_equal(img.cls[sure], cls0[sure])
+    hit = sure & (cls0 > 0)
+    assert np.all(np.abs(img.depth[hit] - d0[hit]) <= dspread[hit] + 1e-6 * d0[hit] + 1e-9)
+
+
+# ---------------------------------------------------------------------------------------
+# Raster rule: bounding-box loop == brute force; fill rule; watertightness
+# ---------------------------------------------------------------------------------------
+
+def _tris(rows):
+    t = np.zeros(len(rows), oracle.TRI_DTYPE)
+    for i, (X, Y, d, prim) in enumerate(rows):
+        t[i]["X"], t[i]["Y"], t[i]["d"], t[i]["prim"] = X, Y, d, prim
+    return t
+
+
+@pytest.mark.parametrize("key_f16", [False, True])
+def test_bbox_raster_equals_bruteforce(key_f16):
+    rng = np.random.default_rng(7)
+    rows = []
+    for i in range(300):
+        X = rng.integers(-300, 1300, 3)
+        Y = rng.integers(-300, 900, 3)
+        if i % 10 == 0:  # some vertices exactly on pixel centres
+            X = 16 * rng.integers(-2, 66, 3) + 8
+            Y = 16 * rng.integers(-2, 50, 3) + 8
+        d = rng.uniform(1e-3, 1.0, 3).astype(np.float32)
+        if i % 7 == 0:
+            d[:] = d[0]  # equal depths -> exact ties between triangles
+        rows.append((X, Y, d, int(rng.integers(0, 60000))))
+    t = _tris(rows)
+    a = oracle.raster(t, 64, 48, key_f16, 1000, 30000)
+    b = oracle.raster(t, 64, 48, key_f16, 1000, 30000, bruteforce=True)
+    assert np.array_equal(a.key, b.key)
+    assert np.array_equal(a.cls, b.cls) and np.array_equal(a.depth, b.depth)
+    assert (a.key != 0).mean() > 0.5
+
+
+def test_fill_rule_top_left_cases():
+    # the centre of pixel (0, 0) is (8, 8) in 1/16 units
+    def covered(X, Y):
+        img = oracle.raster(_tris([(X, Y, [0.5, 0.5, 0.5], 1)]), 4, 4, False, 0, 0)
+        return bool(img.key[0, 0])
+    assert covered([0, 32, 0], [8, 8, 40])        # on a top edge (triangle below it)
+    assert not covered([0, 32, 0], [8, 8, -24])   # on a bottom edge
+    assert covered([8, 8, 40], [0, 32, 16])       # on a left edge (triangle to its right)
+    assert not covered([8, 8, -24], [0, 32, 16])  # on a right edge
+    assert covered([8, 40, 8], [8, 8, 40])        # on the top-left corner vertex
+    assert not covered([8, 40, 8], [8, 8, -24])   # vertex shared with a bottom edge
+    # winding does not matter: either orientation gives the same coverage
+    assert covered([0, 0, 32], [8, 40, 8]) == covered([0, 32, 0], [8, 8, 40])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mesh_is_watertight(seed):
+    """A perturbed lattice mesh tiling a rectangle covers each centre inside exactly once,
+    and on the boundary exactly the left/top lines (top-left rule)."""
+    rng = np.random.default_rng(seed)
+    W, H, nx, ny = 40, 32, 6, 5
+    x0, x1 = 16 * 3 + 8, 16 * 36 + 8   # boundary lines through pixel centres
+    y0, y1 = 16 * 2 + 8, 16 * 29 + 8
+    gx = np.linspace(x0, x1, nx + 1).round().astype(np.int64)
+    gy = np.linspace(y0, y1, ny + 1).round().astype(np.int64)
+    VX = np.tile(gx, (ny + 1, 1))
+    VY = np.tile(gy[:, None], (1, nx + 1))
+    sx, sy = (x1 - x0) // nx, (y1 - y0) // ny
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            if 0 < i < nx:
+                VX[j, i] += rng.integers(-sx // 4, sx // 4 + 1)
+            if 0 < j < ny:
+                VY[j, i] += rng.integers(-sy // 4, sy // 4 + 1)
+            if rng.random() < 0.3:  # snap some vertices onto pixel centres
+                if 0 < i < nx:
+                    VX[j, i] = 16 * (VX[j, i] // 16) + 8
+                if 0 < j < ny:
+                    VY[j, i] = 16 * (VY[j, i] // 16) + 8
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            a, b, c, d = (j, i), (j, i + 1), (j + 1, i + 1), (j + 1, i)
+            split = [(a, b, c), (a, c, d)] if rng.random() < 0.5 else [(a, b, d), (b, c, d)]
+            for tri in split:
+                tris.append(([VX[p] for p in tri], [VY[p] for p in tri]))
+    count = np.zeros((H, W), int)
+    for k, (X, Y) in enumerate(tris):
+        img = oracle.raster(_tris([(X, Y, [0.3, 0.3, 0.3], k)]), W, H, False, 0, 0)
+        count += img.key != 0
+    cx = 16 * np.arange(W)[None, :] + 8
+    cy = 16 * np.arange(H)[:, None] + 8
+    expect = (cx >= x0) & (cx < x1) & (cy >= y0) & (cy < y1)
+    assert np.array_equal(count, expect.astype(int))
+
+
+def test_depth_plane_matches_vertex_values():
+    """At pixel centres that coincide with vertices the plane returns the vertex depth
+    (up to FP32 rounding of the plane evaluation)."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        P = 16 * rng.integers(0, 32, (3, 2)) + 8
+        d = rng.uniform(0.01, 1.0, 3).astype(np.float32)
+        t = _tris([(P[:, 0], P[:, 1], d, 5)])
+        a2 = (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[2, 0] - P[0, 0]) * (P[1, 1] - P[0, 1])
+        if a2 == 0:
+            continue
+        # the vertex pixel is covered unless it sits on a non-top-left edge: use the bruteforce
+        # key of the lone triangle, and compare wherever the vertex pixel is covered
+        img = oracle.raster(t, 32, 32, False, 100, 100)
+        for k in range(3):
+            i, j = (P[k] - 8) // 16
+            if img.key[j, i]:
+                assert abs(float(img.depth[j, i]) - float(d[k])) <= 4e-6 * max(1.0, float(d.max()))
+
+
+# ---------------------------------------------------------------------------------------
+# Number formats
+# ---------------------------------------------------------------------------------------
+
+def test_f16_rounding_matches_numpy():
+    rng = np.random.default_rng(11)
+    bits = rng.integers(0, 2 ** 32, 20000, dtype=np.uint64).astype(np.uint32)
+    x = bits.view(np.float32)
+    special = np.array([0.0, -0.0, 1.0, 65504.0, 65519.99, 65520.0, 1e-8, 2 ** -24, 2 ** -25,
+                        3 * 2 ** -26, 2 ** -14, 2 ** -14 * (1 - 2 ** -11), 1 + 2 ** -11,
+                        1 + 3 * 2 ** -11, 5.9604645e-08, np.inf, -np.inf], np.float32)
+    x = np.concatenate([x, special, rng.uniform(0, 1, 5000).astype(np.float32)])
+    ours = oracle.f32_to_f16_bits(x)
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).view(np.uint16)
+    nan = np.isnan(x)
+    assert np.array_equal(ours[~nan], ref[~nan])
+    assert np.all(np.isnan(ours[nan].view(np.float16)))
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(12)
+    bits = rng.integers(0, 2 ** 32, 20000, dtype=np.uint64).astype(np.uint32)
+    x = np.concatenate([bits.view(np.float32), np.array([1.0, -1.0, 0.5, 1 + 2 ** -8,
+                                                         1 + 3 * 2 ** -8, 3.4e38], np.float32)])
+    x = x[~np.isnan(x)]
+    ours = oracle.f32_to_bf16_bits(x)
+    ref = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(ours, ref)
+
+
+def test_onehot_default_normalisation_is_plus_minus_one():
+    cls = np.array([[0, 1, 2, 3]], np.uint8)
+    out = oracle.onehot_bf16(cls)
+    assert out.shape == (4, 1, 4)
+    for c in range(4):
+        for p in range(4):
+            assert out[c, 0, p] == (0x3F80 if p == c else 0xBF80)
+    out2 = oracle.onehot_bf16(cls, mean=(0.1, 0.2, 0.3, 0.4), std=(0.25, 0.5, 2.0, 4.0))
+    import torch
+    for c, (m, s) in enumerate(zip((0.1, 0.2, 0.3, 0.4), (0.25, 0.5, 2.0, 4.0))):
+        hot = (np.float32(1) - np.float32(m)) / np.float32(s)
+        cold = (np.float32(0) - np.float32(m)) / np.float32(s)
+        want = torch.tensor([cold, hot], dtype=torch.float32).to(torch.bfloat16)
+        want = want.view(torch.int16).numpy().view(np.uint16)
+        assert out2[c, 0, c] == want[1] and out2[c, 0, (c + 1) % 4] == want[0]
+
+
+# ---------------------------------------------------------------------------------------
+# Dynamics and infractions
+# ---------------------------------------------------------------------------------------
+
+def test_paper_constants_golden():
+    g = read_golden("paper_constants.txt")
+    # a straight step with steer -> the wheelbase enters through l_r = wheelbase / 2
+    L, v, steer, dt = 4.0, 10.0, 0.2, g["dt"][0]
+    x, y, yaw, v1 = oracle.bicycle(0, 0, 0, v, L, 0.0, steer, dt)
+    wb = g["wheelbase_fraction"][0] * L
+    beta = math.atan(0.5 * math.tan(steer))
+    assert yaw == pytest.approx(v / (wb / 2) * math.sin(beta) * dt, rel=1e-12)
+
+
+def test_bicycle_straight_closed_form():
+    x0, y0, yaw, v0, a, dt, vmax = 1.0, -2.0, 0.3, 5.0, 1.5, 0.1, 12.0
+    st = (x0, y0, yaw, v0)
+    n = 80
+    for _ in range(n):
+        st = oracle.bicycle(*st, 4.5, a, 0.0, dt, vmax)
+    vs = [min(v0 + k * a * dt, vmax) for k in range(n)]
+    assert st[0] == pytest.approx(x0 + dt * math.cos(yaw) * sum(vs), rel=1e-12)
+    assert st[1] == pytest.approx(y0 + dt * math.sin(yaw) * sum(vs), rel=1e-12)
+    assert st[2] == pytest.approx(yaw, abs=1e-15)
+    assert st[3] == pytest.approx(vmax)
+    # braking clamps at zero
+    st = (0, 0, 0, 1.0)
+    for _ in range(10):
+        st = oracle.bicycle(*st, 4.5, -3.0, 0.0, dt, vmax)
+    assert st[3] == 0.0 and st[0] == pytest.approx(dt * (1.0 + 0.7 + 0.4 + 0.1))
+
+
+def test_bicycle_constant_steer_sum_of_cosines():
+    """Constant speed and steer: heading advances by phi = v sin(beta)/l_r dt per step, so the
+    position is a geometric sum of cosines with the textbook closed form."""
+    x0, y0, th0, v, L, steer, dt = 3.0, 4.0, -0.4, 7.0, 4.6, 0.25, 0.1
+    beta = math.atan(0.5 * math.tan(steer))
+    phi = v * math.sin(beta) / (0.3 * L) * dt
+    n = 37
+    st = (x0, y0, th0, v)
+    pts = [st[:2]]
+    for _ in range(n):
+        st = oracle.bicycle(*st, L, 0.0, steer, dt, 30.0)
+        pts.append(st[:2])
+    k = math.sin(n * phi / 2) / math.sin(phi / 2)
+    mid = th0 + beta + (n - 1) * phi / 2
+    assert st[0] == pytest.approx(x0 + v * dt * k * math.cos(mid), abs=1e-10)
+    assert st[1] == pytest.approx(y0 + v * dt * k * math.sin(mid), abs=1e-10)
+    # the discrete path lies on a circle of radius v dt / (2 sin(phi/2)) (chord v dt, angle phi)
+    rho = v * dt / (2 * math.sin(phi / 2))
+    p = np.array(pts)
+    A = np.c_[2 * p, np.ones(len(p))]
+    sol, *_ = np.linalg.lstsq(A, (p ** 2).sum(1), rcond=None)
+    c = sol[:2]
+    assert np.allclose(np.linalg.norm(p - c, axis=1), rho, rtol=1e-9)
+    # heading wraps into (-pi, pi]
+    st = (0, 0, math.pi - 0.01, 10.0)
+    st = oracle.bicycle(*st, 4.0, 0.0, 0.3, 0.1, 30.0)
+    assert -math.pi < st[2] <= math.pi and st[2] < 0
+
+
+def _poly_clip_area(p, q):
+    """Area of the intersection of two convex CCW polygons (Sutherland-Hodgman)."""
+    out = [tuple(v) for v in p]
+    for k in range(len(q)):
+        a, b = q[k], q[(k + 1) % len(q)]
+        inp, out = out, []
+        if not inp:
+            break
+
+        def side(v):
+            return (b[0] - a[0]) * (v[1] - a[1]) - (b[1] - a[1]) * (v[0] - a[0])
+        for i in range(len(inp)):
+            cur, nxt = inp[i], inp[(i + 1) % len(inp)]
+            sc, sn = side(cur), side(nxt)
+            if sc >= 0:
+                out.append(cur)
+            if (sc >= 0) != (sn >= 0):
+                t = sc / (sc - sn)
+                out.append((cur[0] + t * (nxt[0] - cur[0]), cur[1] + t * (nxt[1] - cur[1])))
+    if len(out) < 3:
+        return 0.0
+    o = np.array(out)
+    return 0.5 * float(np.sum(o[:, 0] * np.roll(o[:, 1], -1) - np.roll(o[:, 0], -1) * o[:, 1]))
+
+
+def _corners(b):
+    c, s = math.cos(b[2]), math.sin(b[2])
+    return [(b[0] + c * lx - s * ly, b[1] + s * lx + c * ly)
+            for lx, ly in ((-b[3] / 2, -b[4] / 2), (b[3] / 2, -b[4] / 2), (b[3] / 2, b[4] / 2),
+                           (-b[3] / 2, b[4] / 2))]
+
+
+def test_sat_matches_polygon_intersection_area():
+    rng = np.random.default_rng(5)
+    seen = {True: 0, False: 0}
+    for _ in range(3000):
+        a = [0.0, 0.0, rng.uniform(-math.pi, math.pi), rng.uniform(3, 6), rng.uniform(1, 3)]
+        b = [rng.uniform(-6, 6), rng.uniform(-6, 6), rng.uniform(-math.pi, math.pi),
+             rng.uniform(3, 6), rng.uniform(1, 3)]
+        area = _poly_clip_area(_corners(a), _corners(b))
+        if 0 < area < 1e-6:
+            continue
+        got = oracle.obb_overlap(a, b)
+        assert got == (area > 0), (a, b, area)
+        seen[got] += 1
+    assert seen[True] > 300 and seen[False] > 300
+
+
+def test_sat_axis_aligned_intervals_and_touching():
+    for dx, dy, want in ((4.0, 0.0, False), (3.999, 0.0, True), (0.0, 2.0, False),
+                         (0.0, 1.99, True), (4.0, 2.0, False), (-3.5, 1.5, True)):
+        assert oracle.obb_overlap([0, 0, 0, 4.0, 2.0], [dx, dy, 0, 4.0, 2.0]) == want
+
+
+def _winding(q, px, py):
+    q = np.asarray(q, np.float64).reshape(4, 2)
+    ang = 0.0
+    for k in range(4):
+        a = math.atan2(q[k][1] - py, q[k][0] - px)
+        b = math.atan2(q[(k + 1) % 4][1] - py, q[(k + 1) % 4][0] - px)
+        d = b - a
+        while d > math.pi:
+            d -= 2 * math.pi
+        while d < -math.pi:
+            d += 2 * math.pi
+        ang += d
+    return round(ang / (2 * math.pi))
+
+
+def test_point_in_quad_matches_winding_number():
+    rng = np.random.default_rng(9)
+    n_in = 0
+    for _ in range(400):
+        c, s = math.cos(t := rng.uniform(-math.pi, math.pi)), math.sin(t)
+        L, Wd = rng.uniform(2, 20), rng.uniform(2, 8)
+        sk = rng.uniform(-1, 1)
+        pts = [(-L / 2, -Wd / 2), (L / 2, -Wd / 2 + sk), (L / 2, Wd / 2 - sk), (-L / 2, Wd / 2)]
+        q = np.array([[c * x - s * y, s * x + c * y] for x, y in pts], np.float32).ravel()
+        for _ in range(10):
+            px, py = rng.uniform(-12, 12), rng.uniform(-12, 12)
+            qq = q.astype(np.float64).reshape(4, 2)
+            dmin = min(abs((qq[(k + 1) % 4][0] - qq[k][0]) * (py - qq[k][1]) -
+                           (qq[(k + 1) % 4][1] - qq[k][1]) * (px - qq[k][0]))
+                       for k in range(4))
+            if dmin < 1e-6:
+                continue
+            w = _winding(q, px, py)
+            got = oracle.point_in_quad(px, py, q)
+            assert got == (w == 1)
+            n_in += got
+    assert n_in > 200
+
+
+def test_step_offroad_halts_and_latches():
+    R = 3.5
+    road = np.array([rect_quad(-50, 50, -R, R)], np.float32)
+    # agent 0 centred, agent 1 with its left side 0.05 m inside the edge, agent 2 outside
+    boxes = np.array([[0, 0, 0, 4.0, 2.0, 1.5], [10, R - 1.05, 0, 4.0, 2.0, 1.5],
+                      [20, R - 0.95, 0, 4.0, 2.0, 1.5]], np.float64)
+    state = np.array([[0, 0, 0, 0], [10, R - 1.05, 0, 0], [20, R - 0.95, 0, 0]], np.float64)
+    flags = np.zeros(3, np.uint8)
+    act = np.zeros((3, 2), np.float32)
+    oracle.step_world(boxes, state, flags, act, road)
+    assert list(flags) == [0, 0, oracle.OFFROAD | oracle.HALTED]
+    # the halted agent ignores actions and stays put; flags latch
+    act[:, 0] = 2.0
+    before = state[2].copy()
+    for _ in range(3):
+        oracle.step_world(boxes, state, flags, act, road)
+    assert np.array_equal(state[2, :3], before[:3]) and state[2, 3] == 0
+    assert flags[2] == oracle.OFFROAD | oracle.HALTED
+    assert state[0, 3] == pytest.approx(0.6) and flags[0] == 0
+
+
+def test_step_collision_flags_agents_only():
+    road = np.array([rect_quad(-100, 100, -10, 10)], np.float32)
+    # agents 0 and 1 drive into each other; agent 2 drives into static box 3
+    boxes = np.array([[0, 0, 0, 4, 2, 1.5], [4.2, 0, math.pi, 4, 2, 1.5],
+                      [30, 5, 0, 4, 2, 1.5], [34.1, 5, 0, 4, 2, 1.5]], np.float64)
+    state = np.array([[0, 0, 0, 2.0], [4.2, 0, math.pi, 2.0], [30, 5, 0, 2.0]], np.float64)
+    flags = np.zeros(3, np.uint8)
+    oracle.step_world(boxes, state, flags, np.zeros((3, 2), np.float32), road)
+    c = oracle.COLLIDED | oracle.HALTED
+    assert list(flags) == [c, c, c]
+    assert np.all(state[:, 3] == 0)
+    assert boxes[3, 0] == 34.1  # static boxes never move
+
+
+def test_bicycle_heading_uses_speed_at_step_start():
+    """With constant steer and acceleration, the heading after n steps is
+    theta0 + sin(beta)/l_r * dt * sum_k v_k with v_k the speed at the start of step k."""
+    L, steer, a, dt, v0 = 4.4, 0.2, 1.3, 0.1, 3.0
+    beta = math.atan(0.5 * math.tan(steer))
+    st = (0.0, 0.0, 0.1, v0)
+    n = 20
+    for _ in range(n):
+        st = oracle.bicycle(*st, L, a, steer, dt, 30.0)
+    vs = [v0 + k * a * dt for k in range(n)]
+    assert st[2] == pytest.approx(0.1 + math.sin(beta) / (0.3 * L) * dt * sum(vs), abs=1e-12)
+
+
+def test_offroad_boundary_counts_as_inside():
+    # corner exactly on the road edge (all values exact in binary): still on the road
+    road = np.array([rect_quad(-50, 50, -3.5, 3.5)], np.float32)
+    assert oracle.point_in_quad(10.0, 3.5, road[0]) and oracle.point_in_quad(50.0, 3.5, road[0])
+    assert not oracle.point_in_quad(10.0, 3.5000001, road[0])
+    boxes = np.array([[0, 2.5, 0, 4.0, 2.0, 1.5]], np.float64)
+    state = np.array([[0, 2.5, 0, 0]], np.float64)
+    flags = np.zeros(1, np.uint8)
+    oracle.step_world(boxes, state, flags, np.zeros((1, 2), np.float32), road)
+    assert flags[0] == 0
+
+
+def test_visible_faces_of_a_box():
+    """A viewpoint sees exactly the faces whose planes it is strictly in front of; a face
+    whose plane contains the camera is edge-on (zero area) and is culled."""
+    cam = CamConfig(64, 64)
+    D, L, Wd, H = 9.0, 4.0, 2.0, 1.25
+    # camera at y = 0 lies in the plane of the box's -y face (y = 0); top face below camera
+    boxes = [ego_box(), [D + L / 2, Wd / 2, 0.0, L, Wd, H]]
+    img, tris = render_scene(cam, boxes)
+    faces = sorted({(int(p) - 12) // 2 for p in tris["prim"]})
+    assert faces == [1, 4]  # -x face and +z (top) face; -y face edge-on, rest back-facing
+    assert (img.cls == 3).any()
+
+
+def test_ego_box_is_not_drawn():
+    # a low ego box (top face below the camera) would cover the bottom of its own image
+    cam = CamConfig(32, 32)
+    img, tris = render_scene(cam, [[0.0, 0.0, 0.0, 4.5, 1.9, 1.4]])
+    assert len(tris) == 0 and not img.cls.any()
+    img2, tris2 = render_scene(cam, [[0.0, 0.0, 0.0, 4.5, 1.9, 1.4]], ego=-1)
+    assert (img2.cls == 3).sum() > 100  # the same box drawn (no ego) shows its top face
+
+
+def test_snapped_vertices_stay_inside_guard_band():
+    """Guard-band clipping bounds every snapped coordinate to the band of 4x the viewport
+    half-extent around its centre, which keeps edge functions inside 32-bit range."""
+    import worldgen as wg
+    w = wg.make_workload(wg.WORKLOADS["tiny"])
+    sim = oracle.Sim(w)
+    for W, H in ((64, 64), (256, 144)):
+        cam = CamConfig(W, H)
+        n_near = 0
+        for a in range(8):
+            for yaw in (0.0, 1.0, -1.0):
+                t = sim.camera_tris(cam, 0, a, yaw)
+                X, Y = t["X"].astype(np.int64), t["Y"].astype(np.int64)
+                assert np.all(np.abs(X - 8 * W) <= 4 * 8 * W + 1)
+                assert np.all(np.abs(Y - 8 * H) <= 4 * 8 * H + 1)
+                n_near += int((np.abs(Y - 8 * H) > 3 * 8 * H).sum())
+        assert n_near > 0  # some ground really is clipped by the guard band
