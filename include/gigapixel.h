@@ -1,0 +1,215 @@
+/*
+ * gigapixel.h -- C ABI of the batched step-and-render library (B300, sm_103a).
+ *
+ * The library simulates thousands of independent driving worlds on one GPU and renders
+ * every agent's ego-centric perspective camera of a bounding-box world into a caller-owned
+ * device tensor.  It follows the problem statement of "Scaling Self-Play for End-to-End
+ * Driving" (Gigapixel): the simulator state is agent boxes plus static map geometry
+ * (Sec. 3.1), each agent receives a rendered ego-centric view, many worlds are stepped and
+ * rendered together in one batched launch, and images stay on the GPU as a batched tensor
+ * with no per-step host transfer (App. A, "High-Throughput Batched Rendering").  Dynamics
+ * and infractions follow App. A ("Action Space and Dynamics", "Other Details").
+ *
+ * Conventions for every entry point:
+ *  - Device pointers are raw CUDA device addresses on the handle's device, contiguous, in
+ *    the layout stated at each call.  The library never frees or keeps a caller pointer
+ *    after a call returns (except inside a captured graph, see gp_step_render).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All work
+ *    is enqueued asynchronously on it; the call returns before the GPU finishes.  Calls on
+ *    one handle must be ordered (one stream, or caller-side events).
+ *  - Errors detectable on the host return a negative gp_status immediately and leave the
+ *    handle unchanged; gp_last_error() then describes the failure.  Conditions found on
+ *    the device (non-finite agent state, internal capacity limits) set bits in a device
+ *    status word read by gp_get_status; kernels never trap and never spin.
+ */
+#ifndef GIGAPIXEL_H
+#define GIGAPIXEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gp_handle gp_handle; /* opaque, owned by the library */
+
+typedef enum gp_status {
+    GP_OK = 0,
+    GP_EINVAL = -1,   /* invalid argument or descriptor */
+    GP_ENOMEM = -2,   /* device or host allocation failed */
+    GP_ECUDA = -3,    /* a CUDA runtime call failed */
+    GP_ELIMIT = -4,   /* a size exceeds a documented limit */
+    GP_EDEVICE = -5,  /* the device status word has a sticky error bit set */
+    GP_ESTATE = -6    /* call not valid in the handle's current state */
+} gp_status;
+
+/* Depth-key precision of the rasteriser. */
+enum { GP_KEY_F32 = 0, GP_KEY_F16 = 1 };
+/* Image encoding written by gp_render. */
+enum { GP_OUT_CLASS_U8 = 0, GP_OUT_ONEHOT_BF16 = 1 };
+/* Per-agent flag bits (latched for the lifetime of the handle or until gp_set_state). */
+enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4 };
+/* Device status bits (sticky until gp_clear_status). */
+enum {
+    GP_DEV_NONFINITE_STATE = 1u << 0, /* an agent's state became NaN/inf */
+    GP_DEV_CLIP_OVERFLOW = 1u << 1,   /* internal clip capacity exceeded (image may be incomplete) */
+    GP_DEV_INJECTED = 1u << 31        /* set by gp_debug_inject_status */
+};
+
+/* Pixel classes of the class image / one-hot channels. */
+enum { GP_CLASS_BACKGROUND = 0, GP_CLASS_ROAD = 1, GP_CLASS_LANE_LINE = 2, GP_CLASS_VEHICLE = 3 };
+
+/* Limits (GP_ELIMIT beyond them). */
+#define GP_MAX_CAMS 8            /* cameras per agent */
+#define GP_MAX_BOXES 128         /* boxes (agents + static) per world */
+#define GP_MAX_QUADS 32767       /* road + lane-line quads per world */
+#define GP_MAX_WIDTH 512         /* image width and height */
+
+/*
+ * Worlds, as host arrays in CSR form over worlds; copied to the device at create time.
+ * Geometry is in metres, world frame x/y on the ground, z up, angles in radians.
+ *   box_off[n_worlds+1]    boxes of world w: [box_off[w], box_off[w+1])
+ *   agent_count[n_worlds]  the first agent_count[w] boxes of world w are agents (each
+ *                          carries the cameras); the rest are static obstacles
+ *   boxes[n_boxes][7]      x, y (footprint centre), yaw, length, width, height, v0
+ *                          (initial speed, agents only)
+ *   road_off/road          road-surface quads [n][8]: four (x, y) corners, counter-clockwise
+ *                          seen from above, on the ground plane z = 0 (class road)
+ *   line_off/line          lane-line strips [n][8], same layout, at z = lane_line_z
+ *                          (class lane line)
+ * Primitive ids of a world (used for the depth tie-break): box b face triangle t ->
+ * 12 b + t; road quad r triangle t -> 12 n_boxes + 2 r + t; lane-line quad l triangle t ->
+ * 12 n_boxes + 2 n_road + 2 l + t.
+ */
+typedef struct gp_world_desc {
+    int32_t n_worlds;
+    const int32_t *box_off;
+    const int32_t *agent_count;
+    const float *boxes;
+    const int32_t *road_off;
+    const float *road;
+    const int32_t *line_off;
+    const float *line;
+} gp_world_desc;
+
+/*
+ * Simulation and camera configuration.  gp_default_config fills the defaults listed here.
+ */
+typedef struct gp_config {
+    int32_t width, height;        /* image size, 16..GP_MAX_WIDTH each, width % 16 == 0
+                                     (default 128 x 128) */
+    int32_t n_cams;               /* cameras per agent, 1..GP_MAX_CAMS (default 1) */
+    float cam_yaw[GP_MAX_CAMS];   /* camera yaw offsets from the agent heading (default 0) */
+    float hfov;                   /* horizontal field of view (default pi/2) */
+    float cam_height;             /* camera height above ground (default 1.5 m) */
+    float near_plane;             /* near clip distance (default 0.1 m) */
+    float lane_line_z;            /* lane-line strip height above the road (default 0.02 m) */
+    float dt;                     /* simulation step (default 0.1 s, App. A) */
+    float v_max;                  /* speed clamp (default 30 m/s) */
+    int32_t key_precision;        /* GP_KEY_F32 (default) or GP_KEY_F16 (reversed-Z binary16) */
+    int32_t output;               /* GP_OUT_CLASS_U8 (default) or GP_OUT_ONEHOT_BF16 */
+    float norm_mean[4];           /* one-hot normalisation (default 0.5 each) */
+    float norm_std[4];            /* (default 0.5 each -> values are exactly +-1) */
+    int32_t autotune;             /* 1: time candidate launch shapes at create (default 0) */
+    int32_t band_rows;            /* rows per screen band, 0 = auto */
+    int32_t threads;              /* render threads per block, 0 = auto */
+    int32_t tri_capacity;         /* triangles per raster batch, 0 = auto */
+} gp_config;
+
+/* Fill `cfg` with the defaults above. */
+gp_status gp_default_config(gp_config *cfg);
+
+/*
+ * Create a batch of worlds on CUDA device `device`.  Copies the descriptor, builds the
+ * device-side world layout (culling clusters, off-road grid, work list), optionally runs
+ * the autotuner, and returns a handle in *out.  Synchronous.  Limits: GP_MAX_BOXES boxes,
+ * GP_MAX_QUADS quads per world; with GP_KEY_F16 a world holds at most 65535 primitive ids.
+ * Errors: GP_EINVAL (malformed CSR, non-finite values, bad config), GP_ELIMIT, GP_ENOMEM,
+ * GP_ECUDA.
+ */
+gp_status gp_create_worlds(const gp_world_desc *desc, const gp_config *cfg, int device,
+                           gp_handle **out);
+
+/* Release every device and host resource of the handle.  NULL is accepted. */
+gp_status gp_destroy(gp_handle *h);
+
+/*
+ * Advance every world by one step (App. A): kinematic bicycle (wheelbase 0.6 L) for each
+ * non-halted agent, then footprint collisions among all box pairs that contain an agent,
+ * then the off-road test (a footprint corner outside every road quad), then halt: flagged
+ * agents get v = 0 and ignore later actions but stay in the scene.
+ *   actions_dev  float [n_agents][2] device: acceleration (m/s^2), steering angle (rad);
+ *                agents ordered by world, then by agent index within the world.
+ * Returns GP_EDEVICE if a previous gp_get_status saw an error bit (until gp_clear_status).
+ */
+gp_status gp_step(gp_handle *h, const float *actions_dev, void *stream);
+
+/*
+ * Render every camera of every agent from the current state (App. A rendering; Sec. 3.1
+ * scene).  Cameras are ordered [world][agent][camera]; n_views = n_agents * n_cams.
+ *   out_dev    GP_OUT_CLASS_U8:    uint8  [n_views][height][width] class ids
+ *              GP_OUT_ONEHOT_BF16: bf16   [n_views][4][height][width], channel c holds
+ *                                  (1[class == c] - norm_mean[c]) / norm_std[c]
+ *   depth_dev  NULL, or reversed-Z depth n / z_view of the visible surface (0 on
+ *              background): float [n_views][height][width] with GP_KEY_F32, binary16 bits
+ *              (uint16) with GP_KEY_F16.
+ * Both pointers must be 16-byte aligned.
+ */
+gp_status gp_render(gp_handle *h, void *out_dev, void *depth_dev, void *stream);
+
+/*
+ * gp_step followed by gp_render, replayed from a CUDA graph (captured on the first call
+ * for this (actions, out, depth) pointer triple; up to 4 triples are cached).  The
+ * pointers must stay valid while their graph is cached (until gp_destroy).
+ */
+gp_status gp_step_render(gp_handle *h, const float *actions_dev, void *out_dev,
+                         void *depth_dev, void *stream);
+
+/*
+ * Per-world path: step or render one world only (one launch each), writing the world's
+ * slice of the same tensors (actions/out/depth point at the start of the FULL arrays).
+ */
+gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions_dev, void *stream);
+gp_status gp_render_world(gp_handle *h, int32_t world, void *out_dev, void *depth_dev,
+                          void *stream);
+
+/*
+ * Agent state: state[n_agents][4] = x, y, yaw, v (float) and flags[n_agents] (uint8).
+ * on_host = 1: host pointers (the call synchronises the stream); 0: device pointers.
+ * gp_set_state also forks/resumes a simulation (e.g. teacher rollouts from a snapshot).
+ */
+gp_status gp_get_state(gp_handle *h, float *state, uint8_t *flags, int on_host, void *stream);
+gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, int on_host,
+                       void *stream);
+
+/* Sizes of a handle. */
+typedef struct gp_info {
+    int32_t n_worlds, n_agents, n_boxes, n_views, width, height, n_cams;
+    int32_t key_precision, output;
+    int64_t out_bytes, depth_bytes;    /* bytes gp_render writes to out_dev / depth_dev */
+    int32_t band_rows, threads, tri_capacity, blocks; /* chosen launch shape */
+} gp_info;
+gp_status gp_get_info(gp_handle *h, gp_info *info);
+
+/* Read (synchronously) / clear the device status word; set bits for tests. */
+gp_status gp_get_status(gp_handle *h, uint32_t *bits);
+gp_status gp_clear_status(gp_handle *h);
+gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits);
+
+/*
+ * Render all cameras (like gp_render) and copy the snapped triangles that camera `view`
+ * rasterised to host memory: records of int32 X[3], Y[3] (1/16 pixel, y down), float d[3]
+ * (n / z_view), uint32 prim, uint32 sub (fan index after clipping); 44 bytes each.  A
+ * triangle that spans several screen bands appears once per band.  *n receives the number
+ * produced (records beyond cap are dropped).  Synchronous.
+ */
+gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out_dev, void *depth_dev,
+                             void *host_tris, int64_t cap, int64_t *n, void *stream);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *gp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIGAPIXEL_H */

@@ -238,15 +238,17 @@ static double plane_dist(const or_cam *cfg, const camera *cm, int k, v3 v) {
 }
 
 /* Sutherland-Hodgman against one plane; the crossing point is always interpolated from
- * the inside vertex towards the outside one. */
+ * the inside vertex towards the outside one.  A convex polygon gains at most one vertex
+ * per plane (at most 8 after five planes); the 16-entry bound only guards rounding on
+ * near-degenerate input. */
 static int clip_plane(const or_cam *cfg, const camera *cm, int k, const v3 *in, int n, v3 *out) {
     int m = 0;
     for (int i = 0; i < n; ++i) {
         v3 a = in[i], b = in[(i + 1) % n];
         double da = plane_dist(cfg, cm, k, a), db = plane_dist(cfg, cm, k, b);
         int ia = da >= 0.0, ib = db >= 0.0;
-        if (ia) out[m++] = a;
-        if (ia != ib) {
+        if (ia && m < 16) out[m++] = a;
+        if (ia != ib && m < 16) {
             v3 vi = ia ? a : b, vo = ia ? b : a;
             double di = ia ? da : db, dov = ia ? db : da;
             double t = di / (di - dov);

@@ -1,0 +1,266 @@
+"""Thin Python binding of the C ABI in include/gigapixel.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``libgigapixel.so`` built in-tree from
+``csrc/``; PyTorch only provides device memory and streams.  There is no CPU fallback:
+if the library cannot be loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgigapixel.so")
+
+GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ELIMIT, GP_EDEVICE, GP_ESTATE = 0, -1, -2, -3, -4, -5, -6
+KEY_F32, KEY_F16 = 0, 1
+OUT_CLASS_U8, OUT_ONEHOT_BF16 = 0, 1
+FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
+DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_INJECTED = 1, 2, 1 << 31
+MAX_CAMS = 8
+
+TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,)),
+                      ("prim", "<u4"), ("sub", "<u4")])
+
+EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render",
+            "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
+            "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
+            "gp_debug_inject_status", "gp_debug_dump_tris", "gp_last_error")
+
+
+class WorldDesc(ctypes.Structure):
+    _fields_ = [("n_worlds", ctypes.c_int32),
+                ("box_off", ctypes.POINTER(ctypes.c_int32)),
+                ("agent_count", ctypes.POINTER(ctypes.c_int32)),
+                ("boxes", ctypes.POINTER(ctypes.c_float)),
+                ("road_off", ctypes.POINTER(ctypes.c_int32)),
+                ("road", ctypes.POINTER(ctypes.c_float)),
+                ("line_off", ctypes.POINTER(ctypes.c_int32)),
+                ("line", ctypes.POINTER(ctypes.c_float))]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_cams", ctypes.c_int32),
+                ("cam_yaw", ctypes.c_float * MAX_CAMS), ("hfov", ctypes.c_float),
+                ("cam_height", ctypes.c_float), ("near_plane", ctypes.c_float),
+                ("lane_line_z", ctypes.c_float), ("dt", ctypes.c_float), ("v_max", ctypes.c_float),
+                ("key_precision", ctypes.c_int32), ("output", ctypes.c_int32),
+                ("norm_mean", ctypes.c_float * 4), ("norm_std", ctypes.c_float * 4),
+                ("autotune", ctypes.c_int32), ("band_rows", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("tri_capacity", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_worlds", ctypes.c_int32), ("n_agents", ctypes.c_int32),
+                ("n_boxes", ctypes.c_int32), ("n_views", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_cams", ctypes.c_int32),
+                ("key_precision", ctypes.c_int32), ("output", ctypes.c_int32),
+                ("out_bytes", ctypes.c_int64), ("depth_bytes", ctypes.c_int64),
+                ("band_rows", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("tri_capacity", ctypes.c_int32), ("blocks", ctypes.c_int32)]
+
+
+class GigapixelError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("gigapixel status %d: %s" % (status, msg))
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it is missing (there is no fallback)."""
+    if not os.path.exists(path):
+        raise ImportError("libgigapixel.so not built: run paper_2606_19641_b300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sigs = {
+        "gp_default_config": [ctypes.POINTER(Config)],
+        "gp_create_worlds": [ctypes.POINTER(WorldDesc), ctypes.POINTER(Config), ctypes.c_int,
+                             ctypes.POINTER(vp)],
+        "gp_destroy": [vp],
+        "gp_step": [vp, vp, vp],
+        "gp_render": [vp, vp, vp, vp],
+        "gp_step_render": [vp, vp, vp, vp, vp],
+        "gp_step_world": [vp, i32, vp, vp],
+        "gp_render_world": [vp, i32, vp, vp, vp],
+        "gp_get_state": [vp, vp, vp, ctypes.c_int, vp],
+        "gp_set_state": [vp, vp, vp, ctypes.c_int, vp],
+        "gp_get_info": [vp, ctypes.POINTER(Info)],
+        "gp_get_status": [vp, ctypes.POINTER(u32)],
+        "gp_clear_status": [vp],
+        "gp_debug_inject_status": [vp, u32],
+        "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.gp_last_error.argtypes = []
+    lib.gp_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != GP_OK:
+        raise GigapixelError(status, lib().gp_last_error().decode())
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    check(lib().gp_default_config(ctypes.byref(c)))
+    for k, v in kw.items():
+        if k == "cam_yaw":
+            vals = list(v)
+            c.n_cams = len(vals)
+            for i, y in enumerate(vals):
+                c.cam_yaw[i] = y
+        elif k in ("norm_mean", "norm_std"):
+            arr = getattr(c, k)
+            for i, y in enumerate(v):
+                arr[i] = y
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def _ptr(t) -> int:
+    """Device/host address of a torch tensor or numpy array (None -> 0)."""
+    if t is None:
+        return 0
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Simulator:
+    """A batch of worlds on one GPU (one gp_handle)."""
+
+    def __init__(self, worlds, config: Config, device: int = 0):
+        keep = []
+        desc = WorldDesc()
+        desc.n_worlds = worlds.n_worlds
+
+        def arr(a, dtype, ct):
+            a = np.ascontiguousarray(a, dtype=dtype)
+            keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ct))
+        desc.box_off = arr(worlds.box_off, np.int32, ctypes.c_int32)
+        desc.agent_count = arr(worlds.agent_count, np.int32, ctypes.c_int32)
+        desc.boxes = arr(worlds.boxes, np.float32, ctypes.c_float)
+        desc.road_off = arr(worlds.road_off, np.int32, ctypes.c_int32)
+        desc.road = arr(worlds.road, np.float32, ctypes.c_float)
+        desc.line_off = arr(worlds.line_off, np.int32, ctypes.c_int32)
+        desc.line = arr(worlds.line, np.float32, ctypes.c_float)
+        self.config = config
+        self.device = device
+        self._h = None
+        h = ctypes.c_void_p()
+        check(lib().gp_create_worlds(ctypes.byref(desc), ctypes.byref(config), device,
+                                     ctypes.byref(h)))
+        self._h = h
+        self.info = Info()
+        check(lib().gp_get_info(self._h, ctypes.byref(self.info)))
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            lib().gp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_agents(self) -> int:
+        return self.info.n_agents
+
+    @property
+    def n_views(self) -> int:
+        return self.info.n_views
+
+    def alloc_outputs(self, depth: bool = True):
+        """Output tensors on the device in the layout gp_render writes."""
+        import torch
+        i = self.info
+        dev = torch.device("cuda", self.device)
+        if i.output == OUT_CLASS_U8:
+            out = torch.empty((i.n_views, i.height, i.width), dtype=torch.uint8, device=dev)
+        else:
+            out = torch.empty((i.n_views, 4, i.height, i.width), dtype=torch.bfloat16, device=dev)
+        d = None
+        if depth:
+            dt = torch.float32 if i.key_precision == KEY_F32 else torch.float16
+            d = torch.empty((i.n_views, i.height, i.width), dtype=dt, device=dev)
+        return out, d
+
+    def step(self, actions, stream=None) -> None:
+        check(lib().gp_step(self._h, _ptr(actions), _stream(stream)))
+
+    def render(self, out, depth=None, stream=None) -> None:
+        check(lib().gp_render(self._h, _ptr(out), _ptr(depth), _stream(stream)))
+
+    def step_render(self, actions, out, depth=None, stream=None) -> None:
+        check(lib().gp_step_render(self._h, _ptr(actions), _ptr(out), _ptr(depth),
+                                   _stream(stream)))
+
+    def step_world(self, world: int, actions, stream=None) -> None:
+        check(lib().gp_step_world(self._h, world, _ptr(actions), _stream(stream)))
+
+    def render_world(self, world: int, out, depth=None, stream=None) -> None:
+        check(lib().gp_render_world(self._h, world, _ptr(out), _ptr(depth), _stream(stream)))
+
+    def get_state(self):
+        """(state float32 [n_agents, 4] = x, y, yaw, v; flags uint8 [n_agents]) on the host."""
+        st = np.zeros((self.n_agents, 4), np.float32)
+        fl = np.zeros(self.n_agents, np.uint8)
+        check(lib().gp_get_state(self._h, _ptr(st), _ptr(fl), 1, _stream(None)))
+        return st, fl
+
+    def get_state_device(self, state, flags, stream=None) -> None:
+        check(lib().gp_get_state(self._h, _ptr(state), _ptr(flags), 0, _stream(stream)))
+
+    def set_state(self, state, flags) -> None:
+        st = np.ascontiguousarray(state, np.float32)
+        fl = np.ascontiguousarray(flags, np.uint8)
+        check(lib().gp_set_state(self._h, _ptr(st), _ptr(fl), 1, _stream(None)))
+
+    def status(self) -> int:
+        bits = ctypes.c_uint32()
+        check(lib().gp_get_status(self._h, ctypes.byref(bits)))
+        return bits.value
+
+    def clear_status(self) -> None:
+        check(lib().gp_clear_status(self._h))
+
+    def inject_status(self, bits: int) -> None:
+        check(lib().gp_debug_inject_status(self._h, bits))
+
+    def dump_tris(self, view: int, out, depth=None, cap: int = 1 << 20) -> np.ndarray:
+        """Render all views and return the snapped triangles view `view` rasterised."""
+        buf = np.zeros(cap, TRI_DTYPE)
+        n = ctypes.c_int64()
+        check(lib().gp_debug_dump_tris(self._h, view, _ptr(out), _ptr(depth), buf.ctypes.data,
+                                       cap, ctypes.byref(n), _stream(None)))
+        assert n.value <= cap, "dump capacity exceeded"
+        return buf[:n.value].copy()

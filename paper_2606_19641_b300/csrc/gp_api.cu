@@ -1,0 +1,946 @@
+// Host runtime and C ABI (include/gigapixel.h): validation, device world layout, launch
+// shapes, CUDA-graph replay, autotuning, state/status/debug calls.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "gp_internal.h"
+
+using namespace gpk;
+
+namespace {
+
+thread_local std::string g_err;
+
+gp_status fail(gp_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(GP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count) {
+        n = count;
+        if (count == 0) return cudaSuccess;
+        return cudaMalloc(&p, sizeof(T) * count);
+    }
+    cudaError_t upload(const std::vector<T> &v) {
+        cudaError_t e = alloc(v.size());
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+struct Shape {
+    int threads = 512, band_rows = 32, tri_cap = 512, blocks = 0;
+    size_t smem = 0;
+};
+
+struct GraphKey {
+    const void *a, *o, *d;
+    bool operator<(const GraphKey &k) const {
+        if (a != k.a) return a < k.a;
+        if (o != k.o) return o < k.o;
+        return d < k.d;
+    }
+};
+
+}  // namespace
+
+struct gp_handle {
+    int device = 0, sms = 148;
+    gp_config cfg{};
+    int n_worlds = 0, n_agents = 0, n_boxes = 0, n_views = 0;
+    std::vector<WorldInfo> worlds_h;
+    std::vector<int> world_item_begin, world_item_count;
+    DevBuf<WorldInfo> worlds;
+    DevBuf<float4> box_pose, box_dim, quad_geo, road_geo;
+    DevBuf<float> speed;
+    DevBuf<uint8_t> flags;
+    DevBuf<int> agent_world, agent_box, cell_off, cell_quads, counter, dump_count;
+    DevBuf<Cluster> clusters;
+    DevBuf<uint32_t> quad_prim, status;
+    DevBuf<int2> items;
+    DevBuf<DumpTri> dump;
+    DevBuf<float> state_stage;
+    DevBuf<uint8_t> flag_stage;
+    Shape shape;
+    uint16_t onehot[4][2];
+    cudaStream_t capture_stream = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    bool sticky = false;
+};
+
+namespace {
+
+bool finite_all(const float *p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+gp_status validate(const gp_world_desc *d, const gp_config *c) {
+    if (!d || !c) return fail(GP_EINVAL, "null descriptor or config");
+    if (d->n_worlds <= 0) return fail(GP_EINVAL, "n_worlds must be positive");
+    if (!d->box_off || !d->agent_count || !d->road_off || !d->line_off)
+        return fail(GP_EINVAL, "null CSR array");
+    if (c->width < 16 || c->height < 16 || c->width > GP_MAX_WIDTH || c->height > GP_MAX_WIDTH)
+        return fail(GP_ELIMIT, "image size must be within 16..512");
+    if (c->width % 16) return fail(GP_EINVAL, "image width must be a multiple of 16");
+    if (c->n_cams < 1 || c->n_cams > GP_MAX_CAMS) return fail(GP_ELIMIT, "n_cams must be 1..8");
+    if (!(c->hfov > 0.01f && c->hfov < 3.0f)) return fail(GP_EINVAL, "hfov out of range");
+    if (!(c->near_plane > 0.f) || !(c->cam_height > 0.f) || !(c->dt > 0.f) || !(c->v_max >= 0.f))
+        return fail(GP_EINVAL, "near_plane, cam_height, dt must be positive, v_max >= 0");
+    if (c->key_precision != GP_KEY_F32 && c->key_precision != GP_KEY_F16)
+        return fail(GP_EINVAL, "key_precision");
+    if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16)
+        return fail(GP_EINVAL, "output");
+    if (c->threads < 0 || c->threads > 1024 || c->threads % 32 || c->band_rows < 0 ||
+        c->tri_capacity < 0 || c->tri_capacity > 4096)
+        return fail(GP_EINVAL, "threads (multiple of 32, <= 1024), band_rows, tri_capacity");
+    for (int k = 0; k < 4; ++k)
+        if (!(c->norm_std[k] != 0.f) || !std::isfinite(c->norm_mean[k]) || !std::isfinite(c->norm_std[k]))
+            return fail(GP_EINVAL, "norm_mean/norm_std");
+    for (int k = 0; k < c->n_cams; ++k)
+        if (!std::isfinite(c->cam_yaw[k])) return fail(GP_EINVAL, "cam_yaw");
+    const int nw = d->n_worlds;
+    if (d->box_off[0] != 0 || d->road_off[0] != 0 || d->line_off[0] != 0)
+        return fail(GP_EINVAL, "CSR offsets must start at 0");
+    for (int w = 0; w < nw; ++w) {
+        const int nb = d->box_off[w + 1] - d->box_off[w];
+        const int na = d->agent_count[w];
+        const int nr = d->road_off[w + 1] - d->road_off[w];
+        const int nl = d->line_off[w + 1] - d->line_off[w];
+        if (nb < 0 || nr < 0 || nl < 0) return fail(GP_EINVAL, "CSR offsets must be non-decreasing");
+        if (na < 0 || na > nb) return fail(GP_EINVAL, "agent_count must be in [0, boxes]");
+        if (nb > GP_MAX_BOXES) return fail(GP_ELIMIT, "more than 128 boxes in a world");
+        if (nr + nl > GP_MAX_QUADS) return fail(GP_ELIMIT, "more than 32767 quads in a world");
+        const long long prims = 12LL * nb + 2LL * (nr + nl);
+        if (c->key_precision == GP_KEY_F16 && prims > 65535)
+            return fail(GP_ELIMIT, "FP16 keys hold at most 65535 primitive ids per world");
+    }
+    const size_t nb = d->box_off[nw], nr = d->road_off[nw], nl = d->line_off[nw];
+    if ((nb && !d->boxes) || (nr && !d->road) || (nl && !d->line))
+        return fail(GP_EINVAL, "null geometry array");
+    if (!finite_all(d->boxes, nb * 7) || !finite_all(d->road, nr * 8) || !finite_all(d->line, nl * 8))
+        return fail(GP_EINVAL, "non-finite geometry");
+    for (size_t b = 0; b < nb; ++b)
+        if (!(d->boxes[7 * b + 3] > 0.f && d->boxes[7 * b + 4] > 0.f && d->boxes[7 * b + 5] > 0.f))
+            return fail(GP_EINVAL, "box dimensions must be positive");
+    return GP_OK;
+}
+
+uint16_t bf16_bits(float x) {
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    uint16_t u;
+    std::memcpy(&u, &b, 2);
+    return u;
+}
+
+size_t smem_limit(int device) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return (size_t)v;
+}
+
+// Complete a launch shape: shared memory and resident blocks (0 blocks = does not fit).
+bool finish_shape(gp_handle *h, Shape &s) {
+    const gp_config &c = h->cfg;
+    if (s.band_rows > c.height) s.band_rows = c.height;
+    if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
+    if (s.tri_cap < (s.threads / 32) * 32 + 6) return false;
+    s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap);
+    if (s.smem + 1024 > smem_limit(h->device)) return false;  // leave room for static smem
+    const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem);
+    if (per_sm < 1) return false;
+    s.blocks = per_sm * h->sms;
+    return true;
+}
+
+Shape default_shape(gp_handle *h) {
+    const gp_config &c = h->cfg;
+    Shape best;
+    const int rows_opts[] = {512, 256, 128, 64, 48, 32, 16, 8};
+    for (int r : rows_opts) {
+        Shape s;
+        s.threads = c.threads ? c.threads : 512;
+        s.tri_cap = c.tri_capacity ? c.tri_capacity : 512;
+        s.band_rows = c.band_rows ? c.band_rows : r;
+        if (!finish_shape(h, s)) {
+            if (c.band_rows) break;
+            continue;
+        }
+        // prefer >= 2 resident blocks per SM, then the tallest band
+        if (best.blocks == 0 || (s.blocks >= 2 * h->sms && best.blocks < 2 * h->sms)) best = s;
+        if (c.band_rows) break;
+        if (best.blocks >= 2 * h->sms) break;
+    }
+    return best;
+}
+
+RenderParams render_params(gp_handle *h, void *out, void *depth) {
+    RenderParams p{};
+    const gp_config &c = h->cfg;
+    p.worlds = h->worlds.p;
+    p.box_pose = h->box_pose.p;
+    p.box_dim = h->box_dim.p;
+    p.agent_world = h->agent_world.p;
+    p.clusters = h->clusters.p;
+    p.quad_geo = h->quad_geo.p;
+    p.quad_prim = h->quad_prim.p;
+    p.items = h->items.p;
+    p.item_begin = 0;
+    p.n_items = (int)h->items.n;
+    p.work_counter = h->counter.p;
+    p.W = c.width;
+    p.H = c.height;
+    p.n_cams = c.n_cams;
+    p.band_rows = h->shape.band_rows;
+    for (int k = 0; k < GP_MAX_CAMS; ++k) p.cam_yaw[k] = c.cam_yaw[k];
+    const double f = 0.5 * c.width / std::tan(0.5 * (double)c.hfov);
+    p.f = (float)f;
+    p.near_plane = c.near_plane;
+    p.cam_h = c.cam_height;
+    p.line_z = c.lane_line_z;
+    p.tx = (float)(0.5 * c.width / f);
+    p.ty = (float)(0.5 * c.height / f);
+    p.guard = 4.0f;
+    p.key_f16 = c.key_precision;
+    p.out_mode = c.output;
+    p.out = out;
+    p.depth = depth;
+    p.view_mod = 0;
+    std::memcpy(p.onehot, h->onehot, sizeof(p.onehot));
+    p.tri_cap = h->shape.tri_cap;
+    p.status = h->status.p;
+    p.dump_view = -1;
+    return p;
+}
+
+StepParams step_params(gp_handle *h, const float *actions) {
+    StepParams p{};
+    p.worlds = h->worlds.p;
+    p.world_begin = 0;
+    p.n_worlds = h->n_worlds;
+    p.box_pose = h->box_pose.p;
+    p.box_dim = h->box_dim.p;
+    p.speed = h->speed.p;
+    p.flags = h->flags.p;
+    p.actions = (const float2 *)actions;
+    p.road_geo = h->road_geo.p;
+    p.cell_off = h->cell_off.p;
+    p.cell_quads = h->cell_quads.p;
+    p.dt = h->cfg.dt;
+    p.vmax = h->cfg.v_max;
+    p.status = h->status.p;
+    return p;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+gp_status check_out(void *out, void *depth) {
+    if (!out) return fail(GP_EINVAL, "out_dev is null");
+    if (!aligned16(out) || (depth && !aligned16(depth)))
+        return fail(GP_EINVAL, "output pointers must be 16-byte aligned");
+    return GP_OK;
+}
+
+cudaError_t enqueue_render(gp_handle *h, const RenderParams &p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(h->counter.p, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    return launch_render(p, h->shape.blocks, h->shape.threads, h->shape.smem, s);
+}
+
+// Work items: worlds in decreasing cost order (ragged batches start with the heaviest
+// worlds), every view of a world together, every band of a view together.
+void build_items(gp_handle *h, int band_rows, std::vector<int2> &items) {
+    const gp_config &c = h->cfg;
+    const int nb = (c.height + band_rows - 1) / band_rows;
+    std::vector<int> order(h->n_worlds);
+    for (int w = 0; w < h->n_worlds; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const WorldInfo &A = h->worlds_h[a], &B = h->worlds_h[b];
+        return (long long)A.n_cl * 16 + A.n_boxes > (long long)B.n_cl * 16 + B.n_boxes;
+    });
+    items.clear();
+    items.reserve((size_t)h->n_views * nb);
+    h->world_item_begin.assign(h->n_worlds, 0);
+    h->world_item_count.assign(h->n_worlds, 0);
+    for (int w : order) {
+        const WorldInfo &wi = h->worlds_h[w];
+        h->world_item_begin[w] = (int)items.size();
+        for (int a = 0; a < wi.n_agents; ++a)
+            for (int cam = 0; cam < c.n_cams; ++cam)
+                for (int b = 0; b < nb; ++b)
+                    items.push_back(make_int2((wi.agent_begin + a) * c.n_cams + cam, b));
+        h->world_item_count[w] = (int)items.size() - h->world_item_begin[w];
+    }
+}
+
+std::string cache_key(gp_handle *h) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, h->device);
+    const gp_config &c = h->cfg;
+    long long quads = 0;
+    for (auto &w : h->worlds_h) quads += w.n_cl;
+    std::ostringstream k;
+    k << prop.name << "|" << c.width << "x" << c.height << "|cams" << c.n_cams << "|key"
+      << c.key_precision << "|out" << c.output << "|views" << h->n_views << "|clusters" << quads;
+    return k.str();
+}
+
+// Flat JSON object of "key": "threads,band_rows,tri_cap" strings.
+std::map<std::string, std::string> read_cache(const char *path) {
+    std::map<std::string, std::string> m;
+    std::ifstream f(path);
+    if (!f) return m;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t i = 0;
+    while (true) {
+        const size_t a = s.find('"', i);
+        if (a == std::string::npos) break;
+        const size_t b = s.find('"', a + 1);
+        if (b == std::string::npos) break;
+        const size_t c = s.find('"', b + 1);
+        if (c == std::string::npos) break;
+        const size_t d = s.find('"', c + 1);
+        if (d == std::string::npos) break;
+        m[s.substr(a + 1, b - a - 1)] = s.substr(c + 1, d - c - 1);
+        i = d + 1;
+    }
+    return m;
+}
+
+void write_cache(const char *path, const std::map<std::string, std::string> &m) {
+    std::ofstream f(path);
+    f << "{\n";
+    size_t i = 0;
+    for (auto &kv : m)
+        f << "  \"" << kv.first << "\": \"" << kv.second << "\"" << (++i < m.size() ? ",\n" : "\n");
+    f << "}\n";
+}
+
+// Time candidate launch shapes on the real worlds (render only, into a scratch output of
+// at most 1 GiB that views share round-robin).  The best shape is cached in the JSON file
+// named by GP_AUTOTUNE_CACHE, if set.
+gp_status autotune(gp_handle *h) {
+    const char *cache_path = std::getenv("GP_AUTOTUNE_CACHE");
+    const std::string key = cache_key(h);
+    if (cache_path) {
+        auto m = read_cache(cache_path);
+        auto it = m.find(key);
+        if (it != m.end()) {
+            Shape s;
+            if (std::sscanf(it->second.c_str(), "%d,%d,%d", &s.threads, &s.band_rows, &s.tri_cap) == 3 &&
+                finish_shape(h, s)) {
+                h->shape = s;
+                return GP_OK;
+            }
+        }
+    }
+    const gp_config &c = h->cfg;
+    const size_t px = (size_t)c.width * c.height;
+    const size_t out_pv = px * (c.output == GP_OUT_CLASS_U8 ? 1 : 8);
+    const size_t dep_pv = px * (c.key_precision == GP_KEY_F32 ? 4 : 2);
+    size_t views = std::min<size_t>((size_t)h->n_views, ((size_t)1 << 30) / (out_pv + dep_pv));
+    views = std::max<size_t>(views, 1);
+    uint8_t *scratch = nullptr;
+    const size_t out_bytes = (views * out_pv + 255) / 256 * 256;
+    CK(cudaMalloc(&scratch, out_bytes + views * dep_pv));
+    uint8_t *depth = scratch + out_bytes;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Shape best;
+    float best_ms = 1e30f;
+    const Shape saved = h->shape;
+    const int thr[] = {256, 512, 1024};
+    const int caps[] = {384, 512, 1024};
+    const int rows[] = {8, 16, 32, 64, 128, 256, 512};
+    for (int t : thr)
+        for (int cap : caps)
+            for (int r : rows) {
+                if (r > c.height && r != rows[0]) continue;
+                Shape s;
+                s.threads = t;
+                s.tri_cap = cap;
+                s.band_rows = r;
+                if (!finish_shape(h, s)) continue;
+                std::vector<int2> items;
+                build_items(h, s.band_rows, items);
+                DevBuf<int2> ditems;
+                if (ditems.upload(items) != cudaSuccess) continue;
+                h->shape = s;
+                RenderParams p = render_params(h, scratch, depth);
+                p.items = ditems.p;
+                p.n_items = (int)items.size();
+                p.view_mod = (int)views;
+                float ms = 1e30f;
+                bool ok = true;
+                for (int rep = 0; rep < 3 && ok; ++rep) {
+                    cudaEventRecord(e0, 0);
+                    ok = enqueue_render(h, p, 0) == cudaSuccess;
+                    cudaEventRecord(e1, 0);
+                    ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+                    float t_ms = 0;
+                    cudaEventElapsedTime(&t_ms, e0, e1);
+                    if (rep > 0) ms = std::min(ms, t_ms);
+                }
+                ditems.release();
+                h->shape = saved;
+                if (!ok) continue;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = s;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    if (best.blocks == 0) return fail(GP_ECUDA, "autotune found no launch shape");
+    h->shape = best;
+    if (cache_path) {
+        auto m = read_cache(cache_path);
+        char buf[64];
+        std::snprintf(buf, sizeof buf, "%d,%d,%d", best.threads, best.band_rows, best.tri_cap);
+        m[key] = buf;
+        write_cache(cache_path, m);
+    }
+    return GP_OK;
+}
+
+void release_all(gp_handle *h) {
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    h->capture_stream = nullptr;
+    h->worlds.release();
+    h->box_pose.release();
+    h->box_dim.release();
+    h->quad_geo.release();
+    h->road_geo.release();
+    h->speed.release();
+    h->flags.release();
+    h->agent_world.release();
+    h->agent_box.release();
+    h->cell_off.release();
+    h->cell_quads.release();
+    h->counter.release();
+    h->dump_count.release();
+    h->clusters.release();
+    h->quad_prim.release();
+    h->status.release();
+    h->items.release();
+    h->dump.release();
+    h->state_stage.release();
+    h->flag_stage.release();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gp_last_error(void) { return g_err.c_str(); }
+
+gp_status gp_default_config(gp_config *c) {
+    if (!c) return fail(GP_EINVAL, "null config");
+    std::memset(c, 0, sizeof *c);
+    c->width = 128;
+    c->height = 128;
+    c->n_cams = 1;
+    c->hfov = 1.5707963267948966f;
+    c->cam_height = 1.5f;
+    c->near_plane = 0.1f;
+    c->lane_line_z = 0.02f;
+    c->dt = 0.1f;
+    c->v_max = 30.f;
+    c->key_precision = GP_KEY_F32;
+    c->output = GP_OUT_CLASS_U8;
+    for (int k = 0; k < 4; ++k) {
+        c->norm_mean[k] = 0.5f;
+        c->norm_std[k] = 0.5f;
+    }
+    return GP_OK;
+}
+
+gp_status gp_destroy(gp_handle *h) {
+    if (!h) return GP_OK;
+    cudaSetDevice(h->device);
+    release_all(h);
+    delete h;
+    return GP_OK;
+}
+
+gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int device,
+                           gp_handle **out) {
+    if (!out) return fail(GP_EINVAL, "null out handle");
+    *out = nullptr;
+    gp_status st = validate(d, cfg);
+    if (st != GP_OK) return st;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(GP_EINVAL, "invalid device");
+    CK(cudaSetDevice(device));
+    gp_handle *h = new gp_handle();
+    h->device = device;
+    h->cfg = *cfg;
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+    const int nw = d->n_worlds;
+    h->n_worlds = nw;
+    const int nbox = d->box_off[nw];
+
+    std::vector<float4> pose(nbox), dim(nbox);
+    std::vector<float> speed;
+    std::vector<int> agent_world, agent_box;
+    for (int b = 0; b < nbox; ++b) {
+        const float *s = d->boxes + 7 * (size_t)b;
+        pose[b] = make_float4(s[0], s[1], s[2], 0.f);
+        dim[b] = make_float4(s[3], s[4], s[5], 0.f);
+    }
+    std::vector<Cluster> clusters;
+    std::vector<float4> quad_geo, road_geo;
+    std::vector<uint32_t> quad_prim;
+    std::vector<int> cell_off(1, 0), cell_quads;
+    h->worlds_h.resize(nw);
+    for (int w = 0; w < nw; ++w) {
+        WorldInfo wi{};
+        wi.box_begin = d->box_off[w];
+        wi.n_boxes = d->box_off[w + 1] - d->box_off[w];
+        wi.agent_begin = (int)agent_world.size();
+        wi.n_agents = d->agent_count[w];
+        for (int a = 0; a < wi.n_agents; ++a) {
+            agent_world.push_back(w);
+            agent_box.push_back(wi.box_begin + a);
+            speed.push_back(d->boxes[7 * (size_t)(wi.box_begin + a) + 6]);
+        }
+        const int r0 = d->road_off[w], nr = d->road_off[w + 1] - r0;
+        const int l0 = d->line_off[w], nl = d->line_off[w + 1] - l0;
+        wi.box_end = 12u * wi.n_boxes;
+        wi.road_end = wi.box_end + 2u * nr;
+        wi.road_begin = (int)road_geo.size() / 2;
+        wi.n_road = nr;
+        float bx0 = 1e30f, by0 = 1e30f, bx1 = -1e30f, by1 = -1e30f;
+        for (int r = 0; r < nr; ++r) {
+            const float *q = d->road + 8 * (size_t)(r0 + r);
+            road_geo.push_back(make_float4(q[0], q[1], q[2], q[3]));
+            road_geo.push_back(make_float4(q[4], q[5], q[6], q[7]));
+            for (int k = 0; k < 4; ++k) {
+                bx0 = std::min(bx0, q[2 * k]);
+                bx1 = std::max(bx1, q[2 * k]);
+                by0 = std::min(by0, q[2 * k + 1]);
+                by1 = std::max(by1, q[2 * k + 1]);
+            }
+        }
+        // off-road grid: 8 m cells over the road bounding box; a quad is listed in every
+        // cell its bounding box touches (widened by one cell), so any point inside it finds it
+        const float cs = 8.f;
+        if (nr == 0) {
+            bx0 = by0 = 0.f;
+            bx1 = by1 = 1.f;
+        }
+        wi.gx0 = bx0;
+        wi.gy0 = by0;
+        wi.ginv = 1.f / cs;
+        wi.gnx = std::max(1, (int)std::ceil((bx1 - bx0) / cs) + 1);
+        wi.gny = std::max(1, (int)std::ceil((by1 - by0) / cs) + 1);
+        wi.cell_begin = (int)cell_off.size() - 1;
+        {
+            std::vector<std::vector<int>> cells((size_t)wi.gnx * wi.gny);
+            for (int r = 0; r < nr; ++r) {
+                const float *q = d->road + 8 * (size_t)(r0 + r);
+                float qx0 = q[0], qx1 = q[0], qy0 = q[1], qy1 = q[1];
+                for (int k = 1; k < 4; ++k) {
+                    qx0 = std::min(qx0, q[2 * k]);
+                    qx1 = std::max(qx1, q[2 * k]);
+                    qy0 = std::min(qy0, q[2 * k + 1]);
+                    qy1 = std::max(qy1, q[2 * k + 1]);
+                }
+                const int cx0 = std::max(0, (int)std::floor((qx0 - bx0) / cs) - 1);
+                const int cx1 = std::min(wi.gnx - 1, (int)std::floor((qx1 - bx0) / cs) + 1);
+                const int cy0 = std::max(0, (int)std::floor((qy0 - by0) / cs) - 1);
+                const int cy1 = std::min(wi.gny - 1, (int)std::floor((qy1 - by0) / cs) + 1);
+                for (int cy = cy0; cy <= cy1; ++cy)
+                    for (int cx = cx0; cx <= cx1; ++cx)
+                        cells[(size_t)cy * wi.gnx + cx].push_back(wi.road_begin + r);
+            }
+            for (auto &cl : cells) {
+                cell_quads.insert(cell_quads.end(), cl.begin(), cl.end());
+                cell_off.push_back((int)cell_quads.size());
+            }
+        }
+        // culling clusters: quads bucketed by the 16 m cell of their centroid, chunks of 16
+        {
+            const float cc = 16.f;
+            struct QRef {
+                long long key;
+                int src;  // index into the combined road + line list
+            };
+            std::vector<QRef> refs;
+            refs.reserve(nr + nl);
+            auto quad_ptr = [&](int i) {
+                return i < nr ? d->road + 8 * (size_t)(r0 + i) : d->line + 8 * (size_t)(l0 + i - nr);
+            };
+            for (int i = 0; i < nr + nl; ++i) {
+                const float *q = quad_ptr(i);
+                const float mx = 0.25f * (q[0] + q[2] + q[4] + q[6]);
+                const float my = 0.25f * (q[1] + q[3] + q[5] + q[7]);
+                const long long kx = (long long)std::floor(mx / cc) + (1 << 20);
+                const long long ky = (long long)std::floor(my / cc) + (1 << 20);
+                refs.push_back({ky * (1LL << 22) + kx, i});
+            }
+            std::stable_sort(refs.begin(), refs.end(),
+                             [](const QRef &a, const QRef &b) { return a.key < b.key; });
+            wi.cl_begin = (int)clusters.size();
+            size_t i = 0;
+            while (i < refs.size()) {
+                size_t j = i;
+                while (j < refs.size() && refs[j].key == refs[i].key && j - i < (size_t)kClusterQuads) ++j;
+                Cluster c{};
+                float x0 = 1e30f, y0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z0 = 1e30f, z1 = -1e30f;
+                c.q0 = (int)quad_prim.size();
+                c.nq = (int)(j - i);
+                for (size_t k = i; k < j; ++k) {
+                    const int src = refs[k].src;
+                    const float *q = quad_ptr(src);
+                    quad_geo.push_back(make_float4(q[0], q[1], q[2], q[3]));
+                    quad_geo.push_back(make_float4(q[4], q[5], q[6], q[7]));
+                    const uint32_t prim = src < nr ? wi.box_end + 2u * src : wi.road_end + 2u * (src - nr);
+                    quad_prim.push_back(prim);
+                    const float z = src < nr ? 0.f : cfg->lane_line_z;
+                    for (int t = 0; t < 4; ++t) {
+                        x0 = std::min(x0, q[2 * t]);
+                        x1 = std::max(x1, q[2 * t]);
+                        y0 = std::min(y0, q[2 * t + 1]);
+                        y1 = std::max(y1, q[2 * t + 1]);
+                    }
+                    z0 = std::min(z0, z);
+                    z1 = std::max(z1, z);
+                }
+                // pad the bounds so that FP32 culling stays conservative
+                const float pad = 1e-3f + 1e-5f * std::max(std::max(std::fabs(x0), std::fabs(x1)),
+                                                           std::max(std::fabs(y0), std::fabs(y1)));
+                c.cx = 0.5f * (x0 + x1);
+                c.cy = 0.5f * (y0 + y1);
+                c.hx = 0.5f * (x1 - x0) + pad;
+                c.hy = 0.5f * (y1 - y0) + pad;
+                c.zlo = z0 - 1e-4f;
+                c.zhi = z1 + 1e-4f;
+                clusters.push_back(c);
+                i = j;
+            }
+            wi.n_cl = (int)clusters.size() - wi.cl_begin;
+            if (wi.n_cl > kMaxClustersPerWorld) {
+                delete h;
+                return fail(GP_ELIMIT, "too many culling clusters in a world");
+            }
+        }
+        h->worlds_h[w] = wi;
+    }
+    h->n_agents = (int)agent_world.size();
+    h->n_boxes = nbox;
+    h->n_views = h->n_agents * cfg->n_cams;
+
+    for (int c = 0; c < 4; ++c) {
+        h->onehot[c][0] = bf16_bits((0.f - cfg->norm_mean[c]) / cfg->norm_std[c]);
+        h->onehot[c][1] = bf16_bits((1.f - cfg->norm_mean[c]) / cfg->norm_std[c]);
+    }
+
+#define UP(buf, vec)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = h->buf.upload(vec);                                                \
+        if (e_ != cudaSuccess) {                                                            \
+            gp_destroy(h);                                                                  \
+            return fail(e_ == cudaErrorMemoryAllocation ? GP_ENOMEM : GP_ECUDA,             \
+                        std::string("upload " #buf ": ") + cudaGetErrorString(e_));         \
+        }                                                                                   \
+    } while (0)
+    UP(worlds, h->worlds_h);
+    UP(box_pose, pose);
+    UP(box_dim, dim);
+    UP(speed, speed);
+    std::vector<uint8_t> zeros(h->n_agents, 0);
+    UP(flags, zeros);
+    UP(agent_world, agent_world);
+    UP(agent_box, agent_box);
+    UP(clusters, clusters);
+    UP(quad_geo, quad_geo);
+    UP(quad_prim, quad_prim);
+    UP(road_geo, road_geo);
+    UP(cell_off, cell_off);
+    UP(cell_quads, cell_quads);
+    std::vector<int> one(1, 0);
+    UP(counter, one);
+    UP(dump_count, one);
+    std::vector<uint32_t> st0(1, 0);
+    UP(status, st0);
+    std::vector<float> stage(4 * (size_t)std::max(1, h->n_agents), 0.f);
+    UP(state_stage, stage);
+    std::vector<uint8_t> fstage(std::max(1, h->n_agents), 0);
+    UP(flag_stage, fstage);
+#undef UP
+
+    if (render_configure(smem_limit(device) - 1024) != cudaSuccess) {
+        gp_destroy(h);
+        return fail(GP_ECUDA, "cannot configure render kernel shared memory");
+    }
+    h->shape = default_shape(h);
+    if (h->shape.blocks == 0) {
+        gp_destroy(h);
+        return fail(GP_ELIMIT, "no launch shape fits this configuration");
+    }
+    if (cfg->autotune) {
+        st = autotune(h);
+        if (st != GP_OK) {
+            gp_destroy(h);
+            return st;
+        }
+    }
+    std::vector<int2> items;
+    build_items(h, h->shape.band_rows, items);
+    if (h->items.upload(items) != cudaSuccess) {
+        gp_destroy(h);
+        return fail(GP_ENOMEM, "upload items");
+    }
+    if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        gp_destroy(h);
+        return fail(GP_ECUDA, "stream create");
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        gp_destroy(h);
+        return fail(GP_ECUDA, "create: device error");
+    }
+    *out = h;
+    return GP_OK;
+}
+
+gp_status gp_step(gp_handle *h, const float *actions, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!actions) return fail(GP_EINVAL, "actions_dev is null");
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    CK(launch_step(step_params(h, actions), 8 * h->sms, (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_render(gp_handle *h, void *out, void *depth, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    CK(enqueue_render(h, render_params(h, out, depth), (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *depth,
+                         void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!actions) return fail(GP_EINVAL, "actions_dev is null");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    GraphKey key{actions, out, depth};
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        if (h->graphs.size() >= 4) {
+            cudaGraphExecDestroy(h->graphs.begin()->second);
+            h->graphs.erase(h->graphs.begin());
+        }
+        cudaStream_t cs = h->capture_stream;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = launch_step(step_params(h, actions), 8 * h->sms, cs);
+        cudaError_t e2 = e1 == cudaSuccess ? enqueue_render(h, render_params(h, out, depth), cs) : e1;
+        cudaGraph_t g = nullptr;
+        cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+        if (e2 != cudaSuccess || e3 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(GP_ECUDA, std::string("graph capture: ") +
+                                      cudaGetErrorString(e2 != cudaSuccess ? e2 : e3));
+        }
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e4 = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e4 != cudaSuccess)
+            return fail(GP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e4));
+        it = h->graphs.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second, (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (world < 0 || world >= h->n_worlds) return fail(GP_EINVAL, "world out of range");
+    if (!actions) return fail(GP_EINVAL, "actions_dev is null");
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    StepParams p = step_params(h, actions);
+    p.world_begin = world;
+    p.n_worlds = 1;
+    CK(launch_step(p, 1, (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_render_world(gp_handle *h, int32_t world, void *out, void *depth, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (world < 0 || world >= h->n_worlds) return fail(GP_EINVAL, "world out of range");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    RenderParams p = render_params(h, out, depth);
+    p.item_begin = h->world_item_begin[world];
+    p.n_items = h->world_item_count[world];
+    p.work_counter = nullptr;
+    CK(launch_render(p, std::max(1, p.n_items), h->shape.threads, h->shape.smem,
+                     (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_get_state(gp_handle *h, float *state, uint8_t *flags, int on_host, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!state && !flags) return fail(GP_EINVAL, "state and flags are both null");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->n_agents;
+    float *ds = (on_host || !state) ? h->state_stage.p : state;
+    uint8_t *df = (on_host || !flags) ? h->flag_stage.p : flags;
+    CK(launch_state(ds, df, h->box_pose.p, h->speed.p, h->flags.p, h->agent_box.p, n, 1, s));
+    if (on_host) {
+        if (state && n) CK(cudaMemcpyAsync(state, ds, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, s));
+        if (flags && n) CK(cudaMemcpyAsync(flags, df, n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return GP_OK;
+}
+
+gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, int on_host,
+                       void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!state || !flags) return fail(GP_EINVAL, "state and flags are required");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->n_agents;
+    if (on_host) {
+        if (!finite_all(state, 4 * (size_t)n)) return fail(GP_EINVAL, "non-finite state");
+        if (n) {
+            CK(cudaMemcpyAsync(h->state_stage.p, state, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(h->flag_stage.p, flags, n, cudaMemcpyHostToDevice, s));
+        }
+        CK(launch_state(h->state_stage.p, h->flag_stage.p, h->box_pose.p, h->speed.p, h->flags.p,
+                        h->agent_box.p, n, 0, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        CK(launch_state(const_cast<float *>(state), const_cast<uint8_t *>(flags), h->box_pose.p,
+                        h->speed.p, h->flags.p, h->agent_box.p, n, 0, s));
+    }
+    return GP_OK;
+}
+
+gp_status gp_get_info(gp_handle *h, gp_info *info) {
+    if (!h || !info) return fail(GP_EINVAL, "null argument");
+    info->n_worlds = h->n_worlds;
+    info->n_agents = h->n_agents;
+    info->n_boxes = h->n_boxes;
+    info->n_views = h->n_views;
+    info->width = h->cfg.width;
+    info->height = h->cfg.height;
+    info->n_cams = h->cfg.n_cams;
+    info->key_precision = h->cfg.key_precision;
+    info->output = h->cfg.output;
+    const long long px = (long long)h->cfg.width * h->cfg.height * h->n_views;
+    info->out_bytes = px * (h->cfg.output == GP_OUT_CLASS_U8 ? 1 : 8);
+    info->depth_bytes = px * (h->cfg.key_precision == GP_KEY_F32 ? 4 : 2);
+    info->band_rows = h->shape.band_rows;
+    info->threads = h->shape.threads;
+    info->tri_capacity = h->shape.tri_cap;
+    info->blocks = h->shape.blocks;
+    return GP_OK;
+}
+
+gp_status gp_get_status(gp_handle *h, uint32_t *bits) {
+    if (!h || !bits) return fail(GP_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(bits, h->status.p, 4, cudaMemcpyDeviceToHost));
+    h->sticky = *bits != 0;
+    return GP_OK;
+}
+
+gp_status gp_clear_status(gp_handle *h) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemset(h->status.p, 0, 4));
+    h->sticky = false;
+    return GP_OK;
+}
+
+gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    CK(cudaSetDevice(h->device));
+    uint32_t cur = 0;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&cur, h->status.p, 4, cudaMemcpyDeviceToHost));
+    cur |= bits;
+    CK(cudaMemcpy(h->status.p, &cur, 4, cudaMemcpyHostToDevice));
+    return GP_OK;
+}
+
+gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out, void *depth, void *host_tris,
+                             int64_t cap, int64_t *n, void *stream) {
+    if (!h || !n) return fail(GP_EINVAL, "null argument");
+    if (view < 0 || view >= h->n_views) return fail(GP_EINVAL, "view out of range");
+    if (cap < 0 || (cap > 0 && !host_tris)) return fail(GP_EINVAL, "bad capacity/buffer");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t want = (size_t)std::max<int64_t>(std::min<int64_t>(cap, 1 << 24), 1);
+    if (h->dump.n < want) {
+        h->dump.release();
+        CK(h->dump.alloc(want));
+    }
+    CK(cudaMemsetAsync(h->dump_count.p, 0, sizeof(int), s));
+    RenderParams p = render_params(h, out, depth);
+    p.dump_view = view;
+    p.dump = h->dump.p;
+    p.dump_count = h->dump_count.p;
+    p.dump_cap = (int)want;
+    CK(enqueue_render(h, p, s));
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, h->dump_count.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n = cnt;
+    const int64_t take = std::min<int64_t>(std::min<int64_t>(cnt, cap), (int64_t)want);
+    if (take > 0) CK(cudaMemcpy(host_tris, h->dump.p, sizeof(DumpTri) * take, cudaMemcpyDeviceToHost));
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal device-side layout of the batched step-and-render library.  Host runtime
+// (gp_api.cu) builds these arrays once at create time; the step and render kernels read
+// them.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gigapixel.h"
+
+namespace gpk {
+
+constexpr int kMaxBoxes = GP_MAX_BOXES;
+constexpr int kClusterQuads = 16;  // quads per culling cluster = 32 triangles = one warp
+constexpr int kMaxClustersPerWorld = 4096;
+
+// Per-world table (device).
+struct WorldInfo {
+    int box_begin, n_boxes;      // global box range; the first n_agents are agents
+    int agent_begin, n_agents;   // global agent range
+    int cl_begin, n_cl;          // culling clusters
+    int road_begin, n_road;      // road quads in original order (off-road test)
+    int cell_begin;              // off-road grid: cells [cell_begin, cell_begin + gnx*gny)
+    int gnx, gny;
+    float gx0, gy0, ginv;        // grid origin and inverse cell size
+    uint32_t box_end, road_end;  // primitive-id class boundaries: box < box_end <= road < road_end
+};
+
+// A culling cluster: up to kClusterQuads ground quads of one grid cell.
+struct Cluster {
+    float cx, cy, hx, hy;  // xy bounding box (centre, half extents)
+    float zlo, zhi;        // z range of the quads
+    int q0, nq;            // quads [q0, q0 + nq) of the cluster-ordered quad arrays
+};
+
+struct StepParams {
+    const WorldInfo *worlds;
+    int world_begin, n_worlds;
+    float4 *box_pose;       // x, y, yaw, 0 (agents updated in place)
+    const float4 *box_dim;  // L, W, H, 0
+    float *speed;           // [n_agents]
+    uint8_t *flags;         // [n_agents]
+    const float2 *actions;  // [n_agents] accel, steer
+    const float4 *road_geo; // 2 per road quad (original order)
+    const int *cell_off;    // CSR of road quads per grid cell
+    const int *cell_quads;
+    float dt, vmax;
+    uint32_t *status;
+};
+
+// Snapped triangle as dumped for parity checks (matches gp_debug_dump_tris records).
+struct DumpTri {
+    int X[3], Y[3];
+    float d[3];
+    uint32_t prim, sub;
+};
+
+struct RenderParams {
+    const WorldInfo *worlds;
+    const float4 *box_pose;
+    const float4 *box_dim;
+    const int *agent_world;  // [n_agents]
+    const Cluster *clusters;
+    const float4 *quad_geo;  // 2 per quad, cluster order
+    const uint32_t *quad_prim;
+    const int2 *items;       // (view, band)
+    int item_begin, n_items;
+    int *work_counter;       // persistent mode if non-null, else one item per block
+
+    int W, H, n_cams, band_rows;
+    float cam_yaw[GP_MAX_CAMS];
+    float f;                 // focal length, px
+    float near_plane, cam_h, line_z;
+    float tx, ty;            // viewport half-extent / f
+    float guard;             // guard band factor
+
+    int key_f16, out_mode;
+    void *out;
+    void *depth;
+    int view_mod;            // 0, or write view v at slot v % view_mod (tuning scratch)
+    uint16_t onehot[4][2];   // bf16 values per channel: [cold, hot]
+
+    int tri_cap;             // triangles per raster batch
+    uint32_t *status;
+
+    int dump_view;           // -1 = off
+    DumpTri *dump;
+    int *dump_count;
+    int dump_cap;
+};
+
+// Shared-memory bytes the render kernel needs for a launch shape.
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap);
+
+cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
+cudaError_t launch_state(float *state, uint8_t *flags, float4 *pose, float *speed, uint8_t *fl,
+                         const int *agent_box, int n, int to_state, cudaStream_t s);
+cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,
+                          cudaStream_t s);
+cudaError_t render_configure(size_t max_smem);
+int render_occupancy(int key_f16, int threads, size_t smem);
+
+}  // namespace gpk

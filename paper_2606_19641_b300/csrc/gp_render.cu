@@ -1,0 +1,816 @@
+// Render kernel: batched perspective rasterisation of bounding-box worlds.
+//
+// One work item = one screen band (full image width, band_rows rows) of one agent camera.
+// Persistent CTAs pull items from a global counter.  Per item:
+//   1. cull: per-world clusters of ground quads and the world's boxes are tested as
+//      axis-aligned boxes against the band's frustum (left/right planes, near plane and the
+//      band's pixel-centre rows; conservative by 1/16 px for snapping);
+//   2. setup: one warp per unit of 32 source triangles (a cluster's 16 quads, or 32 box
+//      face triangles); each lane transforms its triangle to view space, culls, projects,
+//      snaps to 1/16 px (round half to even), back-face culls and keeps it if its snapped
+//      bounding box holds a pixel centre of the band.  Triangles crossing the near plane or
+//      the 4x guard band go to a queue and are clipped (Sutherland-Hodgman, planes in the
+//      order near, left, right, bottom, top) and fan-triangulated;
+//   3. raster: kept triangles are expanded into (triangle, row) items; each item computes
+//      the exact covered span of its row from the integer edge functions (top-left fill
+//      rule) and updates a depth key per pixel in shared memory with atomicMax.  The key
+//      is (depth bits << 32 | ~prim) with FP32 reversed-Z depth, or (binary16 depth << 16 |
+//      ~prim) in FP16 mode: the nearest surface wins, ties go to the smaller primitive id;
+//   4. encode: keys become class ids (uint8) + depth, or a normalised one-hot BF16 NCHW
+//      tensor; the band is one contiguous range of every output plane, written with 16-byte
+//      streaming stores.
+// The depth plane d = d0 + a (X - X0) + b (Y - Y0) and its per-pixel evaluation follow a
+// fixed IEEE FP32 operation sequence (explicit _rn intrinsics), so identical snapped
+// triangles give bit-identical keys on any implementation that follows the same sequence.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "gp_internal.h"
+
+namespace gpk {
+
+namespace {
+
+constexpr int kItemsPerThread = 8;  // row items per thread per raster sub-pass
+constexpr int kPoly = 16;           // clip polygon capacity (a triangle needs at most 8)
+
+struct __align__(16) TriRec {
+    int A[3], B[3], C[3];  // edge functions E_k = A_k gx + B_k gy + C_k, fill-rule bias folded in
+    float invA[3];         // 1 / A_k (estimate only), 0 if A_k == 0
+    float d0, a, b;        // depth plane, per 1/16 px
+    int X0, Y0;            // vertex 0 (origin of gx, gy)
+    uint32_t low;          // low half of the key: inverted primitive id
+    int ispan;             // pixel-centre columns i0 | i1 << 16
+    int jspan;             // pixel-centre rows    j0 | j1 << 16
+};
+static_assert(sizeof(TriRec) == 80, "TriRec layout");
+
+struct Cam {
+    float px, py, s, c;  // camera position and yaw sin/cos
+    int by0, by1;        // band rows, inclusive
+    uint32_t box_end, road_end;
+    int box_begin, ego, cl_begin;
+};
+
+struct Smem {
+    size_t keys, tris, rowoff, map, viscl, visbox, clipq, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, int threads,
+                                            int tri_cap) {
+    Smem s;
+    size_t o = 0;
+    s.keys = o;
+    o += (size_t)W * band_rows * (key_f16 ? 4 : 8);
+    o = align_up(o, 16);
+    s.tris = o;
+    o += (size_t)tri_cap * sizeof(TriRec);
+    s.rowoff = o;
+    o += (size_t)(tri_cap + 1) * 4;
+    o = align_up(o, 16);
+    s.map = o;
+    o += (size_t)threads * kItemsPerThread * 2;
+    o = align_up(o, 16);
+    s.viscl = o;
+    o += (size_t)kMaxClustersPerWorld * 2;
+    s.visbox = o;
+    o += kMaxBoxes;
+    o = align_up(o, 16);
+    s.clipq = o;
+    o += (size_t)threads * 4;
+    s.total = align_up(o, 16);
+    return s;
+}
+
+__device__ __forceinline__ float3 to_view(const RenderParams &p, const Cam &cm, float x, float y,
+                                          float z) {
+    const float dx = __fsub_rn(x, cm.px), dy = __fsub_rn(y, cm.py);
+    return make_float3(__fsub_rn(__fmul_rn(dx, cm.s), __fmul_rn(dy, cm.c)), __fsub_rn(z, p.cam_h),
+                       __fadd_rn(__fmul_rn(dx, cm.c), __fmul_rn(dy, cm.s)));
+}
+
+// Clip-plane values, inside >= 0: near, left, right, bottom, top.
+__device__ __forceinline__ float plane_dist(const RenderParams &p, int k, float x, float y,
+                                            float z) {
+    const float gx = __fmul_rn(__fmul_rn(p.guard, p.tx), z);
+    const float gy = __fmul_rn(__fmul_rn(p.guard, p.ty), z);
+    switch (k) {
+    case 0: return __fsub_rn(z, p.near_plane);
+    case 1: return __fadd_rn(x, gx);
+    case 2: return __fsub_rn(gx, x);
+    case 3: return __fadd_rn(y, gy);
+    default: return __fsub_rn(gy, y);
+    }
+}
+
+__device__ __forceinline__ int outcode(const RenderParams &p, float3 v) {
+    int oc = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) oc |= (plane_dist(p, k, v.x, v.y, v.z) < 0.f) ? (1 << k) : 0;
+    return oc;
+}
+
+__device__ __forceinline__ void project(const RenderParams &p, float x, float y, float z, int &X,
+                                        int &Y) {
+    const float f16 = 16.f * p.f;
+    X = __float2int_rn(__fmaf_rn(f16, __fdiv_rn(x, z), 8.f * (float)p.W));
+    Y = __float2int_rn(__fmaf_rn(-f16, __fdiv_rn(y, z), 8.f * (float)p.H));
+}
+
+// Box corner k: x = +-L/2 (bit 0), y = +-W/2 (bit 1), z = 0 or H (bit 2).
+__device__ __forceinline__ void box_corner(float4 pose, float4 dim, float s, float c, int k,
+                                           float &x, float &y, float &z) {
+    const float lx = (k & 1) ? 0.5f * dim.x : -0.5f * dim.x;
+    const float ly = (k & 2) ? 0.5f * dim.y : -0.5f * dim.y;
+    x = pose.x + (c * lx - s * ly);
+    y = pose.y + (s * lx + c * ly);
+    z = (k & 4) ? dim.z : 0.f;
+}
+
+// Face triangles (corner indices), counter-clockwise seen from outside; faces +x, -x, +y,
+// -y, +z, -z, each quad (q0 q1 q2 q3) split into (q0 q1 q2), (q0 q2 q3).
+__device__ __forceinline__ void box_tri(int t, int &a, int &b, int &c) {
+    // packed 4-bit corner ids per face: q0 q1 q2 q3
+    const unsigned short F[6] = {0x1375, 0x0462, 0x2673, 0x0154, 0x4576, 0x0231};
+    const unsigned short f = F[t >> 1];
+    const int q0 = (f >> 12) & 15, q1 = (f >> 8) & 15, q2 = (f >> 4) & 15, q3 = f & 15;
+    a = q0;
+    b = (t & 1) ? q2 : q1;
+    c = (t & 1) ? q3 : q2;
+}
+
+// a * b + c in 32-bit two's-complement wrap-around (exact whenever the true result fits).
+__device__ __forceinline__ unsigned int wrap_mul_add(int a, int b, unsigned int c) {
+    return (unsigned int)a * (unsigned int)b + c;
+}
+
+// Build a raster record from a front-facing snapped triangle (area2 < 0 in y-down space).
+__device__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float d[3],
+                          uint32_t prim, int key_f16, int i0, int i1, int j0, int j1) {
+    // orient to positive area: keep vertex 0, swap 1 and 2
+    const int vx[3] = {X[0], X[2], X[1]};
+    const int vy[3] = {Y[0], Y[2], Y[1]};
+    const float dv[3] = {d[0], d[2], d[1]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = k, b = (k + 1) % 3;
+        const int A = vy[a] - vy[b], B = vx[b] - vx[a];
+        unsigned int C = wrap_mul_add(A, vx[0] - vx[a], wrap_mul_add(B, vy[0] - vy[a], 0u));
+        const int dxe = vx[b] - vx[a], dye = vy[b] - vy[a];
+        const bool tl = (dye == 0 && dxe > 0) || (dye < 0);
+        if (!tl) C -= 1u;
+        r.A[k] = A;
+        r.B[k] = B;
+        r.C[k] = (int)C;
+        r.invA[k] = A != 0 ? 1.f / (float)A : 0.f;
+    }
+    const float fx1 = (float)(vx[1] - vx[0]), fy1 = (float)(vy[1] - vy[0]);
+    const float fx2 = (float)(vx[2] - vx[0]), fy2 = (float)(vy[2] - vy[0]);
+    const int area2 = (int)(wrap_mul_add(vx[1] - vx[0], vy[2] - vy[0], 0u) -
+                            wrap_mul_add(vx[2] - vx[0], vy[1] - vy[0], 0u));
+    const float e1 = __fsub_rn(dv[1], dv[0]), e2 = __fsub_rn(dv[2], dv[0]);
+    const float fa = __int2float_rn(area2);
+    const float na = __fsub_rn(__fmul_rn(e1, fy2), __fmul_rn(e2, fy1));
+    const float nb = __fsub_rn(__fmul_rn(e2, fx1), __fmul_rn(e1, fx2));
+    r.a = __fdiv_rn(na, fa);
+    r.b = __fdiv_rn(nb, fa);
+    r.d0 = dv[0];
+    r.X0 = vx[0];
+    r.Y0 = vy[0];
+    r.low = key_f16 ? (0xFFFFu - (prim & 0xFFFFu)) : (0xFFFFFFFFu - prim);
+    r.ispan = (i0 & 0xFFFF) | (i1 << 16);
+    r.jspan = (j0 & 0xFFFF) | (j1 << 16);
+}
+
+// Snapped triangle -> keep? (front-facing, bbox holds a pixel centre of the band).
+__device__ __forceinline__ bool tri_bbox(const RenderParams &p, const Cam &cm, const int X[3],
+                                         const int Y[3], int &i0, int &i1, int &j0, int &j1) {
+    const int area2 = (int)(wrap_mul_add(X[1] - X[0], Y[2] - Y[0], 0u) -
+                            wrap_mul_add(X[2] - X[0], Y[1] - Y[0], 0u));
+    if (area2 >= 0) return false;
+    const int mnx = min(X[0], min(X[1], X[2])), mxx = max(X[0], max(X[1], X[2]));
+    const int mny = min(Y[0], min(Y[1], Y[2])), mxy = max(Y[0], max(Y[1], Y[2]));
+    i0 = max((mnx + 7) >> 4, 0);
+    i1 = min((mxx - 8) >> 4, p.W - 1);
+    j0 = max((mny + 7) >> 4, cm.by0);
+    j1 = min((mxy - 8) >> 4, cm.by1);
+    return i0 <= i1 && j0 <= j1;
+}
+
+__device__ __forceinline__ void dump_tri(const RenderParams &p, const int X[3], const int Y[3],
+                                         const float d[3], uint32_t prim, uint32_t sub) {
+    const int k = atomicAdd(p.dump_count, 1);
+    if (k < p.dump_cap) {
+        DumpTri &t = p.dump[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            t.X[i] = X[i];
+            t.Y[i] = Y[i];
+            t.d[i] = d[i];
+        }
+        t.prim = prim;
+        t.sub = sub;
+    }
+}
+
+// Is an axis-aligned box (xy centre/half extents, z range) possibly visible in the band?
+__device__ bool aabb_visible(const RenderParams &p, const Cam &cm, float cx, float cy, float hx,
+                             float hy, float zlo, float zhi) {
+    const float dx = cx - cm.px, dy = cy - cm.py;
+    const float as = fabsf(cm.s), ac = fabsf(cm.c);
+    const float zc = dx * cm.c + dy * cm.s, ze = hx * ac + hy * as;
+    const float zmax = zc + ze;
+    if (zmax < p.near_plane) return false;
+    const float zmin = fmaxf(zc - ze, p.near_plane);
+    const float xc = dx * cm.s - dy * cm.c;
+    // left plane x + tx z >= 0 and right plane tx z - x >= 0 (viewport, not guard band)
+    const float lv = xc + p.tx * zc + hx * fabsf(cm.s + p.tx * cm.c) + hy * fabsf(p.tx * cm.s - cm.c);
+    const float rv = p.tx * zc - xc + hx * fabsf(p.tx * cm.c - cm.s) + hy * fabsf(p.tx * cm.s + cm.c);
+    if (lv < 0.f || rv < 0.f) return false;
+    // rows: y_px = H/2 - f y / z over y in [zlo - h, zhi - h], z in [zmin, zmax]
+    const float ylo = zlo - p.cam_h, yhi = zhi - p.cam_h;
+    const float hh = 0.5f * (float)p.H;
+    const float ymax = hh - p.f * ylo / (ylo < 0.f ? zmin : zmax);
+    const float ymin = hh - p.f * yhi / (yhi > 0.f ? zmin : zmax);
+    const float margin = 0.0625f + 1e-5f * fmaxf(fabsf(ymin), fabsf(ymax));
+    const float jlo = ceilf(ymin - 0.5f - margin), jhi = floorf(ymax - 0.5f + margin);
+    return fmaxf(jlo, (float)cm.by0) <= fminf(jhi, (float)cm.by1);
+}
+
+template <typename Key>
+__device__ __forceinline__ Key make_key(float d, uint32_t low);
+template <>
+__device__ __forceinline__ unsigned long long make_key<unsigned long long>(float d, uint32_t low) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | low;
+}
+template <>
+__device__ __forceinline__ unsigned int make_key<unsigned int>(float d, uint32_t low) {
+    return ((unsigned int)__half_as_ushort(__float2half_rn(d)) << 16) | low;
+}
+
+// Rasterise one row of one triangle: exact covered span, then per-pixel depth keys.
+template <typename Key>
+__device__ __forceinline__ void raster_row(const TriRec &T, int row, int by0, int W, Key *keys) {
+    const int gy = 16 * row + 8 - T.Y0;
+    int lo = T.ispan & 0xFFFF, hi = T.ispan >> 16;
+    const float xo = (float)(T.X0 - 8);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int A = T.A[k];
+        const int R = (int)wrap_mul_add(T.B[k], gy, (unsigned int)T.C[k]);
+        if (A == 0) {
+            if (R < 0) hi = lo - 1;
+            continue;
+        }
+        // E(i) = A (16 i + 8 - X0) + R ; the edge crosses at i* = (X0 - 8 - R / A) / 16.
+        // The float estimate is within one pixel wherever it matters; one exact integer
+        // check on each side fixes it.
+        const float q = (xo - (float)R * T.invA[k]) * 0.0625f;
+        if (A > 0) {  // lower bound: smallest i with E(i) >= 0
+            int i = __float2int_ru(fminf(fmaxf(q, -1e6f), 1e6f));
+            i = min(max(i, lo), hi + 1);
+            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - T.X0, (unsigned int)R) >= 0)
+                --i;
+            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - T.X0, (unsigned int)R) < 0)
+                ++i;
+            lo = i;
+        } else {  // upper bound: largest i with E(i) >= 0
+            int i = __float2int_rd(fminf(fmaxf(q, -1e6f), 1e6f));
+            i = min(max(i, lo - 1), hi);
+            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - T.X0, (unsigned int)R) >= 0)
+                ++i;
+            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - T.X0, (unsigned int)R) < 0)
+                --i;
+            hi = i;
+        }
+    }
+    if (lo > hi) return;
+    const float inner = __fmaf_rn(T.b, (float)gy, T.d0);
+    float fgx = (float)(16 * lo + 8 - T.X0);
+    Key *rowp = keys + (row - by0) * W;
+    for (int i = lo; i <= hi; ++i, fgx += 16.f) {
+        float d = __fmaf_rn(T.a, fgx, inner);
+        d = d > 0.f ? d : 0.f;
+        const Key key = make_key<Key>(d, T.low);
+        if (key > rowp[i]) atomicMax(rowp + i, key);
+    }
+}
+
+// Warp-aggregated append: returns this lane's slot (valid where keep is true).
+__device__ __forceinline__ int warp_append(bool keep, int *counter) {
+    const unsigned int lane = threadIdx.x & 31;
+    const unsigned int m = __ballot_sync(0xffffffffu, keep);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+// Block-wide exclusive scan of per-thread sums (all threads call; returns own prefix).
+__device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) s_warp[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    total = s_warp[nw - 1];
+    const int before = warp > 0 ? s_warp[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
+// Block-wide exclusive max-scan of per-thread values (0 for thread 0).
+__device__ __forceinline__ int block_exclusive_max(int v, int *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = max(x, y);
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w = max(w, y);
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int prev_lane = __shfl_up_sync(0xffffffffu, x, 1);
+    const int before_warp = warp > 0 ? s_warp[warp - 1] : 0;
+    __syncthreads();
+    return lane > 0 ? max(before_warp, prev_lane) : before_warp;
+}
+
+struct Shared {
+    int item, ntri, nclip, nvcl, nvbox;
+    int warp[32];
+};
+
+// Rasterise the current batch of triangles into the band's key buffer.
+template <typename Key>
+__device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *keys, TriRec *tris,
+                      int *rowoff, unsigned short *map) {
+    const int n = min(sh.ntri, p.tri_cap);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // row counts -> exclusive scan (each thread owns a contiguous slice of triangles)
+    const int per = (n + nt - 1) / nt;
+    const int t0 = min(tid * per, n), t1 = min(t0 + per, n);
+    int local = 0;
+    for (int t = t0; t < t1; ++t) {
+        const int js = tris[t].jspan;
+        local += (js >> 16) - (js & 0xFFFF) + 1;
+    }
+    int total = 0;
+    int run = block_exclusive_scan(local, sh.warp, total);
+    for (int t = t0; t < t1; ++t) {
+        rowoff[t] = run;
+        const int js = tris[t].jspan;
+        run += (js >> 16) - (js & 0xFFFF) + 1;
+    }
+    if (tid == 0) rowoff[n] = total;
+    __syncthreads();
+
+    const int chunk = nt * kItemsPerThread;
+    for (int start = 0; start < total; start += chunk) {
+        const int len = min(chunk, total - start);
+        for (int i = tid; i < len; i += nt) map[i] = 0;
+        __syncthreads();
+        for (int t = tid; t < n; t += nt) {
+            const int o = rowoff[t], c = rowoff[t + 1] - o;
+            if (c > 0) {
+                if (o >= start && o < start + len) map[o - start] = (unsigned short)t;
+                else if (o < start && o + c > start) map[0] = (unsigned short)t;
+            }
+        }
+        __syncthreads();
+        // max-scan of the head map: every item gets the triangle it belongs to (heads are
+        // increasing with position, so the running maximum is the latest head)
+        const int m0 = tid * kItemsPerThread;
+        int own = 0;
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k)
+            if (m0 + k < len) own = max(own, (int)map[m0 + k]);
+        int cur = block_exclusive_max(own, sh.warp);
+#pragma unroll
+        for (int k = 0; k < kItemsPerThread; ++k) {
+            if (m0 + k < len) {
+                cur = max(cur, (int)map[m0 + k]);
+                map[m0 + k] = (unsigned short)cur;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < len; i += nt) {
+            const int t = map[i];
+            const TriRec &T = tris[t];
+            const int row = (T.jspan & 0xFFFF) + (start + i - rowoff[t]);
+            raster_row<Key>(T, row, cm.by0, p.W, keys);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) sh.ntri = 0;
+    __syncthreads();
+}
+
+// Append one kept triangle (any lane, not warp-aggregated): used by the clip path.
+__device__ void append_one(const RenderParams &p, Shared &sh, TriRec *tris, int view,
+                           const int X[3], const int Y[3], const float d[3], uint32_t prim,
+                           uint32_t sub, int i0, int i1, int j0, int j1) {
+    const int k = atomicAdd(&sh.ntri, 1);
+    if (k < p.tri_cap) build_rec(tris[k], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
+    else atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);
+    if (view == p.dump_view) dump_tri(p, X, Y, d, prim, sub);
+}
+
+// World-space vertices and primitive id of a source triangle.
+//   code bit 31 set: box triangle, bits 4..11 local box index, bits 0..3 face triangle
+//   otherwise: quad (cluster order) << 1 | triangle
+__device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm, uint32_t code,
+                                           float vx[3], float vy[3], float vz[3],
+                                           uint32_t &prim) {
+    if (code & 0x80000000u) {
+        const int b = (code >> 4) & 0xFF, t = code & 15;
+        const float4 pose = p.box_pose[cm.box_begin + b];
+        const float4 dim = p.box_dim[cm.box_begin + b];
+        float s, c;
+        sincosf(pose.z, &s, &c);
+        int k[3];
+        box_tri(t, k[0], k[1], k[2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) box_corner(pose, dim, s, c, k[i], vx[i], vy[i], vz[i]);
+        prim = 12u * b + t;
+    } else {
+        const int q = code >> 1, t = code & 1;
+        const float4 g0 = p.quad_geo[2 * q], g1 = p.quad_geo[2 * q + 1];
+        const uint32_t base = p.quad_prim[q];
+        const float z = base < cm.road_end ? 0.f : p.line_z;
+        vx[0] = g0.x;
+        vy[0] = g0.y;
+        vx[1] = t ? g1.x : g0.z;
+        vy[1] = t ? g1.y : g0.w;
+        vx[2] = t ? g1.z : g1.x;
+        vy[2] = t ? g1.w : g1.y;
+        vz[0] = vz[1] = vz[2] = z;
+        prim = base + t;
+    }
+}
+
+// Clip a source triangle against near + guard planes, fan-triangulate, keep front faces.
+__device__ void clip_emit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris, int view,
+                          uint32_t code) {
+    float wx[3], wy[3], wz[3];
+    uint32_t prim;
+    source_tri(p, cm, code, wx, wy, wz, prim);
+    // A convex polygon gains at most one vertex per plane (3 + 5 = 8); the arrays allow
+    // twice that so rounding on near-degenerate input cannot write past them.
+    float px[kPoly], py[kPoly], pz[kPoly], qx[kPoly], qy[kPoly], qz[kPoly];
+    int n = 3;
+    for (int i = 0; i < 3; ++i) {
+        const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
+        px[i] = v.x;
+        py[i] = v.y;
+        pz[i] = v.z;
+    }
+    for (int k = 0; k < 5 && n >= 3; ++k) {
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            const int j = (i + 1 == n) ? 0 : i + 1;
+            const float da = plane_dist(p, k, px[i], py[i], pz[i]);
+            const float db = plane_dist(p, k, px[j], py[j], pz[j]);
+            const bool ia = da >= 0.f, ib = db >= 0.f;
+            if (ia && m < kPoly) {
+                qx[m] = px[i];
+                qy[m] = py[i];
+                qz[m] = pz[i];
+                ++m;
+            }
+            if (ia != ib && m < kPoly) {
+                // interpolate from the inside vertex towards the outside one
+                const int vi = ia ? i : j, vo = ia ? j : i;
+                const float di = ia ? da : db, dov = ia ? db : da;
+                const float t = __fdiv_rn(di, __fsub_rn(di, dov));
+                qx[m] = __fmaf_rn(t, __fsub_rn(px[vo], px[vi]), px[vi]);
+                qy[m] = __fmaf_rn(t, __fsub_rn(py[vo], py[vi]), py[vi]);
+                qz[m] = __fmaf_rn(t, __fsub_rn(pz[vo], pz[vi]), pz[vi]);
+                ++m;
+            }
+        }
+        n = m;
+        for (int i = 0; i < n; ++i) {
+            px[i] = qx[i];
+            py[i] = qy[i];
+            pz[i] = qz[i];
+        }
+    }
+    if (n < 3) return;
+    if (n > 8) atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);  // not reachable for exact input
+    int X[kPoly], Y[kPoly];
+    float d[kPoly];
+    for (int i = 0; i < n; ++i) {
+        project(p, px[i], py[i], pz[i], X[i], Y[i]);
+        d[i] = __fdiv_rn(p.near_plane, pz[i]);
+    }
+    for (int k = 1; k + 1 < n; ++k) {
+        const int tX[3] = {X[0], X[k], X[k + 1]}, tY[3] = {Y[0], Y[k], Y[k + 1]};
+        const float td[3] = {d[0], d[k], d[k + 1]};
+        int i0, i1, j0, j1;
+        if (tri_bbox(p, cm, tX, tY, i0, i1, j0, j1))
+            append_one(p, sh, tris, view, tX, tY, td, prim, (uint32_t)(k - 1), i0, i1, j0, j1);
+    }
+}
+
+// One setup unit: 32 source triangles, one per lane (warp-uniform call).
+__device__ void setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
+                           uint32_t *clipq, const unsigned short *viscl,
+                           const unsigned char *visbox, int view, int unit, int n_box_units,
+                           int nbox_items) {
+    const int lane = threadIdx.x & 31;
+    uint32_t code = 0;
+    bool valid;
+    if (unit < n_box_units) {
+        const int item = unit * 32 + lane;
+        valid = item < nbox_items;
+        if (valid) code = 0x80000000u | ((uint32_t)visbox[item / 12] << 4) | (uint32_t)(item % 12);
+    } else {
+        const Cluster cl = p.clusters[cm.cl_begin + viscl[unit - n_box_units]];
+        valid = (lane >> 1) < cl.nq;
+        code = (uint32_t)(cl.q0 + (lane >> 1)) << 1 | (uint32_t)(lane & 1);
+    }
+    bool keep = false, clip = false;
+    int X[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, i0 = 0, i1 = 0, j0 = 0, j1 = 0;
+    float z[3] = {1.f, 1.f, 1.f};
+    uint32_t prim = 0;
+    if (valid) {
+        float wx[3], wy[3], wz[3];
+        source_tri(p, cm, code, wx, wy, wz, prim);
+        int oand = 0x1F, oor = 0;
+        float vx[3], vy[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
+            vx[i] = v.x;
+            vy[i] = v.y;
+            z[i] = v.z;
+            const int oc = outcode(p, v);
+            oand &= oc;
+            oor |= oc;
+        }
+        if (oand == 0) {
+            if (oor == 0) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) project(p, vx[i], vy[i], z[i], X[i], Y[i]);
+                keep = tri_bbox(p, cm, X, Y, i0, i1, j0, j1);
+            } else {
+                clip = true;
+            }
+        }
+    }
+    const int ci = warp_append(clip, &sh.nclip);
+    if (clip) clipq[ci] = code;
+    const int k = warp_append(keep, &sh.ntri);
+    if (keep) {
+        float d[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[i] = __fdiv_rn(p.near_plane, z[i]);
+        build_rec(tris[k], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
+        if (view == p.dump_view) dump_tri(p, X, Y, d, prim, 0u);
+    }
+}
+
+__device__ __forceinline__ uint8_t key_class(unsigned long long k, const Cam &cm) {
+    if (!k) return 0;
+    const uint32_t prim = 0xFFFFFFFFu - (uint32_t)k;
+    return prim < cm.box_end ? 3 : (prim < cm.road_end ? 1 : 2);
+}
+__device__ __forceinline__ uint8_t key_class(unsigned int k, const Cam &cm) {
+    if (!k) return 0;
+    const uint32_t prim = 0xFFFFu - (k & 0xFFFFu);
+    return prim < cm.box_end ? 3 : (prim < cm.road_end ? 1 : 2);
+}
+
+__device__ __forceinline__ uint32_t key_depth_bits(unsigned long long k) { return (uint32_t)(k >> 32); }
+__device__ __forceinline__ uint32_t key_depth_bits(unsigned int k) { return k >> 16; }
+
+// Encode the band's keys into the output tensors and clear them for the next item.
+template <typename Key>
+__device__ void encode_store(const RenderParams &p, const Cam &cm, Key *keys, int view) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
+    const long long slot = p.view_mod ? (view % p.view_mod) : view;
+    const long long plane = (long long)p.H * p.W;
+    const long long off = (long long)cm.by0 * p.W;
+    if (p.out_mode == GP_OUT_CLASS_U8) {
+        uint8_t *o = (uint8_t *)p.out + slot * plane + off;
+        for (int b = tid * 16; b < band_px; b += nt * 16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v |= (uint32_t)key_class(keys[b + 4 * q + r], cm) << (8 * r);
+                w[q] = v;
+            }
+            __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
+        }
+    } else {
+        for (int c = 0; c < 4; ++c) {
+            uint16_t *o = (uint16_t *)p.out + (slot * 4 + c) * plane + off;
+            const uint32_t cold = p.onehot[c][0], hot = p.onehot[c][1];
+            for (int b = tid * 8; b < band_px; b += nt * 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t lo = key_class(keys[b + 2 * q], cm) == c ? hot : cold;
+                    const uint32_t hi = key_class(keys[b + 2 * q + 1], cm) == c ? hot : cold;
+                    w[q] = lo | (hi << 16);
+                }
+                __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
+            }
+        }
+    }
+    if (p.depth) {
+        if (sizeof(Key) == 8) {
+            float *o = (float *)p.depth + slot * plane + off;
+            for (int b = tid * 4; b < band_px; b += nt * 4) {
+                float v[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = __uint_as_float(key_depth_bits(keys[b + r]));
+                __stcs((float4 *)(o + b), make_float4(v[0], v[1], v[2], v[3]));
+            }
+        } else {
+            uint16_t *o = (uint16_t *)p.depth + slot * plane + off;
+            for (int b = tid * 8; b < band_px; b += nt * 8) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = key_depth_bits(keys[b + 2 * q]) | (key_depth_bits(keys[b + 2 * q + 1]) << 16);
+                __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
+            }
+        }
+    }
+    __syncthreads();
+    for (int b = tid; b < band_px; b += nt) keys[b] = 0;
+}
+
+template <typename Key>
+__global__ void __launch_bounds__(1024) render_kernel(RenderParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
+    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap);
+    Key *keys = (Key *)(smem + L.keys);
+    TriRec *tris = (TriRec *)(smem + L.tris);
+    int *rowoff = (int *)(smem + L.rowoff);
+    unsigned short *map = (unsigned short *)(smem + L.map);
+    unsigned short *viscl = (unsigned short *)(smem + L.viscl);
+    unsigned char *visbox = (unsigned char *)(smem + L.visbox);
+    uint32_t *clipq = (uint32_t *)(smem + L.clipq);
+
+    for (int b = tid; b < p.band_rows * p.W; b += nt) keys[b] = 0;
+
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) {
+            int it;
+            if (p.work_counter) it = atomicAdd(p.work_counter, 1);
+            else it = iter == 0 ? (int)blockIdx.x : p.n_items;
+            sh.item = it;
+            sh.ntri = 0;
+            sh.nclip = 0;
+            sh.nvcl = 0;
+            sh.nvbox = 0;
+        }
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= p.n_items) break;
+        const int2 wv = p.items[p.item_begin + item];
+        const int view = wv.x, band = wv.y;
+        const int agent = view / p.n_cams, cam = view - agent * p.n_cams;
+        const WorldInfo wi = p.worlds[p.agent_world[agent]];
+        Cam cm;
+        cm.ego = agent - wi.agent_begin;
+        cm.box_begin = wi.box_begin;
+        cm.cl_begin = wi.cl_begin;
+        cm.box_end = wi.box_end;
+        cm.road_end = wi.road_end;
+        const float4 pose = p.box_pose[wi.box_begin + cm.ego];
+        cm.px = pose.x;
+        cm.py = pose.y;
+        sincosf(pose.z + p.cam_yaw[cam], &cm.s, &cm.c);
+        cm.by0 = band * p.band_rows;
+        cm.by1 = min(cm.by0 + p.band_rows, p.H) - 1;
+
+        // 1. cull clusters and boxes against the band frustum
+        for (int base = 0; base < wi.n_cl; base += nt) {
+            const int c = base + tid;
+            bool keep = false;
+            if (c < wi.n_cl) {
+                const Cluster cl = p.clusters[wi.cl_begin + c];
+                keep = aabb_visible(p, cm, cl.cx, cl.cy, cl.hx, cl.hy, cl.zlo, cl.zhi);
+            }
+            const int k = warp_append(keep, &sh.nvcl);
+            if (keep) viscl[k] = (unsigned short)c;  // world-local cluster index
+        }
+        for (int base = 0; base < wi.n_boxes; base += nt) {
+            const int b = base + tid;
+            bool keep = false;
+            if (b < wi.n_boxes && b != cm.ego) {
+                const float4 bp = p.box_pose[wi.box_begin + b];
+                const float4 bd = p.box_dim[wi.box_begin + b];
+                float s, c;
+                sincosf(bp.z, &s, &c);
+                const float hx = 0.5f * (fabsf(c) * bd.x + fabsf(s) * bd.y);
+                const float hy = 0.5f * (fabsf(s) * bd.x + fabsf(c) * bd.y);
+                keep = aabb_visible(p, cm, bp.x, bp.y, hx * 1.0001f + 1e-4f, hy * 1.0001f + 1e-4f,
+                                    -1e-4f, bd.z + 1e-4f);
+            }
+            const int k = warp_append(keep, &sh.nvbox);
+            if (keep) visbox[k] = (unsigned char)b;
+        }
+        __syncthreads();
+
+        // 2. setup rounds with raster flushes
+        const int nbox_items = sh.nvbox * 12;
+        const int n_box_units = (nbox_items + 31) / 32;
+        const int n_units = n_box_units + sh.nvcl;
+        for (int r0 = 0; r0 < n_units; r0 += nw) {
+            const int u = r0 + warp;
+            if (u < n_units)
+                setup_unit(p, cm, sh, tris, clipq, viscl, visbox, view, u, n_box_units, nbox_items);
+            __syncthreads();
+            // clip queue: each entry may emit up to 6 triangles
+            for (;;) {
+                const int nc = sh.nclip;
+                if (nc == 0) break;
+                const int room = (p.tri_cap - sh.ntri) / 6;
+                if (room <= 0) {
+                    flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+                    continue;
+                }
+                const int take = min(min(nc, room), nt);
+                __syncthreads();
+                if (tid < take) clip_emit(p, cm, sh, tris, view, clipq[nc - take + tid]);
+                __syncthreads();
+                if (tid == 0) sh.nclip = nc - take;
+                __syncthreads();
+            }
+            if (sh.ntri > p.tri_cap - nw * 32) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+        }
+        if (sh.ntri > 0) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+
+        // 3. encode and store the band
+        encode_store<Key>(p, cm, keys, view);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap) {
+    return smem_layout(W, band_rows, key_f16, threads, tri_cap).total;
+}
+
+cudaError_t render_configure(size_t max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(render_kernel<unsigned long long>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(render_kernel<unsigned int>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+
+int render_occupancy(int key_f16, int threads, size_t smem) {
+    int n = 0;
+    cudaError_t e = key_f16
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<unsigned int>, threads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<unsigned long long>, threads, smem);
+    return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,
+                          cudaStream_t s) {
+    if (p.n_items <= 0) return cudaSuccess;
+    if (p.key_f16) render_kernel<unsigned int><<<blocks, threads, smem, s>>>(p);
+    else render_kernel<unsigned long long><<<blocks, threads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace gpk

@@ -1,0 +1,384 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tiers:
+  T1 step      one GPU step from an FP32 state vs one oracle FP64 step from the same state:
+               pose/speed within FP32 rounding, flags identical.
+  T2 geometry  snapped vertices of every triangle the GPU rasterised vs the oracle's FP64
+               geometry from the same state: within 1 unit (1/16 px), matched by
+               (primitive, fan index).
+  T3 raster    the oracle's raster rule applied to the GPU's own snapped triangles gives
+               bit-identical class, depth and one-hot outputs.
+  T4 image     GPU image vs the oracle's full FP64 pipeline: class mismatch fraction and
+               depth error reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import worldgen as wg
+from gpu_common import (cam_config, cls_of, dedupe, expected_planes, gpu_view, oracle_raster_of,
+                        oracle_sim, sim_for, view_loc)
+
+pytestmark = pytest.mark.gpu
+
+# class mismatch bound vs the FP64 pipeline: differences come only from pixel centres
+# within ~1/16 px of an edge whose snapped vertex differs by one unit
+T4_MISMATCH = 2e-3
+
+
+def torch_actions(worlds, step, seed):
+    import torch
+    a = wg.actions(seed, step, worlds.n_agents)
+    return torch.from_numpy(a).cuda(), a
+
+
+def check_t3(sim, cfg, worlds, views, out, depth):
+    """Bit-exact raster parity for the given views (returns total covered pixels)."""
+    covered = 0
+    for v in views:
+        tris = dedupe(sim.dump_tris(v, out, depth))
+        img = oracle_raster_of(worlds, cfg, v, tris)
+        go, gd = gpu_view(cfg, out, depth, v)
+        eo, ed = expected_planes(cfg, img)
+        assert np.array_equal(go, eo), "view %d: class/one-hot differs from the raster rule" % v
+        if depth is not None:
+            assert np.array_equal(gd, ed), "view %d: depth bits differ from the raster rule" % v
+        covered += int((img.cls > 0).sum())
+    return covered
+
+
+def t4_stats(sim, cfg, worlds, views, out, depth):
+    """Class mismatch fraction and depth errors vs the oracle's FP64 pipeline."""
+    osim = oracle_sim(worlds, sim)
+    cam = cam_config(cfg)
+    mism, total, derr = 0, 0, []
+    for v in views:
+        w, a, c = view_loc(worlds, cfg, v)
+        img = osim.render(cam, w, a, float(np.float32(cfg.cam_yaw[c])), bool(cfg.key_precision))
+        go, gd = gpu_view(cfg, out, depth, v)
+        gcls = cls_of(cfg, go)
+        mism += int((gcls != img.cls).sum())
+        total += gcls.size
+        if depth is not None:
+            both = (gcls > 0) & (gcls == img.cls)
+            if int(cfg.key_precision) == 0:
+                g = gd.view(np.float32)[both].astype(np.float64)
+                e = img.depth[both].astype(np.float64)
+            else:
+                g = gd[both].view(np.float16).astype(np.float64)
+                e = img.depth[both].view(np.float16).astype(np.float64)
+            if len(g):
+                derr.append(np.abs(g - e) / np.maximum(e, 1e-6))
+    d = np.concatenate(derr) if derr else np.zeros(1)
+    return mism / max(total, 1), d
+
+
+# ---------------------------------------------------------------------------------------
+# T1 step
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n_worlds,steps", [("tiny", 1, 10), ("uniform", 6, 20),
+                                                 ("ragged", 8, 12)])
+def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl)
+    n_halted = 0
+    for k in range(steps):
+        st0, fl0 = sim.get_state()
+        osim = oracle.Sim(worlds)
+        osim.set_state(st0.astype(np.float64), fl0)
+        act_t, act = torch_actions(worlds, k, wl.seed)
+        sim.step(act_t)
+        osim.step(act)
+        st1, fl1 = sim.get_state()
+        moving = (fl0 & 4) == 0
+        assert np.allclose(st1[:, 0:2], osim.state[:, 0:2], atol=2e-4, rtol=0)
+        dyaw = np.angle(np.exp(1j * (st1[:, 2].astype(np.float64) - osim.state[:, 2])))
+        assert np.all(np.abs(dyaw) < 2e-5)
+        assert np.allclose(st1[:, 3], osim.state[:, 3], atol=2e-5)
+        assert np.array_equal(fl1, osim.flags), "flags differ at step %d" % k
+        assert np.all(st1[~moving, :3] == st0[~moving, :3])  # halted agents do not move
+        n_halted = int((fl1 & 4).astype(bool).sum())
+    if name != "tiny":
+        assert n_halted > 0  # random steering does drive some agents off the road
+
+
+# ---------------------------------------------------------------------------------------
+# T2 / T3 / T4 rendering
+# ---------------------------------------------------------------------------------------
+
+SHAPES = [dict(), dict(band_rows=16), dict(band_rows=8, threads=128, tri_capacity=160),
+          dict(threads=1024, tri_capacity=1056), dict(band_rows=128, threads=256, tri_capacity=300)]
+
+
+@pytest.mark.parametrize("shape", SHAPES,
+                         ids=lambda s: "-".join("%s%s" % kv for kv in s.items()) or "default")
+@pytest.mark.parametrize("name,n_worlds", [("tiny", 1), ("uniform", 3)])
+def test_raster_bit_exact_for_gpu_triangles(name, n_worlds, shape):
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl, **shape)
+    out, depth = sim.alloc_outputs()
+    for k in range(3):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    views = list(range(0, sim.n_views, max(1, sim.n_views // 12)))
+    covered = check_t3(sim, cfg, worlds, views, out, depth)
+    assert covered > 0.2 * len(views) * cfg.width * cfg.height
+
+
+@pytest.mark.parametrize("name,n_worlds,views", [("tiny", 1, 8), ("uniform", 2, 16)])
+def test_snapped_vertices_within_one_unit_of_fp64(name, n_worlds, views):
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl)
+    out, depth = sim.alloc_outputs()
+    for k in range(2):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    torch.cuda.synchronize()
+    osim = oracle_sim(worlds, sim)
+    cam = cam_config(cfg)
+    n_match = n_exact = n_oracle_visible = n_found = 0
+    worst = 0
+    for v in range(0, sim.n_views, max(1, sim.n_views // views)):
+        g = dedupe(sim.dump_tris(v, out, depth))
+        w, a, c = view_loc(worlds, cfg, v)
+        o = osim.camera_tris(cam, w, a, float(np.float32(cfg.cam_yaw[c])))
+        gmap = {(int(t["prim"]), int(t["sub"])): t for t in g}
+        be, re = osim.prim_ranges(w)
+        for t in o:
+            # only triangles that cover a pixel centre matter for the image
+            one = np.zeros(1, oracle.TRI_DTYPE)
+            one[0] = t
+            if not oracle.raster(one, cam.width, cam.height, False, be, re).key.any():
+                continue
+            n_oracle_visible += 1
+            gt = gmap.get((int(t["prim"]), int(t["sub"])))
+            if gt is None:
+                continue
+            n_found += 1
+            dx = np.abs(gt["X"].astype(np.int64) - t["X"]).max()
+            dy = np.abs(gt["Y"].astype(np.int64) - t["Y"]).max()
+            worst = max(worst, int(dx), int(dy))
+            n_match += 1
+            n_exact += int(dx == 0 and dy == 0)
+    print("T2 %s: %d visible oracle triangles, %d found, %d exact, worst %d units" % (
+        name, n_oracle_visible, n_found, n_exact, worst))
+    assert n_oracle_visible > 50
+    assert n_found >= 0.995 * n_oracle_visible
+    assert worst <= 1, "snapped vertex more than 1/16 px from the FP64 oracle"
+    assert n_exact >= 0.9 * n_match
+
+
+@pytest.mark.parametrize("name,n_worlds", [("tiny", 1), ("uniform", 2)])
+def test_image_vs_fp64_pipeline(name, n_worlds):
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl)
+    out, depth = sim.alloc_outputs()
+    for k in range(3):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    views = list(range(0, sim.n_views, max(1, sim.n_views // 16)))
+    frac, derr = t4_stats(sim, cfg, worlds, views, out, depth)
+    print("T4 %s: class mismatch %.2e, depth rel err median %.2e p99 %.2e max %.2e" % (
+        name, frac, np.median(derr), np.percentile(derr, 99), derr.max()))
+    assert frac < T4_MISMATCH
+    assert np.percentile(derr, 99) < 1e-2
+
+
+def test_precision_path_fp16_key_and_bf16_onehot():
+    import torch
+    wl = wg.WORKLOADS["ragged_precision"]
+    worlds = wg.make_workload(wl, n_worlds=4)
+    sim, cfg = sim_for(worlds, wl)
+    out, depth = sim.alloc_outputs()
+    assert out.dtype == torch.bfloat16 and depth.dtype == torch.float16
+    sim.step(torch_actions(worlds, 0, wl.seed)[0])
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    views = list(range(0, sim.n_views, max(1, sim.n_views // 10)))
+    check_t3(sim, cfg, worlds, views, out, depth)
+    # one-hot values are exactly +-1 with the default normalisation
+    u = torch.unique(out.view(torch.int16)).cpu().numpy().view(np.uint16)
+    assert set(u.tolist()) <= {0x3F80, 0xBF80}
+    frac, derr = t4_stats(sim, cfg, worlds, views, out, depth)
+    print("T4 precision: class mismatch %.2e, depth rel err p99 %.2e" % (frac, np.percentile(derr, 99)))
+    assert frac < T4_MISMATCH
+    # without a depth output the one-hot tensor is the same
+    out2, _ = sim.alloc_outputs(depth=False)
+    sim.render(out2, None)
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.int16), out2.view(torch.int16))
+
+
+def test_camera_rig_three_cameras():
+    import torch
+    wl = wg.WORKLOADS["sweep"]
+    worlds = wg.make_workload(wl, n_worlds=2)
+    sim, cfg = sim_for(worlds, wl)
+    assert sim.n_views == 3 * worlds.n_agents
+    out, depth = sim.alloc_outputs()
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    check_t3(sim, cfg, worlds, [0, 1, 2, 3 * 5 + 1, 3 * 40 + 2], out, depth)
+
+
+@pytest.mark.parametrize("size", [(512, 512), (64, 48), (256, 144), (16, 16)])
+def test_resolutions(size):
+    import torch
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl, width=size[0], height=size[1])
+    out, depth = sim.alloc_outputs()
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    check_t3(sim, cfg, worlds, list(range(sim.n_views)), out, depth)
+
+
+def test_edge_case_worlds():
+    """No roads, a lone agent, a world without agents, and a camera facing empty space."""
+    import torch
+    road = np.array([[-20, -4, 20, -4, 20, 4, -20, 4]], np.float32)
+    line = np.array([[-20, -0.1, 20, -0.1, 20, 0.1, -20, 0.1]], np.float32)
+    boxes = np.array([
+        [0, 0, 0, 4.5, 1.9, 1.5, 2.0], [12, 0, 0, 4.5, 1.9, 1.5, 0.0],   # w0: agent + static, no road
+        [0, 0, 0, 4.5, 1.9, 1.4, 1.0],                                   # w1: lone agent on a road
+        [5, 5, 0, 4.5, 1.9, 1.5, 0.0],                                   # w2: static box only
+        [90, 0, 0, 4.5, 1.9, 1.5, 0.0],                                  # w3: agent facing nothing
+    ], np.float32)
+    worlds = wg.Worlds(box_off=np.array([0, 2, 3, 4, 5], np.int32),
+                       agent_count=np.array([1, 1, 0, 1], np.int32), boxes=boxes,
+                       road_off=np.array([0, 0, 1, 1, 2], np.int32), road=np.concatenate([road, road]),
+                       line_off=np.array([0, 0, 1, 1, 1], np.int32), line=line)
+    wl = wg.WORKLOADS["tiny"]
+    sim, cfg = sim_for(worlds, wl)
+    assert sim.n_agents == 3
+    out, depth = sim.alloc_outputs()
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    check_t3(sim, cfg, worlds, [0, 1, 2], out, depth)
+    o = out.cpu().numpy()
+    assert (o[0] == 3).any() and not (o[0] == 1).any()   # box visible, no road
+    assert (o[1] == 1).any() and (o[1] == 2).any()        # road and line, no box
+    assert not o[2].any()                                  # nothing ahead of the third agent
+    act = torch.zeros((3, 2), device="cuda")
+    sim.step(act)
+    st, fl = sim.get_state()
+    assert fl[0] & 2 and fl[0] & 4        # no road at all: off-road, halted
+    assert fl[1] == 0                      # on its road
+
+
+# ---------------------------------------------------------------------------------------
+# Paths, state and status
+# ---------------------------------------------------------------------------------------
+
+def test_graph_and_per_world_paths_match_direct_calls():
+    import torch
+    wl = wg.WORKLOADS["ragged"]
+    worlds = wg.make_workload(wl, n_worlds=6)
+    a, cfg = sim_for(worlds, wl)
+    b, _ = sim_for(worlds, wl)
+    c, _ = sim_for(worlds, wl)
+    oa, da = a.alloc_outputs()
+    ob, db = b.alloc_outputs()
+    oc, dc = c.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(4):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        a.step(act)
+        a.render(oa, da)
+        b.step_render(act, ob, db)
+        for w in range(worlds.n_worlds):
+            c.step_world(w, act)
+        for w in range(worlds.n_worlds):
+            c.render_world(w, oc, dc)
+        torch.cuda.synchronize()
+        assert torch.equal(oa, ob) and torch.equal(da.view(torch.int32), db.view(torch.int32))
+        assert torch.equal(oa, oc) and torch.equal(da.view(torch.int32), dc.view(torch.int32))
+    sa, fa = a.get_state()
+    sb, fb = b.get_state()
+    sc, fc = c.get_state()
+    assert np.array_equal(sa, sb) and np.array_equal(sa, sc)
+    assert np.array_equal(fa, fb) and np.array_equal(fa, fc)
+
+
+def test_state_roundtrip_and_fork():
+    import torch
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=2)
+    sim, cfg = sim_for(worlds, wl)
+    for k in range(3):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    snap_s, snap_f = sim.get_state()
+    out1, d1 = sim.alloc_outputs()
+    out2, d2 = sim.alloc_outputs()
+    for k in range(3, 6):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    sim.render(out1, d1)
+    end_s, end_f = sim.get_state()
+    sim.set_state(snap_s, snap_f)          # fork: rewind and replay the same actions
+    s2, f2 = sim.get_state()
+    assert np.array_equal(s2, snap_s) and np.array_equal(f2, snap_f)
+    for k in range(3, 6):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    sim.render(out2, d2)
+    torch.cuda.synchronize()
+    s3, f3 = sim.get_state()
+    assert np.array_equal(s3, end_s) and np.array_equal(f3, end_f)
+    assert torch.equal(out1, out2) and torch.equal(d1, d2)
+
+
+def test_status_word_injection_and_nonfinite_state():
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl)
+    act = torch.zeros((worlds.n_agents, 2), device="cuda")
+    assert sim.status() == 0
+    sim.inject_status(gp.binding.DEV_INJECTED)
+    assert sim.status() == gp.binding.DEV_INJECTED
+    with pytest.raises(gp.GigapixelError) as e:
+        sim.step(act)
+    assert e.value.status == gp.binding.GP_EDEVICE
+    sim.clear_status()
+    sim.step(act)
+    assert sim.status() == 0
+    # a non-finite action makes the state non-finite: reported, never trapped
+    bad = act.clone()
+    bad[0, 0] = float("nan")
+    sim.step(bad)
+    assert sim.status() & gp.binding.DEV_NONFINITE_STATE
+    sim.clear_status()
+
+
+def test_full_size_uniform_batch_sampled():
+    """The full uniform batch (256 worlds x 32 agents, 128x128) in the benchmark's launch
+    configuration (graph replay): sampled views are bit-exact against the raster rule and
+    within the FP64 mismatch bound; invariants hold on every view."""
+    import torch
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl)
+    out, depth = sim.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(3):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        sim.step_render(act, out, depth)
+    torch.cuda.synchronize()
+    assert int(out.max()) <= 3
+    assert torch.equal(out > 0, depth > 0)
+    rng = np.random.default_rng(0)
+    views = sorted(rng.choice(sim.n_views, 6, replace=False).tolist())
+    out_copy, depth_copy = out.clone(), depth.clone()
+    check_t3(sim, cfg, worlds, views, out, depth)
+    assert torch.equal(out, out_copy) and torch.equal(depth, depth_copy)  # re-render identical
+    frac, derr = t4_stats(sim, cfg, worlds, views, out, depth)
+    assert frac < T4_MISMATCH
