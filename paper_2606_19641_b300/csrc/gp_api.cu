@@ -171,7 +171,8 @@ bool finish_shape(gp_handle *h, Shape &s) {
     const gp_config &c = h->cfg;
     if (s.band_rows > c.height) s.band_rows = c.height;
     if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
-    if (s.tri_cap < (s.threads / 32) * 32 + 6) return false;
+    // a setup round appends at most 32 triangles per warp before the batch is flushed
+    if (s.tri_cap < (s.threads / 32) * 32) return false;
     s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap);
     if (s.smem + 1024 > smem_limit(h->device)) return false;  // leave room for static smem
     const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem);
@@ -186,8 +187,8 @@ Shape default_shape(gp_handle *h) {
     const int rows_opts[] = {512, 256, 128, 64, 48, 32, 16, 8};
     for (int r : rows_opts) {
         Shape s;
-        s.threads = c.threads ? c.threads : 512;
-        s.tri_cap = c.tri_capacity ? c.tri_capacity : 512;
+        s.threads = c.threads ? c.threads : 256;
+        s.tri_cap = c.tri_capacity ? c.tri_capacity : std::max(512, 2 * s.threads);
         s.band_rows = c.band_rows ? c.band_rows : r;
         if (!finish_shape(h, s)) {
             if (c.band_rows) break;

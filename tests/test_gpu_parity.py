@@ -109,7 +109,7 @@ def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
 # ---------------------------------------------------------------------------------------
 
 SHAPES = [dict(), dict(band_rows=16), dict(band_rows=8, threads=128, tri_capacity=160),
-          dict(threads=1024, tri_capacity=1056), dict(band_rows=128, threads=256, tri_capacity=300)]
+          dict(threads=1024, tri_capacity=1024), dict(band_rows=128, threads=256, tri_capacity=300)]
 
 
 @pytest.mark.parametrize("shape", SHAPES,
@@ -351,9 +351,13 @@ def test_status_word_injection_and_nonfinite_state():
     sim.clear_status()
     sim.step(act)
     assert sim.status() == 0
-    # a non-finite action makes the state non-finite: reported, never trapped
+    # a NaN steering angle makes a moving agent's pose non-finite: reported, never
+    # trapped (a NaN acceleration alone is absorbed by the speed clamp)
+    st, fl = sim.get_state()
+    st[:, 3] = 5.0
+    sim.set_state(st, np.zeros_like(fl))
     bad = act.clone()
-    bad[0, 0] = float("nan")
+    bad[0, 1] = float("nan")
     sim.step(bad)
     assert sim.status() & gp.binding.DEV_NONFINITE_STATE
     sim.clear_status()
