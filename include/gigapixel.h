@@ -206,6 +206,27 @@ gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits);
 gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out_dev, void *depth_dev,
                              void *host_tris, int64_t cap, int64_t *n, void *stream);
 
+/*
+ * Same result as gp_debug_dump_tris, but the call allocates no memory: its scratch (the
+ * work counter, the record count and up to GP_NOALLOC_MAX_TRIS records, ~0.7 MB) lives in
+ * one fixed device array inside the library, which every GPU that loads the library keeps
+ * until the process exits.  This serves callers that cannot allocate device memory at
+ * this point: a process whose caching allocator (PyTorch's, for example) already holds
+ * nearly all free HBM, where a fresh cudaMalloc can fail although the caller's pool has
+ * room, and hooks inside a running loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree imply.  The paper has no counterpart; this is
+ * a debugging aid of this library.
+ *  - cap must be at most GP_NOALLOC_MAX_TRIS, otherwise GP_ELIMIT (nothing is launched).
+ *  - The first call on a device looks up the array's device address (no allocation); make
+ *    that first call before any stream capture on that device.
+ *  - All calls share the one array (the counters are cleared at the start of every call;
+ *    the records keep the last call's contents): calls that overlap on the GPU, from
+ *    several threads or streams, race.  Synchronous, like gp_debug_dump_tris.
+ */
+#define GP_NOALLOC_MAX_TRIS 16384
+gp_status gp_debug_dump_tris_noalloc(gp_handle *h, int32_t view, void *out_dev, void *depth_dev,
+                                     void *host_tris, int64_t cap, int64_t *n, void *stream);
+
 /* Description of the last error on the calling thread ("" if none). */
 const char *gp_last_error(void);
 

@@ -28,7 +28,9 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render",
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
-            "gp_debug_inject_status", "gp_debug_dump_tris", "gp_last_error")
+            "gp_debug_inject_status", "gp_debug_dump_tris", "gp_debug_dump_tris_noalloc",
+            "gp_last_error")
+NOALLOC_MAX_TRIS = 16384
 
 
 class WorldDesc(ctypes.Structure):
@@ -92,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_clear_status": [vp],
         "gp_debug_inject_status": [vp, u32],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
+        "gp_debug_dump_tris_noalloc": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -945,3 +946,73 @@ gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out, void *depth,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Triangle dump that allocates nothing (gp_debug_dump_tris_noalloc).
+// ---------------------------------------------------------------------------------------
+
+// Fixed scratch of the allocation-free dump: bytes [0, 4) work counter, [4, 8) record
+// count, records from byte 256.  One copy per device, alive until the process exits.
+static __device__ __align__(256) unsigned char gp_noalloc_scratch[256 + GP_NOALLOC_MAX_TRIS * sizeof(DumpTri)];
+
+namespace {
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kNoAllocDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).  Looked up once
+// per device; the host-side name of the array is not a device address.
+gp_status noalloc_scratch(int device, unsigned char **addr) {
+    if (device < 0 || device >= kNoAllocDevices) return fail(GP_EINVAL, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, gp_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(GP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[device] = (unsigned char *)p;
+    }
+    *addr = g_noalloc_addr[device];
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" gp_status gp_debug_dump_tris_noalloc(gp_handle *h, int32_t view, void *out,
+                                                void *depth, void *host_tris, int64_t cap,
+                                                int64_t *n, void *stream) {
+    if (!h || !n) return fail(GP_EINVAL, "null argument");
+    if (view < 0 || view >= h->n_views) return fail(GP_EINVAL, "view out of range");
+    if (cap < 0 || (cap > 0 && !host_tris)) return fail(GP_EINVAL, "bad capacity/buffer");
+    if (cap > GP_NOALLOC_MAX_TRIS)
+        return fail(GP_ELIMIT, "cap exceeds GP_NOALLOC_MAX_TRIS (16384 records), the size of the "
+                               "fixed scratch of the allocation-free dump");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    CK(cudaSetDevice(h->device));
+    unsigned char *scratch = nullptr;
+    st = noalloc_scratch(h->device, &scratch);
+    if (st != GP_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *counters = (int *)scratch;
+    // the work counter and the record count must start at zero; the records need no clearing
+    CK(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
+    RenderParams p = render_params(h, out, depth);
+    p.work_counter = counters;
+    p.dump_count = counters + 1;
+    p.dump = (DumpTri *)(scratch + 256);
+    p.dump_cap = (int)cap;
+    p.dump_view = view;
+    CK(launch_render(p, h->shape.blocks, h->shape.threads, h->shape.smem, s));
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n = cnt;
+    const int64_t take = std::min<int64_t>(cnt, cap);
+    if (take > 0) {
+        CK(cudaMemcpyAsync(host_tris, p.dump, sizeof(DumpTri) * take, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return GP_OK;
+}
