@@ -172,8 +172,8 @@ bool finish_shape(gp_handle *h, Shape &s) {
     const gp_config &c = h->cfg;
     if (s.band_rows > c.height) s.band_rows = c.height;
     if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
-    // a setup round appends at most 32 triangles per warp before the batch is flushed
-    if (s.tri_cap < (s.threads / 32) * 32) return false;
+    // a setup unit needs at most 32 batch slots; a clip job needs 6
+    if (s.tri_cap < 64) return false;
     s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap);
     if (s.smem + 1024 > smem_limit(h->device)) return false;  // leave room for static smem
     const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem);

@@ -5,12 +5,16 @@
 //   1. cull: per-world clusters of ground quads and the world's boxes are tested as
 //      axis-aligned boxes against the band's frustum (left/right planes, near plane and the
 //      band's pixel-centre rows; conservative by 1/16 px for snapping);
-//   2. setup: one warp per unit of 32 source triangles (a cluster's 16 quads, or 32 box
-//      face triangles); each lane transforms its triangle to view space, culls, projects,
-//      snaps to 1/16 px (round half to even), back-face culls and keeps it if its snapped
-//      bounding box holds a pixel centre of the band.  Triangles crossing the near plane or
-//      the 4x guard band go to a queue and are clipped (Sutherland-Hodgman, planes in the
-//      order near, left, right, bottom, top) and fan-triangulated;
+//   2. setup: warps pull units of 32 source triangles (a cluster's 16 quads, or 32 box
+//      face triangles) from a shared counter, with no block barrier between units.  Each
+//      lane transforms its triangle to view space and rejects it if all three vertices lie
+//      beyond one plane through the eye (near, guard band, or the band's pixel-centre
+//      extent widened by 1/4 px); otherwise it projects, snaps to 1/16 px (round half to even),
+//      back-face culls and keeps the triangle if its snapped bounding box holds a pixel
+//      centre of the band.  A triangle crossing the near plane or the 4x guard band is
+//      clipped in its lane (Sutherland-Hodgman, planes in the order near, left, right,
+//      bottom, top) and fan-triangulated.  A warp reserves batch slots for its unit with one
+//      atomic; when the batch is full the block rasterises it and continues;
 //   3. raster: kept triangles are expanded into (triangle, row) items; each item computes
 //      the exact covered span of its row from the integer edge functions (top-left fill
 //      rule) and updates a depth key per pixel in shared memory with atomicMax.  The key
@@ -33,6 +37,7 @@ namespace {
 
 constexpr int kItemsPerThread = 8;  // row items per thread per raster sub-pass
 constexpr int kPoly = 16;           // clip polygon capacity (a triangle needs at most 8)
+constexpr int kClipQueue = 256;     // queued clip jobs per block
 
 struct __align__(16) TriRec {
     int A[3], B[3], C[3];  // edge functions E_k = A_k gx + B_k gy + C_k, fill-rule bias folded in
@@ -50,6 +55,8 @@ struct Cam {
     int by0, by1;        // band rows, inclusive
     uint32_t box_end, road_end;
     int box_begin, ego, cl_begin;
+    float gtx, gty;      // guard-band planes |x| <= gtx z, |y| <= gty z
+    float vl, vt, vb;    // band edges widened by 1/4 px: |x| <= vl z, vb z <= y <= vt z
 };
 
 struct Smem {
@@ -79,7 +86,7 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     o += kMaxBoxes;
     o = align_up(o, 16);
     s.clipq = o;
-    o += (size_t)threads * 4;
+    o += (size_t)kClipQueue * 4;
     s.total = align_up(o, 16);
     return s;
 }
@@ -105,18 +112,35 @@ __device__ __forceinline__ float plane_dist(const RenderParams &p, int k, float 
     }
 }
 
-__device__ __forceinline__ int outcode(const RenderParams &p, float3 v) {
-    int oc = 0;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) oc |= (plane_dist(p, k, v.x, v.y, v.z) < 0.f) ? (1 << k) : 0;
+// Outcode bits: 0 near, 1-4 guard band (left, right, bottom, top) -- the clip planes --
+// and 5-8 the band's pixel-centre extent widened by 1/4 px (left, right, top, bottom).  All
+// planes pass through the eye, so a triangle with every vertex beyond one plane has no
+// visible part on the inner side.
+__device__ __forceinline__ int outcode(const RenderParams &p, const Cam &cm, float x, float y,
+                                       float z) {
+    int oc = (z < p.near_plane) ? 1 : 0;
+    const float gx = cm.gtx * z, gy = cm.gty * z;
+    oc |= (x < -gx) ? 2 : 0;
+    oc |= (x > gx) ? 4 : 0;
+    oc |= (y < -gy) ? 8 : 0;
+    oc |= (y > gy) ? 16 : 0;
+    const float vx = cm.vl * z;
+    oc |= (x < -vx) ? 32 : 0;
+    oc |= (x > vx) ? 64 : 0;
+    oc |= (y > cm.vt * z) ? 128 : 0;
+    oc |= (y < cm.vb * z) ? 256 : 0;
     return oc;
 }
 
+// Projection and 1/16-px snap (round half to even) with one reciprocal per vertex; also
+// the vertex's reversed-Z depth n / z.
 __device__ __forceinline__ void project(const RenderParams &p, float x, float y, float z, int &X,
-                                        int &Y) {
+                                        int &Y, float &d) {
+    const float r = __fdividef(1.f, z);
     const float f16 = 16.f * p.f;
-    X = __float2int_rn(__fmaf_rn(f16, __fdiv_rn(x, z), 8.f * (float)p.W));
-    Y = __float2int_rn(__fmaf_rn(-f16, __fdiv_rn(y, z), 8.f * (float)p.H));
+    X = __float2int_rn(__fmaf_rn(f16, __fmul_rn(x, r), 8.f * (float)p.W));
+    Y = __float2int_rn(__fmaf_rn(-f16, __fmul_rn(y, r), 8.f * (float)p.H));
+    d = __fmul_rn(p.near_plane, r);
 }
 
 // Box corner k: x = +-L/2 (bit 0), y = +-W/2 (bit 1), z = 0 or H (bit 2).
@@ -164,7 +188,7 @@ __device__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float
         r.A[k] = A;
         r.B[k] = B;
         r.C[k] = (int)C;
-        r.invA[k] = A != 0 ? 1.f / (float)A : 0.f;
+        r.invA[k] = A != 0 ? __fdividef(1.f, (float)A) : 0.f;
     }
     const float fx1 = (float)(vx[1] - vx[0]), fy1 = (float)(vy[1] - vy[0]);
     const float fx2 = (float)(vx[2] - vx[0]), fy2 = (float)(vy[2] - vy[0]);
@@ -363,7 +387,7 @@ __device__ __forceinline__ int block_exclusive_max(int v, int *s_warp) {
 }
 
 struct Shared {
-    int item, ntri, nclip, nvcl, nvbox;
+    int item, resv, next_unit, npend, nvcl, nvbox, cq_n;
     int warp[32];
 };
 
@@ -371,7 +395,7 @@ struct Shared {
 template <typename Key>
 __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *keys, TriRec *tris,
                       int *rowoff, unsigned short *map) {
-    const int n = min(sh.ntri, p.tri_cap);
+    const int n = min(sh.resv, p.tri_cap);
     const int tid = threadIdx.x, nt = blockDim.x;
     // row counts -> exclusive scan (each thread owns a contiguous slice of triangles)
     const int per = (n + nt - 1) / nt;
@@ -424,22 +448,12 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *key
             const int t = map[i];
             const TriRec &T = tris[t];
             const int row = (T.jspan & 0xFFFF) + (start + i - rowoff[t]);
-            raster_row<Key>(T, row, cm.by0, p.W, keys);
+            if (row >= cm.by0 && row <= cm.by1) raster_row<Key>(T, row, cm.by0, p.W, keys);
         }
         __syncthreads();
     }
-    if (tid == 0) sh.ntri = 0;
+    if (tid == 0) sh.resv = 0;
     __syncthreads();
-}
-
-// Append one kept triangle (any lane, not warp-aggregated): used by the clip path.
-__device__ void append_one(const RenderParams &p, Shared &sh, TriRec *tris, int view,
-                           const int X[3], const int Y[3], const float d[3], uint32_t prim,
-                           uint32_t sub, int i0, int i1, int j0, int j1) {
-    const int k = atomicAdd(&sh.ntri, 1);
-    if (k < p.tri_cap) build_rec(tris[k], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
-    else atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);
-    if (view == p.dump_view) dump_tri(p, X, Y, d, prim, sub);
 }
 
 // World-space vertices and primitive id of a source triangle.
@@ -475,23 +489,37 @@ __device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm,
     }
 }
 
-// Clip a source triangle against near + guard planes, fan-triangulate, keep front faces.
-__device__ void clip_emit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris, int view,
-                          uint32_t code) {
+// A batch slot that holds no triangle (zero rows).
+__device__ __forceinline__ void empty_rec(TriRec &r) { r.jspan = 1; }
+
+// Clip a source triangle against the near and guard planes it crosses (planes that no vertex
+// lies beyond cannot change it), fan-triangulate, and write the front-facing pieces that
+// cover a pixel centre of the band into slots[0..6); unused slots become empty.
+__device__ void clip_emit(const RenderParams &p, const Cam &cm, int view, uint32_t code,
+                          TriRec *slots) {
     float wx[3], wy[3], wz[3];
     uint32_t prim;
     source_tri(p, cm, code, wx, wy, wz, prim);
+    float vx[3], vy[3], vz[3];
+    int planes = 0;
+    for (int i = 0; i < 3; ++i) {
+        const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
+        vx[i] = v.x;
+        vy[i] = v.y;
+        vz[i] = v.z;
+        planes |= outcode(p, cm, v.x, v.y, v.z);
+    }
     // A convex polygon gains at most one vertex per plane (3 + 5 = 8); the arrays allow
     // twice that so rounding on near-degenerate input cannot write past them.
     float px[kPoly], py[kPoly], pz[kPoly], qx[kPoly], qy[kPoly], qz[kPoly];
     int n = 3;
     for (int i = 0; i < 3; ++i) {
-        const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
-        px[i] = v.x;
-        py[i] = v.y;
-        pz[i] = v.z;
+        px[i] = vx[i];
+        py[i] = vy[i];
+        pz[i] = vz[i];
     }
     for (int k = 0; k < 5 && n >= 3; ++k) {
+        if (!(planes & (1 << k))) continue;
         int m = 0;
         for (int i = 0; i < n; ++i) {
             const int j = (i + 1 == n) ? 0 : i + 1;
@@ -522,28 +550,44 @@ __device__ void clip_emit(const RenderParams &p, const Cam &cm, Shared &sh, TriR
             pz[i] = qz[i];
         }
     }
-    if (n < 3) return;
-    if (n > 8) atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);  // not reachable for exact input
-    int X[kPoly], Y[kPoly];
-    float d[kPoly];
-    for (int i = 0; i < n; ++i) {
-        project(p, px[i], py[i], pz[i], X[i], Y[i]);
-        d[i] = __fdiv_rn(p.near_plane, pz[i]);
+    int out = 0;
+    if (n >= 3) {
+        if (n > 8) atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);  // not reachable for exact input
+        int X[kPoly], Y[kPoly];
+        float d[kPoly];
+        for (int i = 0; i < n; ++i) project(p, px[i], py[i], pz[i], X[i], Y[i], d[i]);
+        for (int k = 1; k + 1 < n && out < 6; ++k) {
+            const int tX[3] = {X[0], X[k], X[k + 1]}, tY[3] = {Y[0], Y[k], Y[k + 1]};
+            const float td[3] = {d[0], d[k], d[k + 1]};
+            int i0, i1, j0, j1;
+            if (tri_bbox(p, cm, tX, tY, i0, i1, j0, j1)) {
+                build_rec(slots[out++], tX, tY, td, prim, p.key_f16, i0, i1, j0, j1);
+                if (view == p.dump_view) dump_tri(p, tX, tY, td, prim, (uint32_t)(k - 1));
+            }
+        }
     }
-    for (int k = 1; k + 1 < n; ++k) {
-        const int tX[3] = {X[0], X[k], X[k + 1]}, tY[3] = {Y[0], Y[k], Y[k + 1]};
-        const float td[3] = {d[0], d[k], d[k + 1]};
-        int i0, i1, j0, j1;
-        if (tri_bbox(p, cm, tX, tY, i0, i1, j0, j1))
-            append_one(p, sh, tris, view, tX, tY, td, prim, (uint32_t)(k - 1), i0, i1, j0, j1);
+    for (int k = out; k < 6; ++k) empty_rec(slots[k]);
+}
+
+// Reserve [base, base + n) of a counter if it stays within cap; returns base or -1.  The
+// counter only ever grows by successful reservations.
+__device__ __forceinline__ int cas_reserve(int *counter, int n, int cap) {
+    int cur = *(volatile int *)counter;
+    for (;;) {
+        if (cur + n > cap) return -1;
+        const int prev = atomicCAS(counter, cur, cur + n);
+        if (prev == cur) return cur;
+        cur = prev;
     }
 }
 
-// One setup unit: 32 source triangles, one per lane (warp-uniform call).
-__device__ void setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
+// One setup unit: 32 source triangles, one per lane (warp-uniform call).  Returns false if
+// the clip queue or the batch has no room; `clips_queued` tells the retry (after a flush)
+// whether this unit's clip jobs are already queued.
+__device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
                            uint32_t *clipq, const unsigned short *viscl,
                            const unsigned char *visbox, int view, int unit, int n_box_units,
-                           int nbox_items) {
+                           int nbox_items, bool clips_done, bool &clips_queued) {
     const int lane = threadIdx.x & 31;
     uint32_t code = 0;
     bool valid;
@@ -558,43 +602,59 @@ __device__ void setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
     }
     bool keep = false, clip = false;
     int X[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, i0 = 0, i1 = 0, j0 = 0, j1 = 0;
-    float z[3] = {1.f, 1.f, 1.f};
+    float vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f}, vz[3] = {1.f, 1.f, 1.f};
+    float d[3] = {0.f, 0.f, 0.f};
     uint32_t prim = 0;
     if (valid) {
         float wx[3], wy[3], wz[3];
         source_tri(p, cm, code, wx, wy, wz, prim);
-        int oand = 0x1F, oor = 0;
-        float vx[3], vy[3];
+        int oand = 0x1FF, oor = 0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
             vx[i] = v.x;
             vy[i] = v.y;
-            z[i] = v.z;
-            const int oc = outcode(p, v);
+            vz[i] = v.z;
+            const int oc = outcode(p, cm, v.x, v.y, v.z);
             oand &= oc;
             oor |= oc;
         }
         if (oand == 0) {
-            if (oor == 0) {
+            if ((oor & 0x1F) == 0) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i) project(p, vx[i], vy[i], z[i], X[i], Y[i]);
+                for (int i = 0; i < 3; ++i) project(p, vx[i], vy[i], vz[i], X[i], Y[i], d[i]);
                 keep = tri_bbox(p, cm, X, Y, i0, i1, j0, j1);
             } else {
                 clip = true;
             }
         }
     }
-    const int ci = warp_append(clip, &sh.nclip);
-    if (clip) clipq[ci] = code;
-    const int k = warp_append(keep, &sh.ntri);
+    const unsigned int km = __ballot_sync(0xffffffffu, keep);
+    const unsigned int cmask = __ballot_sync(0xffffffffu, clip);
+    const unsigned int lt = (1u << lane) - 1u;
+    // Triangles that need clipping go to the block's clip queue (clipped later by whole
+    // warps).  Reservations never exceed their capacity, so every reserved slot is written.
+    clips_queued = clips_done;
+    if (!clips_done && cmask) {
+        const int nc = __popc(cmask);
+        int qb = 0;
+        if (lane == 0) qb = cas_reserve(&sh.cq_n, nc, kClipQueue);
+        qb = __shfl_sync(0xffffffffu, qb, 0);
+        if (qb < 0) return false;
+        if (clip) clipq[qb + __popc(cmask & lt)] = code;
+    }
+    clips_queued = true;
+    if (!km) return true;
+    const int nk = __popc(km);
+    int base = 0;
+    if (lane == 0) base = cas_reserve(&sh.resv, nk, p.tri_cap);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base < 0) return false;
     if (keep) {
-        float d[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) d[i] = __fdiv_rn(p.near_plane, z[i]);
-        build_rec(tris[k], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
+        build_rec(tris[base + __popc(km & lt)], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
         if (view == p.dump_view) dump_tri(p, X, Y, d, prim, 0u);
     }
+    return true;
 }
 
 __device__ __forceinline__ uint8_t key_class(unsigned long long k, const Cam &cm) {
@@ -611,72 +671,70 @@ __device__ __forceinline__ uint8_t key_class(unsigned int k, const Cam &cm) {
 __device__ __forceinline__ uint32_t key_depth_bits(unsigned long long k) { return (uint32_t)(k >> 32); }
 __device__ __forceinline__ uint32_t key_depth_bits(unsigned int k) { return k >> 16; }
 
-// Encode the band's keys into the output tensors and clear them for the next item.
-template <typename Key>
-__device__ void encode_store(const RenderParams &p, const Cam &cm, Key *keys, int view) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+// Encode the band's keys into the output tensors and clear them for the next item.  Each
+// lane reads adjacent keys with one 16-byte shared load (conflict-free) and writes the
+// matching adjacent outputs, so a warp's stores cover contiguous, fully used sectors.
+__device__ void encode_store(const RenderParams &p, const Cam &cm, unsigned long long *keys,
+                             int view) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
-    const long long off = (long long)cm.by0 * p.W;
-    if (p.out_mode == GP_OUT_CLASS_U8) {
-        uint8_t *o = (uint8_t *)p.out + slot * plane + off;
-        for (int b = tid * 16; b < band_px; b += nt * 16) {
-            uint32_t w[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) v |= (uint32_t)key_class(keys[b + 4 * q + r], cm) << (8 * r);
-                w[q] = v;
-            }
-            __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
-        }
-    } else {
-        for (int c = 0; c < 4; ++c) {
-            uint16_t *o = (uint16_t *)p.out + (slot * 4 + c) * plane + off;
-            const uint32_t cold = p.onehot[c][0], hot = p.onehot[c][1];
-            for (int b = tid * 8; b < band_px; b += nt * 8) {
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t lo = key_class(keys[b + 2 * q], cm) == c ? hot : cold;
-                    const uint32_t hi = key_class(keys[b + 2 * q + 1], cm) == c ? hot : cold;
-                    w[q] = lo | (hi << 16);
-                }
-                __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
-            }
-        }
-    }
-    if (p.depth) {
-        if (sizeof(Key) == 8) {
-            float *o = (float *)p.depth + slot * plane + off;
-            for (int b = tid * 4; b < band_px; b += nt * 4) {
-                float v[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = __uint_as_float(key_depth_bits(keys[b + r]));
-                __stcs((float4 *)(o + b), make_float4(v[0], v[1], v[2], v[3]));
-            }
+    const long long row0 = (long long)cm.by0 * p.W;
+    for (int b = 2 * threadIdx.x; b < band_px; b += 2 * blockDim.x) {
+        const ulonglong2 k = *(const ulonglong2 *)(keys + b);
+        *(ulonglong2 *)(keys + b) = make_ulonglong2(0ull, 0ull);
+        const uint32_t c0 = key_class(k.x, cm), c1 = key_class(k.y, cm);
+        if (p.out_mode == GP_OUT_CLASS_U8) {
+            __stcs((unsigned short *)((uint8_t *)p.out + slot * plane + row0 + b),
+                   (unsigned short)(c0 | (c1 << 8)));
         } else {
-            uint16_t *o = (uint16_t *)p.depth + slot * plane + off;
-            for (int b = tid * 8; b < band_px; b += nt * 8) {
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    w[q] = key_depth_bits(keys[b + 2 * q]) | (key_depth_bits(keys[b + 2 * q + 1]) << 16);
-                __stcs((uint4 *)(o + b), make_uint4(w[0], w[1], w[2], w[3]));
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t v = (uint32_t)p.onehot[c][c0 == (uint32_t)c] |
+                                   ((uint32_t)p.onehot[c][c1 == (uint32_t)c] << 16);
+                __stcs((unsigned int *)((uint16_t *)p.out + (slot * 4 + c) * plane + row0 + b), v);
             }
         }
+        if (p.depth)
+            __stcs((float2 *)((float *)p.depth + slot * plane + row0 + b),
+                   make_float2(__uint_as_float(key_depth_bits(k.x)), __uint_as_float(key_depth_bits(k.y))));
     }
-    __syncthreads();
-    for (int b = tid; b < band_px; b += nt) keys[b] = 0;
+}
+
+__device__ void encode_store(const RenderParams &p, const Cam &cm, unsigned int *keys, int view) {
+    const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
+    const long long slot = p.view_mod ? (view % p.view_mod) : view;
+    const long long plane = (long long)p.H * p.W;
+    const long long row0 = (long long)cm.by0 * p.W;
+    for (int b = 4 * threadIdx.x; b < band_px; b += 4 * blockDim.x) {
+        const uint4 k = *(const uint4 *)(keys + b);
+        *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t c[4] = {key_class(k.x, cm), key_class(k.y, cm), key_class(k.z, cm),
+                               key_class(k.w, cm)};
+        if (p.out_mode == GP_OUT_CLASS_U8) {
+            __stcs((unsigned int *)((uint8_t *)p.out + slot * plane + row0 + b),
+                   c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24));
+        } else {
+            for (int ch = 0; ch < 4; ++ch) {
+                const uint32_t lo = (uint32_t)p.onehot[ch][c[0] == (uint32_t)ch] |
+                                    ((uint32_t)p.onehot[ch][c[1] == (uint32_t)ch] << 16);
+                const uint32_t hi = (uint32_t)p.onehot[ch][c[2] == (uint32_t)ch] |
+                                    ((uint32_t)p.onehot[ch][c[3] == (uint32_t)ch] << 16);
+                __stcs((uint2 *)((uint16_t *)p.out + (slot * 4 + ch) * plane + row0 + b),
+                       make_uint2(lo, hi));
+            }
+        }
+        if (p.depth)
+            __stcs((uint2 *)((uint16_t *)p.depth + slot * plane + row0 + b),
+                   make_uint2(key_depth_bits(k.x) | (key_depth_bits(k.y) << 16),
+                              key_depth_bits(k.z) | (key_depth_bits(k.w) << 16)));
+    }
 }
 
 template <typename Key>
-__global__ void __launch_bounds__(1024) render_kernel(RenderParams p) {
+__global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
-    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap);
     Key *keys = (Key *)(smem + L.keys);
     TriRec *tris = (TriRec *)(smem + L.tris);
@@ -694,10 +752,12 @@ __global__ void __launch_bounds__(1024) render_kernel(RenderParams p) {
             if (p.work_counter) it = atomicAdd(p.work_counter, 1);
             else it = iter == 0 ? (int)blockIdx.x : p.n_items;
             sh.item = it;
-            sh.ntri = 0;
-            sh.nclip = 0;
+            sh.resv = 0;
+            sh.next_unit = 0;
+            sh.npend = 0;
             sh.nvcl = 0;
             sh.nvbox = 0;
+            sh.cq_n = 0;
         }
         __syncthreads();
         const int item = sh.item;
@@ -718,6 +778,13 @@ __global__ void __launch_bounds__(1024) render_kernel(RenderParams p) {
         sincosf(pose.z + p.cam_yaw[cam], &cm.s, &cm.c);
         cm.by0 = band * p.band_rows;
         cm.by1 = min(cm.by0 + p.band_rows, p.H) - 1;
+        cm.gtx = __fmul_rn(p.guard, p.tx);
+        cm.gty = __fmul_rn(p.guard, p.ty);
+        // pixel centres of the band lie in x in [0.5, W - 0.5], y in [by0 + 0.5, by1 + 0.5];
+        // a 1/4 px margin covers snapping (at most 1/32 px) and rounding
+        cm.vl = (0.5f * (float)p.W - 0.25f) / p.f;
+        cm.vt = (0.5f * (float)p.H - (float)cm.by0 - 0.25f) / p.f;
+        cm.vb = (0.5f * (float)p.H - (float)cm.by1 - 0.75f) / p.f;
 
         // 1. cull clusters and boxes against the band frustum
         for (int base = 0; base < wi.n_cl; base += nt) {
@@ -748,37 +815,66 @@ __global__ void __launch_bounds__(1024) render_kernel(RenderParams p) {
         }
         __syncthreads();
 
-        // 2. setup rounds with raster flushes
+        // 2. setup: warps pull units until the units run out or the batch is full; then the
+        //    block rasterises the batch; repeat until every unit is placed.
         const int nbox_items = sh.nvbox * 12;
         const int n_box_units = (nbox_items + 31) / 32;
         const int n_units = n_box_units + sh.nvcl;
-        for (int r0 = 0; r0 < n_units; r0 += nw) {
-            const int u = r0 + warp;
-            if (u < n_units)
-                setup_unit(p, cm, sh, tris, clipq, viscl, visbox, view, u, n_box_units, nbox_items);
-            __syncthreads();
-            // clip queue: each entry may emit up to 6 triangles
+        int pend = -1;           // unit this warp could not place (warp-uniform)
+        bool pend_clips = false;  // its clip jobs are already queued
+        for (;;) {
             for (;;) {
-                const int nc = sh.nclip;
-                if (nc == 0) break;
-                const int room = (p.tri_cap - sh.ntri) / 6;
-                if (room <= 0) {
+                int u;
+                bool done_clips = false;
+                if (pend >= 0) {
+                    u = pend;
+                    done_clips = pend_clips;
+                    pend = -1;
+                } else {
+                    u = 0;
+                    if ((tid & 31) == 0) u = atomicAdd(&sh.next_unit, 1);
+                    u = __shfl_sync(0xffffffffu, u, 0);
+                }
+                if (u >= n_units) break;
+                bool queued = false;
+                if (!setup_unit(p, cm, sh, tris, clipq, viscl, visbox, view, u, n_box_units,
+                                nbox_items, done_clips, queued)) {
+                    pend = u;
+                    pend_clips = queued;
+                    if ((tid & 31) == 0) atomicAdd(&sh.npend, 1);
+                    break;
+                }
+            }
+            __syncthreads();
+            // clip the queued triangles, one job per thread, flushing when the batch is full
+            for (;;) {
+                const int nq = sh.cq_n, rv = sh.resv;
+                if (nq == 0) break;
+                const int room = (p.tri_cap - rv) / 6;
+                if (room == 0) {
                     flush<Key>(p, cm, sh, keys, tris, rowoff, map);
                     continue;
                 }
-                const int take = min(min(nc, room), nt);
+                const int take = min(min(nq, room), nt);
+                if (tid < take) clip_emit(p, cm, view, clipq[nq - take + tid], tris + rv + 6 * tid);
                 __syncthreads();
-                if (tid < take) clip_emit(p, cm, sh, tris, view, clipq[nc - take + tid]);
-                __syncthreads();
-                if (tid == 0) sh.nclip = nc - take;
+                if (tid == 0) {
+                    sh.cq_n = nq - take;
+                    sh.resv = rv + 6 * take;
+                }
                 __syncthreads();
             }
-            if (sh.ntri > p.tri_cap - nw * 32) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+            const bool more = sh.next_unit < n_units || sh.npend > 0;
+            const bool full = sh.resv > 0;
+            __syncthreads();
+            if (tid == 0) sh.npend = 0;
+            if (full) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+            else __syncthreads();
+            if (!more) break;
         }
-        if (sh.ntri > 0) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
 
         // 3. encode and store the band
-        encode_store<Key>(p, cm, keys, view);
+        encode_store(p, cm, keys, view);
         __syncthreads();
     }
 }

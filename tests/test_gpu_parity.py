@@ -108,7 +108,7 @@ def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
 # T2 / T3 / T4 rendering
 # ---------------------------------------------------------------------------------------
 
-SHAPES = [dict(), dict(band_rows=16), dict(band_rows=8, threads=128, tri_capacity=160),
+SHAPES = [dict(), dict(band_rows=16), dict(band_rows=8, threads=128, tri_capacity=224),
           dict(threads=1024, tri_capacity=1024), dict(band_rows=128, threads=256, tri_capacity=300)]
 
 
