@@ -11,7 +11,7 @@
 namespace gpk {
 
 constexpr int kMaxBoxes = GP_MAX_BOXES;
-constexpr int kClusterQuads = 16;  // quads per culling cluster = 32 triangles = one warp
+constexpr int kClusterQuads = 32;  // quads per culling cluster = one quad per lane of a warp
 constexpr int kMaxClustersPerWorld = 4096;
 
 // Per-world table (device).

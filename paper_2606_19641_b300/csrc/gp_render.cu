@@ -5,21 +5,22 @@
 //   1. cull: per-world clusters of ground quads and the world's boxes are tested as
 //      axis-aligned boxes against the band's frustum (left/right planes, near plane and the
 //      band's pixel-centre rows; conservative by 1/16 px for snapping);
-//   2. setup: warps pull units of 32 source triangles (a cluster's 16 quads, or 32 box
-//      face triangles) from a shared counter, with no block barrier between units.  Each
-//      lane transforms its triangle to view space and rejects it if all three vertices lie
+//   2. setup: warps pull units of 32 quads (a cluster of ground quads, or box faces) from
+//      a shared counter, with no block barrier between units.  Each lane transforms its
+//      quad's corners to view space and rejects a triangle if all three vertices lie
 //      beyond one plane through the eye (near, guard band, or the band's pixel-centre
 //      extent widened by 1/4 px); otherwise it projects, snaps to 1/16 px (round half to even),
 //      back-face culls and keeps the triangle if its snapped bounding box holds a pixel
 //      centre of the band.  A triangle crossing the near plane or the 4x guard band is
-//      clipped in its lane (Sutherland-Hodgman, planes in the order near, left, right,
-//      bottom, top) and fan-triangulated.  A warp reserves batch slots for its unit with one
+//      queued and later clipped by an 8-lane warp segment (Sutherland-Hodgman, planes in
+//      the order near, left, right, bottom, top) and fan-triangulated.  A warp reserves batch slots for its unit with one
 //      atomic; when the batch is full the block rasterises it and continues;
-//   3. raster: kept triangles are expanded into (triangle, row) items; each item computes
-//      the exact covered span of its row from the integer edge functions (top-left fill
-//      rule) and updates a depth key per pixel in shared memory with atomicMax.  The key
-//      is (depth bits << 32 | ~prim) with FP32 reversed-Z depth, or (binary16 depth << 16 |
-//      ~prim) in FP16 mode: the nearest surface wins, ties go to the smaller primitive id;
+//   3. raster: kept triangles are expanded into (triangle, row, 64-pixel window) items;
+//      each item computes the exact covered span of its row within the window from the
+//      integer edge functions (top-left fill rule) and resolves depth per pixel in shared
+//      memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or (binary16 depth
+//      << 16 | ~prim) in FP16 mode; the nearest surface wins, ties go to the smaller
+//      primitive id;
 //   4. encode: keys become class ids (uint8) + depth, or a normalised one-hot BF16 NCHW
 //      tensor; the band is one contiguous range of every output plane, written with 16-byte
 //      streaming stores.
@@ -35,20 +36,19 @@ namespace gpk {
 
 namespace {
 
-constexpr int kItemsPerThread = 8;  // row items per thread per raster sub-pass
-constexpr int kPoly = 16;           // clip polygon capacity (a triangle needs at most 8)
+constexpr int kItemsPerThread = 8;  // raster items per thread per raster sub-pass
+constexpr int kSpanWindow = 64;     // pixels per raster item (a row is split into windows)
 constexpr int kClipQueue = 256;     // queued clip jobs per block
 
 struct __align__(16) TriRec {
     int A[3], B[3], C[3];  // edge functions E_k = A_k gx + B_k gy + C_k, fill-rule bias folded in
-    float invA[3];         // 1 / A_k (estimate only), 0 if A_k == 0
     float d0, a, b;        // depth plane, per 1/16 px
-    int X0, Y0;            // vertex 0 (origin of gx, gy)
+    int xy0;               // vertex 0 (origin of gx, gy): X0 low 16 bits, Y0 high 16 bits
     uint32_t low;          // low half of the key: inverted primitive id
     int ispan;             // pixel-centre columns i0 | i1 << 16
     int jspan;             // pixel-centre rows    j0 | j1 << 16
 };
-static_assert(sizeof(TriRec) == 80, "TriRec layout");
+static_assert(sizeof(TriRec) == 64, "TriRec layout");
 
 struct Cam {
     float px, py, s, c;  // camera position and yaw sin/cos
@@ -60,7 +60,7 @@ struct Cam {
 };
 
 struct Smem {
-    size_t keys, tris, rowoff, map, viscl, visbox, clipq, total;
+    size_t keys, tris, rowoff, map, viscl, visbox, clipq, clipscratch, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -87,6 +87,8 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     o = align_up(o, 16);
     s.clipq = o;
     o += (size_t)kClipQueue * 4;
+    s.clipscratch = o;
+    o += (size_t)(threads / 32) * 4 * 24 * 4;  // per warp: 4 jobs x 8 vertices x 3 floats
     s.total = align_up(o, 16);
     return s;
 }
@@ -188,7 +190,6 @@ __device__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float
         r.A[k] = A;
         r.B[k] = B;
         r.C[k] = (int)C;
-        r.invA[k] = A != 0 ? __fdividef(1.f, (float)A) : 0.f;
     }
     const float fx1 = (float)(vx[1] - vx[0]), fy1 = (float)(vy[1] - vy[0]);
     const float fx2 = (float)(vx[2] - vx[0]), fy2 = (float)(vy[2] - vy[0]);
@@ -201,8 +202,8 @@ __device__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float
     r.a = __fdiv_rn(na, fa);
     r.b = __fdiv_rn(nb, fa);
     r.d0 = dv[0];
-    r.X0 = vx[0];
-    r.Y0 = vy[0];
+    // snapped coordinates stay within the 4x guard band: |X|, |Y| <= 40 * 512 < 2^15
+    r.xy0 = (vx[0] & 0xFFFF) | (vy[0] << 16);
     r.low = key_f16 ? (0xFFFFu - (prim & 0xFFFFu)) : (0xFFFFFFFFu - prim);
     r.ispan = (i0 & 0xFFFF) | (i1 << 16);
     r.jspan = (j0 & 0xFFFF) | (j1 << 16);
@@ -263,23 +264,30 @@ __device__ bool aabb_visible(const RenderParams &p, const Cam &cm, float cx, flo
     return fmaxf(jlo, (float)cm.by0) <= fminf(jhi, (float)cm.by1);
 }
 
-template <typename Key>
-__device__ __forceinline__ Key make_key(float d, uint32_t low);
-template <>
-__device__ __forceinline__ unsigned long long make_key<unsigned long long>(float d, uint32_t low) {
-    return ((unsigned long long)__float_as_uint(d) << 32) | low;
-}
-template <>
-__device__ __forceinline__ unsigned int make_key<unsigned int>(float d, uint32_t low) {
+// FP16 mode key: binary16 depth bits above the inverted primitive id.
+__device__ __forceinline__ unsigned int key16(float d, uint32_t low) {
     return ((unsigned int)__half_as_ushort(__float2half_rn(d)) << 16) | low;
 }
 
-// Rasterise one row of one triangle: exact covered span, then per-pixel depth keys.
-template <typename Key>
-__device__ __forceinline__ void raster_row(const TriRec &T, int row, int by0, int W, Key *keys) {
-    const int gy = 16 * row + 8 - T.Y0;
-    int lo = T.ispan & 0xFFFF, hi = T.ispan >> 16;
-    const float xo = (float)(T.X0 - 8);
+// Items of a triangle: rows x windows of kSpanWindow pixels of its bounding columns.
+__device__ __forceinline__ int tri_windows(const TriRec &T) {
+    return (((T.ispan >> 16) - (T.ispan & 0xFFFF)) / kSpanWindow) + 1;
+}
+__device__ __forceinline__ int tri_items(const TriRec &T) {
+    return ((T.jspan >> 16) - (T.jspan & 0xFFFF) + 1) * tri_windows(T);
+}
+
+// Rasterise one row of one triangle within columns [lo, hi]: exact covered span, then
+// per-pixel depth resolution.  The result per pixel is the maximum over fragments of
+// (depth, inverted primitive id), i.e. the nearest surface with ties to the smaller id:
+// FP32 mode keeps one 64-bit key per pixel (FP32 depth bits << 32 | inverted id), FP16
+// mode one 32-bit key (binary16 depth bits << 16 | inverted id).
+template <bool F32>
+__device__ __forceinline__ void raster_row(const TriRec &T, int row, int lo, int hi, int by0,
+                                           int W, void *keys) {
+    const int X0 = (int)(short)(T.xy0 & 0xFFFF), Y0 = T.xy0 >> 16;
+    const int gy = 16 * row + 8 - Y0;
+    const float xo = (float)(X0 - 8);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int A = T.A[k];
@@ -291,34 +299,41 @@ __device__ __forceinline__ void raster_row(const TriRec &T, int row, int by0, in
         // E(i) = A (16 i + 8 - X0) + R ; the edge crosses at i* = (X0 - 8 - R / A) / 16.
         // The float estimate is within one pixel wherever it matters; one exact integer
         // check on each side fixes it.
-        const float q = (xo - (float)R * T.invA[k]) * 0.0625f;
+        const float q = (xo - __fdividef((float)R, (float)A)) * 0.0625f;
         if (A > 0) {  // lower bound: smallest i with E(i) >= 0
             int i = __float2int_ru(fminf(fmaxf(q, -1e6f), 1e6f));
             i = min(max(i, lo), hi + 1);
-            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - T.X0, (unsigned int)R) >= 0)
+            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - X0, (unsigned int)R) >= 0)
                 --i;
-            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - T.X0, (unsigned int)R) < 0)
+            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - X0, (unsigned int)R) < 0)
                 ++i;
             lo = i;
         } else {  // upper bound: largest i with E(i) >= 0
             int i = __float2int_rd(fminf(fmaxf(q, -1e6f), 1e6f));
             i = min(max(i, lo - 1), hi);
-            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - T.X0, (unsigned int)R) >= 0)
+            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - X0, (unsigned int)R) >= 0)
                 ++i;
-            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - T.X0, (unsigned int)R) < 0)
+            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - X0, (unsigned int)R) < 0)
                 --i;
             hi = i;
         }
     }
     if (lo > hi) return;
     const float inner = __fmaf_rn(T.b, (float)gy, T.d0);
-    float fgx = (float)(16 * lo + 8 - T.X0);
-    Key *rowp = keys + (row - by0) * W;
+    float fgx = (float)(16 * lo + 8 - X0);
+    const int o = (row - by0) * W;
     for (int i = lo; i <= hi; ++i, fgx += 16.f) {
         float d = __fmaf_rn(T.a, fgx, inner);
         d = d > 0.f ? d : 0.f;
-        const Key key = make_key<Key>(d, T.low);
-        if (key > rowp[i]) atomicMax(rowp + i, key);
+        if (F32) {
+            unsigned long long *rk = (unsigned long long *)keys + o;
+            const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | T.low;
+            if (key > rk[i]) atomicMax(rk + i, key);
+        } else {
+            unsigned int *rk = (unsigned int *)keys + o;
+            const unsigned int key = key16(d, T.low);
+            if (key > rk[i]) atomicMax(rk + i, key);
+        }
     }
 }
 
@@ -392,8 +407,8 @@ struct Shared {
 };
 
 // Rasterise the current batch of triangles into the band's key buffer.
-template <typename Key>
-__device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *keys, TriRec *tris,
+template <bool F32>
+__device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *keys, TriRec *tris,
                       int *rowoff, unsigned short *map) {
     const int n = min(sh.resv, p.tri_cap);
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -401,16 +416,12 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *key
     const int per = (n + nt - 1) / nt;
     const int t0 = min(tid * per, n), t1 = min(t0 + per, n);
     int local = 0;
-    for (int t = t0; t < t1; ++t) {
-        const int js = tris[t].jspan;
-        local += (js >> 16) - (js & 0xFFFF) + 1;
-    }
+    for (int t = t0; t < t1; ++t) local += tri_items(tris[t]);
     int total = 0;
     int run = block_exclusive_scan(local, sh.warp, total);
     for (int t = t0; t < t1; ++t) {
         rowoff[t] = run;
-        const int js = tris[t].jspan;
-        run += (js >> 16) - (js & 0xFFFF) + 1;
+        run += tri_items(tris[t]);
     }
     if (tid == 0) rowoff[n] = total;
     __syncthreads();
@@ -447,8 +458,13 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, Key *key
         for (int i = tid; i < len; i += nt) {
             const int t = map[i];
             const TriRec &T = tris[t];
-            const int row = (T.jspan & 0xFFFF) + (start + i - rowoff[t]);
-            if (row >= cm.by0 && row <= cm.by1) raster_row<Key>(T, row, cm.by0, p.W, keys);
+            const int nwin = tri_windows(T), k = start + i - rowoff[t];
+            const int r = k / nwin, wdx = k - r * nwin;
+            const int row = (T.jspan & 0xFFFF) + r;
+            const int lo = (T.ispan & 0xFFFF) + wdx * kSpanWindow;
+            const int hi = min(lo + kSpanWindow - 1, T.ispan >> 16);
+            if (row >= cm.by0 && row <= cm.by1 && lo >= 0 && hi < p.W)
+                raster_row<F32>(T, row, lo, hi, cm.by0, p.W, keys);
         }
         __syncthreads();
     }
@@ -490,83 +506,114 @@ __device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm,
 }
 
 // A batch slot that holds no triangle (zero rows).
-__device__ __forceinline__ void empty_rec(TriRec &r) { r.jspan = 1; }
+__device__ __forceinline__ void empty_rec(TriRec &r) {
+    r.ispan = 0;
+    r.jspan = 1;
+}
 
-// Clip a source triangle against the near and guard planes it crosses (planes that no vertex
-// lies beyond cannot change it), fan-triangulate, and write the front-facing pieces that
-// cover a pixel centre of the band into slots[0..6); unused slots become empty.
-__device__ void clip_emit(const RenderParams &p, const Cam &cm, int view, uint32_t code,
-                          TriRec *slots) {
-    float wx[3], wy[3], wz[3];
-    uint32_t prim;
-    source_tri(p, cm, code, wx, wy, wz, prim);
-    float vx[3], vy[3], vz[3];
-    int planes = 0;
-    for (int i = 0; i < 3; ++i) {
-        const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
-        vx[i] = v.x;
-        vy[i] = v.y;
-        vz[i] = v.z;
-        planes |= outcode(p, cm, v.x, v.y, v.z);
-    }
-    // A convex polygon gains at most one vertex per plane (3 + 5 = 8); the arrays allow
-    // twice that so rounding on near-degenerate input cannot write past them.
-    float px[kPoly], py[kPoly], pz[kPoly], qx[kPoly], qy[kPoly], qz[kPoly];
-    int n = 3;
-    for (int i = 0; i < 3; ++i) {
-        px[i] = vx[i];
-        py[i] = vy[i];
-        pz[i] = vz[i];
-    }
-    for (int k = 0; k < 5 && n >= 3; ++k) {
-        if (!(planes & (1 << k))) continue;
-        int m = 0;
-        for (int i = 0; i < n; ++i) {
-            const int j = (i + 1 == n) ? 0 : i + 1;
-            const float da = plane_dist(p, k, px[i], py[i], pz[i]);
-            const float db = plane_dist(p, k, px[j], py[j], pz[j]);
-            const bool ia = da >= 0.f, ib = db >= 0.f;
-            if (ia && m < kPoly) {
-                qx[m] = px[i];
-                qy[m] = py[i];
-                qz[m] = pz[i];
-                ++m;
+// Clip queued triangles cooperatively: an 8-lane segment per job (4 jobs per warp), one
+// polygon vertex per lane.  For every plane the triangle crosses (near, then guard left,
+// right, bottom, top; planes no vertex lies beyond cannot change it), each lane emits its
+// vertex if inside and the crossing point of its edge to the next vertex if the edge
+// crosses (interpolated from the inside vertex), in edge order -- Sutherland-Hodgman --
+// and the segment compacts the outputs through shared scratch.  The polygon is then
+// fan-triangulated from its first vertex, one fan triangle per lane, into slots[6 j ..).
+// Called by all threads of the block for jobs [0, njobs) of `jobs`.
+__device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const uint32_t *jobs,
+                          int njobs, TriRec *slots, float *scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 3, gl = lane & 7, seg0 = lane & ~7;
+    const unsigned int segmask = 0xFFu << seg0, lt = (1u << lane) - 1u;
+    float *sc = scratch + (warp * 4 + g) * 24;  // 8 vertices x (x, y, z) per segment
+    for (int jb = warp * 4; jb < njobs; jb += nw * 4) {
+        const int job = jb + g;
+        const bool active = job < njobs;
+        float x = 0.f, y = 0.f, z = 1.f;
+        uint32_t prim = 0;
+        int n = 0, oc = 0;
+        if (active) {
+            float wx[3], wy[3], wz[3];
+            source_tri(p, cm, jobs[job], wx, wy, wz, prim);
+            n = 3;
+            if (gl < 3) {
+                const float3 v = to_view(p, cm, wx[gl], wy[gl], wz[gl]);
+                x = v.x;
+                y = v.y;
+                z = v.z;
+                oc = outcode(p, cm, x, y, z);
             }
-            if (ia != ib && m < kPoly) {
-                // interpolate from the inside vertex towards the outside one
-                const int vi = ia ? i : j, vo = ia ? j : i;
-                const float di = ia ? da : db, dov = ia ? db : da;
+        }
+        oc |= __shfl_xor_sync(0xffffffffu, oc, 1);
+        oc |= __shfl_xor_sync(0xffffffffu, oc, 2);
+        oc |= __shfl_xor_sync(0xffffffffu, oc, 4);
+        const int planes = oc & 0x1F;
+#pragma unroll 1
+        for (int k = 0; k < 5; ++k) {
+            const bool do_k = active && n >= 3 && (planes & (1 << k));  // segment-uniform
+            const float dk = plane_dist(p, k, x, y, z);
+            const int nxt = seg0 + ((gl + 1 < n) ? gl + 1 : 0);
+            const float xn = __shfl_sync(0xffffffffu, x, nxt);
+            const float yn = __shfl_sync(0xffffffffu, y, nxt);
+            const float zn = __shfl_sync(0xffffffffu, z, nxt);
+            const float dn = __shfl_sync(0xffffffffu, dk, nxt);
+            const bool in_i = dk >= 0.f, in_n = dn >= 0.f;
+            const bool ev = do_k && gl < n && in_i;
+            const bool ex = do_k && gl < n && in_i != in_n;
+            const unsigned int bv = __ballot_sync(0xffffffffu, ev);
+            const unsigned int bx = __ballot_sync(0xffffffffu, ex);
+            const int pos = __popc(bv & segmask & lt) + __popc(bx & segmask & lt);
+            int nn = __popc(bv & segmask) + __popc(bx & segmask);
+            if (ev && pos < 8) {
+                sc[3 * pos] = x;
+                sc[3 * pos + 1] = y;
+                sc[3 * pos + 2] = z;
+            }
+            if (ex && pos + (ev ? 1 : 0) < 8) {
+                const float xi = in_i ? x : xn, yi = in_i ? y : yn, zi = in_i ? z : zn;
+                const float xo = in_i ? xn : x, yo = in_i ? yn : y, zo = in_i ? zn : z;
+                const float di = in_i ? dk : dn, dov = in_i ? dn : dk;
                 const float t = __fdiv_rn(di, __fsub_rn(di, dov));
-                qx[m] = __fmaf_rn(t, __fsub_rn(px[vo], px[vi]), px[vi]);
-                qy[m] = __fmaf_rn(t, __fsub_rn(py[vo], py[vi]), py[vi]);
-                qz[m] = __fmaf_rn(t, __fsub_rn(pz[vo], pz[vi]), pz[vi]);
-                ++m;
+                const int q = pos + (ev ? 1 : 0);
+                sc[3 * q] = __fmaf_rn(t, __fsub_rn(xo, xi), xi);
+                sc[3 * q + 1] = __fmaf_rn(t, __fsub_rn(yo, yi), yi);
+                sc[3 * q + 2] = __fmaf_rn(t, __fsub_rn(zo, zi), zi);
             }
+            __syncwarp();
+            if (do_k) {
+                if (nn > 8) {  // not reachable for exact input: a plane adds at most one vertex
+                    if (gl == 0) atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);
+                    nn = 8;
+                }
+                if (gl < nn) {
+                    x = sc[3 * gl];
+                    y = sc[3 * gl + 1];
+                    z = sc[3 * gl + 2];
+                }
+                n = nn;
+            }
+            __syncwarp();
         }
-        n = m;
-        for (int i = 0; i < n; ++i) {
-            px[i] = qx[i];
-            py[i] = qy[i];
-            pz[i] = qz[i];
-        }
-    }
-    int out = 0;
-    if (n >= 3) {
-        if (n > 8) atomicOr(p.status, GP_DEV_CLIP_OVERFLOW);  // not reachable for exact input
-        int X[kPoly], Y[kPoly];
-        float d[kPoly];
-        for (int i = 0; i < n; ++i) project(p, px[i], py[i], pz[i], X[i], Y[i], d[i]);
-        for (int k = 1; k + 1 < n && out < 6; ++k) {
-            const int tX[3] = {X[0], X[k], X[k + 1]}, tY[3] = {Y[0], Y[k], Y[k + 1]};
-            const float td[3] = {d[0], d[k], d[k + 1]};
+        int X = 0, Y = 0;
+        float d = 0.f;
+        if (active && n >= 3 && gl < n) project(p, x, y, z, X, Y, d);
+        const int s1 = seg0 + min(gl + 1, 7), s2 = seg0 + min(gl + 2, 7);
+        const int tX[3] = {__shfl_sync(0xffffffffu, X, seg0), __shfl_sync(0xffffffffu, X, s1),
+                           __shfl_sync(0xffffffffu, X, s2)};
+        const int tY[3] = {__shfl_sync(0xffffffffu, Y, seg0), __shfl_sync(0xffffffffu, Y, s1),
+                           __shfl_sync(0xffffffffu, Y, s2)};
+        const float td[3] = {__shfl_sync(0xffffffffu, d, seg0), __shfl_sync(0xffffffffu, d, s1),
+                             __shfl_sync(0xffffffffu, d, s2)};
+        if (active && gl < 6) {
+            TriRec &r = slots[6 * job + gl];
             int i0, i1, j0, j1;
-            if (tri_bbox(p, cm, tX, tY, i0, i1, j0, j1)) {
-                build_rec(slots[out++], tX, tY, td, prim, p.key_f16, i0, i1, j0, j1);
-                if (view == p.dump_view) dump_tri(p, tX, tY, td, prim, (uint32_t)(k - 1));
+            if (n >= 3 && gl + 2 < n && tri_bbox(p, cm, tX, tY, i0, i1, j0, j1)) {
+                build_rec(r, tX, tY, td, prim, p.key_f16, i0, i1, j0, j1);
+                if (view == p.dump_view) dump_tri(p, tX, tY, td, prim, (uint32_t)gl);
+            } else {
+                empty_rec(r);
             }
         }
     }
-    for (int k = out; k < 6; ++k) empty_rec(slots[k]);
 }
 
 // Reserve [base, base + n) of a counter if it stays within cap; returns base or -1.  The
@@ -581,126 +628,198 @@ __device__ __forceinline__ int cas_reserve(int *counter, int n, int cap) {
     }
 }
 
-// One setup unit: 32 source triangles, one per lane (warp-uniform call).  Returns false if
-// the clip queue or the batch has no room; `clips_queued` tells the retry (after a flush)
-// whether this unit's clip jobs are already queued.
+// World-space corners of a source quad and the primitive id of its first triangle.
+//   code bit 31 set: box face, bits 4..11 local box index, bits 0..3 face index
+//   otherwise: ground quad index (cluster order)
+// The quad's triangles are (q0 q1 q2) and (q0 q2 q3), primitive ids prim0 and prim0 + 1.
+__device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm, uint32_t code,
+                                            float qx[4], float qy[4], float qz[4],
+                                            uint32_t &prim0) {
+    if (code & 0x80000000u) {
+        const int b = (code >> 4) & 0xFF, face = code & 15;
+        const float4 pose = p.box_pose[cm.box_begin + b];
+        const float4 dim = p.box_dim[cm.box_begin + b];
+        float s, c;
+        sincosf(pose.z, &s, &c);
+        int k0, k1, k2, k3;
+        box_tri(2 * face, k0, k1, k2);      // (q0 q1 q2)
+        box_tri(2 * face + 1, k0, k2, k3);  // (q0 q2 q3)
+        box_corner(pose, dim, s, c, k0, qx[0], qy[0], qz[0]);
+        box_corner(pose, dim, s, c, k1, qx[1], qy[1], qz[1]);
+        box_corner(pose, dim, s, c, k2, qx[2], qy[2], qz[2]);
+        box_corner(pose, dim, s, c, k3, qx[3], qy[3], qz[3]);
+        prim0 = 12u * b + 2u * face;
+    } else {
+        const float4 g0 = p.quad_geo[2 * code], g1 = p.quad_geo[2 * code + 1];
+        prim0 = p.quad_prim[code];
+        const float z = prim0 < cm.road_end ? 0.f : p.line_z;
+        qx[0] = g0.x;
+        qy[0] = g0.y;
+        qx[1] = g0.z;
+        qy[1] = g0.w;
+        qx[2] = g1.x;
+        qy[2] = g1.y;
+        qx[3] = g1.z;
+        qy[3] = g1.w;
+        qz[0] = qz[1] = qz[2] = qz[3] = z;
+    }
+}
+
+// One setup unit: 32 quads (box faces or ground quads), one per lane, two triangles each
+// (warp-uniform call).  Returns false if the clip queue or the batch has no room;
+// `clips_queued` tells the retry (after a flush) whether this unit's clip jobs are already
+// queued.
 __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
                            uint32_t *clipq, const unsigned short *viscl,
                            const unsigned char *visbox, int view, int unit, int n_box_units,
                            int nbox_items, bool clips_done, bool &clips_queued) {
     const int lane = threadIdx.x & 31;
-    uint32_t code = 0;
+    uint32_t qcode = 0, tcode = 0;  // quad code; triangle-code base for the clip queue
     bool valid;
     if (unit < n_box_units) {
         const int item = unit * 32 + lane;
         valid = item < nbox_items;
-        if (valid) code = 0x80000000u | ((uint32_t)visbox[item / 12] << 4) | (uint32_t)(item % 12);
+        if (valid) {
+            const uint32_t b = visbox[item / 6], face = item % 6;
+            qcode = 0x80000000u | (b << 4) | face;
+            tcode = 0x80000000u | (b << 4) | (2u * face);
+        }
     } else {
         const Cluster cl = p.clusters[cm.cl_begin + viscl[unit - n_box_units]];
-        valid = (lane >> 1) < cl.nq;
-        code = (uint32_t)(cl.q0 + (lane >> 1)) << 1 | (uint32_t)(lane & 1);
+        valid = lane < cl.nq;
+        qcode = (uint32_t)(cl.q0 + lane);
+        tcode = qcode << 1;
     }
-    bool keep = false, clip = false;
-    int X[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, i0 = 0, i1 = 0, j0 = 0, j1 = 0;
-    float vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f}, vz[3] = {1.f, 1.f, 1.f};
-    float d[3] = {0.f, 0.f, 0.f};
-    uint32_t prim = 0;
+    bool keep0 = false, keep1 = false, clip0 = false, clip1 = false;
+    int X[4] = {0, 0, 0, 0}, Y[4] = {0, 0, 0, 0};
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    int b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};  // bounding rows/columns per triangle
+    uint32_t prim0 = 0;
     if (valid) {
-        float wx[3], wy[3], wz[3];
-        source_tri(p, cm, code, wx, wy, wz, prim);
-        int oand = 0x1FF, oor = 0;
+        float wx[4], wy[4], wz[4];
+        source_quad(p, cm, qcode, wx, wy, wz, prim0);
+        float vx[4], vy[4], vz[4];
+        int oc[4];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 4; ++i) {
             const float3 v = to_view(p, cm, wx[i], wy[i], wz[i]);
             vx[i] = v.x;
             vy[i] = v.y;
             vz[i] = v.z;
-            const int oc = outcode(p, cm, v.x, v.y, v.z);
-            oand &= oc;
-            oor |= oc;
+            oc[i] = outcode(p, cm, v.x, v.y, v.z);
         }
-        if (oand == 0) {
-            if ((oor & 0x1F) == 0) {
+        const int and0 = oc[0] & oc[1] & oc[2], or0 = oc[0] | oc[1] | oc[2];
+        const int and1 = oc[0] & oc[2] & oc[3], or1 = oc[0] | oc[2] | oc[3];
+        const bool fast0 = and0 == 0 && (or0 & 0x1F) == 0;
+        const bool fast1 = and1 == 0 && (or1 & 0x1F) == 0;
+        clip0 = and0 == 0 && !fast0;
+        clip1 = and1 == 0 && !fast1;
+        if (fast0 || fast1) {
 #pragma unroll
-                for (int i = 0; i < 3; ++i) project(p, vx[i], vy[i], vz[i], X[i], Y[i], d[i]);
-                keep = tri_bbox(p, cm, X, Y, i0, i1, j0, j1);
-            } else {
-                clip = true;
+            for (int i = 0; i < 4; ++i)
+                if ((oc[i] & 0x1F) == 0) project(p, vx[i], vy[i], vz[i], X[i], Y[i], d[i]);
+            if (fast0) {
+                const int tX[3] = {X[0], X[1], X[2]}, tY[3] = {Y[0], Y[1], Y[2]};
+                keep0 = tri_bbox(p, cm, tX, tY, b0[0], b0[1], b0[2], b0[3]);
+            }
+            if (fast1) {
+                const int tX[3] = {X[0], X[2], X[3]}, tY[3] = {Y[0], Y[2], Y[3]};
+                keep1 = tri_bbox(p, cm, tX, tY, b1[0], b1[1], b1[2], b1[3]);
             }
         }
     }
-    const unsigned int km = __ballot_sync(0xffffffffu, keep);
-    const unsigned int cmask = __ballot_sync(0xffffffffu, clip);
+    const unsigned int k0 = __ballot_sync(0xffffffffu, keep0);
+    const unsigned int k1 = __ballot_sync(0xffffffffu, keep1);
+    const unsigned int c0 = __ballot_sync(0xffffffffu, clip0);
+    const unsigned int c1 = __ballot_sync(0xffffffffu, clip1);
     const unsigned int lt = (1u << lane) - 1u;
     // Triangles that need clipping go to the block's clip queue (clipped later by whole
     // warps).  Reservations never exceed their capacity, so every reserved slot is written.
     clips_queued = clips_done;
-    if (!clips_done && cmask) {
-        const int nc = __popc(cmask);
+    if (!clips_done && (c0 | c1)) {
+        const int n0 = __popc(c0), nc = n0 + __popc(c1);
         int qb = 0;
         if (lane == 0) qb = cas_reserve(&sh.cq_n, nc, kClipQueue);
         qb = __shfl_sync(0xffffffffu, qb, 0);
         if (qb < 0) return false;
-        if (clip) clipq[qb + __popc(cmask & lt)] = code;
+        if (clip0) clipq[qb + __popc(c0 & lt)] = tcode;
+        if (clip1) clipq[qb + n0 + __popc(c1 & lt)] = tcode + 1u;
     }
     clips_queued = true;
-    if (!km) return true;
-    const int nk = __popc(km);
+    if (!(k0 | k1)) return true;
+    const int nk0 = __popc(k0), nk = nk0 + __popc(k1);
     int base = 0;
     if (lane == 0) base = cas_reserve(&sh.resv, nk, p.tri_cap);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base < 0) return false;
-    if (keep) {
-        build_rec(tris[base + __popc(km & lt)], X, Y, d, prim, p.key_f16, i0, i1, j0, j1);
-        if (view == p.dump_view) dump_tri(p, X, Y, d, prim, 0u);
+    if (keep0) {
+        const int tX[3] = {X[0], X[1], X[2]}, tY[3] = {Y[0], Y[1], Y[2]};
+        const float td[3] = {d[0], d[1], d[2]};
+        build_rec(tris[base + __popc(k0 & lt)], tX, tY, td, prim0, p.key_f16, b0[0], b0[1], b0[2], b0[3]);
+        if (view == p.dump_view) dump_tri(p, tX, tY, td, prim0, 0u);
+    }
+    if (keep1) {
+        const int tX[3] = {X[0], X[2], X[3]}, tY[3] = {Y[0], Y[2], Y[3]};
+        const float td[3] = {d[0], d[2], d[3]};
+        build_rec(tris[base + nk0 + __popc(k1 & lt)], tX, tY, td, prim0 + 1u, p.key_f16, b1[0], b1[1], b1[2], b1[3]);
+        if (view == p.dump_view) dump_tri(p, tX, tY, td, prim0 + 1u, 0u);
     }
     return true;
 }
 
-__device__ __forceinline__ uint8_t key_class(unsigned long long k, const Cam &cm) {
-    if (!k) return 0;
-    const uint32_t prim = 0xFFFFFFFFu - (uint32_t)k;
-    return prim < cm.box_end ? 3 : (prim < cm.road_end ? 1 : 2);
-}
-__device__ __forceinline__ uint8_t key_class(unsigned int k, const Cam &cm) {
-    if (!k) return 0;
-    const uint32_t prim = 0xFFFFu - (k & 0xFFFFu);
-    return prim < cm.box_end ? 3 : (prim < cm.road_end ? 1 : 2);
+// Class of an inverted primitive id (0 = nothing covered): 3 box, 1 road, 2 lane line.
+__device__ __forceinline__ uint32_t class_of_low(uint32_t low, uint32_t full, const Cam &cm) {
+    if (!low) return 0;
+    const uint32_t prim = full - low;
+    return prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : 2u);
 }
 
-__device__ __forceinline__ uint32_t key_depth_bits(unsigned long long k) { return (uint32_t)(k >> 32); }
-__device__ __forceinline__ uint32_t key_depth_bits(unsigned int k) { return k >> 16; }
+// Store one group of four adjacent pixels' classes (and one-hot channels).
+__device__ __forceinline__ void store_classes(const RenderParams &p, long long slot,
+                                              long long plane, long long px, const uint32_t c[4]) {
+    if (p.out_mode == GP_OUT_CLASS_U8) {
+        __stcs((unsigned int *)((uint8_t *)p.out + slot * plane + px),
+               c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24));
+    } else {
+        for (int ch = 0; ch < 4; ++ch) {
+            const uint32_t lo = (uint32_t)p.onehot[ch][c[0] == (uint32_t)ch] |
+                                ((uint32_t)p.onehot[ch][c[1] == (uint32_t)ch] << 16);
+            const uint32_t hi = (uint32_t)p.onehot[ch][c[2] == (uint32_t)ch] |
+                                ((uint32_t)p.onehot[ch][c[3] == (uint32_t)ch] << 16);
+            __stcs((uint2 *)((uint16_t *)p.out + (slot * 4 + ch) * plane + px), make_uint2(lo, hi));
+        }
+    }
+}
 
-// Encode the band's keys into the output tensors and clear them for the next item.  Each
-// lane reads adjacent keys with one 16-byte shared load (conflict-free) and writes the
-// matching adjacent outputs, so a warp's stores cover contiguous, fully used sectors.
-__device__ void encode_store(const RenderParams &p, const Cam &cm, unsigned long long *keys,
-                             int view) {
+// Encode the band into the output tensors and clear the planes for the next item.  Each
+// lane reads four adjacent words of a plane with one 16-byte shared load (conflict-free)
+// and writes the matching adjacent outputs, so a warp's stores cover contiguous sectors.
+// FP32 mode: one 64-bit key per pixel, FP32 depth bits above the inverted primitive id.
+__device__ void encode_f32(const RenderParams &p, const Cam &cm, unsigned long long *keys,
+                           int view) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
     const long long row0 = (long long)cm.by0 * p.W;
-    for (int b = 2 * threadIdx.x; b < band_px; b += 2 * blockDim.x) {
-        const ulonglong2 k = *(const ulonglong2 *)(keys + b);
+    for (int b = 4 * threadIdx.x; b < band_px; b += 4 * blockDim.x) {
+        const ulonglong2 k01 = *(const ulonglong2 *)(keys + b);
+        const ulonglong2 k23 = *(const ulonglong2 *)(keys + b + 2);
         *(ulonglong2 *)(keys + b) = make_ulonglong2(0ull, 0ull);
-        const uint32_t c0 = key_class(k.x, cm), c1 = key_class(k.y, cm);
-        if (p.out_mode == GP_OUT_CLASS_U8) {
-            __stcs((unsigned short *)((uint8_t *)p.out + slot * plane + row0 + b),
-                   (unsigned short)(c0 | (c1 << 8)));
-        } else {
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t v = (uint32_t)p.onehot[c][c0 == (uint32_t)c] |
-                                   ((uint32_t)p.onehot[c][c1 == (uint32_t)c] << 16);
-                __stcs((unsigned int *)((uint16_t *)p.out + (slot * 4 + c) * plane + row0 + b), v);
-            }
-        }
+        *(ulonglong2 *)(keys + b + 2) = make_ulonglong2(0ull, 0ull);
+        const uint32_t c[4] = {class_of_low((uint32_t)k01.x, 0xFFFFFFFFu, cm),
+                               class_of_low((uint32_t)k01.y, 0xFFFFFFFFu, cm),
+                               class_of_low((uint32_t)k23.x, 0xFFFFFFFFu, cm),
+                               class_of_low((uint32_t)k23.y, 0xFFFFFFFFu, cm)};
+        store_classes(p, slot, plane, row0 + b, c);
         if (p.depth)
-            __stcs((float2 *)((float *)p.depth + slot * plane + row0 + b),
-                   make_float2(__uint_as_float(key_depth_bits(k.x)), __uint_as_float(key_depth_bits(k.y))));
+            __stcs((uint4 *)((float *)p.depth + slot * plane + row0 + b),
+                   make_uint4((uint32_t)(k01.x >> 32), (uint32_t)(k01.y >> 32),
+                              (uint32_t)(k23.x >> 32), (uint32_t)(k23.y >> 32)));
     }
 }
 
-__device__ void encode_store(const RenderParams &p, const Cam &cm, unsigned int *keys, int view) {
+// FP16 mode: one key per pixel, binary16 depth bits above the inverted primitive id.
+__device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *keys, int view) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
@@ -708,43 +827,31 @@ __device__ void encode_store(const RenderParams &p, const Cam &cm, unsigned int 
     for (int b = 4 * threadIdx.x; b < band_px; b += 4 * blockDim.x) {
         const uint4 k = *(const uint4 *)(keys + b);
         *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t c[4] = {key_class(k.x, cm), key_class(k.y, cm), key_class(k.z, cm),
-                               key_class(k.w, cm)};
-        if (p.out_mode == GP_OUT_CLASS_U8) {
-            __stcs((unsigned int *)((uint8_t *)p.out + slot * plane + row0 + b),
-                   c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24));
-        } else {
-            for (int ch = 0; ch < 4; ++ch) {
-                const uint32_t lo = (uint32_t)p.onehot[ch][c[0] == (uint32_t)ch] |
-                                    ((uint32_t)p.onehot[ch][c[1] == (uint32_t)ch] << 16);
-                const uint32_t hi = (uint32_t)p.onehot[ch][c[2] == (uint32_t)ch] |
-                                    ((uint32_t)p.onehot[ch][c[3] == (uint32_t)ch] << 16);
-                __stcs((uint2 *)((uint16_t *)p.out + (slot * 4 + ch) * plane + row0 + b),
-                       make_uint2(lo, hi));
-            }
-        }
+        const uint32_t c[4] = {class_of_low(k.x & 0xFFFFu, 0xFFFFu, cm), class_of_low(k.y & 0xFFFFu, 0xFFFFu, cm),
+                               class_of_low(k.z & 0xFFFFu, 0xFFFFu, cm), class_of_low(k.w & 0xFFFFu, 0xFFFFu, cm)};
+        store_classes(p, slot, plane, row0 + b, c);
         if (p.depth)
             __stcs((uint2 *)((uint16_t *)p.depth + slot * plane + row0 + b),
-                   make_uint2(key_depth_bits(k.x) | (key_depth_bits(k.y) << 16),
-                              key_depth_bits(k.z) | (key_depth_bits(k.w) << 16)));
+                   make_uint2((k.x >> 16) | (k.y & 0xFFFF0000u), (k.z >> 16) | (k.w & 0xFFFF0000u)));
     }
 }
 
-template <typename Key>
+template <bool F32>
 __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     const int tid = threadIdx.x, nt = blockDim.x;
     const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap);
-    Key *keys = (Key *)(smem + L.keys);
+    unsigned int *keys = (unsigned int *)(smem + L.keys);  // 8 B per pixel (FP32) or 4 B
     TriRec *tris = (TriRec *)(smem + L.tris);
     int *rowoff = (int *)(smem + L.rowoff);
     unsigned short *map = (unsigned short *)(smem + L.map);
     unsigned short *viscl = (unsigned short *)(smem + L.viscl);
     unsigned char *visbox = (unsigned char *)(smem + L.visbox);
     uint32_t *clipq = (uint32_t *)(smem + L.clipq);
+    float *clipscratch = (float *)(smem + L.clipscratch);
 
-    for (int b = tid; b < p.band_rows * p.W; b += nt) keys[b] = 0;
+    for (int b = tid; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += nt) keys[b] = 0;
 
     for (int iter = 0;; ++iter) {
         if (tid == 0) {
@@ -817,7 +924,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
 
         // 2. setup: warps pull units until the units run out or the batch is full; then the
         //    block rasterises the batch; repeat until every unit is placed.
-        const int nbox_items = sh.nvbox * 12;
+        const int nbox_items = sh.nvbox * 6;  // one box face (two triangles) per lane
         const int n_box_units = (nbox_items + 31) / 32;
         const int n_units = n_box_units + sh.nvcl;
         int pend = -1;           // unit this warp could not place (warp-uniform)
@@ -846,17 +953,17 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
                 }
             }
             __syncthreads();
-            // clip the queued triangles, one job per thread, flushing when the batch is full
+            // clip the queued triangles (8 lanes per job), flushing when the batch is full
             for (;;) {
                 const int nq = sh.cq_n, rv = sh.resv;
                 if (nq == 0) break;
                 const int room = (p.tri_cap - rv) / 6;
                 if (room == 0) {
-                    flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+                    flush<F32>(p, cm, sh, keys, tris, rowoff, map);
                     continue;
                 }
-                const int take = min(min(nq, room), nt);
-                if (tid < take) clip_emit(p, cm, view, clipq[nq - take + tid], tris + rv + 6 * tid);
+                const int take = min(nq, room);
+                clip_jobs(p, cm, view, clipq + (nq - take), take, tris + rv, clipscratch);
                 __syncthreads();
                 if (tid == 0) {
                     sh.cq_n = nq - take;
@@ -868,13 +975,14 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
             const bool full = sh.resv > 0;
             __syncthreads();
             if (tid == 0) sh.npend = 0;
-            if (full) flush<Key>(p, cm, sh, keys, tris, rowoff, map);
+            if (full) flush<F32>(p, cm, sh, keys, tris, rowoff, map);
             else __syncthreads();
             if (!more) break;
         }
 
         // 3. encode and store the band
-        encode_store(p, cm, keys, view);
+        if (F32) encode_f32(p, cm, (unsigned long long *)keys, view);
+        else encode_f16(p, cm, keys, view);
         __syncthreads();
     }
 }
@@ -886,26 +994,26 @@ size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri
 }
 
 cudaError_t render_configure(size_t max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(render_kernel<unsigned long long>,
+    cudaError_t e = cudaFuncSetAttribute(render_kernel<true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(render_kernel<unsigned int>,
+    return cudaFuncSetAttribute(render_kernel<false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
 }
 
 int render_occupancy(int key_f16, int threads, size_t smem) {
     int n = 0;
     cudaError_t e = key_f16
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<unsigned int>, threads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<unsigned long long>, threads, smem);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<false>, threads, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<true>, threads, smem);
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,
                           cudaStream_t s) {
     if (p.n_items <= 0) return cudaSuccess;
-    if (p.key_f16) render_kernel<unsigned int><<<blocks, threads, smem, s>>>(p);
-    else render_kernel<unsigned long long><<<blocks, threads, smem, s>>>(p);
+    if (p.key_f16) render_kernel<false><<<blocks, threads, smem, s>>>(p);
+    else render_kernel<true><<<blocks, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
