@@ -192,7 +192,7 @@ def main():
     import dataclasses
     wl_rank = dataclasses.replace(wl, seed=wl.seed + 7919 * rank)
     worlds = wg.make_workload(wl_rank)
-    sim = Simulator(worlds, config_for(wl_rank), device=local)
+    sim = Simulator(worlds, config_for(wl_rank, autotune=1), device=local)
     out, depth = sim.alloc_outputs()
     n_agents = sim.n_agents
     px = wl.width * wl.height
@@ -288,6 +288,38 @@ def main():
                    "images stay on the GPU as a batched tensor"}
 
     extras = {}
+
+    def graph_rate(sim2, worlds2, wl2, steps):
+        """agent-steps/s and render roofline of graph replays for another configuration."""
+        o2, d2 = sim2.alloc_outputs(depth=False)
+        a2 = [torch.from_numpy(wg.actions(wl2.seed, k, sim2.n_agents)).cuda() for k in range(steps + 3)]
+        for k in range(3):
+            sim2.step_render(a2[k], o2, d2)
+        barrier()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev2[k][0].record(stream)
+            sim2.step_render(a2[3 + k], o2, d2)
+            ev2[k][1].record(stream)
+        barrier()
+        ms = maxred(sum(a.elapsed_time(b) for a, b in ev2)) / steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for k in range(steps):
+            sim2.render(o2, d2)
+        e1.record(stream)
+        barrier()
+        rms = e0.elapsed_time(e1) / steps
+        rb = sim2.info.out_bytes + 36 * (len(worlds2.road) + len(worlds2.line)) + 32 * len(worlds2.boxes)
+        return {"agent_steps_per_s": world * sim2.n_agents / (ms / 1e3), "ms_per_step": ms,
+                "render_kernel_ms": rms, "render_gbs": rb / (rms / 1e3) / 1e9,
+                "render_frac_of_measured_hbm": rb / (rms / 1e3) / 1e9 / peaks()[0],
+                "cameras": sim2.n_views, "band_rows": sim2.info.band_rows,
+                "threads": sim2.info.threads, "tri_capacity": sim2.info.tri_capacity}
+
     if not args.no_extras:
         # plain per-world path: one step launch and one render launch per world, no graph
         pw_steps = 5
@@ -306,6 +338,22 @@ def main():
             "agent_steps_per_s": world * n_agents / (pw_ms / 1e3), "ms_per_step": pw_ms,
             "launches_per_step": 2 * worlds.n_worlds}
         extras["speedup_vs_per_world_path"] = value / extras["per_world_path"]["agent_steps_per_s"]
+        # batched precision path on the same worlds: FP16 reversed-Z keys, fused BF16 NCHW
+        # normalised one-hot output (8 B/px), CUDA graph
+        sim_p = Simulator(worlds, config_for(wl_rank, key_precision=1, output=1, autotune=1),
+                          device=local)
+        extras["precision_path"] = graph_rate(sim_p, worlds, wl_rank, 20)
+        extras["precision_path"]["output"] = "bf16 NCHW one-hot (4 channels), f16 reversed-Z keys"
+        extras["precision_path"]["speedup_vs_per_world_path"] = (
+            extras["precision_path"]["agent_steps_per_s"] / extras["per_world_path"]["agent_steps_per_s"])
+        sim_p.close()
+        # ragged batch at 256x144, precision path
+        wl_r = dataclasses.replace(wg.WORKLOADS["ragged_precision"], seed=wg.WORKLOADS["ragged_precision"].seed + 7919 * rank)
+        worlds_r = wg.make_workload(wl_r)
+        sim_r = Simulator(worlds_r, config_for(wl_r, autotune=1), device=local)
+        extras["ragged_precision_256x144"] = graph_rate(sim_r, worlds_r, wl_r, 5)
+        extras["ragged_precision_256x144"]["workload"] = wl_r.name
+        sim_r.close()
 
     cpu = None
     if rank == 0:
