@@ -170,6 +170,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--shape", default="",
+                    help="pin the render launch shape ROWS,THREADS,TRI_CAP instead of autotuning "
+                         "(for profiler captures that must skip a known number of launches)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -192,7 +195,12 @@ def main():
     import dataclasses
     wl_rank = dataclasses.replace(wl, seed=wl.seed + 7919 * rank)
     worlds = wg.make_workload(wl_rank)
-    sim = Simulator(worlds, config_for(wl_rank, autotune=1), device=local)
+    if args.shape:
+        rows, threads, cap = (int(v) for v in args.shape.split(","))
+        shape = dict(band_rows=rows, threads=threads, tri_capacity=cap)
+    else:
+        shape = dict(autotune=1)
+    sim = Simulator(worlds, config_for(wl_rank, **shape), device=local)
     out, depth = sim.alloc_outputs()
     n_agents = sim.n_agents
     px = wl.width * wl.height

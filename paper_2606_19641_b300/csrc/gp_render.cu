@@ -15,12 +15,14 @@
 //      queued and later clipped by an 8-lane warp segment (Sutherland-Hodgman, planes in
 //      the order near, left, right, bottom, top) and fan-triangulated.  A warp reserves batch slots for its unit with one
 //      atomic; when the batch is full the block rasterises it and continues;
-//   3. raster: kept triangles are expanded into (triangle, row, 64-pixel window) items;
-//      each item computes the exact covered span of its row within the window from the
-//      integer edge functions (top-left fill rule) and resolves depth per pixel in shared
-//      memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or (binary16 depth
-//      << 16 | ~prim) in FP16 mode; the nearest surface wins, ties go to the smaller
-//      primitive id;
+//   3. raster: kept triangles are expanded into (triangle, row, 64-pixel window) items,
+//      dealt out so that one triangle's rows land in different warps; each item computes
+//      the exact covered span of its row within the window from the integer edge functions
+//      (top-left fill rule); a warp then walks its spans' pixels -- each lane its own span
+//      when the spans are even, 32 fragments at a time when a few long spans dominate --
+//      and resolves depth per pixel in shared memory with atomicMax on a key: (FP32 depth
+//      bits << 32 | ~prim), or (binary16 depth << 16 | ~prim) in FP16 mode; the nearest
+//      surface wins, ties go to the smaller primitive id;
 //   4. encode: keys become class ids (uint8) + depth, or a normalised one-hot BF16 NCHW
 //      tensor; the band is one contiguous range of every output plane, written with 16-byte
 //      streaming stores.
@@ -158,9 +160,10 @@ __device__ __forceinline__ void box_corner(float4 pose, float4 dim, float s, flo
 // Face triangles (corner indices), counter-clockwise seen from outside; faces +x, -x, +y,
 // -y, +z, -z, each quad (q0 q1 q2 q3) split into (q0 q1 q2), (q0 q2 q3).
 __device__ __forceinline__ void box_tri(int t, int &a, int &b, int &c) {
-    // packed 4-bit corner ids per face: q0 q1 q2 q3
-    const unsigned short F[6] = {0x1375, 0x0462, 0x2673, 0x0154, 0x4576, 0x0231};
-    const unsigned short f = F[t >> 1];
+    // packed 4-bit corner ids per face (q0 q1 q2 q3), faces 0..3 in one word, 4..5 in another
+    const int face = t >> 1;
+    const unsigned int f = face < 4 ? (unsigned int)(0x0154267304621375ull >> (16 * face)) & 0xFFFFu
+                                    : (0x02314576u >> (16 * (face - 4))) & 0xFFFFu;
     const int q0 = (f >> 12) & 15, q1 = (f >> 8) & 15, q2 = (f >> 4) & 15, q3 = f & 15;
     a = q0;
     b = (t & 1) ? q2 : q1;
@@ -173,7 +176,7 @@ __device__ __forceinline__ unsigned int wrap_mul_add(int a, int b, unsigned int 
 }
 
 // Build a raster record from a front-facing snapped triangle (area2 < 0 in y-down space).
-__device__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float d[3],
+__device__ __forceinline__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float d[3],
                           uint32_t prim, int key_f16, int i0, int i1, int j0, int j1) {
     // orient to positive area: keep vertex 0, swap 1 and 2
     const int vx[3] = {X[0], X[2], X[1]};
@@ -277,14 +280,9 @@ __device__ __forceinline__ int tri_items(const TriRec &T) {
     return ((T.jspan >> 16) - (T.jspan & 0xFFFF) + 1) * tri_windows(T);
 }
 
-// Rasterise one row of one triangle within columns [lo, hi]: exact covered span, then
-// per-pixel depth resolution.  The result per pixel is the maximum over fragments of
-// (depth, inverted primitive id), i.e. the nearest surface with ties to the smaller id:
-// FP32 mode keeps one 64-bit key per pixel (FP32 depth bits << 32 | inverted id), FP16
-// mode one 32-bit key (binary16 depth bits << 16 | inverted id).
-template <bool F32>
-__device__ __forceinline__ void raster_row(const TriRec &T, int row, int lo, int hi, int by0,
-                                           int W, void *keys) {
+// Exact covered span of one row of a triangle within columns [lo, hi] (narrowed in place;
+// empty if lo > hi afterwards), from the integer edge functions with the fill-rule bias.
+__device__ __forceinline__ void row_span(const TriRec &T, int row, int &lo, int &hi) {
     const int X0 = (int)(short)(T.xy0 & 0xFFFF), Y0 = T.xy0 >> 16;
     const int gy = 16 * row + 8 - Y0;
     const float xo = (float)(X0 - 8);
@@ -318,22 +316,80 @@ __device__ __forceinline__ void raster_row(const TriRec &T, int row, int lo, int
             hi = i;
         }
     }
-    if (lo > hi) return;
-    const float inner = __fmaf_rn(T.b, (float)gy, T.d0);
-    float fgx = (float)(16 * lo + 8 - X0);
-    const int o = (row - by0) * W;
-    for (int i = lo; i <= hi; ++i, fgx += 16.f) {
-        float d = __fmaf_rn(T.a, fgx, inner);
-        d = d > 0.f ? d : 0.f;
-        if (F32) {
-            unsigned long long *rk = (unsigned long long *)keys + o;
-            const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | T.low;
-            if (key > rk[i]) atomicMax(rk + i, key);
-        } else {
-            unsigned int *rk = (unsigned int *)keys + o;
-            const unsigned int key = key16(d, T.low);
-            if (key > rk[i]) atomicMax(rk + i, key);
+}
+
+// Depth test of one fragment: the key's maximum wins per pixel -- FP32 mode one 64-bit key
+// (FP32 depth bits << 32 | inverted id), FP16 mode one 32-bit key (binary16 depth bits << 16
+// | inverted id) -- so the nearest surface wins and ties go to the smaller primitive id.
+// Depth is a * g + inner, clamped to >= 0, g the pixel centre's offset (1/16 px) from the
+// triangle's vertex 0.
+template <bool F32>
+__device__ __forceinline__ void depth_test(void *keys, int ko, int g, float a, float inner,
+                                           uint32_t low) {
+    float d = __fmaf_rn(a, (float)g, inner);
+    d = d > 0.f ? d : 0.f;
+    if (F32) {
+        unsigned long long *rk = (unsigned long long *)keys + ko;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | low;
+        if (key > *rk) atomicMax(rk, key);
+    } else {
+        unsigned int *rk = (unsigned int *)keys + ko;
+        const unsigned int key = key16(d, low);
+        if (key > *rk) atomicMax(rk, key);
+    }
+}
+
+// Relative cost of one cooperative round (32 fragments) against one per-lane iteration:
+// 64-bit key updates favour the cooperative walk.
+constexpr int kCoopCostF32 = 1, kCoopCostF16 = 3;
+
+// Depth resolution of a warp's spans (warp-uniform call).  Lane k brings a span of `cnt`
+// pixels starting at key index `kofs`, whose first pixel centre lies gx0 (1/16 px) right of
+// the triangle's vertex 0.  If the spans are even, each lane walks its own span; if a few
+// long spans dominate, the warp scans the counts and walks the concatenated fragments 32 at
+// a time, each lane finding its span by binary search over the prefix sums, so the cost
+// follows the number of fragments rather than the longest span.
+template <bool F32>
+__device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float a, float inner,
+                                               uint32_t low, void *keys) {
+    const int lane = threadIdx.x & 31;
+    const int maxc = __reduce_max_sync(0xffffffffu, cnt);
+    const int total = __reduce_add_sync(0xffffffffu, cnt);
+    if (maxc <= ((total + 31) >> 5) * (F32 ? kCoopCostF32 : kCoopCostF16)) {
+        for (int t = 0; t < cnt; ++t) depth_test<F32>(keys, kofs + t, gx0 + 16 * t, a, inner, low);
+        return;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - cnt;
+    // two rounds per iteration: independent searches overlap their shuffle latency
+    for (int f0 = 0; f0 < total; f0 += 64) {
+        const int fA = f0 + lane, fB = fA + 32;
+        int oA = 0, oB = 0;  // first lane whose inclusive prefix exceeds f
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int vA = __shfl_sync(0xffffffffu, incl, oA + st - 1);
+            const int vB = __shfl_sync(0xffffffffu, incl, oB + st - 1);
+            if (vA <= fA) oA += st;
+            if (vB <= fB) oB += st;
         }
+        const int tA = fA - __shfl_sync(0xffffffffu, excl, oA);
+        const int tB = fB - __shfl_sync(0xffffffffu, excl, oB);
+        const int kA = __shfl_sync(0xffffffffu, kofs, oA) + tA;
+        const int kB = __shfl_sync(0xffffffffu, kofs, oB) + tB;
+        const int gA = __shfl_sync(0xffffffffu, gx0, oA) + 16 * tA;
+        const int gB = __shfl_sync(0xffffffffu, gx0, oB) + 16 * tB;
+        const float aA = __shfl_sync(0xffffffffu, a, oA), aB = __shfl_sync(0xffffffffu, a, oB);
+        const float iA = __shfl_sync(0xffffffffu, inner, oA);
+        const float iB = __shfl_sync(0xffffffffu, inner, oB);
+        const uint32_t lA = __shfl_sync(0xffffffffu, low, oA);
+        const uint32_t lB = __shfl_sync(0xffffffffu, low, oB);
+        if (fA < total) depth_test<F32>(keys, kA, gA, aA, iA, lA);
+        if (fB < total) depth_test<F32>(keys, kB, gB, aB, iB, lB);
     }
 }
 
@@ -455,16 +511,36 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
             }
         }
         __syncthreads();
-        for (int i = tid; i < len; i += nt) {
-            const int t = map[i];
-            const TriRec &T = tris[t];
-            const int nwin = tri_windows(T), k = start + i - rowoff[t];
-            const int r = k / nwin, wdx = k - r * nwin;
-            const int row = (T.jspan & 0xFFFF) + r;
-            const int lo = (T.ispan & 0xFFFF) + wdx * kSpanWindow;
-            const int hi = min(lo + kSpanWindow - 1, T.ispan >> 16);
-            if (row >= cm.by0 && row <= cm.by1 && lo >= 0 && hi < p.W)
-                raster_row<F32>(T, row, lo, hi, cm.by0, p.W, keys);
+        // Consecutive items (the rows of one triangle) go to different warps, so a large
+        // triangle is spread over the block instead of holding up one warp.
+        const int nw = nt >> 5, mine = (tid & 31) * nw + (tid >> 5);
+        for (int ib = 0; ib < len; ib += nt) {  // warp-uniform trip count
+            const int i = ib + mine;
+            int cnt = 0, kofs = 0, gx0 = 0;
+            float a = 0.f, inner = 0.f;
+            uint32_t low = 0;
+            if (i < len) {
+                const int t = map[i];
+                const TriRec &T = tris[t];
+                const int nwin = tri_windows(T), k = start + i - rowoff[t];
+                const int r = nwin == 1 ? k : k / nwin, wdx = k - r * nwin;
+                const int row = (T.jspan & 0xFFFF) + r;
+                int lo = (T.ispan & 0xFFFF) + wdx * kSpanWindow;
+                int hi = min(lo + kSpanWindow - 1, T.ispan >> 16);
+                if (row >= cm.by0 && row <= cm.by1 && lo >= 0 && hi < p.W) {
+                    row_span(T, row, lo, hi);
+                    if (lo <= hi) {
+                        const int X0 = (int)(short)(T.xy0 & 0xFFFF), Y0 = T.xy0 >> 16;
+                        cnt = hi - lo + 1;
+                        kofs = (row - cm.by0) * p.W + lo;
+                        gx0 = 16 * lo + 8 - X0;
+                        a = T.a;
+                        inner = __fmaf_rn(T.b, (float)(16 * row + 8 - Y0), T.d0);
+                        low = T.low;
+                    }
+                }
+            }
+            warp_fragments<F32>(cnt, kofs, gx0, a, inner, low, keys);
         }
         __syncthreads();
     }
@@ -536,7 +612,9 @@ __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const 
             source_tri(p, cm, jobs[job], wx, wy, wz, prim);
             n = 3;
             if (gl < 3) {
-                const float3 v = to_view(p, cm, wx[gl], wy[gl], wz[gl]);
+                const float3 v = to_view(p, cm, gl == 0 ? wx[0] : (gl == 1 ? wx[1] : wx[2]),
+                                         gl == 0 ? wy[0] : (gl == 1 ? wy[1] : wy[2]),
+                                         gl == 0 ? wz[0] : (gl == 1 ? wz[1] : wz[2]));
                 x = v.x;
                 y = v.y;
                 z = v.z;
