@@ -111,7 +111,7 @@ typedef struct gp_config {
     float norm_mean[4];           /* one-hot normalisation (default 0.5 each) */
     float norm_std[4];            /* (default 0.5 each -> values are exactly +-1) */
     int32_t autotune;             /* 1: time candidate launch shapes at create (default 0) */
-    int32_t band_rows;            /* rows per screen band, 0 = auto */
+    int32_t band_rows;            /* rows per screen band (1..128), 0 = auto */
     int32_t threads;              /* render threads per block, 0 = auto */
     int32_t tri_capacity;         /* triangles per raster batch, 0 = auto */
 } gp_config;

@@ -75,6 +75,7 @@ struct gp_handle {
     int device = 0, sms = 148;
     gp_config cfg{};
     int n_worlds = 0, n_agents = 0, n_boxes = 0, n_views = 0;
+    int max_cl = 1;  // most culling clusters in one world
     std::vector<WorldInfo> worlds_h;
     std::vector<int> world_item_begin, world_item_count;
     DevBuf<WorldInfo> worlds;
@@ -171,10 +172,12 @@ size_t smem_limit(int device) {
 bool finish_shape(gp_handle *h, Shape &s) {
     const gp_config &c = h->cfg;
     if (s.band_rows > c.height) s.band_rows = c.height;
+    if (s.band_rows < 1 || s.band_rows > kMaxBandRows) return false;
     if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
     // a setup unit needs at most 32 batch slots; a clip job needs 6
     if (s.tri_cap < 64) return false;
-    s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap);
+    s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap,
+                               h->max_cl);
     if (s.smem + 1024 > smem_limit(h->device)) return false;  // leave room for static smem
     const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem);
     if (per_sm < 1) return false;
@@ -185,11 +188,11 @@ bool finish_shape(gp_handle *h, Shape &s) {
 Shape default_shape(gp_handle *h) {
     const gp_config &c = h->cfg;
     Shape best;
-    const int rows_opts[] = {512, 256, 128, 64, 48, 32, 16, 8};
+    const int rows_opts[] = {128, 64, 48, 32, 16, 8};
     for (int r : rows_opts) {
         Shape s;
         s.threads = c.threads ? c.threads : 256;
-        s.tri_cap = c.tri_capacity ? c.tri_capacity : std::max(512, 2 * s.threads);
+        s.tri_cap = c.tri_capacity ? c.tri_capacity : std::max(1024, 2 * s.threads);
         s.band_rows = c.band_rows ? c.band_rows : r;
         if (!finish_shape(h, s)) {
             if (c.band_rows) break;
@@ -237,6 +240,7 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     p.view_mod = 0;
     std::memcpy(p.onehot, h->onehot, sizeof(p.onehot));
     p.tri_cap = h->shape.tri_cap;
+    p.max_cl = h->max_cl;
     p.status = h->status.p;
     p.dump_view = -1;
     return p;
@@ -382,8 +386,8 @@ gp_status autotune(gp_handle *h) {
     float best_ms = 1e30f;
     const Shape saved = h->shape;
     const int thr[] = {256, 512, 1024};
-    const int caps[] = {384, 512, 1024};
-    const int rows[] = {8, 16, 32, 64, 128, 256, 512};
+    const int caps[] = {512, 768, 1024, 1536, 2048};
+    const int rows[] = {8, 16, 32, 48, 64, 128};
     for (int t : thr)
         for (int cap : caps)
             for (int r : rows) {
@@ -656,6 +660,7 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
                 i = j;
             }
             wi.n_cl = (int)clusters.size() - wi.cl_begin;
+            h->max_cl = std::max(h->max_cl, wi.n_cl);
             if (wi.n_cl > kMaxClustersPerWorld) {
                 delete h;
                 return fail(GP_ELIMIT, "too many culling clusters in a world");

@@ -13,6 +13,7 @@ namespace gpk {
 constexpr int kMaxBoxes = GP_MAX_BOXES;
 constexpr int kClusterQuads = 32;  // quads per culling cluster = one quad per lane of a warp
 constexpr int kMaxClustersPerWorld = 4096;
+constexpr int kMaxBandRows = 128;  // rows per screen band (raster records pack band-relative rows)
 
 // Per-world table (device).
 struct WorldInfo {
@@ -81,6 +82,7 @@ struct RenderParams {
     uint16_t onehot[4][2];   // bf16 values per channel: [cold, hot]
 
     int tri_cap;             // triangles per raster batch
+    int max_cl;              // most culling clusters in any world of the batch
     uint32_t *status;
 
     int dump_view;           // -1 = off
@@ -89,8 +91,9 @@ struct RenderParams {
     int dump_cap;
 };
 
-// Shared-memory bytes the render kernel needs for a launch shape.
-size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap);
+// Shared-memory bytes the render kernel needs for a launch shape (max_cl: most culling
+// clusters in any world of the batch).
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl);
 
 cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
 cudaError_t launch_state(float *state, uint8_t *flags, float4 *pose, float *speed, uint8_t *fl,

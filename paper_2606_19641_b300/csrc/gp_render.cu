@@ -42,15 +42,23 @@ constexpr int kItemsPerThread = 8;  // raster items per thread per raster sub-pa
 constexpr int kSpanWindow = 64;     // pixels per raster item (a row is split into windows)
 constexpr int kClipQueue = 256;     // queued clip jobs per block
 
+// A triangle ready for raster.  The edge functions are rebuilt from the vertices per row;
+// snapped coordinates stay within the 4x guard band, |X|, |Y| <= 5 * 8 * 512 < 2^15.
 struct __align__(16) TriRec {
-    int A[3], B[3], C[3];  // edge functions E_k = A_k gx + B_k gy + C_k, fill-rule bias folded in
-    float d0, a, b;        // depth plane, per 1/16 px
-    int xy0;               // vertex 0 (origin of gx, gy): X0 low 16 bits, Y0 high 16 bits
-    uint32_t low;          // low half of the key: inverted primitive id
-    int ispan;             // pixel-centre columns i0 | i1 << 16
-    int jspan;             // pixel-centre rows    j0 | j1 << 16
+    int xy[3];      // snapped vertices, positive area (y down): X low 16 bits, Y high 16 bits
+    uint32_t low;   // low half of the key: inverted primitive id
+    float d0, a, b; // depth plane d0 + a (X - X0) + b (Y - Y0), per 1/16 px, origin vertex 0
+    uint32_t span;  // pixel-centre bounds: i0 | i1 << 9 | (j0 - by0) << 18 | (j1 - j0) << 25
 };
-static_assert(sizeof(TriRec) == 64, "TriRec layout");
+static_assert(sizeof(TriRec) == 32, "TriRec layout");
+static_assert(kMaxBandRows <= 128, "(j0 - by0) and (j1 - j0) have 7 bits each");
+
+__device__ __forceinline__ int span_i0(uint32_t s) { return (int)(s & 511u); }
+__device__ __forceinline__ int span_i1(uint32_t s) { return (int)((s >> 9) & 511u); }
+__device__ __forceinline__ int span_j0(uint32_t s) { return (int)((s >> 18) & 127u); }  // band-relative
+__device__ __forceinline__ int span_nj(uint32_t s) { return (int)(s >> 25) + 1; }     // rows
+__device__ __forceinline__ int vtx_x(int xy) { return (int)(short)(xy & 0xFFFF); }
+__device__ __forceinline__ int vtx_y(int xy) { return xy >> 16; }
 
 struct Cam {
     float px, py, s, c;  // camera position and yaw sin/cos
@@ -62,13 +70,15 @@ struct Cam {
 };
 
 struct Smem {
-    size_t keys, tris, rowoff, map, viscl, visbox, clipq, clipscratch, total;
+    size_t keys, tris, rowoff, map, clipscratch, vq0, vnq, visbox, clipq, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Shared memory of a block.  The raster bookkeeping (rowoff, map) and the clip scratch
+// are live in different phases and share one region.
 __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, int threads,
-                                            int tri_cap) {
+                                            int tri_cap, int max_cl) {
     Smem s;
     size_t o = 0;
     s.keys = o;
@@ -76,21 +86,26 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     o = align_up(o, 16);
     s.tris = o;
     o += (size_t)tri_cap * sizeof(TriRec);
+    const size_t shared_base = o;
     s.rowoff = o;
     o += (size_t)(tri_cap + 1) * 4;
     o = align_up(o, 16);
     s.map = o;
     o += (size_t)threads * kItemsPerThread * 2;
     o = align_up(o, 16);
-    s.viscl = o;
-    o += (size_t)kMaxClustersPerWorld * 2;
+    s.clipscratch = shared_base;  // per warp: 4 jobs x 8 vertices x 3 floats
+    const size_t clip_end = shared_base + (size_t)(threads / 32) * 4 * 24 * 4;
+    o = clip_end > o ? clip_end : o;
+    o = align_up(o, 16);
+    s.vq0 = o;  // first quad of each visible cluster
+    o += (size_t)max_cl * 4;
+    s.vnq = o;  // its quad count
+    o += (size_t)max_cl;
     s.visbox = o;
     o += kMaxBoxes;
     o = align_up(o, 16);
     s.clipq = o;
     o += (size_t)kClipQueue * 4;
-    s.clipscratch = o;
-    o += (size_t)(threads / 32) * 4 * 24 * 4;  // per warp: 4 jobs x 8 vertices x 3 floats
     s.total = align_up(o, 16);
     return s;
 }
@@ -175,25 +190,17 @@ __device__ __forceinline__ unsigned int wrap_mul_add(int a, int b, unsigned int 
     return (unsigned int)a * (unsigned int)b + c;
 }
 
-// Build a raster record from a front-facing snapped triangle (area2 < 0 in y-down space).
+// Build a raster record from a front-facing snapped triangle (area2 < 0 in y-down space)
+// with pixel-centre bounds i0..i1, j0..j1 (j within the band starting at row by0).
 __device__ __forceinline__ void build_rec(TriRec &r, const int X[3], const int Y[3], const float d[3],
-                          uint32_t prim, int key_f16, int i0, int i1, int j0, int j1) {
+                                          uint32_t prim, int key_f16, int i0, int i1, int j0,
+                                          int j1, int by0) {
     // orient to positive area: keep vertex 0, swap 1 and 2
     const int vx[3] = {X[0], X[2], X[1]};
     const int vy[3] = {Y[0], Y[2], Y[1]};
     const float dv[3] = {d[0], d[2], d[1]};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int a = k, b = (k + 1) % 3;
-        const int A = vy[a] - vy[b], B = vx[b] - vx[a];
-        unsigned int C = wrap_mul_add(A, vx[0] - vx[a], wrap_mul_add(B, vy[0] - vy[a], 0u));
-        const int dxe = vx[b] - vx[a], dye = vy[b] - vy[a];
-        const bool tl = (dye == 0 && dxe > 0) || (dye < 0);
-        if (!tl) C -= 1u;
-        r.A[k] = A;
-        r.B[k] = B;
-        r.C[k] = (int)C;
-    }
+    for (int k = 0; k < 3; ++k) r.xy[k] = (vx[k] & 0xFFFF) | (vy[k] << 16);
     const float fx1 = (float)(vx[1] - vx[0]), fy1 = (float)(vy[1] - vy[0]);
     const float fx2 = (float)(vx[2] - vx[0]), fy2 = (float)(vy[2] - vy[0]);
     const int area2 = (int)(wrap_mul_add(vx[1] - vx[0], vy[2] - vy[0], 0u) -
@@ -205,11 +212,9 @@ __device__ __forceinline__ void build_rec(TriRec &r, const int X[3], const int Y
     r.a = __fdiv_rn(na, fa);
     r.b = __fdiv_rn(nb, fa);
     r.d0 = dv[0];
-    // snapped coordinates stay within the 4x guard band: |X|, |Y| <= 40 * 512 < 2^15
-    r.xy0 = (vx[0] & 0xFFFF) | (vy[0] << 16);
     r.low = key_f16 ? (0xFFFFu - (prim & 0xFFFFu)) : (0xFFFFFFFFu - prim);
-    r.ispan = (i0 & 0xFFFF) | (i1 << 16);
-    r.jspan = (j0 & 0xFFFF) | (j1 << 16);
+    r.span = (uint32_t)i0 | ((uint32_t)i1 << 9) | ((uint32_t)(j0 - by0) << 18) |
+             ((uint32_t)(j1 - j0) << 25);
 }
 
 // Snapped triangle -> keep? (front-facing, bbox holds a pixel centre of the band).
@@ -272,46 +277,51 @@ __device__ __forceinline__ unsigned int key16(float d, uint32_t low) {
     return ((unsigned int)__half_as_ushort(__float2half_rn(d)) << 16) | low;
 }
 
-// Items of a triangle: rows x windows of kSpanWindow pixels of its bounding columns.
-__device__ __forceinline__ int tri_windows(const TriRec &T) {
-    return (((T.ispan >> 16) - (T.ispan & 0xFFFF)) / kSpanWindow) + 1;
+// Items of a triangle: rows x windows of kSpanWindow pixels of its bounding columns (none
+// for an empty slot, whose i1 < i0).
+__device__ __forceinline__ int tri_windows(uint32_t s) {
+    return (span_i1(s) - span_i0(s)) / kSpanWindow + 1;
 }
-__device__ __forceinline__ int tri_items(const TriRec &T) {
-    return ((T.jspan >> 16) - (T.jspan & 0xFFFF) + 1) * tri_windows(T);
+__device__ __forceinline__ int tri_items(uint32_t s) {
+    return span_i1(s) < span_i0(s) ? 0 : span_nj(s) * tri_windows(s);
 }
 
 // Exact covered span of one row of a triangle within columns [lo, hi] (narrowed in place;
-// empty if lo > hi afterwards), from the integer edge functions with the fill-rule bias.
+// empty if lo > hi afterwards).  Edge k runs from vertex a = k to b = k + 1; its function
+// at pixel centre (16 i + 8, py) is E = A (16 i + 8 - X_a) + B (py - Y_a) - bias with
+// A = Y_a - Y_b, B = X_b - X_a, and bias 0 on a top or left edge, else 1 (top-left fill
+// rule); the pixel is covered if E >= 0 on all three edges.
 __device__ __forceinline__ void row_span(const TriRec &T, int row, int &lo, int &hi) {
-    const int X0 = (int)(short)(T.xy0 & 0xFFFF), Y0 = T.xy0 >> 16;
-    const int gy = 16 * row + 8 - Y0;
-    const float xo = (float)(X0 - 8);
+    const int py = 16 * row + 8;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int A = T.A[k];
-        const int R = (int)wrap_mul_add(T.B[k], gy, (unsigned int)T.C[k]);
+        const int xa = vtx_x(T.xy[k]), ya = vtx_y(T.xy[k]);
+        const int xb = vtx_x(T.xy[(k + 1) % 3]), yb = vtx_y(T.xy[(k + 1) % 3]);
+        const int A = ya - yb, B = xb - xa;
+        const bool top_left = (A == 0 && B > 0) || A > 0;
+        const int R = (int)wrap_mul_add(B, py - ya, top_left ? 0u : 0xFFFFFFFFu);
         if (A == 0) {
             if (R < 0) hi = lo - 1;
             continue;
         }
-        // E(i) = A (16 i + 8 - X0) + R ; the edge crosses at i* = (X0 - 8 - R / A) / 16.
+        // E(i) = A (16 i + 8 - X_a) + R ; the edge crosses at i* = (X_a - 8 - R / A) / 16.
         // The float estimate is within one pixel wherever it matters; one exact integer
         // check on each side fixes it.
-        const float q = (xo - __fdividef((float)R, (float)A)) * 0.0625f;
+        const float q = ((float)(xa - 8) - __fdividef((float)R, (float)A)) * 0.0625f;
         if (A > 0) {  // lower bound: smallest i with E(i) >= 0
             int i = __float2int_ru(fminf(fmaxf(q, -1e6f), 1e6f));
             i = min(max(i, lo), hi + 1);
-            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - X0, (unsigned int)R) >= 0)
+            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - xa, (unsigned int)R) >= 0)
                 --i;
-            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - X0, (unsigned int)R) < 0)
+            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - xa, (unsigned int)R) < 0)
                 ++i;
             lo = i;
         } else {  // upper bound: largest i with E(i) >= 0
             int i = __float2int_rd(fminf(fmaxf(q, -1e6f), 1e6f));
             i = min(max(i, lo - 1), hi);
-            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - X0, (unsigned int)R) >= 0)
+            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - xa, (unsigned int)R) >= 0)
                 ++i;
-            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - X0, (unsigned int)R) < 0)
+            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - xa, (unsigned int)R) < 0)
                 --i;
             hi = i;
         }
@@ -472,12 +482,12 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
     const int per = (n + nt - 1) / nt;
     const int t0 = min(tid * per, n), t1 = min(t0 + per, n);
     int local = 0;
-    for (int t = t0; t < t1; ++t) local += tri_items(tris[t]);
+    for (int t = t0; t < t1; ++t) local += tri_items(tris[t].span);
     int total = 0;
     int run = block_exclusive_scan(local, sh.warp, total);
     for (int t = t0; t < t1; ++t) {
         rowoff[t] = run;
-        run += tri_items(tris[t]);
+        run += tri_items(tris[t].span);
     }
     if (tid == 0) rowoff[n] = total;
     __syncthreads();
@@ -522,15 +532,16 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
             if (i < len) {
                 const int t = map[i];
                 const TriRec &T = tris[t];
-                const int nwin = tri_windows(T), k = start + i - rowoff[t];
+                const uint32_t sp = T.span;
+                const int nwin = tri_windows(sp), k = start + i - rowoff[t];
                 const int r = nwin == 1 ? k : k / nwin, wdx = k - r * nwin;
-                const int row = (T.jspan & 0xFFFF) + r;
-                int lo = (T.ispan & 0xFFFF) + wdx * kSpanWindow;
-                int hi = min(lo + kSpanWindow - 1, T.ispan >> 16);
+                const int row = cm.by0 + span_j0(sp) + r;
+                int lo = span_i0(sp) + wdx * kSpanWindow;
+                int hi = min(lo + kSpanWindow - 1, span_i1(sp));
                 if (row >= cm.by0 && row <= cm.by1 && lo >= 0 && hi < p.W) {
                     row_span(T, row, lo, hi);
                     if (lo <= hi) {
-                        const int X0 = (int)(short)(T.xy0 & 0xFFFF), Y0 = T.xy0 >> 16;
+                        const int X0 = vtx_x(T.xy[0]), Y0 = vtx_y(T.xy[0]);
                         cnt = hi - lo + 1;
                         kofs = (row - cm.by0) * p.W + lo;
                         gx0 = 16 * lo + 8 - X0;
@@ -582,10 +593,7 @@ __device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm,
 }
 
 // A batch slot that holds no triangle (zero rows).
-__device__ __forceinline__ void empty_rec(TriRec &r) {
-    r.ispan = 0;
-    r.jspan = 1;
-}
+__device__ __forceinline__ void empty_rec(TriRec &r) { r.span = 1u; }  // i0 = 1 > i1 = 0
 
 // Clip queued triangles cooperatively: an 8-lane segment per job (4 jobs per warp), one
 // polygon vertex per lane.  For every plane the triangle crosses (near, then guard left,
@@ -685,7 +693,7 @@ __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const 
             TriRec &r = slots[6 * job + gl];
             int i0, i1, j0, j1;
             if (n >= 3 && gl + 2 < n && tri_bbox(p, cm, tX, tY, i0, i1, j0, j1)) {
-                build_rec(r, tX, tY, td, prim, p.key_f16, i0, i1, j0, j1);
+                build_rec(r, tX, tY, td, prim, p.key_f16, i0, i1, j0, j1, cm.by0);
                 if (view == p.dump_view) dump_tri(p, tX, tY, td, prim, (uint32_t)gl);
             } else {
                 empty_rec(r);
@@ -748,7 +756,7 @@ __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm
 // `clips_queued` tells the retry (after a flush) whether this unit's clip jobs are already
 // queued.
 __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
-                           uint32_t *clipq, const unsigned short *viscl,
+                           uint32_t *clipq, const int *vq0, const unsigned char *vnq,
                            const unsigned char *visbox, int view, int unit, int n_box_units,
                            int nbox_items, bool clips_done, bool &clips_queued) {
     const int lane = threadIdx.x & 31;
@@ -763,9 +771,9 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
             tcode = 0x80000000u | (b << 4) | (2u * face);
         }
     } else {
-        const Cluster cl = p.clusters[cm.cl_begin + viscl[unit - n_box_units]];
-        valid = lane < cl.nq;
-        qcode = (uint32_t)(cl.q0 + lane);
+        const int c = unit - n_box_units;
+        valid = lane < (int)vnq[c];
+        qcode = (uint32_t)(vq0[c] + lane);
         tcode = qcode << 1;
     }
     bool keep0 = false, keep1 = false, clip0 = false, clip1 = false;
@@ -833,13 +841,15 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
     if (keep0) {
         const int tX[3] = {X[0], X[1], X[2]}, tY[3] = {Y[0], Y[1], Y[2]};
         const float td[3] = {d[0], d[1], d[2]};
-        build_rec(tris[base + __popc(k0 & lt)], tX, tY, td, prim0, p.key_f16, b0[0], b0[1], b0[2], b0[3]);
+        build_rec(tris[base + __popc(k0 & lt)], tX, tY, td, prim0, p.key_f16, b0[0], b0[1], b0[2],
+                  b0[3], cm.by0);
         if (view == p.dump_view) dump_tri(p, tX, tY, td, prim0, 0u);
     }
     if (keep1) {
         const int tX[3] = {X[0], X[2], X[3]}, tY[3] = {Y[0], Y[2], Y[3]};
         const float td[3] = {d[0], d[2], d[3]};
-        build_rec(tris[base + nk0 + __popc(k1 & lt)], tX, tY, td, prim0 + 1u, p.key_f16, b1[0], b1[1], b1[2], b1[3]);
+        build_rec(tris[base + nk0 + __popc(k1 & lt)], tX, tY, td, prim0 + 1u, p.key_f16, b1[0], b1[1],
+                  b1[2], b1[3], cm.by0);
         if (view == p.dump_view) dump_tri(p, tX, tY, td, prim0 + 1u, 0u);
     }
     return true;
@@ -919,12 +929,13 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap);
+    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap, p.max_cl);
     unsigned int *keys = (unsigned int *)(smem + L.keys);  // 8 B per pixel (FP32) or 4 B
     TriRec *tris = (TriRec *)(smem + L.tris);
     int *rowoff = (int *)(smem + L.rowoff);
     unsigned short *map = (unsigned short *)(smem + L.map);
-    unsigned short *viscl = (unsigned short *)(smem + L.viscl);
+    int *vq0 = (int *)(smem + L.vq0);
+    unsigned char *vnq = smem + L.vnq;
     unsigned char *visbox = (unsigned char *)(smem + L.visbox);
     uint32_t *clipq = (uint32_t *)(smem + L.clipq);
     float *clipscratch = (float *)(smem + L.clipscratch);
@@ -975,12 +986,16 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
         for (int base = 0; base < wi.n_cl; base += nt) {
             const int c = base + tid;
             bool keep = false;
+            Cluster cl{};
             if (c < wi.n_cl) {
-                const Cluster cl = p.clusters[wi.cl_begin + c];
+                cl = p.clusters[wi.cl_begin + c];
                 keep = aabb_visible(p, cm, cl.cx, cl.cy, cl.hx, cl.hy, cl.zlo, cl.zhi);
             }
             const int k = warp_append(keep, &sh.nvcl);
-            if (keep) viscl[k] = (unsigned short)c;  // world-local cluster index
+            if (keep) {  // the cluster's quad range, so setup needs no further lookup
+                vq0[k] = cl.q0;
+                vnq[k] = (unsigned char)cl.nq;
+            }
         }
         for (int base = 0; base < wi.n_boxes; base += nt) {
             const int b = base + tid;
@@ -1022,7 +1037,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
                 }
                 if (u >= n_units) break;
                 bool queued = false;
-                if (!setup_unit(p, cm, sh, tris, clipq, viscl, visbox, view, u, n_box_units,
+                if (!setup_unit(p, cm, sh, tris, clipq, vq0, vnq, visbox, view, u, n_box_units,
                                 nbox_items, done_clips, queued)) {
                     pend = u;
                     pend_clips = queued;
@@ -1067,8 +1082,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
 
 }  // namespace
 
-size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap) {
-    return smem_layout(W, band_rows, key_f16, threads, tri_cap).total;
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl) {
+    return smem_layout(W, band_rows, key_f16, threads, tri_cap, max_cl).total;
 }
 
 cudaError_t render_configure(size_t max_smem) {
