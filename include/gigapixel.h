@@ -53,6 +53,8 @@ enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4 };
 enum {
     GP_DEV_NONFINITE_STATE = 1u << 0, /* an agent's state became NaN/inf */
     GP_DEV_CLIP_OVERFLOW = 1u << 1,   /* internal clip capacity exceeded (image may be incomplete) */
+    GP_DEV_PIPELINE_TIMEOUT = 1u << 2, /* a pipelined render block gave up waiting for its other
+                                          side after 2 s and left its items unfinished */
     GP_DEV_INJECTED = 1u << 31        /* set by gp_debug_inject_status */
 };
 
@@ -114,6 +116,10 @@ typedef struct gp_config {
     int32_t band_rows;            /* rows per screen band (1..128), 0 = auto */
     int32_t threads;              /* render threads per block, 0 = auto */
     int32_t tri_capacity;         /* triangles per raster batch, 0 = auto */
+    int32_t producer_warps;       /* pipelined render: warps per block that cull, set up and
+                                     clip while the others rasterise (double-buffered batches);
+                                     0 = auto (the autotuner may pick it; off otherwise),
+                                     -1 = off, n > 0 = on with n warps */
 } gp_config;
 
 /* Fill `cfg` with the defaults above. */
@@ -188,6 +194,7 @@ typedef struct gp_info {
     int32_t key_precision, output;
     int64_t out_bytes, depth_bytes;    /* bytes gp_render writes to out_dev / depth_dev */
     int32_t band_rows, threads, tri_capacity, blocks; /* chosen launch shape */
+    int32_t producer_warps;            /* 0 = one-phase-at-a-time render kernel */
 } gp_info;
 gp_status gp_get_info(gp_handle *h, gp_info *info);
 

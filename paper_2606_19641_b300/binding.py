@@ -19,7 +19,7 @@ GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ELIMIT, GP_EDEVICE, GP_ESTATE = 0, -1,
 KEY_F32, KEY_F16 = 0, 1
 OUT_CLASS_U8, OUT_ONEHOT_BF16 = 0, 1
 FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
-DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_INJECTED = 1, 2, 1 << 31
+DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
 
 TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,)),
@@ -52,7 +52,8 @@ class Config(ctypes.Structure):
                 ("key_precision", ctypes.c_int32), ("output", ctypes.c_int32),
                 ("norm_mean", ctypes.c_float * 4), ("norm_std", ctypes.c_float * 4),
                 ("autotune", ctypes.c_int32), ("band_rows", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("tri_capacity", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("tri_capacity", ctypes.c_int32),
+                ("producer_warps", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -62,7 +63,8 @@ class Info(ctypes.Structure):
                 ("key_precision", ctypes.c_int32), ("output", ctypes.c_int32),
                 ("out_bytes", ctypes.c_int64), ("depth_bytes", ctypes.c_int64),
                 ("band_rows", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("tri_capacity", ctypes.c_int32), ("blocks", ctypes.c_int32)]
+                ("tri_capacity", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("producer_warps", ctypes.c_int32)]
 
 
 class GigapixelError(RuntimeError):

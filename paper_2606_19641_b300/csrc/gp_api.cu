@@ -56,7 +56,7 @@ struct DevBuf {
 };
 
 struct Shape {
-    int threads = 512, band_rows = 32, tri_cap = 512, blocks = 0;
+    int threads = 512, band_rows = 32, tri_cap = 512, blocks = 0, prod_warps = 0;
     size_t smem = 0;
 };
 
@@ -176,10 +176,12 @@ bool finish_shape(gp_handle *h, Shape &s) {
     if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
     // a setup unit needs at most 32 batch slots; a clip job needs 6
     if (s.tri_cap < 64) return false;
+    // the pipelined kernel needs at least one producer and one consumer warp
+    if (s.prod_warps < 0 || (s.prod_warps > 0 && s.prod_warps >= s.threads / 32)) return false;
     s.smem = render_smem_bytes(c.width, s.band_rows, c.key_precision, s.threads, s.tri_cap,
-                               h->max_cl);
+                               h->max_cl, s.prod_warps);
     if (s.smem + 1024 > smem_limit(h->device)) return false;  // leave room for static smem
-    const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem);
+    const int per_sm = render_occupancy(c.key_precision, s.threads, s.smem, s.prod_warps);
     if (per_sm < 1) return false;
     s.blocks = per_sm * h->sms;
     return true;
@@ -193,6 +195,7 @@ Shape default_shape(gp_handle *h) {
         Shape s;
         s.threads = c.threads ? c.threads : 256;
         s.tri_cap = c.tri_capacity ? c.tri_capacity : std::max(1024, 2 * s.threads);
+        s.prod_warps = c.producer_warps > 0 ? c.producer_warps : 0;
         s.band_rows = c.band_rows ? c.band_rows : r;
         if (!finish_shape(h, s)) {
             if (c.band_rows) break;
@@ -241,6 +244,7 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     std::memcpy(p.onehot, h->onehot, sizeof(p.onehot));
     p.tri_cap = h->shape.tri_cap;
     p.max_cl = h->max_cl;
+    p.prod_warps = h->shape.prod_warps;
     p.status = h->status.p;
     p.dump_view = -1;
     return p;
@@ -318,7 +322,7 @@ std::string cache_key(gp_handle *h) {
     return k.str();
 }
 
-// Flat JSON object of "key": "threads,band_rows,tri_cap" strings.
+// Flat JSON object of "key": "threads,band_rows,tri_cap,producer_warps" strings.
 std::map<std::string, std::string> read_cache(const char *path) {
     std::map<std::string, std::string> m;
     std::ifstream f(path);
@@ -362,8 +366,9 @@ gp_status autotune(gp_handle *h) {
         auto it = m.find(key);
         if (it != m.end()) {
             Shape s;
-            if (std::sscanf(it->second.c_str(), "%d,%d,%d", &s.threads, &s.band_rows, &s.tri_cap) == 3 &&
-                finish_shape(h, s)) {
+            const int got = std::sscanf(it->second.c_str(), "%d,%d,%d,%d", &s.threads,
+                                        &s.band_rows, &s.tri_cap, &s.prod_warps);
+            if ((got == 3 || got == 4) && finish_shape(h, s)) {
                 h->shape = s;
                 return GP_OK;
             }
@@ -390,12 +395,24 @@ gp_status autotune(gp_handle *h) {
     const int rows[] = {8, 16, 32, 48, 64, 128};
     for (int t : thr)
         for (int cap : caps)
-            for (int r : rows) {
+            for (int r : rows)
+                for (int pk = 0; pk < 3; ++pk) {
+                // producer warps: the configured count, else none, a quarter or three
+                // eighths of the block's warps
+                int pw;
+                if (c.producer_warps > 0) {
+                    if (pk > 0) continue;
+                    pw = c.producer_warps;
+                } else {
+                    pw = pk == 0 ? 0 : (pk == 1 ? t / 128 : 3 * t / 256);
+                    if (c.producer_warps < 0 && pw > 0) continue;
+                }
                 if (r > c.height && r != rows[0]) continue;
                 Shape s;
                 s.threads = t;
                 s.tri_cap = cap;
                 s.band_rows = r;
+                s.prod_warps = pw;
                 if (!finish_shape(h, s)) continue;
                 std::vector<int2> items;
                 build_items(h, s.band_rows, items);
@@ -433,7 +450,8 @@ gp_status autotune(gp_handle *h) {
     if (cache_path) {
         auto m = read_cache(cache_path);
         char buf[64];
-        std::snprintf(buf, sizeof buf, "%d,%d,%d", best.threads, best.band_rows, best.tri_cap);
+        std::snprintf(buf, sizeof buf, "%d,%d,%d,%d", best.threads, best.band_rows, best.tri_cap,
+                      best.prod_warps);
         m[key] = buf;
         write_cache(cache_path, m);
     }
@@ -888,6 +906,7 @@ gp_status gp_get_info(gp_handle *h, gp_info *info) {
     info->threads = h->shape.threads;
     info->tri_capacity = h->shape.tri_cap;
     info->blocks = h->shape.blocks;
+    info->producer_warps = h->shape.prod_warps;
     return GP_OK;
 }
 

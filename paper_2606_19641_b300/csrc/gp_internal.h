@@ -83,6 +83,7 @@ struct RenderParams {
 
     int tri_cap;             // triangles per raster batch
     int max_cl;              // most culling clusters in any world of the batch
+    int prod_warps;          // > 0: pipelined kernel with this many producer warps
     uint32_t *status;
 
     int dump_view;           // -1 = off
@@ -93,7 +94,8 @@ struct RenderParams {
 
 // Shared-memory bytes the render kernel needs for a launch shape (max_cl: most culling
 // clusters in any world of the batch).
-size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl);
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl,
+                         int prod_warps);
 
 cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
 cudaError_t launch_state(float *state, uint8_t *flags, float4 *pose, float *speed, uint8_t *fl,
@@ -101,6 +103,6 @@ cudaError_t launch_state(float *state, uint8_t *flags, float4 *pose, float *spee
 cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,
                           cudaStream_t s);
 cudaError_t render_configure(size_t max_smem);
-int render_occupancy(int key_f16, int threads, size_t smem);
+int render_occupancy(int key_f16, int threads, size_t smem, int prod_warps);
 
 }  // namespace gpk

@@ -75,26 +75,31 @@ struct Smem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Shared memory of a block.  The raster bookkeeping (rowoff, map) and the clip scratch
-// are live in different phases and share one region.
+// Shared memory of a block.  In the one-phase-at-a-time kernel the raster bookkeeping
+// (rowoff, map) and the clip scratch are live in different phases and share one region; the
+// pipelined kernel (prod_warps > 0) keeps them apart and double-buffers the batch.
 __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, int threads,
-                                            int tri_cap, int max_cl) {
+                                            int tri_cap, int max_cl, int prod_warps) {
     Smem s;
     size_t o = 0;
     s.keys = o;
     o += (size_t)W * band_rows * (key_f16 ? 4 : 8);
     o = align_up(o, 16);
     s.tris = o;
-    o += (size_t)tri_cap * sizeof(TriRec);
+    o += (size_t)(prod_warps ? 2 : 1) * tri_cap * sizeof(TriRec);
     const size_t shared_base = o;
+    const int raster_threads = threads - 32 * prod_warps;
+    const int clip_warps = prod_warps ? prod_warps : threads / 32;
     s.rowoff = o;
     o += (size_t)(tri_cap + 1) * 4;
     o = align_up(o, 16);
     s.map = o;
-    o += (size_t)threads * kItemsPerThread * 2;
+    o += (size_t)raster_threads * kItemsPerThread * 2;
     o = align_up(o, 16);
-    s.clipscratch = shared_base;  // per warp: 4 jobs x 8 vertices x 3 floats
-    const size_t clip_end = shared_base + (size_t)(threads / 32) * 4 * 24 * 4;
+    // per clipping warp: 4 jobs x 8 vertices x 3 floats; shares space with the raster
+    // bookkeeping unless both sides run at once (pipelined kernel)
+    s.clipscratch = prod_warps ? o : shared_base;
+    const size_t clip_end = s.clipscratch + (size_t)clip_warps * 4 * 24 * 4;
     o = clip_end > o ? clip_end : o;
     o = align_up(o, 16);
     s.vq0 = o;  // first quad of each visible cluster
@@ -413,9 +418,27 @@ __device__ __forceinline__ int warp_append(bool keep, int *counter) {
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
-// Block-wide exclusive scan of per-thread sums (all threads call; returns own prefix).
-__device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Consecutive warps of the block that synchronise among themselves on one hardware
+// barrier: the whole block (barrier 0), or one side of the pipelined kernel.
+struct Group {
+    int tid, nt, bar;  // thread index within the group, group size (multiple of 32), barrier id
+    __device__ __forceinline__ int warp() const { return tid >> 5; }
+    __device__ __forceinline__ int nw() const { return nt >> 5; }
+    // The barrier instruction requires each warp to arrive converged: for a named barrier,
+    // reconverge first and use the compiler's barrier intrinsic, which keeps it converged.
+    __device__ __forceinline__ void sync() const {
+        if (bar == 0) {
+            __syncthreads();
+        } else {
+            __syncwarp();
+            __barrier_sync_count((unsigned)bar, (unsigned)nt);
+        }
+    }
+};
+
+// Group-wide exclusive scan of per-thread sums (all group threads call; returns own prefix).
+__device__ __forceinline__ int group_exclusive_scan(int v, int *s_warp, int &total, const Group &g) {
+    const int lane = g.tid & 31, warp = g.warp(), nw = g.nw();
     int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -423,7 +446,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &tot
         if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
+    g.sync();
     if (warp == 0) {
         int w = lane < nw ? s_warp[lane] : 0;
 #pragma unroll
@@ -433,16 +456,16 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &tot
         }
         if (lane < nw) s_warp[lane] = w;  // inclusive prefix of warp totals
     }
-    __syncthreads();
+    g.sync();
     total = s_warp[nw - 1];
     const int before = warp > 0 ? s_warp[warp - 1] : 0;
-    __syncthreads();
+    g.sync();
     return before + x - v;
 }
 
-// Block-wide exclusive max-scan of per-thread values (0 for thread 0).
-__device__ __forceinline__ int block_exclusive_max(int v, int *s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Group-wide exclusive max-scan of per-thread values (0 for thread 0).
+__device__ __forceinline__ int group_exclusive_max(int v, int *s_warp, const Group &g) {
+    const int lane = g.tid & 31, warp = g.warp(), nw = g.nw();
     int x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -450,7 +473,7 @@ __device__ __forceinline__ int block_exclusive_max(int v, int *s_warp) {
         if (lane >= o) x = max(x, y);
     }
     if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
+    g.sync();
     if (warp == 0) {
         int w = lane < nw ? s_warp[lane] : 0;
 #pragma unroll
@@ -460,43 +483,44 @@ __device__ __forceinline__ int block_exclusive_max(int v, int *s_warp) {
         }
         if (lane < nw) s_warp[lane] = w;
     }
-    __syncthreads();
+    g.sync();
     const int prev_lane = __shfl_up_sync(0xffffffffu, x, 1);
     const int before_warp = warp > 0 ? s_warp[warp - 1] : 0;
-    __syncthreads();
+    g.sync();
     return lane > 0 ? max(before_warp, prev_lane) : before_warp;
 }
 
+// Block state of the setup side (the whole block, or the producer warps).
 struct Shared {
     int item, resv, next_unit, npend, nvcl, nvbox, cq_n;
-    int warp[32];
 };
 
-// Rasterise the current batch of triangles into the band's key buffer.
+// Rasterise a batch of n triangles into the key buffer of the band of rows by0..by1 (all
+// threads of group g call; ends with a group barrier).
 template <bool F32>
-__device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *keys, TriRec *tris,
-                      int *rowoff, unsigned short *map) {
-    const int n = min(sh.resv, p.tri_cap);
-    const int tid = threadIdx.x, nt = blockDim.x;
+__device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys, TriRec *tris,
+                      int *rowoff, unsigned short *map, int *s_warp, const Group &g) {
+    n = min(n, p.tri_cap);
+    const int tid = g.tid, nt = g.nt;
     // row counts -> exclusive scan (each thread owns a contiguous slice of triangles)
     const int per = (n + nt - 1) / nt;
     const int t0 = min(tid * per, n), t1 = min(t0 + per, n);
     int local = 0;
     for (int t = t0; t < t1; ++t) local += tri_items(tris[t].span);
     int total = 0;
-    int run = block_exclusive_scan(local, sh.warp, total);
+    int run = group_exclusive_scan(local, s_warp, total, g);
     for (int t = t0; t < t1; ++t) {
         rowoff[t] = run;
         run += tri_items(tris[t].span);
     }
     if (tid == 0) rowoff[n] = total;
-    __syncthreads();
+    g.sync();
 
     const int chunk = nt * kItemsPerThread;
     for (int start = 0; start < total; start += chunk) {
         const int len = min(chunk, total - start);
         for (int i = tid; i < len; i += nt) map[i] = 0;
-        __syncthreads();
+        g.sync();
         for (int t = tid; t < n; t += nt) {
             const int o = rowoff[t], c = rowoff[t + 1] - o;
             if (c > 0) {
@@ -504,7 +528,7 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
                 else if (o < start && o + c > start) map[0] = (unsigned short)t;
             }
         }
-        __syncthreads();
+        g.sync();
         // max-scan of the head map: every item gets the triangle it belongs to (heads are
         // increasing with position, so the running maximum is the latest head)
         const int m0 = tid * kItemsPerThread;
@@ -512,7 +536,7 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k)
             if (m0 + k < len) own = max(own, (int)map[m0 + k]);
-        int cur = block_exclusive_max(own, sh.warp);
+        int cur = group_exclusive_max(own, s_warp, g);
 #pragma unroll
         for (int k = 0; k < kItemsPerThread; ++k) {
             if (m0 + k < len) {
@@ -520,7 +544,7 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
                 map[m0 + k] = (unsigned short)cur;
             }
         }
-        __syncthreads();
+        g.sync();
         // Consecutive items (the rows of one triangle) go to different warps, so a large
         // triangle is spread over the block instead of holding up one warp.
         const int nw = nt >> 5, mine = (tid & 31) * nw + (tid >> 5);
@@ -535,15 +559,15 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
                 const uint32_t sp = T.span;
                 const int nwin = tri_windows(sp), k = start + i - rowoff[t];
                 const int r = nwin == 1 ? k : k / nwin, wdx = k - r * nwin;
-                const int row = cm.by0 + span_j0(sp) + r;
+                const int row = by0 + span_j0(sp) + r;
                 int lo = span_i0(sp) + wdx * kSpanWindow;
                 int hi = min(lo + kSpanWindow - 1, span_i1(sp));
-                if (row >= cm.by0 && row <= cm.by1 && lo >= 0 && hi < p.W) {
+                if (row >= by0 && row <= by1 && lo >= 0 && hi < p.W) {
                     row_span(T, row, lo, hi);
                     if (lo <= hi) {
                         const int X0 = vtx_x(T.xy[0]), Y0 = vtx_y(T.xy[0]);
                         cnt = hi - lo + 1;
-                        kofs = (row - cm.by0) * p.W + lo;
+                        kofs = (row - by0) * p.W + lo;
                         gx0 = 16 * lo + 8 - X0;
                         a = T.a;
                         inner = __fmaf_rn(T.b, (float)(16 * row + 8 - Y0), T.d0);
@@ -553,10 +577,8 @@ __device__ void flush(const RenderParams &p, const Cam &cm, Shared &sh, void *ke
             }
             warp_fragments<F32>(cnt, kofs, gx0, a, inner, low, keys);
         }
-        __syncthreads();
+        g.sync();
     }
-    if (tid == 0) sh.resv = 0;
-    __syncthreads();
 }
 
 // World-space vertices and primitive id of a source triangle.
@@ -602,10 +624,10 @@ __device__ __forceinline__ void empty_rec(TriRec &r) { r.span = 1u; }  // i0 = 1
 // crosses (interpolated from the inside vertex), in edge order -- Sutherland-Hodgman --
 // and the segment compacts the outputs through shared scratch.  The polygon is then
 // fan-triangulated from its first vertex, one fan triangle per lane, into slots[6 j ..).
-// Called by all threads of the block for jobs [0, njobs) of `jobs`.
+// Called by all threads of group grp for jobs [0, njobs) of `jobs`.
 __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const uint32_t *jobs,
-                          int njobs, TriRec *slots, float *scratch) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                          int njobs, TriRec *slots, float *scratch, const Group &grp) {
+    const int lane = grp.tid & 31, warp = grp.warp(), nw = grp.nw();
     const int g = lane >> 3, gl = lane & 7, seg0 = lane & ~7;
     const unsigned int segmask = 0xFFu << seg0, lt = (1u << lane) - 1u;
     float *sc = scratch + (warp * 4 + g) * 24;  // 8 vertices x (x, y, z) per segment
@@ -884,12 +906,12 @@ __device__ __forceinline__ void store_classes(const RenderParams &p, long long s
 // and writes the matching adjacent outputs, so a warp's stores cover contiguous sectors.
 // FP32 mode: one 64-bit key per pixel, FP32 depth bits above the inverted primitive id.
 __device__ void encode_f32(const RenderParams &p, const Cam &cm, unsigned long long *keys,
-                           int view) {
+                           int view, const Group &g) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
     const long long row0 = (long long)cm.by0 * p.W;
-    for (int b = 4 * threadIdx.x; b < band_px; b += 4 * blockDim.x) {
+    for (int b = 4 * g.tid; b < band_px; b += 4 * g.nt) {
         const ulonglong2 k01 = *(const ulonglong2 *)(keys + b);
         const ulonglong2 k23 = *(const ulonglong2 *)(keys + b + 2);
         *(ulonglong2 *)(keys + b) = make_ulonglong2(0ull, 0ull);
@@ -907,12 +929,13 @@ __device__ void encode_f32(const RenderParams &p, const Cam &cm, unsigned long l
 }
 
 // FP16 mode: one key per pixel, binary16 depth bits above the inverted primitive id.
-__device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *keys, int view) {
+__device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *keys, int view,
+                           const Group &g) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
     const long long row0 = (long long)cm.by0 * p.W;
-    for (int b = 4 * threadIdx.x; b < band_px; b += 4 * blockDim.x) {
+    for (int b = 4 * g.tid; b < band_px; b += 4 * g.nt) {
         const uint4 k = *(const uint4 *)(keys + b);
         *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
         const uint32_t c[4] = {class_of_low(k.x & 0xFFFFu, 0xFFFFu, cm), class_of_low(k.y & 0xFFFFu, 0xFFFFu, cm),
@@ -924,189 +947,414 @@ __device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *k
     }
 }
 
+// Camera and band of a work item.
+__device__ __forceinline__ void make_cam(const RenderParams &p, int item, Cam &cm, WorldInfo &wi,
+                                         int &view) {
+    const int2 wv = p.items[p.item_begin + item];
+    view = wv.x;
+    const int band = wv.y;
+    const int agent = view / p.n_cams, cam = view - agent * p.n_cams;
+    wi = p.worlds[p.agent_world[agent]];
+    cm.ego = agent - wi.agent_begin;
+    cm.box_begin = wi.box_begin;
+    cm.cl_begin = wi.cl_begin;
+    cm.box_end = wi.box_end;
+    cm.road_end = wi.road_end;
+    const float4 pose = p.box_pose[wi.box_begin + cm.ego];
+    cm.px = pose.x;
+    cm.py = pose.y;
+    sincosf(pose.z + p.cam_yaw[cam], &cm.s, &cm.c);
+    cm.by0 = band * p.band_rows;
+    cm.by1 = min(cm.by0 + p.band_rows, p.H) - 1;
+    cm.gtx = __fmul_rn(p.guard, p.tx);
+    cm.gty = __fmul_rn(p.guard, p.ty);
+    // pixel centres of the band lie in x in [0.5, W - 0.5], y in [by0 + 0.5, by1 + 0.5];
+    // a 1/4 px margin covers snapping (at most 1/32 px) and rounding
+    cm.vl = (0.5f * (float)p.W - 0.25f) / p.f;
+    cm.vt = (0.5f * (float)p.H - (float)cm.by0 - 0.25f) / p.f;
+    cm.vb = (0.5f * (float)p.H - (float)cm.by1 - 0.75f) / p.f;
+}
+
+// Take the next work item (thread 0 of g) and reset the setup state; all of g call.
+__device__ __forceinline__ int next_item(const RenderParams &p, Shared &sh, int iter, const Group &g) {
+    if (g.tid == 0) {
+        int it;
+        if (p.work_counter) it = atomicAdd(p.work_counter, 1);
+        else it = iter == 0 ? (int)blockIdx.x : p.n_items;
+        sh.item = it;
+        sh.resv = 0;
+        sh.next_unit = 0;
+        sh.npend = 0;
+        sh.nvcl = 0;
+        sh.nvbox = 0;
+        sh.cq_n = 0;
+    }
+    g.sync();
+    return sh.item;
+}
+
+// Shared memory of the setup side.
+struct SetupMem {
+    TriRec *tris;  // batch being filled
+    uint32_t *clipq;
+    float *clipscratch;
+    int *vq0;
+    unsigned char *vnq, *visbox;
+};
+
+// Cull, set up and clip one (view, band) work item on group g.  Kept triangles fill the
+// current batch m.tris[0, sh.resv).  emit(last) hands the batch over -- whenever it is
+// full, and once with last = true when the item is done (that batch may be empty) -- and
+// returns the batch to fill next, or nullptr to abandon the item; all threads of g call it
+// after a group barrier, and it ends with one.  Returns false if the item was abandoned.
+template <class Emit>
+__device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int view,
+                             Shared &sh, SetupMem &m, const Group &g, Emit &emit) {
+    // 1. cull clusters and boxes against the band frustum
+    for (int base = 0; base < wi.n_cl; base += g.nt) {
+        const int c = base + g.tid;
+        bool keep = false;
+        Cluster cl{};
+        if (c < wi.n_cl) {
+            cl = p.clusters[wi.cl_begin + c];
+            keep = aabb_visible(p, cm, cl.cx, cl.cy, cl.hx, cl.hy, cl.zlo, cl.zhi);
+        }
+        const int k = warp_append(keep, &sh.nvcl);
+        if (keep) {  // the cluster's quad range, so setup needs no further lookup
+            m.vq0[k] = cl.q0;
+            m.vnq[k] = (unsigned char)cl.nq;
+        }
+    }
+    for (int base = 0; base < wi.n_boxes; base += g.nt) {
+        const int b = base + g.tid;
+        bool keep = false;
+        if (b < wi.n_boxes && b != cm.ego) {
+            const float4 bp = p.box_pose[wi.box_begin + b];
+            const float4 bd = p.box_dim[wi.box_begin + b];
+            float s, c;
+            sincosf(bp.z, &s, &c);
+            const float hx = 0.5f * (fabsf(c) * bd.x + fabsf(s) * bd.y);
+            const float hy = 0.5f * (fabsf(s) * bd.x + fabsf(c) * bd.y);
+            keep = aabb_visible(p, cm, bp.x, bp.y, hx * 1.0001f + 1e-4f, hy * 1.0001f + 1e-4f,
+                                -1e-4f, bd.z + 1e-4f);
+        }
+        const int k = warp_append(keep, &sh.nvbox);
+        if (keep) m.visbox[k] = (unsigned char)b;
+    }
+    g.sync();
+
+    // 2. setup: warps pull units until the units run out or the batch is full; then the
+    //    batch is handed over; repeat until every unit is placed.
+    const int nbox_items = sh.nvbox * 6;  // one box face (two triangles) per lane
+    const int n_box_units = (nbox_items + 31) / 32;
+    const int n_units = n_box_units + sh.nvcl;
+    int pend = -1;            // unit this warp could not place (warp-uniform)
+    bool pend_clips = false;  // its clip jobs are already queued
+    for (;;) {
+        for (;;) {
+            int u;
+            bool done_clips = false;
+            if (pend >= 0) {
+                u = pend;
+                done_clips = pend_clips;
+                pend = -1;
+            } else {
+                u = 0;
+                if ((g.tid & 31) == 0) u = atomicAdd(&sh.next_unit, 1);
+                u = __shfl_sync(0xffffffffu, u, 0);
+            }
+            if (u >= n_units) break;
+            bool queued = false;
+            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vnq, m.visbox, view, u,
+                            n_box_units, nbox_items, done_clips, queued)) {
+                pend = u;
+                pend_clips = queued;
+                if ((g.tid & 31) == 0) atomicAdd(&sh.npend, 1);
+                break;
+            }
+        }
+        g.sync();
+        // clip the queued triangles (8 lanes per job), handing the batch over when full
+        for (;;) {
+            const int nq = sh.cq_n, rv = sh.resv;
+            if (nq == 0) break;
+            const int room = (p.tri_cap - rv) / 6;
+            if (room == 0) {
+                m.tris = emit(false);
+                if (!m.tris) return false;
+                continue;
+            }
+            const int take = min(nq, room);
+            clip_jobs(p, cm, view, m.clipq + (nq - take), take, m.tris + rv, m.clipscratch, g);
+            g.sync();
+            if (g.tid == 0) {
+                sh.cq_n = nq - take;
+                sh.resv = rv + 6 * take;
+            }
+            g.sync();
+        }
+        const bool more = sh.next_unit < n_units || sh.npend > 0;
+        const bool full = sh.resv > 0;
+        g.sync();
+        if (g.tid == 0) sh.npend = 0;
+        if (!more) {
+            m.tris = emit(true);
+            return m.tris != nullptr;
+        }
+        if (full) {
+            m.tris = emit(false);
+            if (!m.tris) return false;
+        } else {
+            g.sync();
+        }
+    }
+}
+
+// One block does everything for its items: setup, then raster of each full batch, then
+// the encode of the band.
 template <bool F32>
 __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, nt, p.tri_cap, p.max_cl);
+    __shared__ int s_warp[32];
+    const Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, g.nt, p.tri_cap, p.max_cl, 0);
     unsigned int *keys = (unsigned int *)(smem + L.keys);  // 8 B per pixel (FP32) or 4 B
     TriRec *tris = (TriRec *)(smem + L.tris);
     int *rowoff = (int *)(smem + L.rowoff);
     unsigned short *map = (unsigned short *)(smem + L.map);
-    int *vq0 = (int *)(smem + L.vq0);
-    unsigned char *vnq = smem + L.vnq;
-    unsigned char *visbox = (unsigned char *)(smem + L.visbox);
-    uint32_t *clipq = (uint32_t *)(smem + L.clipq);
-    float *clipscratch = (float *)(smem + L.clipscratch);
+    SetupMem m{tris, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
+               (int *)(smem + L.vq0), smem + L.vnq, smem + L.visbox};
 
-    for (int b = tid; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += nt) keys[b] = 0;
+    for (int b = g.tid; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += g.nt) keys[b] = 0;
 
+    Cam cm;
+    WorldInfo wi;
+    int view = 0;
+    auto emit = [&](bool last) -> TriRec * {
+        const int n = sh.resv;
+        if (n > 0) flush<F32>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, s_warp, g);
+        if (g.tid == 0) sh.resv = 0;
+        g.sync();
+        if (last) {  // 3. encode and store the band
+            if (F32) encode_f32(p, cm, (unsigned long long *)keys, view, g);
+            else encode_f16(p, cm, keys, view, g);
+            g.sync();
+        }
+        return tris;
+    };
     for (int iter = 0;; ++iter) {
-        if (tid == 0) {
-            int it;
-            if (p.work_counter) it = atomicAdd(p.work_counter, 1);
-            else it = iter == 0 ? (int)blockIdx.x : p.n_items;
-            sh.item = it;
-            sh.resv = 0;
-            sh.next_unit = 0;
-            sh.npend = 0;
-            sh.nvcl = 0;
-            sh.nvbox = 0;
-            sh.cq_n = 0;
-        }
-        __syncthreads();
-        const int item = sh.item;
+        const int item = next_item(p, sh, iter, g);
         if (item >= p.n_items) break;
-        const int2 wv = p.items[p.item_begin + item];
-        const int view = wv.x, band = wv.y;
-        const int agent = view / p.n_cams, cam = view - agent * p.n_cams;
-        const WorldInfo wi = p.worlds[p.agent_world[agent]];
+        make_cam(p, item, cm, wi, view);
+        produce_item(p, cm, wi, view, sh, m, g, emit);
+    }
+}
+
+// What a raster batch of the pipelined kernel carries besides its triangles.
+struct BatchMeta {
+    int n, view, by0, by1;
+    uint32_t box_end, road_end;
+    int flags;  // kBatchLast: the item's last batch (encode after it); kBatchEnd: no more work
+};
+constexpr int kBatchLast = 1, kBatchEnd = 2;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // a handoff wait gives up after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];"
+                 : "=l"(state)
+                 : "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait until the phase of parity `parity` of an mbarrier completes; false (and a status bit)
+// if it does not within kWaitNs.  Warp-collective: all 32 lanes call it, poll in lock step
+// and return the same answer together, so the warp leaves converged.
+__device__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t *status) {
+    bool done = mbar_try_wait(bar, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        done = done || mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        const bool late = global_ns() - t0 > kWaitNs;
+        if (__shfl_sync(0xffffffffu, late, 0)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(status, GP_DEV_PIPELINE_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Pipelined variant: the first p.prod_warps warps (producers) cull, set up and clip; the
+// other warps (consumers) rasterise and encode.  Two triangle batches alternate between
+// them: the producers fill one while the consumers rasterise the other.  Batch s lives in
+// buffer s & 1; full[b] completes when the producers have written a batch into buffer b,
+// empty[b] when the consumers are done with it.  Each side synchronises internally on its
+// own hardware barrier (1 producers, 2 consumers).  Every handoff wait is bounded: on a
+// timeout the side records it, sets GP_DEV_PIPELINE_TIMEOUT and leaves as a whole, and the
+// other side then times out too.
+template <bool F32>
+__global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    __shared__ int s_warp[32];
+    __shared__ BatchMeta meta[2];
+    __shared__ __align__(8) unsigned long long bars[4];  // full[0], full[1], empty[0], empty[1]
+    __shared__ int gave_up[3];  // producers; consumers, by parity of the batch they waited for
+    const int nprod = 32 * p.prod_warps, ncons = (int)blockDim.x - nprod;
+    const Smem L = smem_layout(p.W, p.band_rows, p.key_f16, blockDim.x, p.tri_cap, p.max_cl,
+                               p.prod_warps);
+    unsigned int *keys = (unsigned int *)(smem + L.keys);
+    TriRec *tris0 = (TriRec *)(smem + L.tris);  // two batches of tri_cap records
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], nprod);
+        mbar_init(&bars[1], nprod);
+        mbar_init(&bars[2], ncons);
+        mbar_init(&bars[3], ncons);
+        gave_up[0] = 0;
+        gave_up[1] = 0;
+        gave_up[2] = 0;
+    }
+    for (int b = threadIdx.x; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += blockDim.x) keys[b] = 0;
+    __syncthreads();
+
+    if ((int)threadIdx.x < nprod) {
+        const Group g{(int)threadIdx.x, nprod, 1};
+        SetupMem m{tris0, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
+                   (int *)(smem + L.vq0), smem + L.vnq, smem + L.visbox};
         Cam cm;
-        cm.ego = agent - wi.agent_begin;
-        cm.box_begin = wi.box_begin;
-        cm.cl_begin = wi.cl_begin;
-        cm.box_end = wi.box_end;
-        cm.road_end = wi.road_end;
-        const float4 pose = p.box_pose[wi.box_begin + cm.ego];
-        cm.px = pose.x;
-        cm.py = pose.y;
-        sincosf(pose.z + p.cam_yaw[cam], &cm.s, &cm.c);
-        cm.by0 = band * p.band_rows;
-        cm.by1 = min(cm.by0 + p.band_rows, p.H) - 1;
-        cm.gtx = __fmul_rn(p.guard, p.tx);
-        cm.gty = __fmul_rn(p.guard, p.ty);
-        // pixel centres of the band lie in x in [0.5, W - 0.5], y in [by0 + 0.5, by1 + 0.5];
-        // a 1/4 px margin covers snapping (at most 1/32 px) and rounding
-        cm.vl = (0.5f * (float)p.W - 0.25f) / p.f;
-        cm.vt = (0.5f * (float)p.H - (float)cm.by0 - 0.25f) / p.f;
-        cm.vb = (0.5f * (float)p.H - (float)cm.by1 - 0.75f) / p.f;
-
-        // 1. cull clusters and boxes against the band frustum
-        for (int base = 0; base < wi.n_cl; base += nt) {
-            const int c = base + tid;
-            bool keep = false;
-            Cluster cl{};
-            if (c < wi.n_cl) {
-                cl = p.clusters[wi.cl_begin + c];
-                keep = aabb_visible(p, cm, cl.cx, cl.cy, cl.hx, cl.hy, cl.zlo, cl.zhi);
+        WorldInfo wi;
+        int view = 0;
+        int s = 0;  // batches published
+        auto emit = [&](bool last) -> TriRec * {
+            // every producer thread has read the batch state it acted on before thread 0
+            // changes it
+            g.sync();
+            const int b = s & 1;
+            if (g.tid == 0) {
+                meta[b] = BatchMeta{sh.resv, view, cm.by0, cm.by1, cm.box_end, cm.road_end,
+                                    last ? kBatchLast : 0};
+                sh.resv = 0;
             }
-            const int k = warp_append(keep, &sh.nvcl);
-            if (keep) {  // the cluster's quad range, so setup needs no further lookup
-                vq0[k] = cl.q0;
-                vnq[k] = (unsigned char)cl.nq;
+            mbar_arrive(&bars[b]);  // release: this thread's records (and thread 0's meta)
+            ++s;
+            const int nb = s & 1;
+            // batch s - 2 used buffer nb: wait until the consumers are done with it
+            if (s >= 2 && !mbar_wait(&bars[2 + nb], (uint32_t)(((s >> 1) - 1) & 1), p.status))
+                gave_up[0] = 1;
+            g.sync();
+            if (gave_up[0]) return nullptr;
+            return tris0 + (size_t)nb * p.tri_cap;
+        };
+        bool ok = true;
+        for (int iter = 0;; ++iter) {
+            const int item = next_item(p, sh, iter, g);
+            if (item >= p.n_items) break;
+            make_cam(p, item, cm, wi, view);
+            if (!produce_item(p, cm, wi, view, sh, m, g, emit)) {
+                ok = false;
+                break;
             }
         }
-        for (int base = 0; base < wi.n_boxes; base += nt) {
-            const int b = base + tid;
-            bool keep = false;
-            if (b < wi.n_boxes && b != cm.ego) {
-                const float4 bp = p.box_pose[wi.box_begin + b];
-                const float4 bd = p.box_dim[wi.box_begin + b];
-                float s, c;
-                sincosf(bp.z, &s, &c);
-                const float hx = 0.5f * (fabsf(c) * bd.x + fabsf(s) * bd.y);
-                const float hy = 0.5f * (fabsf(s) * bd.x + fabsf(c) * bd.y);
-                keep = aabb_visible(p, cm, bp.x, bp.y, hx * 1.0001f + 1e-4f, hy * 1.0001f + 1e-4f,
-                                    -1e-4f, bd.z + 1e-4f);
-            }
-            const int k = warp_append(keep, &sh.nvbox);
-            if (keep) visbox[k] = (unsigned char)b;
+        if (ok) {  // end marker; its buffer is free (emit waited for it)
+            if (g.tid == 0) meta[s & 1].flags = kBatchEnd;
+            mbar_arrive(&bars[s & 1]);
         }
-        __syncthreads();
-
-        // 2. setup: warps pull units until the units run out or the batch is full; then the
-        //    block rasterises the batch; repeat until every unit is placed.
-        const int nbox_items = sh.nvbox * 6;  // one box face (two triangles) per lane
-        const int n_box_units = (nbox_items + 31) / 32;
-        const int n_units = n_box_units + sh.nvcl;
-        int pend = -1;           // unit this warp could not place (warp-uniform)
-        bool pend_clips = false;  // its clip jobs are already queued
-        for (;;) {
-            for (;;) {
-                int u;
-                bool done_clips = false;
-                if (pend >= 0) {
-                    u = pend;
-                    done_clips = pend_clips;
-                    pend = -1;
-                } else {
-                    u = 0;
-                    if ((tid & 31) == 0) u = atomicAdd(&sh.next_unit, 1);
-                    u = __shfl_sync(0xffffffffu, u, 0);
-                }
-                if (u >= n_units) break;
-                bool queued = false;
-                if (!setup_unit(p, cm, sh, tris, clipq, vq0, vnq, visbox, view, u, n_box_units,
-                                nbox_items, done_clips, queued)) {
-                    pend = u;
-                    pend_clips = queued;
-                    if ((tid & 31) == 0) atomicAdd(&sh.npend, 1);
-                    break;
-                }
+    } else {
+        const Group g{(int)threadIdx.x - nprod, ncons, 2};
+        int *rowoff = (int *)(smem + L.rowoff);
+        unsigned short *map = (unsigned short *)(smem + L.map);
+        for (int s = 0;; ++s) {
+            const int b = s & 1;
+            // a flag per batch parity: a thread already waiting for batch s + 1 cannot change
+            // the flag the others still read for batch s
+            if (!mbar_wait(&bars[b], (uint32_t)((s >> 1) & 1), p.status)) gave_up[1 + b] = 1;
+            g.sync();
+            if (gave_up[1 + b]) break;
+            const BatchMeta mt = meta[b];
+            if (mt.flags & kBatchEnd) break;
+            if (mt.n > 0)
+                flush<F32>(p, mt.by0, mt.by1, mt.n, keys, tris0 + (size_t)b * p.tri_cap, rowoff,
+                           map, s_warp, g);
+            mbar_arrive(&bars[2 + b]);  // release: this thread is done reading buffer b
+            if (mt.flags & kBatchLast) {
+                Cam cm;
+                cm.by0 = mt.by0;
+                cm.by1 = mt.by1;
+                cm.box_end = mt.box_end;
+                cm.road_end = mt.road_end;
+                if (F32) encode_f32(p, cm, (unsigned long long *)keys, mt.view, g);
+                else encode_f16(p, cm, keys, mt.view, g);
+                g.sync();
             }
-            __syncthreads();
-            // clip the queued triangles (8 lanes per job), flushing when the batch is full
-            for (;;) {
-                const int nq = sh.cq_n, rv = sh.resv;
-                if (nq == 0) break;
-                const int room = (p.tri_cap - rv) / 6;
-                if (room == 0) {
-                    flush<F32>(p, cm, sh, keys, tris, rowoff, map);
-                    continue;
-                }
-                const int take = min(nq, room);
-                clip_jobs(p, cm, view, clipq + (nq - take), take, tris + rv, clipscratch);
-                __syncthreads();
-                if (tid == 0) {
-                    sh.cq_n = nq - take;
-                    sh.resv = rv + 6 * take;
-                }
-                __syncthreads();
-            }
-            const bool more = sh.next_unit < n_units || sh.npend > 0;
-            const bool full = sh.resv > 0;
-            __syncthreads();
-            if (tid == 0) sh.npend = 0;
-            if (full) flush<F32>(p, cm, sh, keys, tris, rowoff, map);
-            else __syncthreads();
-            if (!more) break;
         }
-
-        // 3. encode and store the band
-        if (F32) encode_f32(p, cm, (unsigned long long *)keys, view);
-        else encode_f16(p, cm, keys, view);
-        __syncthreads();
     }
 }
 
 }  // namespace
 
-size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl) {
-    return smem_layout(W, band_rows, key_f16, threads, tri_cap, max_cl).total;
+size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl,
+                         int prod_warps) {
+    return smem_layout(W, band_rows, key_f16, threads, tri_cap, max_cl, prod_warps).total;
 }
 
 cudaError_t render_configure(size_t max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(render_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(render_kernel<false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    const void *fns[4] = {(const void *)render_kernel<true>, (const void *)render_kernel<false>,
+                          (const void *)render_kernel_ws<true>, (const void *)render_kernel_ws<false>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)max_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-int render_occupancy(int key_f16, int threads, size_t smem) {
+static const void *render_fn(int key_f16, int prod_warps) {
+    if (prod_warps > 0)
+        return key_f16 ? (const void *)render_kernel_ws<false> : (const void *)render_kernel_ws<true>;
+    return key_f16 ? (const void *)render_kernel<false> : (const void *)render_kernel<true>;
+}
+
+int render_occupancy(int key_f16, int threads, size_t smem, int prod_warps) {
     int n = 0;
-    cudaError_t e = key_f16
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<false>, threads, smem)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, render_kernel<true>, threads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, render_fn(key_f16, prod_warps), threads, smem);
     return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,
                           cudaStream_t s) {
     if (p.n_items <= 0) return cudaSuccess;
-    if (p.key_f16) render_kernel<false><<<blocks, threads, smem, s>>>(p);
-    else render_kernel<true><<<blocks, threads, smem, s>>>(p);
+    if (p.prod_warps > 0) {
+        if (p.key_f16) render_kernel_ws<false><<<blocks, threads, smem, s>>>(p);
+        else render_kernel_ws<true><<<blocks, threads, smem, s>>>(p);
+    } else {
+        if (p.key_f16) render_kernel<false><<<blocks, threads, smem, s>>>(p);
+        else render_kernel<true><<<blocks, threads, smem, s>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -109,7 +109,11 @@ def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
 # ---------------------------------------------------------------------------------------
 
 SHAPES = [dict(), dict(band_rows=16), dict(band_rows=8, threads=128, tri_capacity=224),
-          dict(threads=1024, tri_capacity=1024), dict(band_rows=128, threads=256, tri_capacity=300)]
+          dict(threads=1024, tri_capacity=1024), dict(band_rows=128, threads=256, tri_capacity=300),
+          # pipelined kernel: producer warps set up batches while the rest rasterise
+          dict(producer_warps=4), dict(band_rows=8, threads=128, tri_capacity=224, producer_warps=1),
+          dict(threads=1024, tri_capacity=512, producer_warps=12),
+          dict(band_rows=128, threads=512, tri_capacity=300, producer_warps=6)]
 
 
 @pytest.mark.parametrize("shape", SHAPES,
@@ -125,6 +129,8 @@ def test_raster_bit_exact_for_gpu_triangles(name, n_worlds, shape):
         sim.step(torch_actions(worlds, k, wl.seed)[0])
     sim.render(out, depth)
     torch.cuda.synchronize()
+    assert sim.info.producer_warps == shape.get("producer_warps", 0)
+    assert sim.status() == 0
     views = list(range(0, sim.n_views, max(1, sim.n_views // 12)))
     covered = check_t3(sim, cfg, worlds, views, out, depth)
     assert covered > 0.2 * len(views) * cfg.width * cfg.height
@@ -193,11 +199,13 @@ def test_image_vs_fp64_pipeline(name, n_worlds):
     assert np.percentile(derr, 99) < 1e-2
 
 
-def test_precision_path_fp16_key_and_bf16_onehot():
+@pytest.mark.parametrize("shape", [dict(), dict(threads=512, tri_capacity=1024, producer_warps=4)],
+                         ids=["default", "pipelined"])
+def test_precision_path_fp16_key_and_bf16_onehot(shape):
     import torch
     wl = wg.WORKLOADS["ragged_precision"]
     worlds = wg.make_workload(wl, n_worlds=4)
-    sim, cfg = sim_for(worlds, wl)
+    sim, cfg = sim_for(worlds, wl, **shape)
     out, depth = sim.alloc_outputs()
     assert out.dtype == torch.bfloat16 and depth.dtype == torch.float16
     sim.step(torch_actions(worlds, 0, wl.seed)[0])
@@ -279,13 +287,14 @@ def test_edge_case_worlds():
 # Paths, state and status
 # ---------------------------------------------------------------------------------------
 
-def test_graph_and_per_world_paths_match_direct_calls():
+@pytest.mark.parametrize("shape", [dict(), dict(producer_warps=2)], ids=["default", "pipelined"])
+def test_graph_and_per_world_paths_match_direct_calls(shape):
     import torch
     wl = wg.WORKLOADS["ragged"]
     worlds = wg.make_workload(wl, n_worlds=6)
-    a, cfg = sim_for(worlds, wl)
-    b, _ = sim_for(worlds, wl)
-    c, _ = sim_for(worlds, wl)
+    a, cfg = sim_for(worlds, wl, **shape)
+    b, _ = sim_for(worlds, wl, **shape)
+    c, _ = sim_for(worlds, wl, **shape)
     oa, da = a.alloc_outputs()
     ob, db = b.alloc_outputs()
     oc, dc = c.alloc_outputs()
@@ -365,12 +374,14 @@ def test_status_word_injection_and_nonfinite_state():
 
 def test_full_size_uniform_batch_sampled():
     """The full uniform batch (256 worlds x 32 agents, 128x128) in the benchmark's launch
-    configuration (graph replay): sampled views are bit-exact against the raster rule and
-    within the FP64 mismatch bound; invariants hold on every view."""
+    configuration (autotuned launch shape, graph replay): sampled views are bit-exact against
+    the raster rule and within the FP64 mismatch bound; invariants hold on every view."""
     import torch
     wl = wg.WORKLOADS["uniform"]
     worlds = wg.make_workload(wl)
-    sim, cfg = sim_for(worlds, wl)
+    sim, cfg = sim_for(worlds, wl, autotune=1)
+    print("launch shape", sim.info.band_rows, sim.info.threads, sim.info.tri_capacity,
+          sim.info.producer_warps)
     out, depth = sim.alloc_outputs()
     act = torch.empty((worlds.n_agents, 2), device="cuda")
     for k in range(3):
@@ -386,3 +397,4 @@ def test_full_size_uniform_batch_sampled():
     assert torch.equal(out, out_copy) and torch.equal(depth, depth_copy)  # re-render identical
     frac, derr = t4_stats(sim, cfg, worlds, views, out, depth)
     assert frac < T4_MISMATCH
+    assert sim.status() == 0
