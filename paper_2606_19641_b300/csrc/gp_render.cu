@@ -70,7 +70,7 @@ struct Cam {
 };
 
 struct Smem {
-    size_t keys, tris, rowoff, map, clipscratch, vq0, vnq, visbox, clipq, total;
+    size_t keys, tris, rowoff, map, clipscratch, vq0, vpre, vnq, visbox, clipq, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -103,6 +103,8 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     o = clip_end > o ? clip_end : o;
     o = align_up(o, 16);
     s.vq0 = o;  // first quad of each visible cluster
+    o += (size_t)max_cl * 4;
+    s.vpre = o;  // visible quads before it (exclusive prefix of the counts)
     o += (size_t)max_cl * 4;
     s.vnq = o;  // its quad count
     o += (size_t)max_cl;
@@ -492,7 +494,7 @@ __device__ __forceinline__ int group_exclusive_max(int v, int *s_warp, const Gro
 
 // Block state of the setup side (the whole block, or the producer warps).
 struct Shared {
-    int item, resv, next_unit, npend, nvcl, nvbox, cq_n;
+    int item, resv, next_unit, npend, nvcl, nvbox, cq_n, nvq;
 };
 
 // Rasterise a batch of n triangles into the key buffer of the band of rows by0..by1 (all
@@ -658,6 +660,7 @@ __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const 
 #pragma unroll 1
         for (int k = 0; k < 5; ++k) {
             const bool do_k = active && n >= 3 && (planes & (1 << k));  // segment-uniform
+            if (!__any_sync(0xffffffffu, do_k)) continue;  // no job of this warp crosses plane k
             const float dk = plane_dist(p, k, x, y, z);
             const int nxt = seg0 + ((gl + 1 < n) ? gl + 1 : 0);
             const float xn = __shfl_sync(0xffffffffu, x, nxt);
@@ -773,12 +776,13 @@ __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm
     }
 }
 
-// One setup unit: 32 quads (box faces or ground quads), one per lane, two triangles each
+// One setup unit: 32 quads (box faces, or the visible clusters' ground quads packed back to
+// back), one per lane, two triangles each
 // (warp-uniform call).  Returns false if the clip queue or the batch has no room;
 // `clips_queued` tells the retry (after a flush) whether this unit's clip jobs are already
 // queued.
 __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
-                           uint32_t *clipq, const int *vq0, const unsigned char *vnq,
+                           uint32_t *clipq, const int *vq0, const int *vpre, int nvcl, int nvq,
                            const unsigned char *visbox, int view, int unit, int n_box_units,
                            int nbox_items, bool clips_done, bool &clips_queued) {
     const int lane = threadIdx.x & 31;
@@ -793,9 +797,17 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
             tcode = 0x80000000u | (b << 4) | (2u * face);
         }
     } else {
-        const int c = unit - n_box_units;
-        valid = lane < (int)vnq[c];
-        qcode = (uint32_t)(vq0[c] + lane);
+        // the visible clusters' quads, packed 32 per unit: find this lane's cluster (the
+        // last one whose first packed index is <= gq)
+        const int gq = (unit - n_box_units) * 32 + lane;
+        valid = gq < nvq;
+        int lo = 0, hi = nvcl - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (vpre[mid] <= gq) lo = mid;
+            else hi = mid - 1;
+        }
+        qcode = valid ? (uint32_t)(vq0[lo] + (gq - vpre[lo])) : 0u;
         tcode = qcode << 1;
     }
     bool keep0 = false, keep1 = false, clip0 = false, clip1 = false;
@@ -998,7 +1010,7 @@ struct SetupMem {
     TriRec *tris;  // batch being filled
     uint32_t *clipq;
     float *clipscratch;
-    int *vq0;
+    int *vq0, *vpre;
     unsigned char *vnq, *visbox;
 };
 
@@ -1042,12 +1054,32 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
         if (keep) m.visbox[k] = (unsigned char)b;
     }
     g.sync();
+    // packed positions of the visible clusters' quads (warp 0 scans the counts)
+    if (g.warp() == 0) {
+        const int lane = g.tid & 31, nv = sh.nvcl;
+        int run = 0;
+        for (int base = 0; base < nv; base += 32) {
+            const int c = base + lane;
+            const int v = c < nv ? (int)m.vnq[c] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (c < nv) m.vpre[c] = run + x - v;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) sh.nvq = run;
+    }
+    g.sync();
 
     // 2. setup: warps pull units until the units run out or the batch is full; then the
     //    batch is handed over; repeat until every unit is placed.
     const int nbox_items = sh.nvbox * 6;  // one box face (two triangles) per lane
     const int n_box_units = (nbox_items + 31) / 32;
-    const int n_units = n_box_units + sh.nvcl;
+    const int nvcl = sh.nvcl, nvq = sh.nvq;
+    const int n_units = n_box_units + (nvq + 31) / 32;
     int pend = -1;            // unit this warp could not place (warp-uniform)
     bool pend_clips = false;  // its clip jobs are already queued
     for (;;) {
@@ -1065,8 +1097,8 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
             }
             if (u >= n_units) break;
             bool queued = false;
-            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vnq, m.visbox, view, u,
-                            n_box_units, nbox_items, done_clips, queued)) {
+            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vpre, nvcl, nvq, m.visbox, view,
+                            u, n_box_units, nbox_items, done_clips, queued)) {
                 pend = u;
                 pend_clips = queued;
                 if ((g.tid & 31) == 0) atomicAdd(&sh.npend, 1);
@@ -1124,7 +1156,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     int *rowoff = (int *)(smem + L.rowoff);
     unsigned short *map = (unsigned short *)(smem + L.map);
     SetupMem m{tris, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
-               (int *)(smem + L.vq0), smem + L.vnq, smem + L.visbox};
+               (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
+               smem + L.visbox};
 
     for (int b = g.tid; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += g.nt) keys[b] = 0;
 
@@ -1244,7 +1277,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
     if ((int)threadIdx.x < nprod) {
         const Group g{(int)threadIdx.x, nprod, 1};
         SetupMem m{tris0, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
-                   (int *)(smem + L.vq0), smem + L.vnq, smem + L.visbox};
+                   (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
+               smem + L.visbox};
         Cam cm;
         WorldInfo wi;
         int view = 0;
