@@ -5,27 +5,30 @@
 //   1. cull: per-world clusters of ground quads and the world's boxes are tested as
 //      axis-aligned boxes against the band's frustum (left/right planes, near plane and the
 //      band's pixel-centre rows; conservative by 1/16 px for snapping);
-//   2. setup: warps pull units of 32 quads (a cluster of ground quads, or box faces) from
-//      a shared counter, with no block barrier between units.  Each lane transforms its
-//      quad's corners to view space and rejects a triangle if all three vertices lie
-//      beyond one plane through the eye (near, guard band, or the band's pixel-centre
-//      extent widened by 1/4 px); otherwise it projects, snaps to 1/16 px (round half to even),
-//      back-face culls and keeps the triangle if its snapped bounding box holds a pixel
-//      centre of the band.  A triangle crossing the near plane or the 4x guard band is
-//      queued and later clipped by an 8-lane warp segment (Sutherland-Hodgman, planes in
-//      the order near, left, right, bottom, top) and fan-triangulated.  A warp reserves batch slots for its unit with one
-//      atomic; when the batch is full the block rasterises it and continues;
-//   3. raster: kept triangles are expanded into (triangle, row, 64-pixel window) items,
-//      dealt out so that one triangle's rows land in different warps; each item computes
-//      the exact covered span of its row within the window from the integer edge functions
-//      (top-left fill rule); a warp then walks its spans' pixels -- each lane its own span
-//      when the spans are even, 32 fragments at a time when a few long spans dominate --
-//      and resolves depth per pixel in shared memory with atomicMax on a key: (FP32 depth
-//      bits << 32 | ~prim), or (binary16 depth << 16 | ~prim) in FP16 mode; the nearest
-//      surface wins, ties go to the smaller primitive id;
+//   2. setup: warps pull units of 32 quads (the visible clusters' ground quads packed back
+//      to back, or box faces) from a shared counter, with no block barrier between units.
+//      Each lane transforms its quad's corners to view space and rejects a triangle if all
+//      three vertices lie beyond one plane through the eye (near, guard band, or the band's
+//      pixel-centre extent widened by 1/4 px); otherwise it projects, snaps to 1/16 px
+//      (round half to even), back-face culls and keeps the triangle if its snapped bounding
+//      box holds a pixel centre of the band.  A triangle crossing the near plane or the 4x
+//      guard band is queued and later clipped by an 8-lane warp segment (Sutherland-Hodgman,
+//      planes in the order near, left, right, bottom, top) and fan-triangulated.  A warp
+//      reserves batch slots for its unit with one atomic; when the batch is full it is
+//      rasterised and setup continues;
+//   3. raster: kept triangles are expanded into (triangle, row) items, dealt out so that
+//      one triangle's rows land in different warps; each item computes the exact covered
+//      span of its row from the integer edge functions (top-left fill rule); a warp then
+//      walks its spans' pixels -- each lane its own span when the spans are even, 32
+//      fragments at a time when a few long spans dominate -- and resolves depth per pixel
+//      in shared memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or
+//      (binary16 depth << 16 | ~prim) in FP16 mode; the nearest surface wins, ties go to
+//      the smaller primitive id;
 //   4. encode: keys become class ids (uint8) + depth, or a normalised one-hot BF16 NCHW
 //      tensor; the band is one contiguous range of every output plane, written with 16-byte
 //      streaming stores.
+// A pipelined variant splits the block into producer warps (steps 1-2) and consumer warps
+// (steps 3-4) that hand double-buffered triangle batches to each other.
 // The depth plane d = d0 + a (X - X0) + b (Y - Y0) and its per-pixel evaluation follow a
 // fixed IEEE FP32 operation sequence (explicit _rn intrinsics), so identical snapped
 // triangles give bit-identical keys on any implementation that follows the same sequence.
@@ -39,7 +42,6 @@ namespace gpk {
 namespace {
 
 constexpr int kItemsPerThread = 8;  // raster items per thread per raster sub-pass
-constexpr int kSpanWindow = 64;     // pixels per raster item (a row is split into windows)
 constexpr int kClipQueue = 256;     // queued clip jobs per block
 
 // A triangle ready for raster.  The edge functions are rebuilt from the vertices per row;
@@ -284,13 +286,10 @@ __device__ __forceinline__ unsigned int key16(float d, uint32_t low) {
     return ((unsigned int)__half_as_ushort(__float2half_rn(d)) << 16) | low;
 }
 
-// Items of a triangle: rows x windows of kSpanWindow pixels of its bounding columns (none
-// for an empty slot, whose i1 < i0).
-__device__ __forceinline__ int tri_windows(uint32_t s) {
-    return (span_i1(s) - span_i0(s)) / kSpanWindow + 1;
-}
+// Raster items of a triangle: one per row of its bounding box (none for an empty slot,
+// whose i1 < i0).
 __device__ __forceinline__ int tri_items(uint32_t s) {
-    return span_i1(s) < span_i0(s) ? 0 : span_nj(s) * tri_windows(s);
+    return span_i1(s) < span_i0(s) ? 0 : span_nj(s);
 }
 
 // Exact covered span of one row of a triangle within columns [lo, hi] (narrowed in place;
@@ -559,11 +558,8 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
                 const int t = map[i];
                 const TriRec &T = tris[t];
                 const uint32_t sp = T.span;
-                const int nwin = tri_windows(sp), k = start + i - rowoff[t];
-                const int r = nwin == 1 ? k : k / nwin, wdx = k - r * nwin;
-                const int row = by0 + span_j0(sp) + r;
-                int lo = span_i0(sp) + wdx * kSpanWindow;
-                int hi = min(lo + kSpanWindow - 1, span_i1(sp));
+                const int row = by0 + span_j0(sp) + (start + i - rowoff[t]);
+                int lo = span_i0(sp), hi = span_i1(sp);
                 if (row >= by0 && row <= by1 && lo >= 0 && hi < p.W) {
                     row_span(T, row, lo, hi);
                     if (lo <= hi) {
