@@ -162,6 +162,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profiled_traffic(shape):
+    """DRAM bytes per render launch from the committed ncu summary, if that capture was taken
+    of the current render source at the same launch shape; else None."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(here, "profiles", "render_kernel_uniform_128x128.md")).read()
+        src = open(os.path.join(here, "paper_2606_19641_b300", "csrc", "gp_render.cu"), "rb").read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch: (\d+) \(render source sha256 ([0-9a-f]+), "
+                  r"shape ([0-9,]+)\)", text)
+    if not m or m.group(3) != shape:
+        return None
+    if hashlib.sha256(src).hexdigest()[:len(m.group(2))] != m.group(2):
+        return None
+    return int(m.group(1))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,8 +286,10 @@ def main():
     algo_bytes = out_bytes + geo_bytes
     peak, peak_kind = peaks()
     achieved = algo_bytes / (render_ms / 1e3) / 1e9
+    shape_s = "%d,%d,%d" % (sim.info.band_rows, sim.info.threads, sim.info.tri_capacity)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "render_kernel",
+                "frac": achieved / peak, "traffic": profiled_traffic(shape_s),
+                "kernel": "render_kernel",
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
                 "avg_launch_ms": render_ms, "frac_of_nominal_8tbs": achieved / 8000.0}
 
