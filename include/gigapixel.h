@@ -204,6 +204,17 @@ gp_status gp_clear_status(gp_handle *h);
 gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits);
 
 /*
+ * Failure-path test of the pipelined render kernel: launch it (with the handle's bands and
+ * a pipelined launch shape) with producer warps that publish nothing, so every consumer's
+ * first handoff wait runs out after wait_ns nanoseconds (1e6..2e9, else GP_EINVAL).  The
+ * kernel then sets GP_DEV_PIPELINE_TIMEOUT in the status word and returns; nothing is
+ * written to out_dev/depth_dev and the context stays usable.  Synchronous.  GP_ELIMIT if no
+ * pipelined shape fits.  The paper has no counterpart; this is a test aid of this library.
+ */
+gp_status gp_debug_stall_pipeline(gp_handle *h, void *out_dev, void *depth_dev, int64_t wait_ns,
+                                  void *stream);
+
+/*
  * Render all cameras (like gp_render) and copy the snapped triangles that camera `view`
  * rasterised to host memory: records of int32 X[3], Y[3] (1/16 pixel, y down), float d[3]
  * (n / z_view), uint32 prim, uint32 sub (fan index after clipping); 44 bytes each.  A

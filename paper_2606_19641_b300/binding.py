@@ -28,7 +28,8 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render",
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
-            "gp_debug_inject_status", "gp_debug_dump_tris", "gp_debug_dump_tris_noalloc",
+            "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
+            "gp_debug_dump_tris_noalloc",
             "gp_last_error")
 NOALLOC_MAX_TRIS = 16384
 
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_get_status": [vp, ctypes.POINTER(u32)],
         "gp_clear_status": [vp],
         "gp_debug_inject_status": [vp, u32],
+        "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
         "gp_debug_dump_tris_noalloc": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
     }
@@ -260,6 +262,12 @@ class Simulator:
 
     def inject_status(self, bits: int) -> None:
         check(lib().gp_debug_inject_status(self._h, bits))
+
+    def debug_stall_pipeline(self, out, depth=None, wait_ns: int = 50_000_000) -> None:
+        """Run the pipelined render kernel with producers that publish nothing (its bounded
+        handoff wait runs out and sets DEV_PIPELINE_TIMEOUT)."""
+        check(lib().gp_debug_stall_pipeline(self._h, _ptr(out), _ptr(depth), wait_ns,
+                                            _stream(None)))
 
     def dump_tris(self, view: int, out, depth=None, cap: int = 1 << 20) -> np.ndarray:
         """Render all views and return the snapped triangles view `view` rasterised."""

@@ -245,6 +245,8 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     p.tri_cap = h->shape.tri_cap;
     p.max_cl = h->max_cl;
     p.prod_warps = h->shape.prod_warps;
+    p.wait_ns = 2000000000ull;  // 2 s: far beyond any legitimate handoff
+    p.debug_stall = 0;
     p.status = h->status.p;
     p.dump_view = -1;
     return p;
@@ -936,6 +938,29 @@ gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits) {
     CK(cudaMemcpy(&cur, h->status.p, 4, cudaMemcpyDeviceToHost));
     cur |= bits;
     CK(cudaMemcpy(h->status.p, &cur, 4, cudaMemcpyHostToDevice));
+    return GP_OK;
+}
+
+gp_status gp_debug_stall_pipeline(gp_handle *h, void *out, void *depth, int64_t wait_ns,
+                                  void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (wait_ns < 1000000 || wait_ns > 2000000000) return fail(GP_EINVAL, "wait_ns outside 1e6..2e9");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    CK(cudaSetDevice(h->device));
+    Shape s = h->shape;  // same bands as the handle's work list
+    s.prod_warps = std::max(1, s.threads / 128);
+    if (!finish_shape(h, s)) {
+        s.tri_cap = 256;
+        if (!finish_shape(h, s)) return fail(GP_ELIMIT, "no pipelined launch shape fits");
+    }
+    RenderParams p = render_params(h, out, depth);
+    p.prod_warps = s.prod_warps;
+    p.tri_cap = s.tri_cap;
+    p.wait_ns = (unsigned long long)wait_ns;
+    p.debug_stall = 1;
+    CK(launch_render(p, s.blocks, s.threads, s.smem, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
     return GP_OK;
 }
 

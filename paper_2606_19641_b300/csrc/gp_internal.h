@@ -84,6 +84,8 @@ struct RenderParams {
     int tri_cap;             // triangles per raster batch
     int max_cl;              // most culling clusters in any world of the batch
     int prod_warps;          // > 0: pipelined kernel with this many producer warps
+    unsigned long long wait_ns;  // pipelined kernel: a handoff wait gives up after this long
+    int debug_stall;         // pipelined kernel: producers publish nothing (timeout test)
     uint32_t *status;
 
     int dump_view;           // -1 = off

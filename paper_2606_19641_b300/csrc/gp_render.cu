@@ -1187,7 +1187,6 @@ struct BatchMeta {
     int flags;  // kBatchLast: the item's last batch (encode after it); kBatchEnd: no more work
 };
 constexpr int kBatchLast = 1, kBatchEnd = 2;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // a handoff wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
     return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -1220,16 +1219,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Wait until the phase of parity `parity` of an mbarrier completes; false (and a status bit)
-// if it does not within kWaitNs.  Warp-collective: all 32 lanes call it, poll in lock step
+// if it does not within wait_ns.  Warp-collective: all 32 lanes call it, poll in lock step
 // and return the same answer together, so the warp leaves converged.
-__device__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t *status) {
+__device__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long wait_ns,
+                          uint32_t *status) {
     bool done = mbar_try_wait(bar, parity);
     if (__all_sync(0xffffffffu, done)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         done = done || mbar_try_wait(bar, parity);
         if (__all_sync(0xffffffffu, done)) return true;
-        const bool late = global_ns() - t0 > kWaitNs;
+        const bool late = global_ns() - t0 > wait_ns;
         if (__shfl_sync(0xffffffffu, late, 0)) {
             if ((threadIdx.x & 31) == 0) atomicOr(status, GP_DEV_PIPELINE_TIMEOUT);
             return false;
@@ -1242,9 +1242,9 @@ __device__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t *st
 // them: the producers fill one while the consumers rasterise the other.  Batch s lives in
 // buffer s & 1; full[b] completes when the producers have written a batch into buffer b,
 // empty[b] when the consumers are done with it.  Each side synchronises internally on its
-// own hardware barrier (1 producers, 2 consumers).  Every handoff wait is bounded: on a
-// timeout the side records it, sets GP_DEV_PIPELINE_TIMEOUT and leaves as a whole, and the
-// other side then times out too.
+// own hardware barrier (1 producers, 2 consumers).  Every handoff wait is bounded (p.wait_ns):
+// on a timeout the side records it, sets GP_DEV_PIPELINE_TIMEOUT and leaves as a whole, and
+// the other side then times out too.
 template <bool F32>
 __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1271,6 +1271,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
     __syncthreads();
 
     if ((int)threadIdx.x < nprod) {
+        if (p.debug_stall) return;  // test mode: the consumers' first wait runs out
         const Group g{(int)threadIdx.x, nprod, 1};
         SetupMem m{tris0, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
                    (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
@@ -1293,7 +1294,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             ++s;
             const int nb = s & 1;
             // batch s - 2 used buffer nb: wait until the consumers are done with it
-            if (s >= 2 && !mbar_wait(&bars[2 + nb], (uint32_t)(((s >> 1) - 1) & 1), p.status))
+            if (s >= 2 && !mbar_wait(&bars[2 + nb], (uint32_t)(((s >> 1) - 1) & 1), p.wait_ns,
+                                     p.status))
                 gave_up[0] = 1;
             g.sync();
             if (gave_up[0]) return nullptr;
@@ -1321,7 +1323,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             const int b = s & 1;
             // a flag per batch parity: a thread already waiting for batch s + 1 cannot change
             // the flag the others still read for batch s
-            if (!mbar_wait(&bars[b], (uint32_t)((s >> 1) & 1), p.status)) gave_up[1 + b] = 1;
+            if (!mbar_wait(&bars[b], (uint32_t)((s >> 1) & 1), p.wait_ns, p.status))
+                gave_up[1 + b] = 1;
             g.sync();
             if (gave_up[1 + b]) break;
             const BatchMeta mt = meta[b];
