@@ -382,8 +382,10 @@ __device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float
         if (lane >= o) incl += y;
     }
     const int excl = incl - cnt;
-    // two rounds per iteration: independent searches overlap their shuffle latency
-    for (int f0 = 0; f0 < total; f0 += 64) {
+    // two rounds per iteration (independent searches overlap their shuffle latency), then
+    // at most one single round for a tail of up to 32 fragments
+    int f0 = 0;
+    for (; f0 + 32 < total; f0 += 64) {
         const int fA = f0 + lane, fB = fA + 32;
         int oA = 0, oB = 0;  // first lane whose inclusive prefix exceeds f
 #pragma unroll
@@ -404,8 +406,24 @@ __device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float
         const float iB = __shfl_sync(0xffffffffu, inner, oB);
         const uint32_t lA = __shfl_sync(0xffffffffu, low, oA);
         const uint32_t lB = __shfl_sync(0xffffffffu, low, oB);
-        if (fA < total) depth_test<F32>(keys, kA, gA, aA, iA, lA);
+        depth_test<F32>(keys, kA, gA, aA, iA, lA);  // fA < total here
         if (fB < total) depth_test<F32>(keys, kB, gB, aB, iB, lB);
+    }
+    if (f0 < total) {
+        const int f = f0 + lane;
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, o + st - 1);
+            if (v <= f) o += st;
+        }
+        const int t = f - __shfl_sync(0xffffffffu, excl, o);
+        const int k = __shfl_sync(0xffffffffu, kofs, o) + t;
+        const int gg = __shfl_sync(0xffffffffu, gx0, o) + 16 * t;
+        const float fa = __shfl_sync(0xffffffffu, a, o);
+        const float fi = __shfl_sync(0xffffffffu, inner, o);
+        const uint32_t lw = __shfl_sync(0xffffffffu, low, o);
+        if (f < total) depth_test<F32>(keys, k, gg, fa, fi, lw);
     }
 }
 
