@@ -131,6 +131,29 @@ def oracle_sample(worlds, wl, seconds, rank_seed_step=0):
     return done_agents / el, el, done_agents
 
 
+def rank_workload(wl, rank):
+    """This rank's own batch: the workload with a rank-specific seed.  Ranks share no data
+    and exchange nothing on the data path (the worlds are independent)."""
+    import dataclasses
+    return dataclasses.replace(wl, seed=wl.seed + 7919 * rank)
+
+
+def reduce_over_ranks(x, op, world, device):
+    """x reduced over the ranks with torch.distributed op `op` ("max" or "sum")."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(total_agents, steps, max_ms):
+    """Whole-job agent-steps/s: every rank's agents over the slowest rank's time."""
+    return total_agents * steps / (max_ms / 1e3)
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, on this machine's host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -212,8 +235,7 @@ def main():
 
     wl = WORKLOAD
     # each rank simulates its own batch of worlds (different seed): no data-path collective
-    import dataclasses
-    wl_rank = dataclasses.replace(wl, seed=wl.seed + 7919 * rank)
+    wl_rank = rank_workload(wl, rank)
     worlds = wg.make_workload(wl_rank)
     if args.shape:
         rows, threads, cap = (int(v) for v in args.shape.split(","))
@@ -237,11 +259,7 @@ def main():
         torch.cuda.synchronize()
 
     def maxred(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", world, "cuda")
 
     # warm-up (graph capture happens on the first replay)
     for k in range(args.warmup):
@@ -264,7 +282,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = maxred(sum(step_ms))
     ms_per_step = total_ms / args.steps
-    value = world * n_agents * args.steps / (total_ms / 1e3)
+    total_agents = reduce_over_ranks(n_agents, "sum", world, "cuda")
+    value = job_rate(total_agents, args.steps, total_ms)
 
     # --- render-kernel time inside a timed loop of direct calls (roofline) ---
     evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -311,7 +330,7 @@ def main():
         h_flags.copy_(d_flags, non_blocking=True)
         stream.synchronize()
     e2e_s = maxred(time.perf_counter() - t0)
-    e2e = {"value": world * n_agents * e2e_steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(total_agents, e2e_steps, 1e3 * e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": h_act.numel() * 4,
            "d2h_bytes_per_step": h_state.numel() * 4 + h_flags.numel(),
            "note": "actions host->device and agent state/flags device->host every step; "
@@ -344,7 +363,8 @@ def main():
         barrier()
         rms = e0.elapsed_time(e1) / steps
         rb = sim2.info.out_bytes + 36 * (len(worlds2.road) + len(worlds2.line)) + 32 * len(worlds2.boxes)
-        return {"agent_steps_per_s": world * sim2.n_agents / (ms / 1e3), "ms_per_step": ms,
+        agents2 = reduce_over_ranks(sim2.n_agents, "sum", world, "cuda")
+        return {"agent_steps_per_s": job_rate(agents2, 1, ms), "ms_per_step": ms,
                 "render_kernel_ms": rms, "render_gbs": rb / (rms / 1e3) / 1e9,
                 "render_frac_of_measured_hbm": rb / (rms / 1e3) / 1e9 / peaks()[0],
                 "cameras": sim2.n_views, "band_rows": sim2.info.band_rows,
@@ -365,7 +385,7 @@ def main():
         barrier()
         pw_ms = maxred(e0.elapsed_time(e1)) / pw_steps
         extras["per_world_path"] = {
-            "agent_steps_per_s": world * n_agents / (pw_ms / 1e3), "ms_per_step": pw_ms,
+            "agent_steps_per_s": job_rate(total_agents, 1, pw_ms), "ms_per_step": pw_ms,
             "launches_per_step": 2 * worlds.n_worlds}
         extras["speedup_vs_per_world_path"] = value / extras["per_world_path"]["agent_steps_per_s"]
         # batched precision path on the same worlds: FP16 reversed-Z keys, fused BF16 NCHW
@@ -378,7 +398,7 @@ def main():
             extras["precision_path"]["agent_steps_per_s"] / extras["per_world_path"]["agent_steps_per_s"])
         sim_p.close()
         # ragged batch at 256x144, precision path
-        wl_r = dataclasses.replace(wg.WORKLOADS["ragged_precision"], seed=wg.WORKLOADS["ragged_precision"].seed + 7919 * rank)
+        wl_r = rank_workload(wg.WORKLOADS["ragged_precision"], rank)
         worlds_r = wg.make_workload(wl_r)
         sim_r = Simulator(worlds_r, config_for(wl_r, autotune=1), device=local)
         extras["ragged_precision_256x144"] = graph_rate(sim_r, worlds_r, wl_r, 5)
