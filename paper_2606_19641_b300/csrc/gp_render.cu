@@ -54,6 +54,7 @@ struct __align__(16) TriRec {
 };
 static_assert(sizeof(TriRec) == 32, "TriRec layout");
 static_assert(kMaxBandRows <= 128, "(j0 - by0) and (j1 - j0) have 7 bits each");
+static_assert(kMaxBandRows * GP_MAX_WIDTH <= 65536, "a band's key index fits 16 bits");
 
 __device__ __forceinline__ int span_i0(uint32_t s) { return (int)(s & 511u); }
 __device__ __forceinline__ int span_i1(uint32_t s) { return (int)((s >> 9) & 511u); }
@@ -381,49 +382,59 @@ __device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    const int excl = incl - cnt;
-    // two rounds per iteration (independent searches overlap their shuffle latency), then
-    // at most one single round for a tail of up to 32 fragments
+    // key index and pixel offset in one word: kofs < band rows x W <= 2^16, |gx0| < 2^15
+    const int kg = (int)(((unsigned int)gx0 << 16) | ((unsigned int)kofs & 0xFFFFu));
+    // Each lane finds the first lane whose inclusive prefix exceeds its fragment index f by
+    // binary search; the last probe that moved the search right holds that lane's exclusive
+    // prefix (0 if none did).  Two rounds per iteration (independent searches overlap their
+    // shuffle latency), then at most one single round for a tail of up to 32 fragments.
     int f0 = 0;
     for (; f0 + 32 < total; f0 += 64) {
         const int fA = f0 + lane, fB = fA + 32;
-        int oA = 0, oB = 0;  // first lane whose inclusive prefix exceeds f
+        int oA = 0, oB = 0, eA = 0, eB = 0;
 #pragma unroll
         for (int st = 16; st > 0; st >>= 1) {
             const int vA = __shfl_sync(0xffffffffu, incl, oA + st - 1);
             const int vB = __shfl_sync(0xffffffffu, incl, oB + st - 1);
-            if (vA <= fA) oA += st;
-            if (vB <= fB) oB += st;
+            if (vA <= fA) {
+                oA += st;
+                eA = vA;
+            }
+            if (vB <= fB) {
+                oB += st;
+                eB = vB;
+            }
         }
-        const int tA = fA - __shfl_sync(0xffffffffu, excl, oA);
-        const int tB = fB - __shfl_sync(0xffffffffu, excl, oB);
-        const int kA = __shfl_sync(0xffffffffu, kofs, oA) + tA;
-        const int kB = __shfl_sync(0xffffffffu, kofs, oB) + tB;
-        const int gA = __shfl_sync(0xffffffffu, gx0, oA) + 16 * tA;
-        const int gB = __shfl_sync(0xffffffffu, gx0, oB) + 16 * tB;
+        const int tA = fA - eA, tB = fB - eB;
+        const int kgA = __shfl_sync(0xffffffffu, kg, oA);
+        const int kgB = __shfl_sync(0xffffffffu, kg, oB);
         const float aA = __shfl_sync(0xffffffffu, a, oA), aB = __shfl_sync(0xffffffffu, a, oB);
         const float iA = __shfl_sync(0xffffffffu, inner, oA);
         const float iB = __shfl_sync(0xffffffffu, inner, oB);
         const uint32_t lA = __shfl_sync(0xffffffffu, low, oA);
         const uint32_t lB = __shfl_sync(0xffffffffu, low, oB);
-        depth_test<F32>(keys, kA, gA, aA, iA, lA);  // fA < total here
-        if (fB < total) depth_test<F32>(keys, kB, gB, aB, iB, lB);
+        // fA < total here
+        depth_test<F32>(keys, (kgA & 0xFFFF) + tA, (kgA >> 16) + 16 * tA, aA, iA, lA);
+        if (fB < total)
+            depth_test<F32>(keys, (kgB & 0xFFFF) + tB, (kgB >> 16) + 16 * tB, aB, iB, lB);
     }
     if (f0 < total) {
         const int f = f0 + lane;
-        int o = 0;
+        int o = 0, e = 0;
 #pragma unroll
         for (int st = 16; st > 0; st >>= 1) {
             const int v = __shfl_sync(0xffffffffu, incl, o + st - 1);
-            if (v <= f) o += st;
+            if (v <= f) {
+                o += st;
+                e = v;
+            }
         }
-        const int t = f - __shfl_sync(0xffffffffu, excl, o);
-        const int k = __shfl_sync(0xffffffffu, kofs, o) + t;
-        const int gg = __shfl_sync(0xffffffffu, gx0, o) + 16 * t;
+        const int t = f - e;
+        const int kgo = __shfl_sync(0xffffffffu, kg, o);
         const float fa = __shfl_sync(0xffffffffu, a, o);
         const float fi = __shfl_sync(0xffffffffu, inner, o);
         const uint32_t lw = __shfl_sync(0xffffffffu, low, o);
-        if (f < total) depth_test<F32>(keys, k, gg, fa, fi, lw);
+        if (f < total) depth_test<F32>(keys, (kgo & 0xFFFF) + t, (kgo >> 16) + 16 * t, fa, fi, lw);
     }
 }
 
