@@ -109,34 +109,48 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
             }
         }
 
-        // off-road: every footprint corner must lie in some road quad
-        unsigned int off = 0;
-        if (tid < na) {
-            const Footprint b = fp[tid];
-            const float sx[4] = {-1.f, 1.f, 1.f, -1.f};
-            const float sy[4] = {-1.f, -1.f, 1.f, 1.f};
-            for (int k = 0; k < 4 && !off; ++k) {
-                const float lx = sx[k] * b.hl, ly = sy[k] * b.hw;
-                const float px = b.x + b.c * lx - b.s * ly;
-                const float py = b.y + b.s * lx + b.c * ly;
-                const float fx = floorf((px - wi.gx0) * wi.ginv);
-                const float fy = floorf((py - wi.gy0) * wi.ginv);
-                bool inside = false;
-                if (fx >= 0.f && fy >= 0.f && fx < (float)wi.gnx && fy < (float)wi.gny) {
-                    const int cell = wi.cell_begin + (int)fy * wi.gnx + (int)fx;
-                    for (int q = p.cell_off[cell]; q < p.cell_off[cell + 1] && !inside; ++q) {
-                        const int r = p.cell_quads[q];
-                        inside = in_quad(px, py, p.road_geo[2 * r], p.road_geo[2 * r + 1]);
+        // off-road: every footprint corner must lie in some road quad; one (agent, corner)
+        // pair per thread, so the candidate-quad searches of an agent's corners run side by
+        // side
+        for (int pc = tid; pc < 4 * na; pc += blockDim.x) {
+            const int i = pc >> 2, k = pc & 3;
+            const Footprint b = fp[i];
+            const float lx = ((k == 1 || k == 2) ? 1.f : -1.f) * b.hl;
+            const float ly = (k >= 2 ? 1.f : -1.f) * b.hw;
+            const float px = b.x + b.c * lx - b.s * ly;
+            const float py = b.y + b.s * lx + b.c * ly;
+            const float fx = floorf((px - wi.gx0) * wi.ginv);
+            const float fy = floorf((py - wi.gy0) * wi.ginv);
+            bool inside = false;
+            if (fx >= 0.f && fy >= 0.f && fx < (float)wi.gnx && fy < (float)wi.gny) {
+                const int cell = wi.cell_begin + (int)fy * wi.gnx + (int)fx;
+                // four candidates per round trip: their loads are independent
+                const int q1 = p.cell_off[cell + 1];
+                for (int q = p.cell_off[cell]; q < q1 && !inside; q += 4) {
+                    int r[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) r[u] = q + u < q1 ? p.cell_quads[q + u] : -1;
+                    float4 g0[4], g1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        g0[u] = g1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r[u] >= 0) {
+                            g0[u] = p.road_geo[2 * r[u]];
+                            g1[u] = p.road_geo[2 * r[u] + 1];
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (r[u] >= 0 && in_quad(px, py, g0[u], g1[u])) inside = true;
                 }
-                if (!inside) off = GP_FLAG_OFFROAD;
             }
+            if (!inside) atomicOr(&sflag[i], GP_FLAG_OFFROAD);
         }
         __syncthreads();
 
         if (tid < na) {
             const int a = wi.agent_begin + tid;
-            fl |= sflag[tid] | off;
+            fl |= sflag[tid];
             if (fl & (GP_FLAG_COLLIDED | GP_FLAG_OFFROAD)) {
                 fl |= GP_FLAG_HALTED;
                 v = 0.f;
