@@ -468,3 +468,59 @@ def test_full_size_ragged_precision_sampled():
         frac, np.percentile(derr, 99)))
     assert frac < T4_MISMATCH
     assert sim.status() == 0
+
+
+def test_full_size_ragged_batch_sampled():
+    """The full ragged batch (1024 worlds, agents U{1..64}, road segments U{100..2000},
+    128x128, u8 class + f32 depth), autotuned, graph replay: sampled views bit-exact against
+    the raster rule and within the FP64 mismatch bound."""
+    import torch
+    wl = wg.WORKLOADS["ragged"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl, autotune=1)
+    out, depth = sim.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(2):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        sim.step_render(act, out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    assert int(out.max()) <= 3
+    assert torch.equal(out > 0, depth > 0)
+    rng = np.random.default_rng(2)
+    views = sorted(rng.choice(sim.n_views, 4, replace=False).tolist())
+    check_t3(sim, cfg, worlds, views, out, depth)
+    frac, derr = t4_stats(sim, cfg, worlds, views, out, depth)
+    assert frac < T4_MISMATCH
+
+
+@pytest.mark.parametrize("size", [64, 512])
+@pytest.mark.parametrize("precision", [False, True], ids=["plain", "precision"])
+def test_full_size_sweep_three_cameras_sampled(size, precision):
+    """The camera and resolution sweep at full size (256 worlds x 32 agents x 3 cameras at
+    0 and +-60 deg, 64 boxes and 1000 road segments per world) at the smallest and largest
+    square resolution, plain and precision paths: sampled views of every camera bit-exact
+    against the raster rule and within the FP64 mismatch bound."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["sweep"]
+    worlds = wg.make_workload(wl)
+    extra = dict(key_precision=gp.KEY_F16, output=gp.OUT_ONEHOT_BF16) if precision else {}
+    sim, cfg = sim_for(worlds, wl, width=size, height=size, **extra)
+    assert sim.n_views == 3 * worlds.n_agents
+    out, depth = sim.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(2):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        sim.step_render(act, out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    rng = np.random.default_rng(size)
+    agents = rng.choice(worlds.n_agents, 2, replace=False).tolist()
+    views = sorted(3 * a + c for a in agents for c in range(3))
+    check_t3(sim, cfg, worlds, views, out, depth)
+    frac, derr = t4_stats(sim, cfg, worlds, views[:3], out, depth)
+    assert frac < T4_MISMATCH
+    del out, depth
+    sim.close()
+    torch.cuda.empty_cache()
