@@ -86,6 +86,9 @@ def _lib():
         lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
         lib.or_f32_to_bf16.restype = ctypes.c_uint16
         lib.or_onehot_bf16.argtypes = [c_u8p, ctypes.c_int64, c_f32p, c_f32p, c_u16p]
+        lib.or_shade_rgb.argtypes = [c_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
+                                     ctypes.c_uint32, c_f64p, c_f64p, c_f64p, ctypes.c_double,
+                                     c_u8p]
         _lib_handle = lib
     return _lib_handle
 
@@ -199,6 +202,32 @@ def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: in
     return Image(key, cls, d16 if key_f16 else d32)
 
 
+# Default RGB appearance (readings; the paper gives only "blue" for vehicles and static
+# objects): class colours in [0, 1] and the light direction towards the light.
+RGB_COLOURS = ((0.55, 0.75, 0.95), (0.33, 0.33, 0.35), (0.92, 0.92, 0.85), (0.15, 0.35, 0.85))
+RGB_LIGHT = (0.3, 0.4, 0.866)
+RGB_AMBIENT = 0.35
+
+
+def unit(v) -> np.ndarray:
+    a = np.asarray(v, np.float64)
+    return a / np.sqrt(float(np.dot(a, a)))
+
+
+def shade_rgb(key: np.ndarray, key_f16: bool, box_end: int, road_end: int, boxes6: np.ndarray,
+              colour=RGB_COLOURS, light=RGB_LIGHT, ambient: float = RGB_AMBIENT) -> np.ndarray:
+    """uint8 [3, H, W] RGB observation from the raster's keys (see or_shade_rgb)."""
+    k = _c(key, np.uint64)
+    b = _c(boxes6, np.float64).reshape(-1, 6)
+    col = _c(colour, np.float64).reshape(4, 3)
+    l = _c(unit(light), np.float64)
+    out = np.zeros((3,) + k.shape, np.uint8)
+    _lib().or_shade_rgb(_p(k, c_u64p), k.size, int(key_f16), box_end, road_end,
+                        _p(b, c_f64p), _p(col, c_f64p), _p(l, c_f64p), float(ambient),
+                        _p(out, c_u8p))
+    return out
+
+
 def f32_to_f16_bits(x) -> np.ndarray:
     a = np.asarray(x, np.float32).ravel()
     lib = _lib()
@@ -278,6 +307,13 @@ class Sim:
         nb = int(self.w.box_off[w + 1] - self.w.box_off[w])
         nr = int(self.w.road_off[w + 1] - self.w.road_off[w])
         return 12 * nb, 12 * nb + 2 * nr
+
+    def render_rgb(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float,
+                   key_f16: bool = False, **appearance) -> np.ndarray:
+        """uint8 [3, H, W] RGB observation of one camera (FP64 pipeline)."""
+        img = self.render(cam, w, agent_local, cam_yaw, key_f16)
+        be, re = self.prim_ranges(w)
+        return shade_rgb(img.key, key_f16, be, re, self.boxes6(w), **appearance)
 
     def render(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float,
                key_f16: bool = False) -> Image:

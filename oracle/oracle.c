@@ -549,6 +549,57 @@ void or_raster_bruteforce(const or_tri *tris, int64_t n, int32_t W, int32_t H, i
 }
 
 /*
+ * RGB observation (App. A "High-Throughput Batched Rendering": minimal shading, one
+ * directional light per agent, a colour per instance -- blue for every vehicle and static
+ * object in the paper's experiments).  Reading: a pixel's colour is
+ *     base * (ambient + (1 - ambient) * max(0, n . l))
+ * with base the winning primitive's class colour (all boxes share one colour), n its
+ * outward unit normal in the world frame -- a box face's normal turned by the box's yaw,
+ * +z for road and lane-line strips -- and l the unit direction towards the light (the same
+ * light in every world).  Background pixels take the background colour unshaded.  Each
+ * channel is quantised as rint(255 * clamp(v, 0, 1)) (round half to even).
+ *   key [npx]: the raster's per-pixel keys; boxes [n][6]: x, y, yaw, L, W, H of the world's
+ *   boxes (post-step); colour [4][3]: classes 0 background, 1 road, 2 lane line, 3 box;
+ *   light [3] unit -> rgb [3][npx]
+ */
+void or_shade_rgb(const uint64_t *key, int64_t npx, int32_t key_f16, uint32_t box_end,
+                  uint32_t road_end, const double *boxes, const double *colour,
+                  const double *light, double ambient, uint8_t *rgb) {
+    for (int64_t p = 0; p < npx; ++p) {
+        const uint64_t k = key[p];
+        int cls = 0;
+        double shade = 1.0;
+        if (k) {
+            const uint32_t prim = key_f16 ? (0xFFFFu - (uint32_t)(k & 0xFFFFu))
+                                          : (0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
+            cls = prim_class(prim, box_end, road_end);
+            double nx = 0.0, ny = 0.0, nz = 1.0;
+            if (cls == 3) {
+                const uint32_t b = prim / 12, face = (prim % 12) / 2;
+                const double c = cos(boxes[6 * b + 2]), sn = sin(boxes[6 * b + 2]);
+                switch (face) { /* +x, -x, +y, -y, +z, -z in the box frame */
+                case 0: nx = c; ny = sn; nz = 0.0; break;
+                case 1: nx = -c; ny = -sn; nz = 0.0; break;
+                case 2: nx = -sn; ny = c; nz = 0.0; break;
+                case 3: nx = sn; ny = -c; nz = 0.0; break;
+                case 4: nx = 0.0; ny = 0.0; nz = 1.0; break;
+                default: nx = 0.0; ny = 0.0; nz = -1.0; break;
+                }
+            }
+            double ndl = nx * light[0] + ny * light[1] + nz * light[2];
+            if (ndl < 0.0) ndl = 0.0;
+            shade = ambient + (1.0 - ambient) * ndl;
+        }
+        for (int ch = 0; ch < 3; ++ch) {
+            double v = colour[3 * cls + ch] * shade;
+            if (v < 0.0) v = 0.0;
+            if (v > 1.0) v = 1.0;
+            rgb[(int64_t)ch * npx + p] = (uint8_t)rint(255.0 * v);
+        }
+    }
+}
+
+/*
  * Policy-input encoding: 4-channel one-hot of the class image, normalised per channel,
  * bfloat16, NCHW.  value(c) = bf16((onehot_c - mean_c) / std_c), computed in FP32.
  *   cls [n] -> out [4][n]

@@ -31,6 +31,13 @@ MUTANTS = {
     "ego drawn": ("if (b == ego) continue;", ""),
     "guard band off": ("double g = cfg->guard;", "double g = 1e9;"),
     "near clip t flipped": ("double t = di / (di - dov);", "double t = dov / (dov - di);"),
+    "shade ignores box yaw": ("const double c = cos(boxes[6 * b + 2]), sn = sin(boxes[6 * b + 2]);",
+                              "const double c = 1.0, sn = 0.0;"),
+    "shade no light floor": ("if (ndl < 0.0) ndl = 0.0;", ""),
+    "shade +x/-x normals swapped": ("case 0: nx = c; ny = sn;", "case 0: nx = -c; ny = -sn;"),
+    "shade +y normal rotated wrong": ("case 2: nx = -sn; ny = c;", "case 2: nx = sn; ny = c;"),
+    "shade ground faces down": ("double nx = 0.0, ny = 0.0, nz = 1.0;", "double nx = 0.0, ny = 0.0, nz = -1.0;"),
+    "shade background lit": ("double shade = 1.0;", "double shade = 0.5;"),
 }
 
 

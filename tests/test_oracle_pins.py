@@ -742,3 +742,91 @@ def test_snapped_vertices_stay_inside_guard_band():
                 assert np.all(np.abs(Y - 8 * H) <= 4 * 8 * H + 1)
                 n_near += int((np.abs(Y - 8 * H) > 3 * 8 * H).sum())
         assert n_near > 0  # some ground really is clipped by the guard band
+
+
+# ---------------------------------------------------------------------------------------
+# RGB observation: one directional light, a colour per class (closed forms)
+# ---------------------------------------------------------------------------------------
+
+def _rgb8(v):
+    """Expected 8-bit channel value: round half to even of 255 * clamp(v, 0, 1)."""
+    return int(np.rint(255.0 * min(max(v, 0.0), 1.0)))
+
+
+def test_rgb_empty_scene_is_unshaded_background():
+    cam = CamConfig(32, 24)
+    boxes = [ego_box()]
+    img, _ = render_scene(cam, boxes)
+    col = ((0.2, 0.4, 0.6), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    rgb = oracle.shade_rgb(img.key, False, 12, 12, np.array(boxes), colour=col,
+                           light=(0.0, 0.0, -1.0), ambient=0.1)
+    assert rgb.shape == (3, 24, 32)
+    for ch, v in enumerate((51, 102, 153)):  # 255 * (0.2, 0.4, 0.6), no light involved
+        assert np.all(rgb[ch] == v)
+
+
+@pytest.mark.parametrize("box_yaw,light,lit", [
+    (0.0, (-0.6, 0.0, 0.8), 0.6),      # the visible face (-x of the box) faces the light
+    (math.pi, (-0.6, 0.0, 0.8), 0.6),  # turned round: the box's +x face now faces the camera
+    (0.0, (0.6, 0.0, 0.8), 0.0),       # light from behind the face: ambient only
+    (math.pi, (0.6, 0.0, 0.8), 0.0),
+])
+def test_rgb_front_face_lambert(box_yaw, light, lit):
+    W, H, D, hw, bh = 64, 64, Fraction(10), Fraction(1), Fraction(16, 10)
+    cols, rows, margin = _box_face_expectation(W, H, D, hw, bh)
+    assert margin >= Fraction(1, 16)
+    L = 4.5
+    boxes = [ego_box(), [float(D) + L / 2, 0.0, box_yaw, L, 2 * float(hw), float(bh)]]
+    img, _ = render_scene(CamConfig(W, H), boxes)
+    face = np.zeros((H, W), bool)
+    face[rows[0]:rows[-1] + 1, cols[0]:cols[-1] + 1] = True
+    assert np.array_equal(img.cls == 3, face)
+    bg, blue, ambient = (0.5, 0.5, 0.5), (0.1, 0.3, 0.9), 0.25
+    col = (bg, (0.3, 0.3, 0.3), (0.9, 0.9, 0.9), blue)
+    rgb = oracle.shade_rgb(img.key, False, 24, 24, np.array(boxes), colour=col, light=light,
+                           ambient=ambient)
+    shade = ambient + (1.0 - ambient) * lit
+    for ch in range(3):
+        assert np.all(rgb[ch][face] == _rgb8(blue[ch] * shade))
+        assert np.all(rgb[ch][~face] == _rgb8(bg[ch]))
+
+
+def test_rgb_ground_is_lit_from_above():
+    """Road pieces are horizontal: their shade is ambient + (1 - ambient) * l_z."""
+    W, H = 48, 32
+    boxes = [ego_box()]
+    road = [rect_quad(-5.0, 200.0, -3.5, 3.5)]
+    img, _ = render_scene(CamConfig(W, H), boxes, road=road)
+    ground = img.cls == 1
+    assert ground.sum() > 100
+    light = oracle.unit((0.5, -0.2, 0.7))
+    col = ((0.0, 0.0, 0.0), (0.4, 0.5, 0.6), (1.0, 1.0, 1.0), (0.0, 0.0, 1.0))
+    rgb = oracle.shade_rgb(img.key, False, 12, 14, np.array(boxes), colour=col, light=light,
+                           ambient=0.3)
+    shade = 0.3 + 0.7 * float(light[2])
+    for ch in range(3):
+        assert np.all(rgb[ch][ground] == _rgb8(col[1][ch] * shade))
+        assert np.all(rgb[ch][~ground] == 0)
+
+
+def test_rgb_side_face_normal_follows_box_yaw():
+    """A box seen from its side: its +y face (normal (-sin yaw, cos yaw, 0)) faces a camera
+    placed on the box's +y side; a light along that normal gives full shade."""
+    W, H = 64, 64
+    yaw = 0.7
+    n = np.array([-math.sin(yaw), math.cos(yaw), 0.0])
+    centre = np.array([0.0, 0.0])
+    cam_pos = centre + 12.0 * n[:2]
+    cam_heading = math.atan2(-n[1], -n[0])  # looking back at the box along -n
+    boxes = [ego_box(cam_pos[0], cam_pos[1], cam_heading), [0.0, 0.0, yaw, 4.5, 1.9, 1.6]]
+    img, _ = render_scene(CamConfig(W, H), boxes, pose=(cam_pos[0], cam_pos[1], cam_heading))
+    side = img.cls == 3
+    assert side.sum() > 20
+    col = ((0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.2, 0.6, 1.0))
+    rgb = oracle.shade_rgb(img.key, False, 24, 24, np.array(boxes), colour=col,
+                           light=tuple(n), ambient=0.5)
+    prim = 0xFFFFFFFF - (img.key[side] & 0xFFFFFFFF).astype(np.uint64)
+    faces = set(((prim % 12) // 2).tolist())
+    assert faces == {2}  # only the +y face is visible
+    for ch in range(3):
+        assert np.all(rgb[ch][side] == _rgb8(col[3][ch]))
