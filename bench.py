@@ -404,6 +404,16 @@ def main():
         extras["ragged_precision_256x144"] = graph_rate(sim_r, worlds_r, wl_r, 5)
         extras["ragged_precision_256x144"]["workload"] = wl_r.name
         sim_r.close()
+        # the paper's observation rig: 4 cameras (0, +-60, 180 deg) at 434x252, shaded RGB
+        wl_g = rank_workload(wg.WORKLOADS["paper_rig_434x252"], rank)
+        worlds_g = wg.make_workload(wl_g)
+        sim_g = Simulator(worlds_g, config_for(wl_g, autotune=1), device=local)
+        extras["paper_rig_434x252_rgb"] = graph_rate(sim_g, worlds_g, wl_g, 5)
+        extras["paper_rig_434x252_rgb"]["workload"] = wl_g.name
+        extras["paper_rig_434x252_rgb"]["mpix_per_s"] = (
+            extras["paper_rig_434x252_rgb"]["cameras"] * wl_g.width * wl_g.height /
+            (extras["paper_rig_434x252_rgb"]["ms_per_step"] / 1e3) / 1e6)
+        sim_g.close()
 
     cpu = None
     if rank == 0:

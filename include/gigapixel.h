@@ -46,7 +46,7 @@ typedef enum gp_status {
 /* Depth-key precision of the rasteriser. */
 enum { GP_KEY_F32 = 0, GP_KEY_F16 = 1 };
 /* Image encoding written by gp_render. */
-enum { GP_OUT_CLASS_U8 = 0, GP_OUT_ONEHOT_BF16 = 1 };
+enum { GP_OUT_CLASS_U8 = 0, GP_OUT_ONEHOT_BF16 = 1, GP_OUT_RGB_U8 = 2 };
 /* Per-agent flag bits (latched for the lifetime of the handle or until gp_set_state). */
 enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4 };
 /* Device status bits (sticky until gp_clear_status). */
@@ -98,7 +98,7 @@ typedef struct gp_world_desc {
  * Simulation and camera configuration.  gp_default_config fills the defaults listed here.
  */
 typedef struct gp_config {
-    int32_t width, height;        /* image size, 16..GP_MAX_WIDTH each, width % 16 == 0
+    int32_t width, height;        /* image size, 16..GP_MAX_WIDTH each, both even
                                      (default 128 x 128) */
     int32_t n_cams;               /* cameras per agent, 1..GP_MAX_CAMS (default 1) */
     float cam_yaw[GP_MAX_CAMS];   /* camera yaw offsets from the agent heading (default 0) */
@@ -109,7 +109,8 @@ typedef struct gp_config {
     float dt;                     /* simulation step (default 0.1 s, App. A) */
     float v_max;                  /* speed clamp (default 30 m/s) */
     int32_t key_precision;        /* GP_KEY_F32 (default) or GP_KEY_F16 (reversed-Z binary16) */
-    int32_t output;               /* GP_OUT_CLASS_U8 (default) or GP_OUT_ONEHOT_BF16 */
+    int32_t output;               /* GP_OUT_CLASS_U8 (default), GP_OUT_ONEHOT_BF16 or
+                                     GP_OUT_RGB_U8 */
     float norm_mean[4];           /* one-hot normalisation (default 0.5 each) */
     float norm_std[4];            /* (default 0.5 each -> values are exactly +-1) */
     int32_t autotune;             /* 1: time candidate launch shapes at create (default 0) */
@@ -120,6 +121,15 @@ typedef struct gp_config {
                                      clip while the others rasterise (double-buffered batches);
                                      0 = auto (the autotuner may pick it; off otherwise),
                                      -1 = off, n > 0 = on with n warps */
+    /* GP_OUT_RGB_U8 appearance (App. A: one directional light per agent, a colour per
+     * instance).  colour = class colour * (ambient + (1 - ambient) * max(0, n . l)), n the
+     * surface's outward normal (box faces turn with the box yaw; the ground faces +z), l
+     * the unit direction towards the light (normalised at create); background unshaded;
+     * channels rint(255 * clamp(., 0, 1)). */
+    float light_dir[3];           /* towards the light, world frame (default 0.3 0.4 0.866) */
+    float ambient;                /* 0..1 (default 0.35) */
+    float colour[4][3];           /* RGB in 0..1 of classes background, road, lane line,
+                                     vehicle/static box (defaults: sky, grey, off-white, blue) */
 } gp_config;
 
 /* Fill `cfg` with the defaults above. */
@@ -156,6 +166,7 @@ gp_status gp_step(gp_handle *h, const float *actions_dev, void *stream);
  *   out_dev    GP_OUT_CLASS_U8:    uint8  [n_views][height][width] class ids
  *              GP_OUT_ONEHOT_BF16: bf16   [n_views][4][height][width], channel c holds
  *                                  (1[class == c] - norm_mean[c]) / norm_std[c]
+ *              GP_OUT_RGB_U8:      uint8  [n_views][3][height][width] shaded RGB
  *   depth_dev  NULL, or reversed-Z depth n / z_view of the visible surface (0 on
  *              background): float [n_views][height][width] with GP_KEY_F32, binary16 bits
  *              (uint16) with GP_KEY_F16.

@@ -5,7 +5,7 @@ The compute path is the CUDA library ``libgigapixel.so`` (C ABI in include/gigap
 the first call does, and raises if it was not built.
 """
 from .binding import (Config, GigapixelError, Simulator, default_config, lib, load_library,
-                      KEY_F16, KEY_F32, OUT_CLASS_U8, OUT_ONEHOT_BF16, FLAG_COLLIDED,
+                      KEY_F16, KEY_F32, OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8, FLAG_COLLIDED,
                       FLAG_HALTED, FLAG_OFFROAD, TRI_DTYPE)
 
 
@@ -17,6 +17,7 @@ def config_for(workload, **overrides) -> Config:
               hfov=math.radians(workload.hfov_deg), cam_height=workload.cam_height,
               dt=workload.dt,
               key_precision=KEY_F16 if workload.precision == "f16" else KEY_F32,
-              output=OUT_ONEHOT_BF16 if workload.output == "onehot_bf16" else OUT_CLASS_U8)
+              output={"onehot_bf16": OUT_ONEHOT_BF16, "rgb_u8": OUT_RGB_U8}.get(workload.output,
+                                                                                 OUT_CLASS_U8))
     kw.update(overrides)
     return default_config(**kw)

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgigapixel.so")
 
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ELIMIT, GP_EDEVICE, GP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 KEY_F32, KEY_F16 = 0, 1
-OUT_CLASS_U8, OUT_ONEHOT_BF16 = 0, 1
+OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8 = 0, 1, 2
 FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
@@ -54,7 +54,9 @@ class Config(ctypes.Structure):
                 ("norm_mean", ctypes.c_float * 4), ("norm_std", ctypes.c_float * 4),
                 ("autotune", ctypes.c_int32), ("band_rows", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("tri_capacity", ctypes.c_int32),
-                ("producer_warps", ctypes.c_int32)]
+                ("producer_warps", ctypes.c_int32),
+                ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
+                ("colour", (ctypes.c_float * 3) * 4)]
 
 
 class Info(ctypes.Structure):
@@ -133,10 +135,14 @@ def default_config(**kw) -> Config:
             c.n_cams = len(vals)
             for i, y in enumerate(vals):
                 c.cam_yaw[i] = y
-        elif k in ("norm_mean", "norm_std"):
+        elif k in ("norm_mean", "norm_std", "light_dir"):
             arr = getattr(c, k)
             for i, y in enumerate(v):
                 arr[i] = y
+        elif k == "colour":
+            for i, row in enumerate(v):
+                for j, y in enumerate(row):
+                    c.colour[i][j] = y
         else:
             setattr(c, k, v)
     return c
@@ -213,6 +219,8 @@ class Simulator:
         dev = torch.device("cuda", self.device)
         if i.output == OUT_CLASS_U8:
             out = torch.empty((i.n_views, i.height, i.width), dtype=torch.uint8, device=dev)
+        elif i.output == OUT_RGB_U8:
+            out = torch.empty((i.n_views, 3, i.height, i.width), dtype=torch.uint8, device=dev)
         else:
             out = torch.empty((i.n_views, 4, i.height, i.width), dtype=torch.bfloat16, device=dev)
         d = None

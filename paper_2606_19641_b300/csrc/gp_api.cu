@@ -111,15 +111,23 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
         return fail(GP_EINVAL, "null CSR array");
     if (c->width < 16 || c->height < 16 || c->width > GP_MAX_WIDTH || c->height > GP_MAX_WIDTH)
         return fail(GP_ELIMIT, "image size must be within 16..512");
-    if (c->width % 16) return fail(GP_EINVAL, "image width must be a multiple of 16");
+    if (c->width % 2 || c->height % 2) return fail(GP_EINVAL, "image width and height must be even");
     if (c->n_cams < 1 || c->n_cams > GP_MAX_CAMS) return fail(GP_ELIMIT, "n_cams must be 1..8");
     if (!(c->hfov > 0.01f && c->hfov < 3.0f)) return fail(GP_EINVAL, "hfov out of range");
     if (!(c->near_plane > 0.f) || !(c->cam_height > 0.f) || !(c->dt > 0.f) || !(c->v_max >= 0.f))
         return fail(GP_EINVAL, "near_plane, cam_height, dt must be positive, v_max >= 0");
     if (c->key_precision != GP_KEY_F32 && c->key_precision != GP_KEY_F16)
         return fail(GP_EINVAL, "key_precision");
-    if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16)
+    if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16 && c->output != GP_OUT_RGB_U8)
         return fail(GP_EINVAL, "output");
+    if (c->output == GP_OUT_RGB_U8) {
+        const double l2 = (double)c->light_dir[0] * c->light_dir[0] +
+                          (double)c->light_dir[1] * c->light_dir[1] +
+                          (double)c->light_dir[2] * c->light_dir[2];
+        if (!(l2 > 1e-12) || !finite_all(c->light_dir, 3) || !(c->ambient >= 0.f && c->ambient <= 1.f) ||
+            !finite_all(&c->colour[0][0], 12))
+            return fail(GP_EINVAL, "RGB appearance: light_dir non-zero, ambient in 0..1, finite colours");
+    }
     if (c->threads < 0 || c->threads > 1024 || c->threads % 32 || c->band_rows < 0 ||
         c->tri_capacity < 0 || c->tri_capacity > 4096)
         return fail(GP_EINVAL, "threads (multiple of 32, <= 1024), band_rows, tri_capacity");
@@ -173,6 +181,8 @@ bool finish_shape(gp_handle *h, Shape &s) {
     const gp_config &c = h->cfg;
     if (s.band_rows > c.height) s.band_rows = c.height;
     if (s.band_rows < 1 || s.band_rows > kMaxBandRows) return false;
+    // 4-pixel vector stores: every band must hold a multiple of 4 pixels
+    if (c.width % 4 && s.band_rows % 2) return false;
     if (s.threads < 32 || s.threads > 1024 || s.threads % 32) return false;
     // a setup unit needs at most 32 batch slots; a clip job needs 6
     if (s.tri_cap < 64) return false;
@@ -238,6 +248,15 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     p.guard = 4.0f;
     p.key_f16 = c.key_precision;
     p.out_mode = c.output;
+    {
+        const double l0 = c.light_dir[0], l1 = c.light_dir[1], l2 = c.light_dir[2];
+        const double n = std::sqrt(l0 * l0 + l1 * l1 + l2 * l2);
+        p.light[0] = n > 0 ? (float)(l0 / n) : 0.f;
+        p.light[1] = n > 0 ? (float)(l1 / n) : 0.f;
+        p.light[2] = n > 0 ? (float)(l2 / n) : 1.f;
+        p.ambient = c.ambient;
+        std::memcpy(p.colour, c.colour, sizeof(p.colour));
+    }
     p.out = out;
     p.depth = depth;
     p.view_mod = 0;
@@ -378,7 +397,7 @@ gp_status autotune(gp_handle *h) {
     }
     const gp_config &c = h->cfg;
     const size_t px = (size_t)c.width * c.height;
-    const size_t out_pv = px * (c.output == GP_OUT_CLASS_U8 ? 1 : 8);
+    const size_t out_pv = px * (c.output == GP_OUT_CLASS_U8 ? 1 : (c.output == GP_OUT_RGB_U8 ? 3 : 8));
     const size_t dep_pv = px * (c.key_precision == GP_KEY_F32 ? 4 : 2);
     size_t views = std::min<size_t>((size_t)h->n_views, ((size_t)1 << 30) / (out_pv + dep_pv));
     views = std::max<size_t>(views, 1);
@@ -507,6 +526,13 @@ gp_status gp_default_config(gp_config *c) {
     c->v_max = 30.f;
     c->key_precision = GP_KEY_F32;
     c->output = GP_OUT_CLASS_U8;
+    c->light_dir[0] = 0.3f;
+    c->light_dir[1] = 0.4f;
+    c->light_dir[2] = 0.866f;
+    c->ambient = 0.35f;
+    const float col[4][3] = {{0.55f, 0.75f, 0.95f}, {0.33f, 0.33f, 0.35f}, {0.92f, 0.92f, 0.85f},
+                             {0.15f, 0.35f, 0.85f}};
+    std::memcpy(c->colour, col, sizeof col);
     for (int k = 0; k < 4; ++k) {
         c->norm_mean[k] = 0.5f;
         c->norm_std[k] = 0.5f;
@@ -902,7 +928,7 @@ gp_status gp_get_info(gp_handle *h, gp_info *info) {
     info->key_precision = h->cfg.key_precision;
     info->output = h->cfg.output;
     const long long px = (long long)h->cfg.width * h->cfg.height * h->n_views;
-    info->out_bytes = px * (h->cfg.output == GP_OUT_CLASS_U8 ? 1 : 8);
+    info->out_bytes = px * (h->cfg.output == GP_OUT_CLASS_U8 ? 1 : (h->cfg.output == GP_OUT_RGB_U8 ? 3 : 8));
     info->depth_bytes = px * (h->cfg.key_precision == GP_KEY_F32 ? 4 : 2);
     info->band_rows = h->shape.band_rows;
     info->threads = h->shape.threads;

@@ -76,6 +76,8 @@ struct RenderParams {
     float guard;             // guard band factor
 
     int key_f16, out_mode;
+    float light[3], ambient;  // RGB output: unit direction towards the light, ambient term
+    float colour[4][3];       // RGB output: class colours in [0, 1]
     void *out;
     void *depth;
     int view_mod;            // 0, or write view v at slot v % view_mod (tuning scratch)

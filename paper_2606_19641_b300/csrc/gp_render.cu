@@ -921,12 +921,62 @@ __device__ __forceinline__ uint32_t class_of_low(uint32_t low, uint32_t full, co
     return prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : 2u);
 }
 
-// Store one group of four adjacent pixels' classes (and one-hot channels).
-__device__ __forceinline__ void store_classes(const RenderParams &p, long long slot,
-                                              long long plane, long long px, const uint32_t c[4]) {
+// RGB observation of one pixel, 8 bits per channel in bytes 0..2 (App. A: one directional
+// light, a colour per instance): class colour x (ambient + (1 - ambient) max(0, n . l)), n
+// the winning surface's outward normal -- a box face's normal turned by the box yaw, +z for
+// the ground strips -- and the background unshaded; each channel rint(255 clamp(v, 0, 1)).
+// low = inverted primitive id (0 = background), full = the id's all-ones value.
+__device__ __forceinline__ uint32_t shade_rgb(const RenderParams &p, const Cam &cm, uint32_t low,
+                                              uint32_t full) {
+    uint32_t cls = 0;
+    float shade = 1.f;
+    if (low) {
+        const uint32_t prim = full - low;
+        cls = prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : 2u);
+        float nx = 0.f, ny = 0.f, nz = 1.f;
+        if (cls == 3u) {
+            const uint32_t b = prim / 12u, face = (prim % 12u) >> 1;
+            float sn, c;
+            sincosf(p.box_pose[cm.box_begin + b].z, &sn, &c);
+            // faces +x, -x, +y, -y, +z, -z of the box frame
+            nx = face == 0 ? c : (face == 1 ? -c : (face == 2 ? -sn : (face == 3 ? sn : 0.f)));
+            ny = face == 0 ? sn : (face == 1 ? -sn : (face == 2 ? c : (face == 3 ? -c : 0.f)));
+            nz = face == 4 ? 1.f : (face == 5 ? -1.f : 0.f);
+        }
+        const float ndl = fmaxf(nx * p.light[0] + ny * p.light[1] + nz * p.light[2], 0.f);
+        shade = p.ambient + (1.f - p.ambient) * ndl;
+    }
+    uint32_t rgb = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float base = cls == 0u ? p.colour[0][ch]
+                                     : (cls == 1u ? p.colour[1][ch]
+                                                  : (cls == 2u ? p.colour[2][ch] : p.colour[3][ch]));
+        const float v = fminf(fmaxf(base * shade, 0.f), 1.f);
+        rgb |= (uint32_t)__float2int_rn(255.f * v) << (8 * ch);
+    }
+    return rgb;
+}
+
+// Store one group of four adjacent pixels: class ids, normalised one-hot channels, or RGB.
+// c: classes; low: inverted primitive ids (full: the id's all-ones value).
+__device__ __forceinline__ void store_classes(const RenderParams &p, const Cam &cm, long long slot,
+                                              long long plane, long long px, const uint32_t c[4],
+                                              const uint32_t low[4], uint32_t full) {
     if (p.out_mode == GP_OUT_CLASS_U8) {
         __stcs((unsigned int *)((uint8_t *)p.out + slot * plane + px),
                c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24));
+    } else if (p.out_mode == GP_OUT_RGB_U8) {
+        uint32_t q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = shade_rgb(p, cm, low[k], full);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const int sh = 8 * ch;
+            __stcs((unsigned int *)((uint8_t *)p.out + (slot * 3 + ch) * plane + px),
+                   ((q[0] >> sh) & 0xFFu) | (((q[1] >> sh) & 0xFFu) << 8) |
+                       (((q[2] >> sh) & 0xFFu) << 16) | (((q[3] >> sh) & 0xFFu) << 24));
+        }
     } else {
         for (int ch = 0; ch < 4; ++ch) {
             const uint32_t lo = (uint32_t)p.onehot[ch][c[0] == (uint32_t)ch] |
@@ -953,11 +1003,10 @@ __device__ void encode_f32(const RenderParams &p, const Cam &cm, unsigned long l
         const ulonglong2 k23 = *(const ulonglong2 *)(keys + b + 2);
         *(ulonglong2 *)(keys + b) = make_ulonglong2(0ull, 0ull);
         *(ulonglong2 *)(keys + b + 2) = make_ulonglong2(0ull, 0ull);
-        const uint32_t c[4] = {class_of_low((uint32_t)k01.x, 0xFFFFFFFFu, cm),
-                               class_of_low((uint32_t)k01.y, 0xFFFFFFFFu, cm),
-                               class_of_low((uint32_t)k23.x, 0xFFFFFFFFu, cm),
-                               class_of_low((uint32_t)k23.y, 0xFFFFFFFFu, cm)};
-        store_classes(p, slot, plane, row0 + b, c);
+        const uint32_t low[4] = {(uint32_t)k01.x, (uint32_t)k01.y, (uint32_t)k23.x, (uint32_t)k23.y};
+        const uint32_t c[4] = {class_of_low(low[0], 0xFFFFFFFFu, cm), class_of_low(low[1], 0xFFFFFFFFu, cm),
+                               class_of_low(low[2], 0xFFFFFFFFu, cm), class_of_low(low[3], 0xFFFFFFFFu, cm)};
+        store_classes(p, cm, slot, plane, row0 + b, c, low, 0xFFFFFFFFu);
         if (p.depth)
             __stcs((uint4 *)((float *)p.depth + slot * plane + row0 + b),
                    make_uint4((uint32_t)(k01.x >> 32), (uint32_t)(k01.y >> 32),
@@ -975,9 +1024,10 @@ __device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *k
     for (int b = 4 * g.tid; b < band_px; b += 4 * g.nt) {
         const uint4 k = *(const uint4 *)(keys + b);
         *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t c[4] = {class_of_low(k.x & 0xFFFFu, 0xFFFFu, cm), class_of_low(k.y & 0xFFFFu, 0xFFFFu, cm),
-                               class_of_low(k.z & 0xFFFFu, 0xFFFFu, cm), class_of_low(k.w & 0xFFFFu, 0xFFFFu, cm)};
-        store_classes(p, slot, plane, row0 + b, c);
+        const uint32_t low[4] = {k.x & 0xFFFFu, k.y & 0xFFFFu, k.z & 0xFFFFu, k.w & 0xFFFFu};
+        const uint32_t c[4] = {class_of_low(low[0], 0xFFFFu, cm), class_of_low(low[1], 0xFFFFu, cm),
+                               class_of_low(low[2], 0xFFFFu, cm), class_of_low(low[3], 0xFFFFu, cm)};
+        store_classes(p, cm, slot, plane, row0 + b, c, low, 0xFFFFu);
         if (p.depth)
             __stcs((uint2 *)((uint16_t *)p.depth + slot * plane + row0 + b),
                    make_uint2((k.x >> 16) | (k.y & 0xFFFF0000u), (k.z >> 16) | (k.w & 0xFFFF0000u)));
@@ -1211,7 +1261,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
 
 // What a raster batch of the pipelined kernel carries besides its triangles.
 struct BatchMeta {
-    int n, view, by0, by1;
+    int n, view, by0, by1, box_begin;
     uint32_t box_end, road_end;
     int flags;  // kBatchLast: the item's last batch (encode after it); kBatchEnd: no more work
 };
@@ -1315,8 +1365,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             g.sync();
             const int b = s & 1;
             if (g.tid == 0) {
-                meta[b] = BatchMeta{sh.resv, view, cm.by0, cm.by1, cm.box_end, cm.road_end,
-                                    last ? kBatchLast : 0};
+                meta[b] = BatchMeta{sh.resv, view, cm.by0, cm.by1, cm.box_begin, cm.box_end,
+                                    cm.road_end, last ? kBatchLast : 0};
                 sh.resv = 0;
             }
             mbar_arrive(&bars[b]);  // release: this thread's records (and thread 0's meta)
@@ -1366,6 +1416,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
                 Cam cm;
                 cm.by0 = mt.by0;
                 cm.by1 = mt.by1;
+                cm.box_begin = mt.box_begin;
                 cm.box_end = mt.box_end;
                 cm.road_end = mt.road_end;
                 if (F32) encode_f32(p, cm, (unsigned long long *)keys, mt.view, g);

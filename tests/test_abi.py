@@ -88,7 +88,11 @@ def _good():
     (lambda w, c: w.update(agents=[3]), -1),
     (lambda w, c: w.update(boxes=[[0, 0, 0, 4, 2, 1.5, 1], [10, 0, np.nan, 4, 2, 1.5, 0]]), -1),
     (lambda w, c: w.update(boxes=[[0, 0, 0, 4, 2, 1.5, 1], [10, 0, 0, 0, 2, 1.5, 0]]), -1),
-    (lambda w, c: setattr(c, "width", 100), -1),
+    (lambda w, c: setattr(c, "width", 101), -1),
+    (lambda w, c: setattr(c, "height", 63), -1),
+    (lambda w, c: setattr(c, "output", 3), -1),
+    (lambda w, c: (setattr(c, "output", 2), [c.light_dir.__setitem__(i, 0.0) for i in range(3)]), -1),
+    (lambda w, c: (setattr(c, "output", 2), setattr(c, "ambient", -0.1)), -1),
     (lambda w, c: setattr(c, "width", 1024), -4),
     (lambda w, c: setattr(c, "n_cams", 9), -4),
     (lambda w, c: setattr(c, "key_precision", 7), -1),

@@ -110,7 +110,7 @@ class Workload:
     height: int
     cam_yaw_deg: Tuple[float, ...] = (0.0,)
     precision: str = "f32"           # depth key precision: "f32" or "f16"
-    output: str = "class_u8"         # "class_u8" or "onehot_bf16"
+    output: str = "class_u8"         # "class_u8", "onehot_bf16" or "rgb_u8"
     steps: int = 10
     seed: int = 1000
     dt: float = 0.1
@@ -140,6 +140,17 @@ WORKLOADS = {
     "sweep": Workload("sweep: 256 worlds x 32 agents x 3 cameras, 64 boxes, 1000 segments",
                       256, (32, 32), (1000, 1000), 64, 128, 128,
                       cam_yaw_deg=(0.0, 60.0, -60.0), steps=10, seed=1004),
+    # The paper's observation rig (App. A rendering; training details): four cameras --
+    # front, front-left, front-right (read as +-60 deg), rear -- at its two training
+    # resolutions, shaded RGB with one directional light.
+    "paper_rig_210x126": Workload(
+        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 210x126 RGB",
+        256, (32, 32), (500, 500), 32, 210, 126, cam_yaw_deg=(0.0, 60.0, -60.0, 180.0),
+        precision="f16", output="rgb_u8", steps=10, seed=1005),
+    "paper_rig_434x252": Workload(
+        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 434x252 RGB",
+        256, (32, 32), (500, 500), 32, 434, 252, cam_yaw_deg=(0.0, 60.0, -60.0, 180.0),
+        precision="f16", output="rgb_u8", steps=10, seed=1006),
 }
 
 
