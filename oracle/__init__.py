@@ -86,6 +86,13 @@ def _lib():
         lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
         lib.or_f32_to_bf16.restype = ctypes.c_uint16
         lib.or_onehot_bf16.argtypes = [c_u8p, ctypes.c_int64, c_f32p, c_f32p, c_u16p]
+        lib.or_lane_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, c_f32p,
+                                      ctypes.c_double, c_f64p, c_f64p]
+        lib.or_lane_frame.restype = ctypes.c_int
+        lib.or_rewards_world.argtypes = [ctypes.c_int32, c_f64p, c_u8p, c_f64p, c_u8p, c_f32p,
+                                         c_f64p, c_f64p, c_f64p, ctypes.c_int32, c_f32p,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, c_f64p, c_f64p]
         lib.or_shade_rgb.argtypes = [c_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                      ctypes.c_uint32, c_f64p, c_f64p, c_f64p, ctypes.c_double,
                                      c_u8p]
@@ -200,6 +207,44 @@ def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: in
     fn(t.ctypes.data, len(t), width, height, int(key_f16), box_end, road_end, _p(key, c_u64p),
        _p(cls, c_u8p), _p(d32, c_f32p), _p(d16, c_u16p))
     return Image(key, cls, d16 if key_f16 else d32)
+
+
+# Reward weights at inference (Table "Reward terms", rightmost column), in the order
+# collision, off-road, comfort, alignment, centering, velocity, traffic light, time,
+# reverse, overspeed.
+REWARD_WEIGHTS = (3.0, 3.0, 0.05, 0.025, 3.8e-3, 2.5e-3, 1.0, 2.5e-5, 5e-3, 0.0)
+LANE_WIDTH = 3.5
+
+
+def lane_frame(px: float, py: float, road: np.ndarray, lane_w: float = LANE_WIDTH):
+    """(lane direction, lateral offset x_f) of a point, or None off the road."""
+    rd = _c(road, np.float32).reshape(-1, 8)
+    d, x = ctypes.c_double(), ctypes.c_double()
+    ok = _lib().or_lane_frame(float(px), float(py), rd.shape[0], _p(rd, c_f32p), float(lane_w),
+                              ctypes.byref(d), ctypes.byref(x))
+    return (d.value, x.value) if ok else None
+
+
+def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weights, road,
+                  lane_w=LANE_WIDTH, v_lim=30.0, dt=0.1, vmax=30.0):
+    """Per-agent reward and ego state [n, 6] of one step (see or_rewards_world); `acc`
+    [n, 2] (previous accelerations) is updated in place."""
+    b = _c(before, np.float64).reshape(-1, 4)
+    n = b.shape[0]
+    a = _c(after, np.float64).reshape(-1, 4)
+    fb, fa = _c(fl_before, np.uint8), _c(fl_after, np.uint8)
+    act = _c(actions, np.float32).reshape(-1, 2)
+    dm = _c(dims, np.float64).reshape(-1, 2)
+    assert acc.dtype == np.float64 and acc.flags.c_contiguous and acc.shape == (n, 2)
+    w = _c(weights, np.float64).reshape(-1, 10)
+    rd = _c(road, np.float32).reshape(-1, 8)
+    reward = np.zeros(n, np.float64)
+    ego = np.zeros((n, 6), np.float64)
+    _lib().or_rewards_world(n, _p(b, c_f64p), _p(fb, c_u8p), _p(a, c_f64p), _p(fa, c_u8p),
+                            _p(act, c_f32p), _p(dm, c_f64p), _p(acc, c_f64p), _p(w, c_f64p),
+                            rd.shape[0], _p(rd, c_f32p), float(lane_w), float(v_lim), float(dt),
+                            float(vmax), _p(reward, c_f64p), _p(ego, c_f64p))
+    return reward, ego
 
 
 # Default RGB appearance (readings; the paper gives only "blue" for vehicles and static

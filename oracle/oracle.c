@@ -176,6 +176,106 @@ void or_step_world(int32_t n_boxes, int32_t n_agents, double *boxes, double *sta
     }
 }
 
+/*
+ * Lane frame of a point: the road quad of smallest index that contains it (boundary
+ * inside).  Road quads run from their q0-q3 edge to their q1-q2 edge; with right-hand
+ * traffic on a two-lane road the half right of the centre line (lateral offset s < 0,
+ * measured along the left normal from the quad centre) runs along that direction and the
+ * left half against it; x_f is the offset from the lane's centre line (+-lane_w / 2).
+ * Returns 0 if no road quad contains the point.
+ */
+int or_lane_frame(double px, double py, int32_t n_road, const float *road, double lane_w,
+                  double *lane_dir, double *xf) {
+    for (int32_t r = 0; r < n_road; ++r) {
+        const float *q = road + 8 * r;
+        if (!or_point_in_quad(px, py, q)) continue;
+        const double m0x = 0.5 * ((double)q[0] + q[6]), m0y = 0.5 * ((double)q[1] + q[7]);
+        const double m1x = 0.5 * ((double)q[2] + q[4]), m1y = 0.5 * ((double)q[3] + q[5]);
+        double dx = m1x - m0x, dy = m1y - m0y;
+        const double len = sqrt(dx * dx + dy * dy);
+        dx /= len;
+        dy /= len;
+        const double cx = 0.25 * ((double)q[0] + q[2] + q[4] + q[6]);
+        const double cy = 0.25 * ((double)q[1] + q[3] + q[5] + q[7]);
+        const double s = (px - cx) * (-dy) + (py - cy) * dx;
+        if (s < 0.0) {
+            *lane_dir = atan2(dy, dx);
+            *xf = s + 0.5 * lane_w;
+        } else {
+            *lane_dir = atan2(-dy, -dx);
+            *xf = s - 0.5 * lane_w;
+        }
+        return 1;
+    }
+    return 0;
+}
+
+/*
+ * Per-step reward and ego state of one world's agents (App. A "Reward Functions and Reward
+ * Conditioning", Table "Reward terms"; "Observations": ego state), evaluated for a step of
+ * or_step_world.  Readings:
+ *   - a_lon = (v' - v) / dt and a_lat = v * dyaw / dt with v the speed at the step start,
+ *     v' = clip(v + a dt, 0, v_max) and dyaw = (v / l_r) sin(beta) dt the bicycle's
+ *     increments (before any halt); jerks are their differences to the previous step / dt;
+ *   - collision and off-road are this step's new flags, the collision scaled by |v|;
+ *   - theta_f in [0, pi] is the heading's misalignment with the lane of the post-step
+ *     position (or_lane_frame) and x_f the lateral offset from its centre line; the lane
+ *     terms are 0 off the road;
+ *   - the traffic-light and goal terms are 0: the synthetic worlds have no signals or
+ *     goals; an agent halted before the step earns 0 and has zero accelerations;
+ *   - ego state: v'' / v_max (v'' the post-step speed), a_lon / 10, a_lat / 10, L / 10,
+ *     W / 5 (each clipped to [-1, 1]) and the collision flag (0 or 1).
+ *   before/after [n][4] x, y, yaw, v; fl_before/fl_after [n]; actions [n][2] accel, steer;
+ *   dims [n][2] L, W; acc [n][2] previous a_lon, a_lat (overwritten with this step's);
+ *   weights [n][10] collision, off-road, comfort, alignment, centering, velocity, traffic
+ *   light, time, reverse, overspeed -> reward [n], ego [n][6]
+ */
+void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
+                      const double *after, const uint8_t *fl_after, const float *actions,
+                      const double *dims, double *acc, const double *weights, int32_t n_road,
+                      const float *road, double lane_w, double v_lim, double dt, double vmax,
+                      double *reward, double *ego) {
+    for (int32_t i = 0; i < n; ++i) {
+        const double *w = weights + 10 * i;
+        double a_lon = 0.0, a_lat = 0.0, r = 0.0;
+        if (!(fl_before[i] & OR_HALTED)) {
+            const double v0 = before[4 * i + 3];
+            const double lr = 0.3 * dims[2 * i];
+            const double beta = atan(0.5 * tan((double)actions[2 * i + 1]));
+            double vn = v0 + (double)actions[2 * i] * dt;
+            if (vn < 0.0) vn = 0.0;
+            if (vn > vmax) vn = vmax;
+            const double dyaw = (v0 / lr) * sin(beta) * dt;
+            a_lon = (vn - v0) / dt;
+            a_lat = v0 * dyaw / dt;
+            const double j_lon = (a_lon - acc[2 * i]) / dt, j_lat = (a_lat - acc[2 * i + 1]) / dt;
+            if (fl_after[i] & OR_COLLIDED) r -= w[0] + 0.1 * fabs(v0);
+            if (fl_after[i] & OR_OFFROAD) r -= w[1];
+            r -= w[2] * ((fabs(a_lon) > 3.0) + (fabs(a_lat) > 3.0) +
+                         (fabs(j_lon) > 5.0 || fabs(j_lat) > 5.0));
+            double lane_dir, xf;
+            if (or_lane_frame(after[4 * i], after[4 * i + 1], n_road, road, lane_w, &lane_dir,
+                              &xf)) {
+                const double th = fabs(wrap_pi(after[4 * i + 2] - lane_dir));
+                const double ct = cos(th);
+                r += w[3] * dt * (fmin(ct, 0.0) + fmin(vn * ct, 0.0) + 0.0025 * (1.0 - 2.0 * th / M_PI));
+                r -= w[4] * dt * ((ct > 0.5 ? fabs(xf) : 0.0) - 0.05 * exp(0.5 - fabs(xf)));
+                if (fabs(vn) > 2.5) r += w[5] * dt * fmax(ct, 0.0);
+            }
+            if (fabs(vn) > 0.0 || a_lon != 0.0 || a_lat != 0.0) r -= w[7] * dt;
+            if (vn < 0.0) r -= w[8] * dt;
+            if (fabs(vn) > v_lim) r -= w[9];
+        }
+        acc[2 * i] = a_lon;
+        acc[2 * i + 1] = a_lat;
+        reward[i] = r;
+        const double e[5] = {after[4 * i + 3] / vmax, a_lon / 10.0, a_lat / 10.0,
+                             dims[2 * i] / 10.0, dims[2 * i + 1] / 5.0};
+        for (int k = 0; k < 5; ++k) ego[6 * i + k] = fmax(-1.0, fmin(1.0, e[k]));
+        ego[6 * i + 5] = (fl_after[i] & OR_COLLIDED) ? 1.0 : 0.0;
+    }
+}
+
 /* ------------------------------------------------------------------------------------
  * Geometry: camera, scene triangles, clipping, projection, snapping (FP64)
  * ------------------------------------------------------------------------------------ */

@@ -38,6 +38,18 @@ MUTANTS = {
     "shade +y normal rotated wrong": ("case 2: nx = -sn; ny = c;", "case 2: nx = sn; ny = c;"),
     "shade ground faces down": ("double nx = 0.0, ny = 0.0, nz = 1.0;", "double nx = 0.0, ny = 0.0, nz = -1.0;"),
     "shade background lit": ("double shade = 1.0;", "double shade = 0.5;"),
+    "left-hand traffic": ("        if (s < 0.0) {\n            *lane_dir = atan2(dy, dx);",
+                          "        if (s > 0.0) {\n            *lane_dir = atan2(dy, dx);"),
+    "lane centre offset sign": ("*xf = s + 0.5 * lane_w;", "*xf = s - 0.5 * lane_w;"),
+    "collision ignores speed": ("r -= w[0] + 0.1 * fabs(v0);", "r -= w[0];"),
+    "jerk needs both axes": ("(fabs(j_lon) > 5.0 || fabs(j_lat) > 5.0)", "(fabs(j_lon) > 5.0 && fabs(j_lat) > 5.0)"),
+    "centering sign": ("r -= w[4] * dt * ((ct > 0.5", "r += w[4] * dt * ((ct > 0.5"),
+    "velocity without threshold": ("if (fabs(vn) > 2.5) r += w[5]", "if (fabs(vn) > 0.0) r += w[5]"),
+    "misalignment signed": ("const double th = fabs(wrap_pi(after[4 * i + 2] - lane_dir));",
+                            "const double th = wrap_pi(after[4 * i + 2] - lane_dir);"),
+    "halted agents rewarded": ("if (!(fl_before[i] & OR_HALTED)) {\n            const double v0",
+                               "if (1) {\n            const double v0"),
+    "ego speed unnormalised": ("const double e[5] = {after[4 * i + 3] / vmax,", "const double e[5] = {after[4 * i + 3],"),
 }
 
 

@@ -830,3 +830,104 @@ def test_rgb_side_face_normal_follows_box_yaw():
     assert faces == {2}  # only the +y face is visible
     for ch in range(3):
         assert np.all(rgb[ch][side] == _rgb8(col[3][ch]))
+
+
+# ---------------------------------------------------------------------------------------
+# Reward terms (Table "Reward terms") and ego state: closed forms on a two-lane road
+# ---------------------------------------------------------------------------------------
+
+W_INF = oracle.REWARD_WEIGHTS  # collision, off-road, comfort, alignment, centering,
+#                                velocity, traffic light, time, reverse, overspeed
+STRAIGHT = np.array([rect_quad(-100.0, 100.0, -3.5, 3.5)], np.float32)  # runs along +x
+
+
+def _reward_step(y, yaw, v0, accel=0.0, steer=0.0, fl_after=0, fl_before=0, acc=(0.0, 0.0),
+                 road=STRAIGHT, x=0.0, L=4.5, Wd=1.9, weights=W_INF):
+    before = np.array([[x, y, yaw, v0]], np.float64)
+    after = before.copy()
+    if not fl_before & 4:
+        after[0] = oracle.bicycle(x, y, yaw, v0, L, accel, steer)
+    if fl_after & 3:
+        after[0, 3] = 0.0  # halted this step
+    a = np.array([acc], np.float64)
+    r, ego = oracle.rewards_world(before, [fl_before], after, [fl_after | (4 if fl_after & 3 else 0)],
+                                  [[accel, steer]], [[L, Wd]], a, [weights], road)
+    return float(r[0]), ego[0], a[0]
+
+
+def _lane_terms(theta, v, xf, dt=0.1, w=W_INF):
+    ct = math.cos(theta)
+    aln = w[3] * dt * (min(ct, 0.0) + min(v * ct, 0.0) + 0.0025 * (1 - 2 * theta / math.pi))
+    ctr = -w[4] * dt * ((abs(xf) if ct > 0.5 else 0.0) - 0.05 * math.exp(0.5 - abs(xf)))
+    vel = w[5] * dt * max(ct, 0.0) if abs(v) > 2.5 else 0.0
+    return aln + ctr + vel
+
+
+def test_reward_cruising_in_lane():
+    r, _, _ = _reward_step(-1.75, 0.0, 10.0)
+    assert r == pytest.approx(_lane_terms(0.0, 10.0, 0.0) - W_INF[7] * 0.1, rel=1e-12, abs=1e-15)
+
+
+def test_reward_wrong_way_lane():
+    # right-hand traffic: the left half of the road runs against the quad's direction
+    r, _, _ = _reward_step(+1.75, 0.0, 10.0)
+    assert r == pytest.approx(_lane_terms(math.pi, 10.0, 0.0) - W_INF[7] * 0.1, rel=1e-12)
+    assert r < -0.02  # wrong-way driving is penalised
+
+
+def test_reward_lateral_offset_and_misalignment():
+    r, _, _ = _reward_step(-1.75 + 0.6, -0.2, 10.0)
+    th, xf = 0.2, 0.6 + 10.0 * math.sin(-0.2) * 0.1  # the step moves the agent sideways
+    assert r == pytest.approx(_lane_terms(th, 10.0, xf) - W_INF[7] * 0.1, rel=1e-9)
+
+
+def test_reward_slow_agent_gets_no_velocity_term():
+    r, _, _ = _reward_step(-1.75, 0.0, 2.0)
+    assert r == pytest.approx(_lane_terms(0.0, 2.0, 0.0) - W_INF[7] * 0.1, rel=1e-12)
+    assert _lane_terms(0.0, 2.0, 0.0) < _lane_terms(0.0, 3.0, 0.0)
+
+
+def test_reward_harsh_braking_and_jerk():
+    r, ego, acc = _reward_step(-1.75, 0.0, 10.0, accel=-5.0)
+    assert acc[0] == pytest.approx(-5.0) and acc[1] == 0.0
+    base = _lane_terms(0.0, 9.5, 0.0) - W_INF[7] * 0.1
+    assert r == pytest.approx(base - 2 * W_INF[2], rel=1e-9)  # |a_lon| > 3 and jerk > 5
+    # the same deceleration again: no jerk, still harsh
+    r2, _, _ = _reward_step(-1.75, 0.0, 10.0, accel=-5.0, acc=(-5.0, 0.0))
+    assert r2 == pytest.approx(base - W_INF[2], rel=1e-9)
+    assert ego[1] == pytest.approx(-0.5)
+
+
+def test_reward_collision_scales_with_speed_and_offroad():
+    r, ego, _ = _reward_step(-1.75, 0.0, 10.0, fl_after=1)
+    assert r == pytest.approx(_lane_terms(0.0, 10.0, 0.0) - W_INF[7] * 0.1 - (W_INF[0] + 0.1 * 10.0),
+                              rel=1e-9)
+    assert ego[5] == 1.0 and ego[0] == 0.0  # collided; speed zeroed by the halt
+    r, _, _ = _reward_step(50.0, 0.0, 10.0, fl_after=2)  # off the road: no lane terms
+    assert r == pytest.approx(-W_INF[1] - W_INF[7] * 0.1, rel=1e-12)
+
+
+def test_reward_halted_agent_earns_nothing():
+    r, ego, acc = _reward_step(-1.75, 0.0, 0.0, fl_before=4 | 1, fl_after=4 | 1, acc=(3.0, 1.0))
+    assert r == 0.0 and acc[0] == 0.0 and acc[1] == 0.0
+    assert ego[5] == 1.0
+
+
+def test_lane_frame_follows_road_direction():
+    phi = 0.9
+    c, s = math.cos(phi), math.sin(phi)
+    local = [(-20, -3.5), (20, -3.5), (20, 3.5), (-20, 3.5)]
+    quad = np.array([[v for (u, w) in local for v in (u * c - w * s, u * s + w * c)]], np.float32)
+    for lat, want_dir, want_xf in ((-1.75, phi, 0.0), (-1.0, phi, 0.75), (2.0, phi - math.pi, 0.25)):
+        px, py = -lat * s, lat * c
+        d, xf = oracle.lane_frame(px, py, quad)
+        assert math.cos(d - want_dir) == pytest.approx(1.0, abs=1e-9)
+        assert xf == pytest.approx(want_xf, abs=1e-6)
+    assert oracle.lane_frame(100.0, 100.0, quad) is None
+
+
+def test_ego_state_normalisation():
+    _, ego, _ = _reward_step(-1.75, 0.0, 15.0, accel=1.0, L=4.2, Wd=1.8)
+    assert ego[0] == pytest.approx(15.1 / 30.0)
+    assert ego[1] == pytest.approx(0.1) and ego[2] == 0.0
+    assert ego[3] == pytest.approx(0.42) and ego[4] == pytest.approx(0.36) and ego[5] == 0.0
