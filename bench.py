@@ -397,6 +397,12 @@ def main():
         extras["precision_path"]["speedup_vs_per_world_path"] = (
             extras["precision_path"]["agent_steps_per_s"] / extras["per_world_path"]["agent_steps_per_s"])
         sim_p.close()
+        # the same batch with the reward terms and ego state computed in every step
+        sim_w = Simulator(worlds, config_for(wl_rank, rewards=1, autotune=1), device=local)
+        extras["with_rewards"] = graph_rate(sim_w, worlds, wl_rank, 20)
+        extras["with_rewards"]["note"] = ("step computes the reward table's terms and the ego "
+                                          "state for every agent (gp_get_rewards)")
+        sim_w.close()
         # ragged batch at 256x144, precision path
         wl_r = rank_workload(wg.WORKLOADS["ragged_precision"], rank)
         worlds_r = wg.make_workload(wl_r)

@@ -130,6 +130,11 @@ typedef struct gp_config {
     float ambient;                /* 0..1 (default 0.35) */
     float colour[4][3];           /* RGB in 0..1 of classes background, road, lane line,
                                      vehicle/static box (defaults: sky, grey, off-white, blue) */
+    /* Per-step reward terms and ego state (App. A reward table and observations), computed
+     * in gp_step when rewards = 1 (default 0) and read with gp_get_rewards. */
+    int32_t rewards;
+    float lane_width;             /* lane width of the two-lane roads (default 3.5 m) */
+    float v_limit;                /* speed limit of the overspeed term (default 30 m/s) */
 } gp_config;
 
 /* Fill `cfg` with the defaults above. */
@@ -208,6 +213,31 @@ typedef struct gp_info {
     int32_t producer_warps;            /* 0 = one-phase-at-a-time render kernel */
 } gp_info;
 gp_status gp_get_info(gp_handle *h, gp_info *info);
+
+/*
+ * Rewards and ego state of the last gp_step (gp_config.rewards = 1, else GP_ESTATE).
+ * reward [n_agents] float: the weighted sum of the reward table's terms (App. A) --
+ *   collision -(w0 + 0.1 |v|), off-road -w1, comfort -w2 (1[|a_lon| > 3] + 1[|a_lat| > 3]
+ *   + 1[|jerk_lon| > 5 or |jerk_lat| > 5]), lane alignment, lane centering and velocity
+ *   (w3..w5, from the lane frame of the road quad of smallest index under the agent,
+ *   right-hand traffic, 0 off the road), time -w7 dt, reverse -w8 dt, overspeed -w9
+ *   (|v| > v_limit); traffic-light (w6) and goal terms are 0 (no signals or goals).
+ *   Accelerations are the bicycle's increments of the step (speed before any halt):
+ *   a_lon = (v' - v) / dt, a_lat = v dyaw / dt; an agent halted before the step earns 0.
+ * ego [n_agents][6] float: speed / v_max, a_lon / 10, a_lat / 10, L / 10, W / 5 (clipped to
+ *   [-1, 1]) and the collision flag (0 or 1).
+ * Either pointer may be NULL.  on_host != 0: host memory, synchronous; else device
+ * memory, asynchronous on `stream`.
+ */
+gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, void *stream);
+/*
+ * Per-agent reward weights [n_agents][10] in the order collision, off-road, comfort,
+ * alignment, centering, velocity, traffic light, time, reverse, overspeed (positive
+ * magnitudes; defaults: the table's inference column 3, 3, 0.05, 0.025, 0.0038, 0.0025,
+ * 1, 2.5e-5, 0.005, 0).  on_host as above.  gp_set_state resets the previous-step
+ * accelerations to 0.
+ */
+gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host, void *stream);
 
 /* Read (synchronously) / clear the device status word; set bits for tests. */
 gp_status gp_get_status(gp_handle *h, uint32_t *bits);

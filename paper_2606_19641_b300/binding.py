@@ -28,6 +28,7 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render",
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
+            "gp_get_rewards", "gp_set_reward_weights",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -56,7 +57,9 @@ class Config(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("tri_capacity", ctypes.c_int32),
                 ("producer_warps", ctypes.c_int32),
                 ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
-                ("colour", (ctypes.c_float * 3) * 4)]
+                ("colour", (ctypes.c_float * 3) * 4),
+                ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
+                ("v_limit", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):
@@ -98,6 +101,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_get_status": [vp, ctypes.POINTER(u32)],
         "gp_clear_status": [vp],
         "gp_debug_inject_status": [vp, u32],
+        "gp_get_rewards": [vp, vp, vp, i32, vp],
+        "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
         "gp_debug_dump_tris_noalloc": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -270,6 +275,26 @@ class Simulator:
 
     def inject_status(self, bits: int) -> None:
         check(lib().gp_debug_inject_status(self._h, bits))
+
+    def rewards(self, stream=None):
+        """(reward [n_agents], ego state [n_agents, 6]) of the last step, float32 on the
+        device (the handle must have been created with rewards = 1)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        r = torch.empty((self.n_agents,), dtype=torch.float32, device=dev)
+        e = torch.empty((self.n_agents, 6), dtype=torch.float32, device=dev)
+        check(lib().gp_get_rewards(self._h, _ptr(r), _ptr(e), 0, _stream(stream)))
+        return r, e
+
+    def set_reward_weights(self, weights) -> None:
+        """Per-agent reward weights [n_agents, 10] (host array or device tensor)."""
+        if isinstance(weights, np.ndarray):
+            w = np.ascontiguousarray(weights, np.float32)
+            assert w.shape == (self.n_agents, 10)
+            check(lib().gp_set_reward_weights(self._h, w.ctypes.data, 1, _stream(None)))
+        else:
+            assert tuple(weights.shape) == (self.n_agents, 10) and weights.is_contiguous()
+            check(lib().gp_set_reward_weights(self._h, _ptr(weights), 0, _stream(None)))
 
     def debug_stall_pipeline(self, out, depth=None, wait_ns: int = 50_000_000) -> None:
         """Run the pipelined render kernel with producers that publish nothing (its bounded

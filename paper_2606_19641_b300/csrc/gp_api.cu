@@ -88,6 +88,8 @@ struct gp_handle {
     DevBuf<int2> items;
     DevBuf<DumpTri> dump;
     DevBuf<float> state_stage;
+    DevBuf<float> reward, ego, weights;  // per-step rewards: [n_agents], [n_agents][6], [n_agents][10]
+    DevBuf<float2> acc;                  // previous-step accelerations
     DevBuf<uint8_t> flag_stage;
     Shape shape;
     uint16_t onehot[4][2];
@@ -120,6 +122,9 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
         return fail(GP_EINVAL, "key_precision");
     if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16 && c->output != GP_OUT_RGB_U8)
         return fail(GP_EINVAL, "output");
+    if (c->rewards != 0 && c->rewards != 1) return fail(GP_EINVAL, "rewards must be 0 or 1");
+    if (c->rewards && !(c->lane_width > 0.f && c->v_limit >= 0.f))
+        return fail(GP_EINVAL, "lane_width must be positive, v_limit >= 0");
     if (c->output == GP_OUT_RGB_U8) {
         const double l2 = (double)c->light_dir[0] * c->light_dir[0] +
                           (double)c->light_dir[1] * c->light_dir[1] +
@@ -287,6 +292,13 @@ StepParams step_params(gp_handle *h, const float *actions) {
     p.dt = h->cfg.dt;
     p.vmax = h->cfg.v_max;
     p.status = h->status.p;
+    p.rewards = h->cfg.rewards;
+    p.lane_w = h->cfg.lane_width;
+    p.vlim = h->cfg.v_limit;
+    p.weights = h->weights.p;
+    p.acc = h->acc.p;
+    p.reward = h->reward.p;
+    p.ego = h->ego.p;
     return p;
 }
 
@@ -490,6 +502,10 @@ void release_all(gp_handle *h) {
     h->quad_geo.release();
     h->road_geo.release();
     h->speed.release();
+    h->reward.release();
+    h->ego.release();
+    h->weights.release();
+    h->acc.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -530,6 +546,9 @@ gp_status gp_default_config(gp_config *c) {
     c->light_dir[1] = 0.4f;
     c->light_dir[2] = 0.866f;
     c->ambient = 0.35f;
+    c->rewards = 0;
+    c->lane_width = 3.5f;
+    c->v_limit = 30.f;
     const float col[4][3] = {{0.55f, 0.75f, 0.95f}, {0.33f, 0.33f, 0.35f}, {0.92f, 0.92f, 0.85f},
                              {0.15f, 0.35f, 0.85f}};
     std::memcpy(c->colour, col, sizeof col);
@@ -755,6 +774,18 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(state_stage, stage);
     std::vector<uint8_t> fstage(std::max(1, h->n_agents), 0);
     UP(flag_stage, fstage);
+    {
+        const size_t na = (size_t)std::max(1, h->n_agents);
+        std::vector<float> r0(na, 0.f), e0(6 * na, 0.f), w0(10 * na);
+        const float inference[10] = {3.f, 3.f, 0.05f, 0.025f, 3.8e-3f, 2.5e-3f, 1.f, 2.5e-5f, 5e-3f, 0.f};
+        for (size_t i = 0; i < na; ++i)
+            for (int k = 0; k < 10; ++k) w0[10 * i + k] = inference[k];
+        std::vector<float2> a0(na, make_float2(0.f, 0.f));
+        UP(reward, r0);
+        UP(ego, e0);
+        UP(weights, w0);
+        UP(acc, a0);
+    }
 #undef UP
 
     if (render_configure(smem_limit(device) - 1024) != cudaSuccess) {
@@ -912,6 +943,35 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     } else {
         CK(launch_state(const_cast<float *>(state), const_cast<uint8_t *>(flags), h->box_pose.p,
                         h->speed.p, h->flags.p, h->agent_box.p, n, 0, s));
+    }
+    if (n) CK(cudaMemsetAsync(h->acc.p, 0, sizeof(float2) * n, s));  // accelerations restart
+    return GP_OK;
+}
+
+gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!h->cfg.rewards) return fail(GP_ESTATE, "rewards are off (gp_config.rewards = 0)");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    const cudaMemcpyKind k = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (reward && n) CK(cudaMemcpyAsync(reward, h->reward.p, sizeof(float) * n, k, s));
+    if (ego && n) CK(cudaMemcpyAsync(ego, h->ego.p, sizeof(float) * 6 * n, k, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
+gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host, void *stream) {
+    if (!h || !weights) return fail(GP_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    if (on_host) {
+        if (!finite_all(weights, 10 * n)) return fail(GP_EINVAL, "non-finite reward weights");
+        if (n) CK(cudaMemcpyAsync(h->weights.p, weights, sizeof(float) * 10 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    } else if (n) {
+        CK(cudaMemcpyAsync(h->weights.p, weights, sizeof(float) * 10 * n, cudaMemcpyDeviceToDevice, s));
     }
     return GP_OK;
 }

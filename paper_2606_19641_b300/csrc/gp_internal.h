@@ -47,6 +47,13 @@ struct StepParams {
     const int *cell_quads;
     float dt, vmax;
     uint32_t *status;
+    // per-step reward terms and ego state (only if rewards != 0)
+    int rewards;
+    float lane_w, vlim;
+    const float *weights;   // [n_agents][10]
+    float2 *acc;            // [n_agents] previous a_lon, a_lat (updated)
+    float *reward;          // [n_agents]
+    float *ego;             // [n_agents][6]
 };
 
 // Snapped triangle as dumped for parity checks (matches gp_debug_dump_tris records).

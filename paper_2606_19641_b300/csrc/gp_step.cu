@@ -53,6 +53,91 @@ __device__ __forceinline__ bool in_quad(float px, float py, float4 g0, float4 g1
     return true;
 }
 
+__device__ __forceinline__ float wrap_pi(float a) {
+    if (a > kPi) a -= 2.f * kPi;
+    if (a <= -kPi) a += 2.f * kPi;
+    return a;
+}
+
+// Lane frame of a point: the road quad of smallest index containing it (boundary inside);
+// the quad runs from its q0-q3 edge to its q1-q2 edge; with right-hand traffic on two lanes
+// the half right of the centre line runs along that direction, the left half against it.
+// x_f = offset from the lane's centre line.  False off the road.
+__device__ bool lane_frame(const StepParams &p, const WorldInfo &wi, float px, float py,
+                           float &lane_dir, float &xf) {
+    const float fx = floorf((px - wi.gx0) * wi.ginv);
+    const float fy = floorf((py - wi.gy0) * wi.ginv);
+    if (!(fx >= 0.f && fy >= 0.f && fx < (float)wi.gnx && fy < (float)wi.gny)) return false;
+    const int cell = wi.cell_begin + (int)fy * wi.gnx + (int)fx;
+    int best = 0x7FFFFFFF;
+    for (int q = p.cell_off[cell]; q < p.cell_off[cell + 1]; ++q) {
+        const int r = p.cell_quads[q];
+        if (r < best && in_quad(px, py, p.road_geo[2 * r], p.road_geo[2 * r + 1])) best = r;
+    }
+    if (best == 0x7FFFFFFF) return false;
+    const float4 g0 = p.road_geo[2 * best], g1 = p.road_geo[2 * best + 1];  // q0 q1 | q2 q3
+    const float m0x = 0.5f * (g0.x + g1.z), m0y = 0.5f * (g0.y + g1.w);
+    const float m1x = 0.5f * (g0.z + g1.x), m1y = 0.5f * (g0.w + g1.y);
+    float dx = m1x - m0x, dy = m1y - m0y;
+    const float inv = rsqrtf(dx * dx + dy * dy);
+    dx *= inv;
+    dy *= inv;
+    const float cx = 0.25f * (g0.x + g0.z + g1.x + g1.z), cy = 0.25f * (g0.y + g0.w + g1.y + g1.w);
+    const float s = (px - cx) * (-dy) + (py - cy) * dx;
+    if (s < 0.f) {
+        lane_dir = atan2f(dy, dx);
+        xf = s + 0.5f * p.lane_w;
+    } else {
+        lane_dir = atan2f(-dy, -dx);
+        xf = s - 0.5f * p.lane_w;
+    }
+    return true;
+}
+
+// Reward terms of one agent's step (App. A reward table; inference weights by default) and
+// its ego state.  Accelerations are the bicycle's increments of the step (speed before any
+// halt); an agent halted before the step earns 0.  The traffic-light and goal terms are 0.
+__device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, float px, float py,
+                             float yaw, float v_after, float v0, float2 act, float L, float W,
+                             unsigned int fl0, unsigned int fl1) {
+    const float *w = p.weights + 10 * a;
+    float a_lon = 0.f, a_lat = 0.f, r = 0.f;
+    if (!(fl0 & GP_FLAG_HALTED)) {
+        const float lr = 0.3f * L;
+        const float beta = atanf(0.5f * tanf(act.y));
+        const float vn = fminf(fmaxf(v0 + act.x * p.dt, 0.f), p.vmax);
+        const float dyaw = (v0 / lr) * sinf(beta) * p.dt;
+        a_lon = (vn - v0) / p.dt;
+        a_lat = v0 * dyaw / p.dt;
+        const float2 ap = p.acc[a];
+        const float j_lon = (a_lon - ap.x) / p.dt, j_lat = (a_lat - ap.y) / p.dt;
+        if (fl1 & GP_FLAG_COLLIDED) r -= w[0] + 0.1f * fabsf(v0);
+        if (fl1 & GP_FLAG_OFFROAD) r -= w[1];
+        r -= w[2] * (float)((fabsf(a_lon) > 3.f) + (fabsf(a_lat) > 3.f) +
+                            (fabsf(j_lon) > 5.f || fabsf(j_lat) > 5.f));
+        float lane_dir, xf;
+        if (lane_frame(p, wi, px, py, lane_dir, xf)) {
+            const float th = fabsf(wrap_pi(yaw - lane_dir));
+            const float ct = cosf(th);
+            r += w[3] * p.dt * (fminf(ct, 0.f) + fminf(vn * ct, 0.f) + 0.0025f * (1.f - 2.f * th / kPi));
+            r -= w[4] * p.dt * ((ct > 0.5f ? fabsf(xf) : 0.f) - 0.05f * expf(0.5f - fabsf(xf)));
+            if (fabsf(vn) > 2.5f) r += w[5] * p.dt * fmaxf(ct, 0.f);
+        }
+        if (fabsf(vn) > 0.f || a_lon != 0.f || a_lat != 0.f) r -= w[7] * p.dt;
+        if (vn < 0.f) r -= w[8] * p.dt;
+        if (fabsf(vn) > p.vlim) r -= w[9];
+    }
+    p.acc[a] = make_float2(a_lon, a_lat);
+    p.reward[a] = r;
+    float *e = p.ego + 6 * a;
+    e[0] = fmaxf(-1.f, fminf(1.f, v_after / p.vmax));
+    e[1] = fmaxf(-1.f, fminf(1.f, a_lon / 10.f));
+    e[2] = fmaxf(-1.f, fminf(1.f, a_lat / 10.f));
+    e[3] = fmaxf(-1.f, fminf(1.f, L / 10.f));
+    e[4] = fmaxf(-1.f, fminf(1.f, W / 5.f));
+    e[5] = (fl1 & GP_FLAG_COLLIDED) ? 1.f : 0.f;
+}
+
 __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
     __shared__ Footprint fp[kMaxBoxes];
     __shared__ unsigned int sflag[kMaxBoxes];
@@ -61,8 +146,9 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
     for (int wl = blockIdx.x; wl < p.n_worlds; wl += gridDim.x) {
         const WorldInfo wi = p.worlds[p.world_begin + wl];
         float4 pose = make_float4(0.f, 0.f, 0.f, 0.f), dim = pose;
-        float v = 0.f;
-        unsigned int fl = 0;
+        float v = 0.f, v0 = 0.f;
+        unsigned int fl = 0, fl0 = 0;
+        float2 act = make_float2(0.f, 0.f);
         if (tid < wi.n_boxes) {
             pose = p.box_pose[wi.box_begin + tid];
             dim = p.box_dim[wi.box_begin + tid];
@@ -70,9 +156,11 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
         if (tid < wi.n_agents) {
             const int a = wi.agent_begin + tid;
             fl = p.flags[a];
+            fl0 = fl;
             v = p.speed[a];
+            v0 = v;
             if (!(fl & GP_FLAG_HALTED)) {
-                const float2 act = p.actions[a];
+                act = p.actions[a];
                 const float lr = 0.3f * dim.x;
                 const float beta = atanf(0.5f * tanf(act.y));
                 float sb, cb;
@@ -158,6 +246,8 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
             p.box_pose[wi.box_begin + tid] = pose;
             p.speed[a] = v;
             p.flags[a] = (uint8_t)fl;
+            if (p.rewards)
+                agent_reward(p, wi, a, pose.x, pose.y, pose.z, v, v0, act, dim.x, dim.y, fl0, fl);
         }
         __syncthreads();
     }

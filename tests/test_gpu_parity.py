@@ -594,3 +594,72 @@ def test_rgb_rejects_bad_appearance():
         sim_for(worlds, wl, ambient=1.5)
     with pytest.raises(gp.GigapixelError):
         sim_for(worlds, wl, width=211)  # odd widths are rejected
+
+
+# ---------------------------------------------------------------------------------------
+# Rewards and ego state (App. A reward table and observations)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n_worlds,steps", [("uniform", 4, 12), ("ragged", 6, 10)])
+def test_rewards_match_oracle(name, n_worlds, steps):
+    """Per-step rewards and ego states against the oracle evaluated on the GPU's own
+    before/after states and flags; random per-agent weights from the table's ranges."""
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl, rewards=1)
+    na = worlds.n_agents
+    rng = np.random.default_rng(5)
+    lo = np.array([0, 0, 0, 2.5e-4, 2.5e-4, 0, 0, 0, 2.5e-4, 0])
+    hi = np.array([3, 3, 0.05, 2.5e-2, 7.5e-3, 5e-3, 1, 5e-5, 7.5e-3, 1])
+    weights = (lo + (hi - lo) * rng.random((na, 10))).astype(np.float32)
+    sim.set_reward_weights(weights)
+    off = worlds.agent_offsets()
+    acc = np.zeros((na, 2), np.float64)
+    dims = np.zeros((na, 2), np.float64)
+    for w in range(worlds.n_worlds):
+        b0 = int(worlds.box_off[w])
+        a0, a1 = int(off[w]), int(off[w + 1])
+        dims[a0:a1] = worlds.boxes[b0:b0 + (a1 - a0), 3:5]
+    n_bad = n_total = 0
+    seen_collision = False
+    for k in range(steps):
+        st0, fl0 = sim.get_state()
+        act_t, act = torch_actions(worlds, k, wl.seed)
+        sim.step(act_t)
+        st1, fl1 = sim.get_state()
+        r, e = sim.rewards()
+        torch.cuda.synchronize()
+        r, e = r.cpu().numpy(), e.cpu().numpy()
+        for w in range(worlds.n_worlds):
+            a0, a1 = int(off[w]), int(off[w + 1])
+            road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
+            acc_w = np.ascontiguousarray(acc[a0:a1])
+            rr, ee = oracle.rewards_world(st0[a0:a1], fl0[a0:a1], st1[a0:a1], fl1[a0:a1],
+                                          act[a0:a1], dims[a0:a1], acc_w, weights[a0:a1], road)
+            acc[a0:a1] = acc_w
+            d = np.abs(r[a0:a1] - rr)
+            n_bad += int((d > 1e-4 + 1e-4 * np.abs(rr)).sum())
+            n_total += a1 - a0
+            # the only admissible larger difference: one comfort indicator flipped at its
+            # threshold by FP32 rounding of the acceleration
+            assert np.all((d <= 1e-4 + 1e-4 * np.abs(rr)) | (d <= weights[a0:a1, 2] + 1e-4))
+            assert np.allclose(e[a0:a1], ee, atol=2e-5)
+            seen_collision |= bool((fl1[a0:a1] & 1).any())
+    assert n_bad <= 0.005 * n_total
+    assert sim.status() == 0
+
+
+def test_rewards_off_by_default_and_weights_validated():
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, _ = sim_for(worlds, wl)
+    with pytest.raises(gp.GigapixelError) as e:
+        sim.rewards()
+    assert e.value.status == gp.binding.GP_ESTATE
+    sim2, _ = sim_for(worlds, wl, rewards=1)
+    bad = np.ones((worlds.n_agents, 10), np.float32)
+    bad[0, 3] = np.nan
+    with pytest.raises(gp.GigapixelError):
+        sim2.set_reward_weights(bad)
