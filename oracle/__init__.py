@@ -86,6 +86,10 @@ def _lib():
         lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
         lib.or_f32_to_bf16.restype = ctypes.c_uint16
         lib.or_onehot_bf16.argtypes = [c_u8p, ctypes.c_int64, c_f32p, c_f32p, c_u16p]
+        lib.or_trace_view.argtypes = [P(OrCam), ctypes.c_int32, c_f64p, ctypes.c_int32,
+                                      ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, c_u8p, c_f32p, P(ctypes.c_uint32)]
         lib.or_lane_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, c_f32p,
                                       ctypes.c_double, c_f64p, c_f64p]
         lib.or_lane_frame.restype = ctypes.c_int
@@ -184,6 +188,38 @@ def camera_tris(cam: CamConfig, boxes6: np.ndarray, ego: int, road: np.ndarray,
                            float(ayaw), float(cam_yaw), out.ctypes.data, cap)
     assert n <= cap
     return out[:n].copy()
+
+
+@dataclasses.dataclass
+class Traced:
+    cls: np.ndarray      # uint8 [H, W]
+    depth: np.ndarray    # float32 [H, W], near / t (0 on background)
+    prim: np.ndarray     # uint32 [H, W], the hit's primitive id (0xFFFFFFFF background)
+
+    def key(self, key_f16: bool = False) -> np.ndarray:
+        """Keys in the raster's layout (for shade_rgb): id half only, 0 on background."""
+        k = np.zeros(self.prim.shape, np.uint64)
+        hit = self.prim != 0xFFFFFFFF
+        full = 0xFFFF if key_f16 else 0xFFFFFFFF
+        k[hit] = (np.uint64(1) << np.uint64(40)) | (full - self.prim[hit].astype(np.uint64))
+        return k
+
+
+def trace_view(cam: CamConfig, boxes6: np.ndarray, ego: int, road: np.ndarray, line: np.ndarray,
+               ax: float, ay: float, ayaw: float, cam_yaw: float) -> Traced:
+    """Ray-traced view (see or_trace_view)."""
+    b = _c(boxes6, np.float64).reshape(-1, 6)
+    rd = _c(road, np.float32).reshape(-1, 8)
+    ln = _c(line, np.float32).reshape(-1, 8)
+    cls = np.zeros((cam.height, cam.width), np.uint8)
+    dep = np.zeros((cam.height, cam.width), np.float32)
+    pr = np.zeros((cam.height, cam.width), np.uint32)
+    c = cam.c()
+    _lib().or_trace_view(ctypes.byref(c), b.shape[0], _p(b, c_f64p), int(ego), rd.shape[0],
+                         _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), float(ax), float(ay),
+                         float(ayaw), float(cam_yaw), _p(cls, c_u8p), _p(dep, c_f32p),
+                         pr.ctypes.data_as(P(ctypes.c_uint32)))
+    return Traced(cls, dep, pr)
 
 
 @dataclasses.dataclass
@@ -347,6 +383,11 @@ class Sim:
         a = int(self.agent_off[w]) + agent_local
         return camera_tris(cam, self.boxes6(w), agent_local, self.road(w), self.line(w),
                            self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw)
+
+    def trace(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> Traced:
+        a = int(self.agent_off[w]) + agent_local
+        return trace_view(cam, self.boxes6(w), agent_local, self.road(w), self.line(w),
+                          self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw)
 
     def prim_ranges(self, w: int):
         nb = int(self.w.box_off[w + 1] - self.w.box_off[w])

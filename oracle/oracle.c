@@ -456,6 +456,101 @@ int64_t or_camera_tris(const or_cam *cfg, int32_t n_boxes, const double *boxes, 
 }
 
 /* ------------------------------------------------------------------------------------
+ * Ray-traced view (App. A: the renderer's ray-traced backend)
+ * ------------------------------------------------------------------------------------ */
+
+/*
+ * One ray per pixel centre from the camera: direction right * x + up * y + forward with
+ * x = (i + 1/2 - W/2) / f, y = (H/2 - j - 1/2) / f, so the ray parameter t is the view
+ * depth z.  Nearest hit with t >= near among every box except the ego's (slab test in the
+ * box frame, z from 0 to H), road quads on z = 0 and lane-line strips on z = line_z (plane
+ * hit, point in quad with the boundary inside); ties go to the lower object (boxes by index,
+ * then road quads, then lines).  Per pixel: class (0 background, 1 road, 2 lane line, 3 box),
+ * reversed-Z depth near / t rounded to FP32 (0 background), and the hit's primitive id in
+ * the raster's numbering -- box b's entry face f gives 12 b + 2 f (faces +x, -x, +y, -y, +z,
+ * -z), road quad r gives 12 n_boxes + 2 r, line l gives 12 n_boxes + 2 n_road + 2 l --
+ * or 0xFFFFFFFF on background, so the RGB shading applies unchanged.
+ */
+void or_trace_view(const or_cam *cfg, int32_t n_boxes, const double *boxes, int32_t ego,
+                   int32_t n_road, const float *road, int32_t n_line, const float *line,
+                   double ax, double ay, double ayaw, double cam_yaw, uint8_t *cls, float *depth,
+                   uint32_t *prim) {
+    const double yaw = ayaw + cam_yaw;
+    const double fx = cos(yaw), fy = sin(yaw);  /* forward */
+    const double rx = sin(yaw), ry = -cos(yaw); /* right */
+    const double f = 0.5 * cfg->width / tan(0.5 * cfg->hfov);
+    const double oz = cfg->cam_height;
+    for (int32_t j = 0; j < cfg->height; ++j)
+        for (int32_t i = 0; i < cfg->width; ++i) {
+            const double x = (i + 0.5 - 0.5 * cfg->width) / f;
+            const double y = (0.5 * cfg->height - j - 0.5) / f;
+            const double dx = rx * x + fx, dy = ry * x + fy, dz = y;
+            double best = INFINITY;
+            int c = 0;
+            uint32_t pr = 0xFFFFFFFFu;
+            for (int32_t b = 0; b < n_boxes; ++b) {
+                if (b == ego) continue;
+                const double *bx = boxes + 6 * b;
+                const double cs = cos(bx[2]), sn = sin(bx[2]);
+                const double px = ax - bx[0], py = ay - bx[1];
+                const double o[3] = {cs * px + sn * py, -sn * px + cs * py, oz};
+                const double d[3] = {cs * dx + sn * dy, -sn * dx + cs * dy, dz};
+                const double lo[3] = {-0.5 * bx[3], -0.5 * bx[4], 0.0};
+                const double hi[3] = {0.5 * bx[3], 0.5 * bx[4], bx[5]};
+                double t0 = -INFINITY, t1 = INFINITY;
+                int face = -1, inside = 1;
+                for (int k = 0; k < 3 && inside; ++k) {
+                    if (d[k] == 0.0) {
+                        if (o[k] < lo[k] || o[k] > hi[k]) inside = 0;
+                        continue;
+                    }
+                    double ta = (lo[k] - o[k]) / d[k], tb = (hi[k] - o[k]) / d[k];
+                    /* entering through the low side (face -k) when moving up the axis */
+                    int fa = 2 * k + 1, fb = 2 * k;
+                    if (ta > tb) {
+                        const double tt = ta;
+                        ta = tb;
+                        tb = tt;
+                        fa = 2 * k;
+                        fb = 2 * k + 1;
+                    }
+                    (void)fb;
+                    if (ta > t0) {
+                        t0 = ta;
+                        face = fa;
+                    }
+                    if (tb < t1) t1 = tb;
+                }
+                if (!inside || face < 0 || t0 > t1 || t0 < cfg->near || !(t0 < best)) continue;
+                best = t0;
+                c = 3;
+                pr = (uint32_t)(12 * b + 2 * face);
+            }
+            if (dz < 0.0) {
+                for (int pass = 0; pass < 2; ++pass) {
+                    const double z = pass ? cfg->line_z : 0.0;
+                    const double t = (z - oz) / dz;
+                    if (t < cfg->near || !(t < best)) continue;
+                    const double hx = ax + t * dx, hy = ay + t * dy;
+                    const int32_t nq = pass ? n_line : n_road;
+                    const float *qs = pass ? line : road;
+                    for (int32_t q = 0; q < nq; ++q)
+                        if (or_point_in_quad(hx, hy, qs + 8 * q)) {
+                            best = t;
+                            c = pass ? 2 : 1;
+                            pr = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road + 2 * q : 2 * q));
+                            break;
+                        }
+                }
+            }
+            const int64_t pix = (int64_t)j * cfg->width + i;
+            cls[pix] = (uint8_t)c;
+            depth[pix] = c ? (float)(cfg->near / best) : 0.0f;
+            prim[pix] = pr;
+        }
+}
+
+/* ------------------------------------------------------------------------------------
  * Raster rule on snapped triangles (integer coverage + FP32 depth)
  * ------------------------------------------------------------------------------------ */
 

@@ -49,6 +49,11 @@ MUTANTS = {
                             "const double th = wrap_pi(after[4 * i + 2] - lane_dir);"),
     "halted agents rewarded": ("if (!(fl_before[i] & OR_HALTED)) {\n            const double v0",
                                "if (1) {\n            const double v0"),
+    "trace entry face mirrored": ("int fa = 2 * k + 1, fb = 2 * k;", "int fa = 2 * k, fb = 2 * k + 1;"),
+    "trace lines on road plane": ("const double z = pass ? cfg->line_z : 0.0;", "const double z = 0.0;"),
+    "trace near ignored": ("t0 > t1 || t0 < cfg->near ||", "t0 > t1 ||"),
+    "trace last road quad wins": ("                            pr = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road + 2 * q : 2 * q));\n                            break;",
+                                  "                            pr = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road + 2 * q : 2 * q));"),
     "ego speed unnormalised": ("const double e[5] = {after[4 * i + 3] / vmax,", "const double e[5] = {after[4 * i + 3],"),
 }
 

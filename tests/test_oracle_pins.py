@@ -931,3 +931,99 @@ def test_ego_state_normalisation():
     assert ego[0] == pytest.approx(15.1 / 30.0)
     assert ego[1] == pytest.approx(0.1) and ego[2] == 0.0
     assert ego[3] == pytest.approx(0.42) and ego[4] == pytest.approx(0.36) and ego[5] == 0.0
+
+
+# ---------------------------------------------------------------------------------------
+# Ray-traced view: closed forms and the independent NumPy ray caster above
+# ---------------------------------------------------------------------------------------
+
+def trace_scene(cam, boxes, road=(), line=(), pose=(0.0, 0.0, 0.0), cam_yaw=0.0, ego=0):
+    b = np.array(boxes, np.float64).reshape(-1, 6)
+    rd = np.array(road, np.float32).reshape(-1, 8)
+    ln = np.array(line, np.float32).reshape(-1, 8)
+    return oracle.trace_view(cam, b, ego, rd, ln, pose[0], pose[1], pose[2], cam_yaw)
+
+
+@pytest.mark.parametrize("W,H,D,hw,bh", _generic_box_cases())
+def test_trace_box_face_rectangle(W, H, D, hw, bh):
+    cols, rows, margin = _box_face_expectation(W, H, D, hw, bh)
+    L = 4.2
+    tr = trace_scene(CamConfig(W, H), [ego_box(), [float(D) + L / 2, 0.0, 0.0, L, 2 * float(hw), float(bh)]])
+    expect = np.zeros((H, W), bool)
+    expect[rows[0]:rows[-1] + 1, cols[0]:cols[-1] + 1] = True
+    assert np.array_equal(tr.cls == 3, expect) and np.array_equal(tr.cls != 0, expect)
+    assert np.all(tr.depth[expect] == np.float32(0.1 / float(D)))
+    assert np.all(tr.prim[expect] == 12 * 1 + 2 * 1)  # box 1, its -x face
+    assert np.all(tr.prim[~expect] == 0xFFFFFFFF) and np.all(tr.depth[~expect] == 0)
+
+
+def test_trace_ground_rows_and_lines_above_road():
+    W = H = 64
+    f, h, n, r = 32.0, 1.5, 0.1, 1.3137
+    road = [rect_quad(-5.0, 200.0, -r, r)]
+    line = [rect_quad(-5.0, 200.0, -0.075, 0.075)]
+    tr = trace_scene(CamConfig(W, H), [ego_box()], road=road, line=line)
+    u = np.arange(W) + 0.5
+    v = np.arange(H) + 0.5 - H / 2
+    for j in range(H):
+        if v[j] <= 0:
+            assert not tr.cls[j].any()
+            continue
+        half = r / h * v[j]
+        sure = np.abs(np.abs(u - W / 2) - half) > 1e-6
+        inside = np.abs(u - W / 2) < half
+        assert np.array_equal(tr.cls[j][sure] != 0, inside[sure])
+        road_px = tr.cls[j] == 1
+        assert np.allclose(tr.depth[j][road_px], n * v[j] / (f * h), rtol=1e-6)
+        # the lane line (raised by line_z) is nearer: its depth is n (v - H/2 ...) / (f (h - z))
+        line_px = tr.cls[j] == 2
+        assert np.allclose(tr.depth[j][line_px], n * v[j] / (f * (h - 0.02)), rtol=1e-6)
+    assert (tr.cls == 2).sum() > 20
+
+
+def test_trace_entry_faces_follow_box_yaw():
+    W, H, L = 64, 64, 4.5
+    # the face whose outward normal points back at the camera (along -x): -x at yaw 0, +x
+    # at yaw pi, +y (normal (-sin, cos)) at yaw pi/2, -y at yaw -pi/2
+    for yaw, face in ((0.0, 1), (math.pi, 0), (math.pi / 2, 2), (-math.pi / 2, 3)):
+        tr = trace_scene(CamConfig(W, H), [ego_box(), [10.0 + L / 2, 0.0, yaw, L, 1.9, 1.6]])
+        hit = tr.cls == 3
+        assert hit.sum() > 20
+        assert set(((tr.prim[hit] - 12) // 2).tolist()) == {face}
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("W,H", [(16, 16), (40, 24)])
+def test_trace_equals_numpy_raycast(seed, W, H):
+    rng = np.random.default_rng(300 + seed)
+    boxes, road, line = _random_scene(rng)
+    cam_yaw = rng.uniform(-0.3, 0.3)
+    tr = trace_scene(CamConfig(W, H), boxes, road, line, cam_yaw=cam_yaw)
+    cls0, d0, obj0 = raycast(W, H, boxes, 0, road, line, (0, 0, 0), cam_yaw)
+    assert np.array_equal(tr.cls, cls0)
+    assert np.allclose(tr.depth, d0.astype(np.float32), rtol=1e-6, atol=0)
+    nb, nr = len(boxes), len(road)
+    box = cls0 == 3
+    assert np.array_equal((tr.prim[box] // 12), obj0[box])
+    rd = cls0 == 1
+    assert np.array_equal((tr.prim[rd] - 12 * nb) // 2, obj0[rd] - 1000)
+    ln = cls0 == 2
+    assert np.array_equal((tr.prim[ln] - 12 * nb - 2 * nr) // 2, obj0[ln] - 100000)
+
+
+def test_trace_ignores_boxes_behind_the_camera():
+    """A box behind the camera (or nearer than the near plane along the ray) is not hit."""
+    W = H = 32
+    tr = trace_scene(CamConfig(W, H), [ego_box(), [-10.0, 0.0, 0.3, 4.5, 1.9, 1.6],
+                                       [-6.0, 1.0, 0.0, 4.5, 1.9, 2.5]])
+    assert not tr.cls.any() and np.all(tr.prim == 0xFFFFFFFF)
+
+
+def test_trace_overlapping_road_quads_tie_to_lower_index():
+    W = H = 32
+    road = [rect_quad(-5.0, 100.0, -4.0, 4.0), rect_quad(-5.0, 100.0, -4.0, 4.0),
+            rect_quad(0.0, 50.0, -2.0, 3.0)]  # inside quad 0
+    tr = trace_scene(CamConfig(W, H), [ego_box()], road=road)
+    rd = tr.cls == 1
+    assert rd.sum() > 100
+    assert np.all(tr.prim[rd] == 12)  # road quad 0 wins every tie
