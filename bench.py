@@ -397,6 +397,25 @@ def main():
         extras["precision_path"]["speedup_vs_per_world_path"] = (
             extras["precision_path"]["agent_steps_per_s"] / extras["per_world_path"]["agent_steps_per_s"])
         sim_p.close()
+        # the ray-traced backend on the same batch and outputs (step + trace per step)
+        barrier()
+        et = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tr_steps = 10
+        for k in range(2):
+            sim.trace(out, depth)
+        barrier()
+        et[0].record(stream)
+        for k in range(tr_steps):
+            sim.trace(out, depth)
+        et[1].record(stream)
+        barrier()
+        tr_ms = maxred(et[0].elapsed_time(et[1])) / tr_steps
+        extras["ray_traced"] = {
+            "trace_kernel_ms": tr_ms,
+            "agent_steps_per_s_step_plus_trace": job_rate(total_agents, 1, tr_ms + stepk_ms),
+            "render_gbs": algo_bytes / (tr_ms / 1e3) / 1e9,
+            "render_frac_of_measured_hbm": algo_bytes / (tr_ms / 1e3) / 1e9 / peak,
+            "note": "one ray per pixel: box slabs, lane-line and road plane hits via the grid"}
         # the same batch with the reward terms and ego state computed in every step
         sim_w = Simulator(worlds, config_for(wl_rank, rewards=1, autotune=1), device=local)
         extras["with_rewards"] = graph_rate(sim_w, worlds, wl_rank, 20)

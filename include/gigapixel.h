@@ -180,6 +180,17 @@ gp_status gp_step(gp_handle *h, const float *actions_dev, void *stream);
 gp_status gp_render(gp_handle *h, void *out_dev, void *depth_dev, void *stream);
 
 /*
+ * Ray-traced render (App. A: the renderer's ray-traced backend): one ray per pixel centre
+ * from each camera; the nearest hit at or beyond the near plane among the boxes (exact box
+ * slabs), the lane-line strips and the road quads (exact plane hits, point in quad, boundary
+ * inside); ties go to the lower object.  Same output formats and layouts as gp_render; the
+ * depth is near / t of the hit (FP32, or its binary16 bits with GP_KEY_F16), and RGB
+ * shading uses the hit surface's normal.  Unlike the raster there is no snapping, fill rule
+ * or clipping, so the two differ only along silhouettes.  Asynchronous on `stream`.
+ */
+gp_status gp_trace(gp_handle *h, void *out_dev, void *depth_dev, void *stream);
+
+/*
  * gp_step followed by gp_render, replayed from a CUDA graph (captured on the first call
  * for this (actions, out, depth) pointer triple; up to 4 triples are cached).  The
  * pointers must stay valid while their graph is cached (until gp_destroy).

@@ -25,7 +25,7 @@ MAX_CAMS = 8
 TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,)),
                       ("prim", "<u4"), ("sub", "<u4")])
 
-EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render",
+EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render", "gp_trace",
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights",
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_clear_status": [vp],
         "gp_debug_inject_status": [vp, u32],
         "gp_get_rewards": [vp, vp, vp, i32, vp],
+        "gp_trace": [vp, vp, vp, vp],
         "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -275,6 +276,10 @@ class Simulator:
 
     def inject_status(self, bits: int) -> None:
         check(lib().gp_debug_inject_status(self._h, bits))
+
+    def trace(self, out, depth=None, stream=None) -> None:
+        """Ray-traced render of every camera into the same tensors as render()."""
+        check(lib().gp_trace(self._h, _ptr(out), _ptr(depth), _stream(stream)))
 
     def rewards(self, stream=None):
         """(reward [n_agents], ego state [n_agents, 6]) of the last step, float32 on the

@@ -79,10 +79,11 @@ struct gp_handle {
     std::vector<WorldInfo> worlds_h;
     std::vector<int> world_item_begin, world_item_count;
     DevBuf<WorldInfo> worlds;
-    DevBuf<float4> box_pose, box_dim, quad_geo, road_geo;
+    DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo;
     DevBuf<float> speed;
     DevBuf<uint8_t> flags;
-    DevBuf<int> agent_world, agent_box, cell_off, cell_quads, counter, dump_count;
+    DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, counter,
+        dump_count;
     DevBuf<Cluster> clusters;
     DevBuf<uint32_t> quad_prim, status;
     DevBuf<int2> items;
@@ -269,6 +270,13 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     p.tri_cap = h->shape.tri_cap;
     p.max_cl = h->max_cl;
     p.prod_warps = h->shape.prod_warps;
+    p.road_geo = h->road_geo.p;
+    p.line_geo = h->line_geo.p;
+    p.cell_off = h->cell_off.p;
+    p.cell_quads = h->cell_quads.p;
+    p.lcell_off = h->lcell_off.p;
+    p.lcell_quads = h->lcell_quads.p;
+    p.trace_view0 = 0;
     p.wait_ns = 2000000000ull;  // 2 s: far beyond any legitimate handoff
     p.debug_stall = 0;
     p.status = h->status.p;
@@ -511,6 +519,9 @@ void release_all(gp_handle *h) {
     h->agent_box.release();
     h->cell_off.release();
     h->cell_quads.release();
+    h->line_geo.release();
+    h->lcell_off.release();
+    h->lcell_quads.release();
     h->counter.release();
     h->dump_count.release();
     h->clusters.release();
@@ -594,9 +605,9 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         dim[b] = make_float4(s[3], s[4], s[5], 0.f);
     }
     std::vector<Cluster> clusters;
-    std::vector<float4> quad_geo, road_geo;
+    std::vector<float4> quad_geo, road_geo, line_geo;
     std::vector<uint32_t> quad_prim;
-    std::vector<int> cell_off(1, 0), cell_quads;
+    std::vector<int> cell_off(1, 0), cell_quads, lcell_off(1, 0), lcell_quads;
     h->worlds_h.resize(nw);
     for (int w = 0; w < nw; ++w) {
         WorldInfo wi{};
@@ -616,10 +627,13 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         wi.road_begin = (int)road_geo.size() / 2;
         wi.n_road = nr;
         float bx0 = 1e30f, by0 = 1e30f, bx1 = -1e30f, by1 = -1e30f;
-        for (int r = 0; r < nr; ++r) {
-            const float *q = d->road + 8 * (size_t)(r0 + r);
-            road_geo.push_back(make_float4(q[0], q[1], q[2], q[3]));
-            road_geo.push_back(make_float4(q[4], q[5], q[6], q[7]));
+        wi.line_begin = (int)line_geo.size() / 2;
+        wi.n_line = nl;
+        for (int r = 0; r < nr + nl; ++r) {
+            const float *q = r < nr ? d->road + 8 * (size_t)(r0 + r) : d->line + 8 * (size_t)(l0 + r - nr);
+            std::vector<float4> &geo = r < nr ? road_geo : line_geo;
+            geo.push_back(make_float4(q[0], q[1], q[2], q[3]));
+            geo.push_back(make_float4(q[4], q[5], q[6], q[7]));
             for (int k = 0; k < 4; ++k) {
                 bx0 = std::min(bx0, q[2 * k]);
                 bx1 = std::max(bx1, q[2 * k]);
@@ -627,10 +641,11 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
                 by1 = std::max(by1, q[2 * k + 1]);
             }
         }
-        // off-road grid: 8 m cells over the road bounding box; a quad is listed in every
-        // cell its bounding box touches (widened by one cell), so any point inside it finds it
+        // off-road grid: 8 m cells over the bounding box of the road and lane-line quads; a
+        // quad is listed in every cell its bounding box touches (widened by one cell), so any
+        // point inside it finds it.  A second CSR over the same cells lists the lane lines.
         const float cs = 8.f;
-        if (nr == 0) {
+        if (nr + nl == 0) {
             bx0 = by0 = 0.f;
             bx1 = by1 = 1.f;
         }
@@ -639,11 +654,11 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         wi.ginv = 1.f / cs;
         wi.gnx = std::max(1, (int)std::ceil((bx1 - bx0) / cs) + 1);
         wi.gny = std::max(1, (int)std::ceil((by1 - by0) / cs) + 1);
-        wi.cell_begin = (int)cell_off.size() - 1;
-        {
+        auto build_cells = [&](const float *quads, int n, int index_base, std::vector<int> &off,
+                               std::vector<int> &list) {
             std::vector<std::vector<int>> cells((size_t)wi.gnx * wi.gny);
-            for (int r = 0; r < nr; ++r) {
-                const float *q = d->road + 8 * (size_t)(r0 + r);
+            for (int r = 0; r < n; ++r) {
+                const float *q = quads + 8 * (size_t)r;
                 float qx0 = q[0], qx1 = q[0], qy0 = q[1], qy1 = q[1];
                 for (int k = 1; k < 4; ++k) {
                     qx0 = std::min(qx0, q[2 * k]);
@@ -657,13 +672,17 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
                 const int cy1 = std::min(wi.gny - 1, (int)std::floor((qy1 - by0) / cs) + 1);
                 for (int cy = cy0; cy <= cy1; ++cy)
                     for (int cx = cx0; cx <= cx1; ++cx)
-                        cells[(size_t)cy * wi.gnx + cx].push_back(wi.road_begin + r);
+                        cells[(size_t)cy * wi.gnx + cx].push_back(index_base + r);
             }
             for (auto &cl : cells) {
-                cell_quads.insert(cell_quads.end(), cl.begin(), cl.end());
-                cell_off.push_back((int)cell_quads.size());
+                list.insert(list.end(), cl.begin(), cl.end());
+                off.push_back((int)list.size());
             }
-        }
+        };
+        wi.cell_begin = (int)cell_off.size() - 1;
+        build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, cell_off, cell_quads);
+        wi.lcell_begin = (int)lcell_off.size() - 1;
+        build_cells(d->line + 8 * (size_t)l0, nl, wi.line_begin, lcell_off, lcell_quads);
         // culling clusters: quads bucketed by the 16 m cell of their centroid, chunks of 16
         {
             const float cc = 16.f;
@@ -765,6 +784,9 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(road_geo, road_geo);
     UP(cell_off, cell_off);
     UP(cell_quads, cell_quads);
+    UP(line_geo, line_geo);
+    UP(lcell_off, lcell_off);
+    UP(lcell_quads, lcell_quads);
     std::vector<int> one(1, 0);
     UP(counter, one);
     UP(dump_count, one);
@@ -888,6 +910,16 @@ gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions, void 
     p.world_begin = world;
     p.n_worlds = 1;
     CK(launch_step(p, 1, (cudaStream_t)stream));
+    return GP_OK;
+}
+
+gp_status gp_trace(gp_handle *h, void *out, void *depth, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    gp_status st = check_out(out, depth);
+    if (st != GP_OK) return st;
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    CK(cudaSetDevice(h->device));
+    if (h->n_views) CK(launch_trace(render_params(h, out, depth), h->n_views, (cudaStream_t)stream));
     return GP_OK;
 }
 

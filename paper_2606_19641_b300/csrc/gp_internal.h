@@ -21,7 +21,9 @@ struct WorldInfo {
     int agent_begin, n_agents;   // global agent range
     int cl_begin, n_cl;          // culling clusters
     int road_begin, n_road;      // road quads in original order (off-road test)
+    int line_begin, n_line;      // lane-line quads in original order (ray tracing)
     int cell_begin;              // off-road grid: cells [cell_begin, cell_begin + gnx*gny)
+    int lcell_begin;             // the same grid over lane-line quads
     int gnx, gny;
     float gx0, gy0, ginv;        // grid origin and inverse cell size
     uint32_t box_end, road_end;  // primitive-id class boundaries: box < box_end <= road < road_end
@@ -90,6 +92,11 @@ struct RenderParams {
     int view_mod;            // 0, or write view v at slot v % view_mod (tuning scratch)
     uint16_t onehot[4][2];   // bf16 values per channel: [cold, hot]
 
+    // ray tracing: ground quads in original order and their per-world grids
+    const float4 *road_geo, *line_geo;
+    const int *cell_off, *cell_quads, *lcell_off, *lcell_quads;
+    int trace_view0;         // first view of a ray-tracing launch
+
     int tri_cap;             // triangles per raster batch
     int max_cl;              // most culling clusters in any world of the batch
     int prod_warps;          // > 0: pipelined kernel with this many producer warps
@@ -115,5 +122,7 @@ cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t
                           cudaStream_t s);
 cudaError_t render_configure(size_t max_smem);
 int render_occupancy(int key_f16, int threads, size_t smem, int prod_warps);
+// Ray-traced views [0, n_views) in the render output formats (grid rows of 65535 views).
+cudaError_t launch_trace(const RenderParams &p, int n_views, cudaStream_t s);
 
 }  // namespace gpk

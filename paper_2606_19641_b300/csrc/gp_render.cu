@@ -32,6 +32,7 @@
 // The depth plane d = d0 + a (X - X0) + b (Y - Y0) and its per-pixel evaluation follow a
 // fixed IEEE FP32 operation sequence (explicit _rn intrinsics), so identical snapped
 // triangles give bit-identical keys on any implementation that follows the same sequence.
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -1034,6 +1035,198 @@ __device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *k
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Ray-traced backend: one ray per pixel centre, nearest hit among the boxes (slab test),
+// the lane-line strips and the road quads (plane hit, point in quad); ties go to the lower
+// object (boxes by index, then lines over the road below them, then roads).  The result is
+// written in the same formats as the raster; the primitive id of a hit follows the raster's
+// numbering (box b's entry face f: 12 b + 2 f), so the RGB shading applies unchanged.
+// ------------------------------------------------------------------------------------
+
+// Camera of a view (agent pose + rig yaw) and its world.
+__device__ __forceinline__ void view_cam(const RenderParams &p, int view, Cam &cm, WorldInfo &wi) {
+    const int agent = view / p.n_cams, cam = view - agent * p.n_cams;
+    wi = p.worlds[p.agent_world[agent]];
+    cm.ego = agent - wi.agent_begin;
+    cm.box_begin = wi.box_begin;
+    cm.cl_begin = wi.cl_begin;
+    cm.box_end = wi.box_end;
+    cm.road_end = wi.road_end;
+    const float4 pose = p.box_pose[wi.box_begin + cm.ego];
+    cm.px = pose.x;
+    cm.py = pose.y;
+    sincosf(pose.z + p.cam_yaw[cam], &cm.s, &cm.c);
+}
+
+__device__ __forceinline__ bool quad_contains(float px, float py, float4 g0, float4 g1) {
+    const float qx[4] = {g0.x, g0.z, g1.x, g1.z};
+    const float qy[4] = {g0.y, g0.w, g1.y, g1.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int n = (k + 1) & 3;
+        if ((qx[n] - qx[k]) * (py - qy[k]) - (qy[n] - qy[k]) * (px - qx[k]) < 0.f) return false;
+    }
+    return true;
+}
+
+// The quad of smallest index among those listed in the point's grid cell that contain it;
+// -1 if none.  A cell lists its quads in increasing index order, so the first that contains
+// the point is the one.
+__device__ int ground_quad(const WorldInfo &wi, float px, float py, const int *off,
+                           const int *list, int cell_base, const float4 *geo) {
+    const float fx = floorf((px - wi.gx0) * wi.ginv), fy = floorf((py - wi.gy0) * wi.ginv);
+    if (!(fx >= 0.f && fy >= 0.f && fx < (float)wi.gnx && fy < (float)wi.gny)) return -1;
+    const int cell = cell_base + (int)fy * wi.gnx + (int)fx;
+    for (int q = off[cell]; q < off[cell + 1]; ++q) {
+        const int r = list[q];
+        if (quad_contains(px, py, geo[2 * r], geo[2 * r + 1])) return r;
+    }
+    return -1;
+}
+
+// A box as one view's rays see it: yaw cos/sin, the camera position in the box frame, half
+// extents and height; skipped (the ego's box, or entirely behind the camera) if hl < 0.
+struct TraceBox {
+    float cs, sn, ox, oy, hl, hw, h, pad;
+};
+
+// Ray-traced class (0 background) and, on a hit, primitive id and view depth t of pixel (i, j).
+__device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int i, int j,
+                           const TraceBox *tb, uint32_t &prim, float &t_hit) {
+    const float x = ((float)i + 0.5f - 0.5f * (float)p.W) / p.f;
+    const float y = (0.5f * (float)p.H - (float)j - 0.5f) / p.f;
+    // right = (sin psi, -cos psi, 0), up = +z, forward = (cos psi, sin psi, 0)
+    const float dx = cm.s * x + cm.c, dy = -cm.c * x + cm.s, dz = y;
+    const float oz = p.cam_h;
+    float best = INFINITY;
+    int cls = 0;
+    prim = 0xFFFFFFFFu;
+    for (int b = 0; b < wi.n_boxes; ++b) {
+        const TraceBox B = tb[b];
+        if (B.hl < 0.f) continue;
+        const float cs = B.cs, sn = B.sn;
+        const float o[3] = {B.ox, B.oy, oz};
+        const float d[3] = {cs * dx + sn * dy, -sn * dx + cs * dy, dz};
+        const float lo[3] = {-B.hl, -B.hw, 0.f};
+        const float hi[3] = {B.hl, B.hw, B.h};
+        float t0 = -INFINITY, t1 = INFINITY;
+        int face = -1;
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (d[k] == 0.f) {
+                if (o[k] < lo[k] || o[k] > hi[k]) inside = false;
+                continue;
+            }
+            float ta = (lo[k] - o[k]) / d[k], tb = (hi[k] - o[k]) / d[k];
+            int fa = 2 * k + 1;  // entering through the low side: face -k
+            if (ta > tb) {
+                const float tt = ta;
+                ta = tb;
+                tb = tt;
+                fa = 2 * k;
+            }
+            if (ta > t0) {
+                t0 = ta;
+                face = fa;
+            }
+            t1 = fminf(t1, tb);
+        }
+        if (!inside || face < 0 || t0 > t1 || t0 < p.near_plane || !(t0 < best)) continue;
+        best = t0;
+        cls = 3;
+        prim = (uint32_t)(12 * b + 2 * face);
+    }
+    if (dz < 0.f) {
+        // lane-line strips lie above the road: a line hit is nearer than the road below it
+        const float tl = (p.line_z - oz) / dz;
+        bool line_hit = false;
+        if (tl >= p.near_plane && tl < best) {
+            const int q = ground_quad(wi, cm.px + tl * dx, cm.py + tl * dy, p.lcell_off,
+                                      p.lcell_quads, wi.lcell_begin, p.line_geo);
+            if (q >= 0) {
+                best = tl;
+                cls = 2;
+                prim = wi.road_end + 2u * (uint32_t)(q - wi.line_begin);
+                line_hit = true;
+            }
+        }
+        const float tr = -oz / dz;
+        if (!line_hit && tr >= p.near_plane && tr < best) {
+            const int q = ground_quad(wi, cm.px + tr * dx, cm.py + tr * dy, p.cell_off,
+                                      p.cell_quads, wi.cell_begin, p.road_geo);
+            if (q >= 0) {
+                best = tr;
+                cls = 1;
+                prim = wi.box_end + 2u * (uint32_t)(q - wi.road_begin);
+            }
+        }
+    }
+    t_hit = best;
+    return cls;
+}
+
+// One thread traces four consecutive pixels of one view and stores them like the raster's
+// encode (class / one-hot / RGB, and FP32 depth or its binary16 bits).
+__global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
+    __shared__ TraceBox tb[kMaxBoxes];
+    const int view = p.trace_view0 + (int)blockIdx.y;
+    const long long plane = (long long)p.H * p.W;
+    const int px0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    Cam cm;
+    WorldInfo wi;
+    view_cam(p, view, cm, wi);
+    // the world's boxes in index order (ties keep going to the lower index), each once per
+    // block: yaw sin/cos and the camera in the box frame
+    for (int b = threadIdx.x; b < wi.n_boxes; b += blockDim.x) {
+        const float4 bp = p.box_pose[wi.box_begin + b];
+        const float4 bd = p.box_dim[wi.box_begin + b];
+        TraceBox B;
+        sincosf(bp.z, &B.sn, &B.cs);
+        const float ox = cm.px - bp.x, oy = cm.py - bp.y;
+        B.ox = B.cs * ox + B.sn * oy;
+        B.oy = -B.sn * ox + B.cs * oy;
+        B.hl = 0.5f * bd.x;
+        B.hw = 0.5f * bd.y;
+        B.h = bd.z;
+        B.pad = 0.f;
+        // no ray can hit a box whose footprint circle (radius = half diagonal) lies wholly
+        // behind the near plane or wholly outside the left or right frustum plane
+        const float fwd = -(ox * cm.c + oy * cm.s), side = -ox * cm.s + oy * cm.c;
+        const float rad = sqrtf(B.hl * B.hl + B.hw * B.hw);
+        const float nrm = sqrtf(1.f + p.tx * p.tx);
+        const bool culled = fwd + rad < p.near_plane || (side + p.tx * fwd) < -rad * nrm ||
+                            (p.tx * fwd - side) < -rad * nrm;
+        if (b == cm.ego || culled) B.hl = -1.f;
+        tb[b] = B;
+    }
+    __syncthreads();
+    if (px0 >= plane) return;
+    const uint32_t full = p.key_f16 ? 0xFFFFu : 0xFFFFFFFFu;
+    uint32_t c[4], low[4];
+    float d[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int pix = px0 + k, j = pix / p.W, i = pix - j * p.W;
+        uint32_t prim;
+        float t;
+        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, prim, t);
+        low[k] = c[k] ? full - prim : 0u;
+        d[k] = c[k] ? __fdiv_rn(p.near_plane, t) : 0.f;
+    }
+    const long long slot = view;
+    store_classes(p, cm, slot, plane, px0, c, low, full);
+    if (p.depth) {
+        if (p.key_f16) {
+            const uint32_t h0 = __half_as_ushort(__float2half_rn(d[0])), h1 = __half_as_ushort(__float2half_rn(d[1]));
+            const uint32_t h2 = __half_as_ushort(__float2half_rn(d[2])), h3 = __half_as_ushort(__float2half_rn(d[3]));
+            __stcs((uint2 *)((uint16_t *)p.depth + slot * plane + px0), make_uint2(h0 | (h1 << 16), h2 | (h3 << 16)));
+        } else {
+            __stcs((float4 *)((float *)p.depth + slot * plane + px0), make_float4(d[0], d[1], d[2], d[3]));
+        }
+    }
+}
+
 // Camera and band of a work item.
 __device__ __forceinline__ void make_cam(const RenderParams &p, int item, Cam &cm, WorldInfo &wi,
                                          int &view) {
@@ -1428,6 +1621,19 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
 }
 
 }  // namespace
+
+cudaError_t launch_trace(const RenderParams &p, int n_views, cudaStream_t s) {
+    const long long plane = (long long)p.H * p.W;
+    const int bx = (int)((plane / 4 + 127) / 128);
+    for (int v0 = 0; v0 < n_views; v0 += 65535) {
+        RenderParams q = p;
+        q.trace_view0 = v0;
+        trace_kernel<<<dim3(bx, (unsigned)std::min(65535, n_views - v0)), 128, 0, s>>>(q);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri_cap, int max_cl,
                          int prod_warps) {
