@@ -90,6 +90,10 @@ def _lib():
                                       ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, c_u8p, c_f32p, P(ctypes.c_uint32)]
+        lib.or_observe_world.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p,
+                                         ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                         ctypes.c_double, c_f64p, c_f64p, c_f64p]
         lib.or_lane_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, c_f32p,
                                       ctypes.c_double, c_f64p, c_f64p]
         lib.or_lane_frame.restype = ctypes.c_int
@@ -250,6 +254,26 @@ def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: in
 # reverse, overspeed.
 REWARD_WEIGHTS = (3.0, 3.0, 0.05, 0.025, 3.8e-3, 2.5e-3, 1.0, 2.5e-5, 5e-3, 0.0)
 LANE_WIDTH = 3.5
+
+
+OBS_AGENTS, OBS_AGENT_RADIUS, OBS_ROADS, OBS_ROAD_RADIUS = 16, 100.0, 32, 30.0
+
+
+def observe_world(boxes6, speed, road, line, K=OBS_AGENTS, r_agents=OBS_AGENT_RADIUS,
+                  M=OBS_ROADS, r_roads=OBS_ROAD_RADIUS, n_agents=None):
+    """O_vec of one world's agents: (agents [n_agents, K, 8], roads [n_agents, M, 8])."""
+    b = _c(boxes6, np.float64).reshape(-1, 6)
+    sp = _c(speed, np.float64)
+    rd = _c(road, np.float32).reshape(-1, 8)
+    ln = _c(line, np.float32).reshape(-1, 8)
+    na = b.shape[0] if n_agents is None else n_agents
+    ao = np.zeros((na, K, 8), np.float64)
+    ro = np.zeros((na, M, 8), np.float64)
+    scratch = np.zeros(2 * max(1, b.shape[0], rd.shape[0] + ln.shape[0]), np.float64)
+    _lib().or_observe_world(b.shape[0], na, _p(b, c_f64p), _p(sp, c_f64p), rd.shape[0],
+                            _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), K, float(r_agents), M,
+                            float(r_roads), _p(ao, c_f64p), _p(ro, c_f64p), _p(scratch, c_f64p))
+    return ao, ro
 
 
 def lane_frame(px: float, py: float, road: np.ndarray, lane_w: float = LANE_WIDTH):

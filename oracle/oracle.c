@@ -31,6 +31,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* ------------------------------------------------------------------------------------
@@ -273,6 +274,107 @@ void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
                              dims[2 * i] / 10.0, dims[2 * i + 1] / 5.0};
         for (int k = 0; k < 5; ++k) ego[6 * i + k] = fmax(-1.0, fmin(1.0, e[k]));
         ego[6 * i + 5] = (fl_after[i] & OR_COLLIDED) ? 1.0 : 0.0;
+    }
+}
+
+/*
+ * Vectorized observations O_vec (App. A "Observations": surrounding agents and road
+ * geometry; no traffic controls in the synthetic worlds).  Readings, per agent i with
+ * centre c_i, heading th_i, speed v_i and the ego frame (x forward, y left):
+ *   agents: the other boxes j (agents and static boxes, speed 0 for static ones) with
+ *     |c_j - c_i| <= r_agents, nearest first (ties to the lower index), at most K; slot =
+ *     [1, x / r_agents, y / r_agents, L_j / 10, W_j / 5, cos(th_j - th_i), sin(th_j - th_i),
+ *     (v_j - v_i) / 30];
+ *   roads: segments = the centre lines of the road quads (type 0) and of the lane-line
+ *     strips (type 1), each from the midpoint of its q0-q3 edge to that of its q1-q2 edge;
+ *     those with midpoint within r_roads, nearest midpoint first (ties: road quads before
+ *     lines, then lower index), at most M; slot = [1, x / r_roads, y / r_roads,
+ *     length / r_roads, cos(phi - th_i), sin(phi - th_i), 1[type 0], 1[type 1]] with phi
+ *     the segment's direction;
+ *   unused slots are all zero.
+ *   boxes [n_boxes][6] x, y, yaw, L, W, H; speed [n_boxes] -> agents_out [n_agents][K][8],
+ *   roads_out [n_agents][M][8]
+ */
+static int cmp_key(const void *a, const void *b) {
+    const double *x = (const double *)a, *y = (const double *)b;
+    if (x[0] < y[0]) return -1;
+    if (x[0] > y[0]) return 1;
+    return (x[1] < y[1]) ? -1 : (x[1] > y[1]);
+}
+
+static void seg_of(const float *q, double *mx, double *my, double *len, double *phi) {
+    const double ax = 0.5 * ((double)q[0] + q[6]), ay = 0.5 * ((double)q[1] + q[7]);
+    const double bx = 0.5 * ((double)q[2] + q[4]), by = 0.5 * ((double)q[3] + q[5]);
+    *mx = 0.5 * (ax + bx);
+    *my = 0.5 * (ay + by);
+    *len = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay));
+    *phi = atan2(by - ay, bx - ax);
+}
+
+void or_observe_world(int32_t n_boxes, int32_t n_agents, const double *boxes, const double *speed,
+                      int32_t n_road, const float *road, int32_t n_line, const float *line,
+                      int32_t K, double r_agents, int32_t M, double r_roads, double *agents_out,
+                      double *roads_out, double *scratch /* >= 2 * max(n_boxes, n_road + n_line) */) {
+    for (int32_t i = 0; i < n_agents; ++i) {
+        const double *bi = boxes + 6 * i;
+        const double c = cos(bi[2]), sn = sin(bi[2]);
+        double *ao = agents_out + (int64_t)i * K * 8;
+        double *ro = roads_out + (int64_t)i * M * 8;
+        memset(ao, 0, sizeof(double) * K * 8);
+        memset(ro, 0, sizeof(double) * M * 8);
+        int32_t n = 0;
+        for (int32_t j = 0; j < n_boxes; ++j) {
+            if (j == i) continue;
+            const double d = hypot(boxes[6 * j] - bi[0], boxes[6 * j + 1] - bi[1]);
+            if (d <= r_agents) {
+                scratch[2 * n] = d;
+                scratch[2 * n + 1] = j;
+                ++n;
+            }
+        }
+        qsort(scratch, (size_t)n, 2 * sizeof(double), cmp_key);
+        for (int32_t k = 0; k < n && k < K; ++k) {
+            const double *bj = boxes + 6 * (int32_t)scratch[2 * k + 1];
+            const double dx = bj[0] - bi[0], dy = bj[1] - bi[1];
+            double *o = ao + 8 * k;
+            o[0] = 1.0;
+            o[1] = (dx * c + dy * sn) / r_agents;
+            o[2] = (-dx * sn + dy * c) / r_agents;
+            o[3] = bj[3] / 10.0;
+            o[4] = bj[4] / 5.0;
+            o[5] = cos(bj[2] - bi[2]);
+            o[6] = sin(bj[2] - bi[2]);
+            o[7] = (speed[(int32_t)scratch[2 * k + 1]] - speed[i]) / 30.0;
+        }
+        n = 0;
+        for (int32_t s = 0; s < n_road + n_line; ++s) {
+            const float *q = s < n_road ? road + 8 * s : line + 8 * (s - n_road);
+            double mx, my, len, phi;
+            seg_of(q, &mx, &my, &len, &phi);
+            const double d = hypot(mx - bi[0], my - bi[1]);
+            if (d <= r_roads) {
+                scratch[2 * n] = d;
+                scratch[2 * n + 1] = s;
+                ++n;
+            }
+        }
+        qsort(scratch, (size_t)n, 2 * sizeof(double), cmp_key);
+        for (int32_t k = 0; k < n && k < M; ++k) {
+            const int32_t s = (int32_t)scratch[2 * k + 1];
+            const float *q = s < n_road ? road + 8 * s : line + 8 * (s - n_road);
+            double mx, my, len, phi;
+            seg_of(q, &mx, &my, &len, &phi);
+            const double dx = mx - bi[0], dy = my - bi[1];
+            double *o = ro + 8 * k;
+            o[0] = 1.0;
+            o[1] = (dx * c + dy * sn) / r_roads;
+            o[2] = (-dx * sn + dy * c) / r_roads;
+            o[3] = len / r_roads;
+            o[4] = cos(phi - bi[2]);
+            o[5] = sin(phi - bi[2]);
+            o[6] = s < n_road ? 1.0 : 0.0;
+            o[7] = s < n_road ? 0.0 : 1.0;
+        }
     }
 }
 

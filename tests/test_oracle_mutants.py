@@ -54,6 +54,11 @@ MUTANTS = {
     "trace near ignored": ("t0 > t1 || t0 < cfg->near ||", "t0 > t1 ||"),
     "trace last road quad wins": ("                            pr = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road + 2 * q : 2 * q));\n                            break;",
                                   "                            pr = (uint32_t)(12 * n_boxes + (pass ? 2 * n_road + 2 * q : 2 * q));"),
+    "ovec lateral sign": ("            o[2] = (-dx * sn + dy * c) / r_agents;", "            o[2] = (dx * sn - dy * c) / r_agents;"),
+    "ovec radius exclusive of far": ("            if (d <= r_agents) {", "            if (d <= 1.5 * r_agents) {"),
+    "ovec speed difference sign": ("(speed[(int32_t)scratch[2 * k + 1]] - speed[i]) / 30.0;", "(speed[i] - speed[(int32_t)scratch[2 * k + 1]]) / 30.0;"),
+    "ovec segment from quad edge": ("const double ax = 0.5 * ((double)q[0] + q[6]), ay = 0.5 * ((double)q[1] + q[7]);", "const double ax = q[0], ay = q[1];"),
+    "ovec self included": ("            if (j == i) continue;\n            const double d = hypot", "            const double d = hypot"),
     "ego speed unnormalised": ("const double e[5] = {after[4 * i + 3] / vmax,", "const double e[5] = {after[4 * i + 3],"),
 }
 

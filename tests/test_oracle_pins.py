@@ -1027,3 +1027,97 @@ def test_trace_overlapping_road_quads_tie_to_lower_index():
     rd = tr.cls == 1
     assert rd.sum() > 100
     assert np.all(tr.prim[rd] == 12)  # road quad 0 wins every tie
+
+
+# ---------------------------------------------------------------------------------------
+# Vectorized observations O_vec: hand-computed slots and an independent brute force
+# ---------------------------------------------------------------------------------------
+
+def test_ovec_agents_in_ego_frame():
+    # ego at the origin facing +y: world +y is ego-forward (x), world -x is ego-left (y)
+    boxes = [[0.0, 0.0, math.pi / 2, 4.5, 1.9, 1.5],
+             [0.0, 20.0, math.pi / 2 + 0.3, 4.2, 1.8, 1.5],   # 20 m ahead
+             [-10.0, 0.0, 0.0, 4.0, 2.0, 1.6],                 # 10 m to the left
+             [0.0, -100.5, 0.0, 4.0, 2.0, 1.6]]                # beyond 100 m
+    speed = [10.0, 12.0, 0.0, 0.0]
+    ao, _ = oracle.observe_world(boxes, speed, np.zeros((0, 8)), np.zeros((0, 8)), n_agents=1)
+    s = ao[0]
+    # nearest: the box 10 m to the left (heading 0 = -90 deg relative to the ego)
+    assert s[0] == pytest.approx([1, 0.0, 10 / 100, 0.4, 2.0 / 5, 0.0, -1.0, -10 / 30], abs=1e-12)
+    assert s[1] == pytest.approx([1, 0.2, 0.0, 0.42, 0.36, math.cos(0.3), math.sin(0.3), 2 / 30], abs=1e-12)
+    assert not s[2:].any()
+
+
+def test_ovec_ties_and_truncation():
+    boxes = [[0.0, 0.0, 0.0, 4.5, 1.9, 1.5]] + [[10.0 * math.cos(a), 10.0 * math.sin(a), 0.0, 4.0, 2.0, 1.5]
+                                                for a in np.linspace(0, 2 * math.pi, 20, endpoint=False)]
+    ao, _ = oracle.observe_world(boxes, np.zeros(21), np.zeros((0, 8)), np.zeros((0, 8)), K=16,
+                                 n_agents=1)
+    # all at 10 m (to rounding): the 16 lowest indices after nearest-first ordering
+    x = ao[0, :, 1] * 100
+    y = ao[0, :, 2] * 100
+    assert np.allclose(np.hypot(x, y), 10.0)
+    ang = np.arctan2(y, x) % (2 * math.pi)
+    assert ao[0, :, 0].all() and len(set(np.round(ang, 6))) == 16
+
+
+def test_ovec_road_segment_features():
+    road = np.array([rect_quad(-20.0, 20.0, -3.5, 3.5)], np.float32)
+    line = np.array([rect_quad(-20.0, 20.0, -0.075, 0.075), rect_quad(100.0, 140.0, -0.1, 0.1)],
+                    np.float32)
+    boxes = [[5.0, 1.0, math.pi, 4.5, 1.9, 1.5]]
+    _, ro = oracle.observe_world(boxes, [0.0], road, line, n_agents=1)
+    r = ro[0]
+    # midpoint (0, 0) seen from (5, 1) facing -x: 5 m ahead, 1 m to the right
+    assert r[0] == pytest.approx([1, 5 / 30, 1 / 30, 40 / 30, -1.0, 0.0, 1, 0], abs=1e-6)
+    assert r[1] == pytest.approx([1, 5 / 30, 1 / 30, 40 / 30, -1.0, 0.0, 0, 1], abs=1e-6)
+    assert not r[2:].any()  # the far line is beyond 30 m
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_ovec_matches_numpy_brute_force(seed):
+    rng = np.random.default_rng(500 + seed)
+    nb = 40
+    boxes = np.column_stack([rng.uniform(-120, 120, nb), rng.uniform(-120, 120, nb),
+                             rng.uniform(-math.pi, math.pi, nb), rng.uniform(4, 5, nb),
+                             rng.uniform(1.8, 2, nb), rng.uniform(1.4, 1.7, nb)])
+    speed = rng.uniform(0, 20, nb)
+    def quads(n):
+        c = rng.uniform(-60, 60, (n, 2))
+        h = rng.uniform(-math.pi, math.pi, n)
+        L, Wd = rng.uniform(5, 30, n), rng.uniform(0.1, 7, n)
+        out = []
+        for (cx, cy), hh, l, w in zip(c, h, L, Wd):
+            cc, ss = math.cos(hh), math.sin(hh)
+            pts = [(-l / 2, -w / 2), (l / 2, -w / 2), (l / 2, w / 2), (-l / 2, w / 2)]
+            out.append([v for (a, b) in pts for v in (cx + cc * a - ss * b, cy + ss * a + cc * b)])
+        return np.array(out, np.float32)
+    road, line = quads(60), quads(90)
+    na = 12
+    ao, ro = oracle.observe_world(boxes, speed, road, line, n_agents=na)
+    segs = np.concatenate([road, line]).astype(np.float64).reshape(-1, 4, 2)
+    a = 0.5 * (segs[:, 0] + segs[:, 3])
+    b = 0.5 * (segs[:, 1] + segs[:, 2])
+    mid, vec = 0.5 * (a + b), b - a
+    for i in range(na):
+        x, y, th = boxes[i, :3]
+        c, s = math.cos(th), math.sin(th)
+        d = np.hypot(boxes[:, 0] - x, boxes[:, 1] - y)
+        order = [j for j in np.lexsort((np.arange(nb), d)) if j != i and d[j] <= 100][:16]
+        for k, j in enumerate(order):
+            dx, dy = boxes[j, 0] - x, boxes[j, 1] - y
+            want = [1, (dx * c + dy * s) / 100, (-dx * s + dy * c) / 100, boxes[j, 3] / 10,
+                    boxes[j, 4] / 5, math.cos(boxes[j, 2] - th), math.sin(boxes[j, 2] - th),
+                    (speed[j] - speed[i]) / 30]
+            assert ao[i, k] == pytest.approx(want, abs=1e-9)
+        assert not ao[i, len(order):].any()
+        dm = np.hypot(mid[:, 0] - x, mid[:, 1] - y)
+        sel = [q for q in np.lexsort((np.arange(len(dm)), dm)) if dm[q] <= 30][:32]
+        for k, q in enumerate(sel):
+            dx, dy = mid[q, 0] - x, mid[q, 1] - y
+            phi = math.atan2(vec[q, 1], vec[q, 0])
+            want = [1, (dx * c + dy * s) / 30, (-dx * s + dy * c) / 30,
+                    math.hypot(*vec[q]) / 30, math.cos(phi - th), math.sin(phi - th),
+                    float(q < 60), float(q >= 60)]
+            assert ro[i, k] == pytest.approx(want, abs=1e-9)
+        assert not ro[i, len(sel):].any()
