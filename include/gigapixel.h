@@ -66,6 +66,11 @@ enum { GP_CLASS_BACKGROUND = 0, GP_CLASS_ROAD = 1, GP_CLASS_LANE_LINE = 2, GP_CL
 #define GP_MAX_BOXES 128         /* boxes (agents + static) per world */
 #define GP_MAX_QUADS 32767       /* road + lane-line quads per world */
 #define GP_MAX_WIDTH 512         /* image width and height */
+/* Vectorized observations (gp_observe_vec) */
+#define GP_OBS_AGENTS 16         /* surrounding-agent slots per agent */
+#define GP_OBS_AGENT_RADIUS 100.0f
+#define GP_OBS_ROADS 32          /* road-segment slots per agent */
+#define GP_OBS_ROAD_RADIUS 30.0f
 
 /*
  * Worlds, as host arrays in CSR form over worlds; copied to the device at create time.
@@ -249,6 +254,22 @@ gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, v
  * accelerations to 0.
  */
 gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host, void *stream);
+
+/*
+ * Vectorized observations O_vec of every agent from the current state (App. A
+ * "Observations"; the synthetic worlds have no traffic controls).  Ego frame: x forward,
+ * y left.
+ *   agents_dev  float [n_agents][GP_OBS_AGENTS][8]: the other boxes (agents and static
+ *               boxes) within GP_OBS_AGENT_RADIUS, nearest first (ties to the lower index);
+ *               slot = [1, x / R, y / R, L / 10, W / 5, cos dth, sin dth, (v_j - v_i) / 30]
+ *   roads_dev   float [n_agents][GP_OBS_ROADS][8]: the centre lines of the road quads and
+ *               lane-line strips (from the midpoint of the q0-q3 edge to that of q1-q2)
+ *               with midpoint within GP_OBS_ROAD_RADIUS, nearest first (ties: roads before
+ *               lines, then lower index), found through the world's spatial grid;
+ *               slot = [1, x / R, y / R, length / R, cos dphi, sin dphi, 1[road], 1[line]]
+ * Unused slots are zero.  Either pointer may be NULL; both 16-byte aligned.  Asynchronous.
+ */
+gp_status gp_observe_vec(gp_handle *h, float *agents_dev, float *roads_dev, void *stream);
 
 /* Read (synchronously) / clear the device status word; set bits for tests. */
 gp_status gp_get_status(gp_handle *h, uint32_t *bits);

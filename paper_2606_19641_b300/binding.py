@@ -28,7 +28,7 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render", "gp_trace",
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
-            "gp_get_rewards", "gp_set_reward_weights",
+            "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_debug_inject_status": [vp, u32],
         "gp_get_rewards": [vp, vp, vp, i32, vp],
         "gp_trace": [vp, vp, vp, vp],
+        "gp_observe_vec": [vp, vp, vp, vp],
         "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -280,6 +281,15 @@ class Simulator:
     def trace(self, out, depth=None, stream=None) -> None:
         """Ray-traced render of every camera into the same tensors as render()."""
         check(lib().gp_trace(self._h, _ptr(out), _ptr(depth), _stream(stream)))
+
+    def observe_vec(self, stream=None):
+        """(agents [n_agents, 16, 8], roads [n_agents, 32, 8]) float32 O_vec on the device."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        a = torch.empty((self.n_agents, 16, 8), dtype=torch.float32, device=dev)
+        r = torch.empty((self.n_agents, 32, 8), dtype=torch.float32, device=dev)
+        check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _stream(stream)))
+        return a, r
 
     def rewards(self, stream=None):
         """(reward [n_agents], ego state [n_agents, 6]) of the last step, float32 on the

@@ -980,6 +980,29 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     return GP_OK;
 }
 
+gp_status gp_observe_vec(gp_handle *h, float *agents, float *roads, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if ((agents && !aligned16(agents)) || (roads && !aligned16(roads)))
+        return fail(GP_EINVAL, "outputs must be 16-byte aligned");
+    CK(cudaSetDevice(h->device));
+    ObsParams p{};
+    p.worlds = h->worlds.p;
+    p.n_worlds = h->n_worlds;
+    p.box_pose = h->box_pose.p;
+    p.box_dim = h->box_dim.p;
+    p.speed = h->speed.p;
+    p.road_geo = h->road_geo.p;
+    p.line_geo = h->line_geo.p;
+    p.cell_off = h->cell_off.p;
+    p.cell_quads = h->cell_quads.p;
+    p.lcell_off = h->lcell_off.p;
+    p.lcell_quads = h->lcell_quads.p;
+    p.agents_out = agents;
+    p.roads_out = roads;
+    CK(launch_obs(p, 8 * h->sms, (cudaStream_t)stream));
+    return GP_OK;
+}
+
 gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, void *stream) {
     if (!h) return fail(GP_EINVAL, "null handle");
     if (!h->cfg.rewards) return fail(GP_ESTATE, "rewards are off (gp_config.rewards = 0)");

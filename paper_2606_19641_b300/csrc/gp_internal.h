@@ -58,6 +58,19 @@ struct StepParams {
     float *ego;             // [n_agents][6]
 };
 
+// Vectorized observations (gp_observe_vec).
+struct ObsParams {
+    const WorldInfo *worlds;
+    int n_worlds;
+    const float4 *box_pose, *box_dim;
+    const float *speed;
+    const float4 *road_geo, *line_geo;
+    const int *cell_off, *cell_quads, *lcell_off, *lcell_quads;
+    float *agents_out;  // [n_agents][GP_OBS_AGENTS][8] or null
+    float *roads_out;   // [n_agents][GP_OBS_ROADS][8] or null
+};
+cudaError_t launch_obs(const ObsParams &p, int max_blocks, cudaStream_t s);
+
 // Snapped triangle as dumped for parity checks (matches gp_debug_dump_tris records).
 struct DumpTri {
     int X[3], Y[3];

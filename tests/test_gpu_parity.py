@@ -735,3 +735,74 @@ def test_trace_and_raster_agree_away_from_silhouettes():
     agree = (o1 == o2).float().mean().item()
     print("raster vs trace class agreement %.4f" % agree)
     assert agree > 0.97
+
+
+# ---------------------------------------------------------------------------------------
+# Vectorized observations O_vec
+# ---------------------------------------------------------------------------------------
+
+def _sure_limit(d, cap, radius, eps):
+    """(limit, tied): the selection of candidates nearer than limit cannot depend on
+    rounding.  tied if a candidate lies within eps of the radius, or the cap-th and the next
+    nearest (when more than cap are in range) are within eps of each other; else limit is
+    infinite (the whole selection is determined)."""
+    limit, tied = np.inf, False
+    if np.any(np.abs(d - radius) < eps):
+        limit, tied = radius - eps, True
+    ds = np.sort(d[d <= radius])
+    if len(ds) > cap and ds[cap] - ds[cap - 1] < eps:
+        limit, tied = min(limit, ds[cap - 1] - eps), True
+    return limit, tied
+
+
+def _rows(x, scale, limit):
+    """Valid slots nearer than limit, as a set: rows sorted by their rounded features
+    (near-equal distances may order differently in FP32 and FP64)."""
+    v = x[x[:, 0] > 0]
+    v = v[np.hypot(v[:, 1], v[:, 2]) * scale < limit]
+    return v[np.lexsort(np.round(v, 3).T[::-1])]
+
+
+@pytest.mark.parametrize("name,n_worlds", [("uniform", 3), ("ragged", 4)])
+def test_observe_vec_matches_oracle(name, n_worlds):
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl)
+    for k in range(3):
+        sim.step(torch_actions(worlds, k, wl.seed)[0])
+    ga, gr = sim.observe_vec()
+    torch.cuda.synchronize()
+    ga, gr = ga.cpu().numpy(), gr.cpu().numpy()
+    st, fl = sim.get_state()
+    osim = oracle_sim(worlds, sim)
+    off = worlds.agent_offsets()
+    checked = skipped = 0
+    compared_rows = [0]
+    for w in range(worlds.n_worlds):
+        a0, a1 = int(off[w]), int(off[w + 1])
+        b = osim.boxes6(w)
+        sp = np.zeros(len(b))
+        sp[:a1 - a0] = st[a0:a1, 3]
+        road, line = osim.road(w), osim.line(w)
+        oa, orr = oracle.observe_world(b, sp, road, line, n_agents=a1 - a0)
+        segs = np.concatenate([road, line]).astype(np.float64).reshape(-1, 4, 2)
+        mid = 0.25 * (segs[:, 0] + segs[:, 3] + segs[:, 1] + segs[:, 2])
+        for i in range(a1 - a0):
+            db = np.delete(np.hypot(b[:, 0] - b[i, 0], b[:, 1] - b[i, 1]), i)
+            dm = np.hypot(mid[:, 0] - b[i, 0], mid[:, 1] - b[i, 1])
+            (la, ta), (lr, tr) = _sure_limit(db, 16, 100.0, 1e-3), _sure_limit(dm, 32, 30.0, 1e-3)
+            full = not (ta or tr)
+            checked += int(full)
+            skipped += int(not full)
+            for g, o, scale, lim in ((ga[a0 + i], oa[i], 100.0, la), (gr[a0 + i], orr[i], 30.0, lr)):
+                ra, rb = _rows(g, scale, lim), _rows(o, scale, lim)
+                assert ra.shape == rb.shape and np.allclose(ra, rb, atol=2e-5), "agent %d" % (a0 + i)
+                compared_rows[0] += len(ra)
+                # nearest first: the GPU's slot distances are non-decreasing
+                v = g[g[:, 0] > 0]
+                assert np.all(np.diff(np.hypot(v[:, 1], v[:, 2]) * scale) >= -1e-3)
+    print("O_vec %s: %d agents fully checked, %d up to a near-tie at the cutoff, %d slots compared"
+          % (name, checked, skipped, compared_rows[0]))
+    assert checked > 0.5 * (checked + skipped)
+    assert compared_rows[0] > 1000
