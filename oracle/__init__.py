@@ -65,6 +65,11 @@ def _lib():
     if _lib_handle is None:
         lib = ctypes.CDLL(build())
         lib.or_bicycle.argtypes = [c_f64p, c_f64p, c_f64p, c_f64p] + [ctypes.c_double] * 5
+        lib.or_jerk_bicycle.argtypes = [c_f64p, c_f64p, c_f64p, c_f64p] + [ctypes.c_double] * 3 + \
+            [c_f64p, ctypes.c_double, ctypes.c_double]
+        lib.or_step_world_jerk.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p, c_u8p,
+                                           c_f32p, ctypes.c_int32, c_f32p, ctypes.c_double,
+                                           ctypes.c_double, c_f64p]
         lib.or_obb_overlap.argtypes = [c_f64p, c_f64p]
         lib.or_obb_overlap.restype = ctypes.c_int
         lib.or_point_in_quad.argtypes = [ctypes.c_double, ctypes.c_double, c_f32p]
@@ -100,7 +105,7 @@ def _lib():
         lib.or_rewards_world.argtypes = [ctypes.c_int32, c_f64p, c_u8p, c_f64p, c_u8p, c_f32p,
                                          c_f64p, c_f64p, c_f64p, ctypes.c_int32, c_f32p,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, c_f64p, c_f64p]
+                                         ctypes.c_double, c_f64p, c_f64p, c_f64p]
         lib.or_shade_rgb.argtypes = [c_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                      ctypes.c_uint32, c_f64p, c_f64p, c_f64p, ctypes.c_double,
                                      c_u8p]
@@ -128,6 +133,20 @@ def bicycle(x, y, yaw, v, L, accel, steer, dt=0.1, vmax=30.0):
     return cx.value, cy.value, cyaw.value, cv.value
 
 
+# The paper's discrete action set: longitudinal x lateral jerk (m/s^3).
+JERK_ACTIONS = tuple((jl, jt) for jl in (-15.0, -4.0, 0.0, 4.0) for jt in (-4.0, 0.0, 4.0))
+
+
+def jerk_bicycle(x, y, yaw, v, L, j_lon, j_lat, st, dt=0.1, vmax=30.0):
+    """One jerk-actuated bicycle step; st = [a_lon, a_lat, steer] (updated in place);
+    returns x, y, yaw, v."""
+    assert st.dtype == np.float64 and st.shape == (3,)
+    cx, cy, cyaw, cv = (ctypes.c_double(float(t)) for t in (x, y, yaw, v))
+    _lib().or_jerk_bicycle(ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(cyaw), ctypes.byref(cv),
+                           float(L), float(j_lon), float(j_lat), _p(st, c_f64p), float(dt), float(vmax))
+    return cx.value, cy.value, cyaw.value, cv.value
+
+
 def obb_overlap(a: Sequence[float], b: Sequence[float]) -> bool:
     """Footprint interiors intersect (x, y, yaw, L, W each)."""
     aa, bb = _c(a[:5], np.float64), _c(b[:5], np.float64)
@@ -140,20 +159,30 @@ def point_in_quad(px: float, py: float, quad: Sequence[float]) -> bool:
 
 
 def step_world(boxes6: np.ndarray, state: np.ndarray, flags: np.ndarray, actions: np.ndarray,
-               road: np.ndarray, dt: float = 0.1, vmax: float = 30.0) -> None:
+               road: np.ndarray, dt: float = 0.1, vmax: float = 30.0,
+               jerk: Optional[np.ndarray] = None) -> None:
     """One step of one world in place (App. A dynamics + infractions + halt).
 
     boxes6 float64 [n_boxes, 6]; state float64 [n_agents, 4]; flags uint8 [n_agents];
-    actions float32 [n_agents, 2]; road float32 [n_road, 8].
+    actions float32 [n_agents, 2] (accel, steer; or j_lon, j_lat when `jerk` is given);
+    road float32 [n_road, 8]; jerk float64 [n_agents, 3] (a_lon, a_lat, steer), updated.
     """
     assert boxes6.dtype == np.float64 and boxes6.flags.c_contiguous
     assert state.dtype == np.float64 and state.flags.c_contiguous
     assert flags.dtype == np.uint8 and flags.flags.c_contiguous
     act = _c(actions, np.float32)
     rd = _c(road, np.float32).reshape(-1, 8)
-    _lib().or_step_world(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p), _p(state, c_f64p),
-                         _p(flags, c_u8p), _p(act, c_f32p), rd.shape[0], _p(rd, c_f32p),
-                         float(dt), float(vmax))
+    if jerk is None:
+        _lib().or_step_world(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p),
+                             _p(state, c_f64p), _p(flags, c_u8p), _p(act, c_f32p), rd.shape[0],
+                             _p(rd, c_f32p), float(dt), float(vmax))
+    else:
+        assert jerk.dtype == np.float64 and jerk.flags.c_contiguous
+        assert jerk.shape == (state.shape[0], 3)
+        _lib().or_step_world_jerk(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p),
+                                  _p(state, c_f64p), _p(flags, c_u8p), _p(act, c_f32p),
+                                  rd.shape[0], _p(rd, c_f32p), float(dt), float(vmax),
+                                  _p(jerk, c_f64p))
 
 
 # ---------------------------------------------------------------------------------------
@@ -286,9 +315,10 @@ def lane_frame(px: float, py: float, road: np.ndarray, lane_w: float = LANE_WIDT
 
 
 def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weights, road,
-                  lane_w=LANE_WIDTH, v_lim=30.0, dt=0.1, vmax=30.0):
-    """Per-agent reward and ego state [n, 6] of one step (see or_rewards_world); `acc`
-    [n, 2] (previous accelerations) is updated in place."""
+                  lane_w=LANE_WIDTH, v_lim=30.0, dt=0.1, vmax=30.0, jerk=None):
+    """Per-agent reward and ego state [n, 9] of one step (see or_rewards_world); `acc`
+    [n, 2] (previous accelerations) is updated in place; `jerk` [n, 3] is the post-step
+    jerk-dynamics state (a_lon, a_lat, steer) or None under direct control."""
     b = _c(before, np.float64).reshape(-1, 4)
     n = b.shape[0]
     a = _c(after, np.float64).reshape(-1, 4)
@@ -299,11 +329,13 @@ def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weight
     w = _c(weights, np.float64).reshape(-1, 10)
     rd = _c(road, np.float32).reshape(-1, 8)
     reward = np.zeros(n, np.float64)
-    ego = np.zeros((n, 6), np.float64)
+    ego = np.zeros((n, 9), np.float64)
+    jk = None if jerk is None else _c(jerk, np.float64).reshape(n, 3)
     _lib().or_rewards_world(n, _p(b, c_f64p), _p(fb, c_u8p), _p(a, c_f64p), _p(fa, c_u8p),
                             _p(act, c_f32p), _p(dm, c_f64p), _p(acc, c_f64p), _p(w, c_f64p),
                             rd.shape[0], _p(rd, c_f32p), float(lane_w), float(v_lim), float(dt),
-                            float(vmax), _p(reward, c_f64p), _p(ego, c_f64p))
+                            float(vmax), None if jk is None else _p(jk, c_f64p),
+                            _p(reward, c_f64p), _p(ego, c_f64p))
     return reward, ego
 
 
@@ -361,13 +393,15 @@ def onehot_bf16(cls: np.ndarray, mean=(0.5,) * 4, std=(0.5,) * 4) -> np.ndarray:
 class Sim:
     """Oracle simulation of a batch of worlds: FP64 agent state, latched flags."""
 
-    def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0):
+    def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0, jerk_dynamics: bool = False):
         self.w = worlds
         self.dt, self.vmax = dt, vmax
         na = worlds.n_agents
         self.agent_off = worlds.agent_offsets()
         self.state = np.zeros((na, 4), np.float64)
         self.flags = np.zeros(na, np.uint8)
+        # jerk-dynamics actuator state a_lon, a_lat, steer (None under direct control)
+        self.jerk = np.zeros((na, 3), np.float64) if jerk_dynamics else None
         for w in range(worlds.n_worlds):
             b0 = int(worlds.box_off[w])
             a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
@@ -375,9 +409,11 @@ class Sim:
             self.state[a0:a1, 0:3] = bx[:, 0:3]
             self.state[a0:a1, 3] = bx[:, 6]
 
-    def set_state(self, state, flags) -> None:
+    def set_state(self, state, flags, jerk=None) -> None:
         self.state[:] = np.asarray(state, np.float64)
         self.flags[:] = np.asarray(flags, np.uint8)
+        if self.jerk is not None:
+            self.jerk[:] = 0.0 if jerk is None else np.asarray(jerk, np.float64)
 
     def boxes6(self, w: int) -> np.ndarray:
         b0, b1 = int(self.w.box_off[w]), int(self.w.box_off[w + 1])
@@ -399,9 +435,12 @@ class Sim:
             b = self.boxes6(w)
             st = np.ascontiguousarray(self.state[a0:a1])
             fl = np.ascontiguousarray(self.flags[a0:a1])
-            step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax)
+            jk = None if self.jerk is None else np.ascontiguousarray(self.jerk[a0:a1])
+            step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax, jk)
             self.state[a0:a1] = st
             self.flags[a0:a1] = fl
+            if jk is not None:
+                self.jerk[a0:a1] = jk
 
     def camera_tris(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> np.ndarray:
         a = int(self.agent_off[w]) + agent_local

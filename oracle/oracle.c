@@ -66,6 +66,36 @@ void or_bicycle(double *x, double *y, double *yaw, double *v, double L, double a
     *v = vn;
 }
 
+/*
+ * Jerk-actuated kinematic bicycle (App. A "Action Space and Dynamics": the selected
+ * longitudinal and lateral jerks are integrated into accelerations and then into velocity
+ * and steering, accelerations clipped to g-force limits, speed to the speed limit, steering
+ * angle and rate bounded; wheelbase 60 % of the length).  The paper defers the limits to
+ * Gigaflow; readings: a_lon in [-5, 3] m/s^2, |a_lat| <= 4 m/s^2, |steer| <= 0.5 rad,
+ * |d steer / dt| <= 0.5 rad/s; the steering target realises a_lat on the bicycle's curvature,
+ * steer* = atan(kappa * 0.6 L) with kappa = a_lat / max(v^2, 1); then the bicycle above with
+ * accel = a_lon and the limited steer.  st[3] = a_lon, a_lat, steer (updated).
+ */
+void or_jerk_bicycle(double *x, double *y, double *yaw, double *v, double L, double j_lon,
+                     double j_lat, double *st, double dt, double vmax) {
+    double a_lon = st[0] + j_lon * dt, a_lat = st[1] + j_lat * dt;
+    if (a_lon < -5.0) a_lon = -5.0;
+    if (a_lon > 3.0) a_lon = 3.0;
+    if (a_lat < -4.0) a_lat = -4.0;
+    if (a_lat > 4.0) a_lat = 4.0;
+    const double v2 = (*v) * (*v) > 1.0 ? (*v) * (*v) : 1.0;
+    double target = atan((a_lat / v2) * 0.6 * L);
+    const double step = 0.5 * dt;
+    if (target > st[2] + step) target = st[2] + step;
+    if (target < st[2] - step) target = st[2] - step;
+    if (target > 0.5) target = 0.5;
+    if (target < -0.5) target = -0.5;
+    st[0] = a_lon;
+    st[1] = a_lat;
+    st[2] = target;
+    or_bicycle(x, y, yaw, v, L, a_lon, target, dt, vmax);
+}
+
 /* Footprint corners of a box (x, y, yaw, L, W), counter-clockwise from above. */
 static void footprint(double x, double y, double yaw, double L, double W, double c[4][2]) {
     double cs = cos(yaw), sn = sin(yaw);
@@ -128,16 +158,40 @@ int or_point_in_quad(double px, double py, const float *q) {
  * an agent; then flag agents with a footprint corner outside every road quad; then halt
  * every flagged agent (v = 0).  Halted agents stay in place and stay in the scene.
  */
+static void step_world_impl(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
+                            uint8_t *flags, const float *actions, int32_t n_road,
+                            const float *road, double dt, double vmax, double *jerk_state);
+
 void or_step_world(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
                    uint8_t *flags, const float *actions, int32_t n_road, const float *road,
                    double dt, double vmax) {
+    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, dt, vmax, 0);
+}
+
+/* The same step with the jerk-actuated bicycle: actions are (j_lon, j_lat) in m/s^3 and
+ * jerk_state [n_agents][3] (a_lon, a_lat, steer) is updated for moving agents. */
+void or_step_world_jerk(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
+                        uint8_t *flags, const float *actions, int32_t n_road, const float *road,
+                        double dt, double vmax, double *jerk_state) {
+    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, dt, vmax,
+                    jerk_state);
+}
+
+static void step_world_impl(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
+                            uint8_t *flags, const float *actions, int32_t n_road,
+                            const float *road, double dt, double vmax, double *jerk_state) {
     for (int32_t i = 0; i < n_agents; ++i) {
         double *s = state + 4 * i;
         if (!(flags[i] & OR_HALTED)) {
-            or_bicycle(&s[0], &s[1], &s[2], &s[3], boxes[6 * i + 3], actions[2 * i],
-                       actions[2 * i + 1], dt, vmax);
+            if (jerk_state)
+                or_jerk_bicycle(&s[0], &s[1], &s[2], &s[3], boxes[6 * i + 3], actions[2 * i],
+                                actions[2 * i + 1], jerk_state + 3 * i, dt, vmax);
+            else
+                or_bicycle(&s[0], &s[1], &s[2], &s[3], boxes[6 * i + 3], actions[2 * i],
+                           actions[2 * i + 1], dt, vmax);
         } else {
             s[3] = 0.0;
+            if (jerk_state) jerk_state[3 * i] = jerk_state[3 * i + 1] = jerk_state[3 * i + 2] = 0.0;
         }
         boxes[6 * i + 0] = s[0];
         boxes[6 * i + 1] = s[1];
@@ -225,17 +279,21 @@ int or_lane_frame(double px, double py, int32_t n_road, const float *road, doubl
  *   - the traffic-light and goal terms are 0: the synthetic worlds have no signals or
  *     goals; an agent halted before the step earns 0 and has zero accelerations;
  *   - ego state: v'' / v_max (v'' the post-step speed), a_lon / 10, a_lat / 10, L / 10,
- *     W / 5 (each clipped to [-1, 1]) and the collision flag (0 or 1).
- *   before/after [n][4] x, y, yaw, v; fl_before/fl_after [n]; actions [n][2] accel, steer;
- *   dims [n][2] L, W; acc [n][2] previous a_lon, a_lat (overwritten with this step's);
- *   weights [n][10] collision, off-road, comfort, alignment, centering, velocity, traffic
- *   light, time, reverse, overspeed -> reward [n], ego [n][6]
+ *     W / 5 (each clipped to [-1, 1]) and the collision flag (0 or 1); under the jerk
+ *     dynamics also the post-step steering angle / 0.5, and the actuator accelerations
+ *     a_lon / 5 and a_lat / 4 of or_jerk_bicycle (zero under direct control).
+ *   before/after [n][4] x, y, yaw, v; fl_before/fl_after [n]; actions [n][2] accel, steer
+ *   (under the jerk dynamics: the resolved a_lon and steer of the step); dims [n][2] L, W;
+ *   acc [n][2] previous a_lon, a_lat (overwritten with this step's); weights [n][10]
+ *   collision, off-road, comfort, alignment, centering, velocity, traffic light, time,
+ *   reverse, overspeed; jerk [n][3] post-step a_lon, a_lat, steer or NULL
+ *   -> reward [n], ego [n][9]
  */
 void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
                       const double *after, const uint8_t *fl_after, const float *actions,
                       const double *dims, double *acc, const double *weights, int32_t n_road,
                       const float *road, double lane_w, double v_lim, double dt, double vmax,
-                      double *reward, double *ego) {
+                      const double *jerk, double *reward, double *ego) {
     for (int32_t i = 0; i < n; ++i) {
         const double *w = weights + 10 * i;
         double a_lon = 0.0, a_lat = 0.0, r = 0.0;
@@ -272,8 +330,11 @@ void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
         reward[i] = r;
         const double e[5] = {after[4 * i + 3] / vmax, a_lon / 10.0, a_lat / 10.0,
                              dims[2 * i] / 10.0, dims[2 * i + 1] / 5.0};
-        for (int k = 0; k < 5; ++k) ego[6 * i + k] = fmax(-1.0, fmin(1.0, e[k]));
-        ego[6 * i + 5] = (fl_after[i] & OR_COLLIDED) ? 1.0 : 0.0;
+        for (int k = 0; k < 5; ++k) ego[9 * i + k] = fmax(-1.0, fmin(1.0, e[k]));
+        ego[9 * i + 5] = (fl_after[i] & OR_COLLIDED) ? 1.0 : 0.0;
+        ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;
+        ego[9 * i + 7] = jerk ? jerk[3 * i] / 5.0 : 0.0;
+        ego[9 * i + 8] = jerk ? jerk[3 * i + 1] / 4.0 : 0.0;
     }
 }
 

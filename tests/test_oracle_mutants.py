@@ -60,6 +60,15 @@ MUTANTS = {
     "ovec segment from quad edge": ("const double ax = 0.5 * ((double)q[0] + q[6]), ay = 0.5 * ((double)q[1] + q[7]);", "const double ax = q[0], ay = q[1];"),
     "ovec self included": ("            if (j == i) continue;\n            const double d = hypot", "            const double d = hypot"),
     "ego speed unnormalised": ("const double e[5] = {after[4 * i + 3] / vmax,", "const double e[5] = {after[4 * i + 3],"),
+    "jerk accel cap": ("    if (a_lon > 3.0) a_lon = 3.0;\n", ""),
+    "jerk braking cap": ("    if (a_lon < -5.0) a_lon = -5.0;\n", ""),
+    "jerk steer rate unbounded": ("    if (target > st[2] + step) target = st[2] + step;\n", ""),
+    "jerk steer angle unbounded": ("    if (target > 0.5) target = 0.5;\n", ""),
+    "jerk curvature on wheelbase/2": ("double target = atan((a_lat / v2) * 0.6 * L);",
+                                      "double target = atan((a_lat / v2) * 0.3 * L);"),
+    "jerk lateral unclipped": ("    if (a_lat > 4.0) a_lat = 4.0;\n", ""),
+    "jerk halted state kept": ("            if (jerk_state) jerk_state[3 * i] = jerk_state[3 * i + 1] = jerk_state[3 * i + 2] = 0.0;\n", ""),
+    "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 
 

@@ -1121,3 +1121,115 @@ def test_ovec_matches_numpy_brute_force(seed):
                     float(q < 60), float(q >= 60)]
             assert ro[i, k] == pytest.approx(want, abs=1e-9)
         assert not ro[i, len(sel):].any()
+
+
+# ---------------------------------------------------------------------------------------
+# Jerk-actuated bicycle (App. A "Action Space and Dynamics"): closed forms of the
+# integration chain jerk -> acceleration -> speed / steering, its limits and symmetry
+# ---------------------------------------------------------------------------------------
+
+def _jerk_roll(j_lon, j_lat, n, v0=0.0, L=4.5, st0=(0.0, 0.0, 0.0), yaw0=0.0):
+    st = np.array(st0, np.float64)
+    x, y, yaw, v = 0.0, 0.0, yaw0, v0
+    traj = []
+    for _ in range(n):
+        x, y, yaw, v = oracle.jerk_bicycle(x, y, yaw, v, L, j_lon, j_lat, st)
+        traj.append((x, y, yaw, v, *st))
+    return np.array(traj)
+
+
+def test_jerk_action_set_is_the_papers_twelve():
+    assert len(oracle.JERK_ACTIONS) == 12
+    assert sorted({a for a, _ in oracle.JERK_ACTIONS}) == [-15.0, -4.0, 0.0, 4.0]
+    assert sorted({b for _, b in oracle.JERK_ACTIONS}) == [-4.0, 0.0, 4.0]
+
+
+def test_jerk_zero_from_rest_state_is_straight_cruise():
+    t = _jerk_roll(0.0, 0.0, 20, v0=12.0)
+    assert np.all(t[:, 3] == 12.0) and np.all(t[:, 1] == 0.0) and np.all(t[:, 2] == 0.0)
+    assert t[-1, 0] == pytest.approx(20 * 12.0 * 0.1, rel=1e-12)
+
+
+def test_jerk_longitudinal_ramp_and_acceleration_limit():
+    # a_k = min(0.4 k, 3): 0.4 .. 2.8 over seven steps, then held at the 3 m/s^2 limit
+    n = 12
+    t = _jerk_roll(4.0, 0.0, n)
+    a = np.minimum(0.4 * np.arange(1, n + 1), 3.0)
+    assert np.allclose(t[:, 4], a, atol=1e-12)
+    v = np.cumsum(a) * 0.1  # speed after each step (Euler on the new acceleration)
+    assert np.allclose(t[:, 3], v, atol=1e-12)
+    # positions advance with the speed at the start of each step
+    x = np.cumsum(np.concatenate([[0.0], v[:-1]])) * 0.1
+    assert np.allclose(t[:, 0], x, atol=1e-12)
+    assert t[6, 3] == pytest.approx(1.12, abs=1e-12)  # sum 0.4 .. 2.8 = 11.2 -> 1.12 m/s
+
+
+def test_jerk_hard_braking_hits_the_deceleration_limit_and_stops():
+    t = _jerk_roll(-15.0, 0.0, 30, v0=10.0)
+    assert t[0, 4] == pytest.approx(-1.5) and t[1, 4] == pytest.approx(-3.0)
+    assert t[2, 4] == pytest.approx(-4.5) and np.all(t[3:, 4] == -5.0)
+    assert t[1, 3] == pytest.approx(10.0 - 0.15 - 0.30)
+    assert np.all(np.diff(t[:, 3]) <= 0.0) and t[-1, 3] == 0.0  # no reversing
+
+
+def test_jerk_steering_rate_and_angle_bounds():
+    # at walking pace the curvature target exceeds every bound: the steering angle moves
+    # by exactly 0.05 rad (0.5 rad/s x 0.1 s) per step and then holds at 0.5 rad
+    t = _jerk_roll(0.0, 4.0, 14, v0=0.5)
+    steer = t[:, 6]
+    assert np.allclose(steer[:10], 0.05 * np.arange(1, 11), atol=1e-12)
+    assert np.allclose(steer[9:], 0.5, atol=1e-12) and np.all(steer <= 0.5)
+    assert np.all(np.abs(t[:, 5]) <= 4.0) and t[-1, 5] == 4.0  # lateral limit
+
+
+def test_jerk_lateral_acceleration_is_realised_on_the_bicycle():
+    # at speed the steering settles to the curvature kappa = a_lat / v^2; the bicycle's
+    # yaw rate v sin(beta) / l_r then reproduces a_lat up to the small-angle error
+    v, L = 20.0, 4.5
+    t = _jerk_roll(0.0, 4.0, 5, v0=v, L=L)  # a_lat ramps 0.4 .. 2.0
+    st = np.array([0.0, 2.0, t[-1, 6]], np.float64)
+    x, y, yaw, vv = oracle.jerk_bicycle(0.0, 0.0, 0.0, v, L, 0.0, 0.0, st)
+    assert st[1] == pytest.approx(2.0)
+    kappa = 2.0 / v ** 2
+    assert st[2] == pytest.approx(math.atan(kappa * 0.6 * L), rel=1e-12)
+    a_lat = v * (yaw / 0.1)
+    assert a_lat == pytest.approx(2.0, rel=2e-4)
+
+
+def test_jerk_mirror_symmetry():
+    a = _jerk_roll(4.0, 4.0, 25, v0=8.0)
+    b = _jerk_roll(4.0, -4.0, 25, v0=8.0)
+    assert np.allclose(a[:, 0], b[:, 0], atol=1e-12) and np.allclose(a[:, 3], b[:, 3], atol=1e-12)
+    assert np.allclose(a[:, 1], -b[:, 1], atol=1e-12) and np.allclose(a[:, 2], -b[:, 2], atol=1e-12)
+    assert np.allclose(a[:, 6], -b[:, 6], atol=1e-12) and np.allclose(a[:, 5], -b[:, 5], atol=1e-12)
+    assert a[-1, 1] > 1.0  # it did turn left
+
+
+def test_jerk_step_world_halted_agent_resets_actuators():
+    # two agents in one world; the second starts halted: it neither moves nor keeps
+    # its actuator state, the first follows jerk_bicycle exactly
+    road = np.array([rect_quad(-100.0, 100.0, -10.0, 10.0)], np.float32)
+    boxes = np.array([[0.0, -5.0, 0.0, 4.5, 1.9, 1.6], [0.0, 5.0, 0.0, 4.5, 1.9, 1.6]], np.float64)
+    state = np.array([[0.0, -5.0, 0.0, 5.0], [0.0, 5.0, 0.0, 0.0]], np.float64)
+    flags = np.array([0, 4 | 1], np.uint8)
+    jerk = np.array([[0.5, 0.2, 0.01], [1.0, 1.0, 0.3]], np.float64)
+    oracle.step_world(boxes, state, flags, np.array([[4.0, -4.0], [4.0, 4.0]], np.float32), road,
+                      jerk=jerk)
+    st = np.array([0.5, 0.2, 0.01])
+    want = oracle.jerk_bicycle(0.0, -5.0, 0.0, 5.0, 4.5, 4.0, -4.0, st)
+    assert np.allclose(state[0], want, atol=1e-12) and np.allclose(jerk[0], st, atol=1e-15)
+    assert np.all(jerk[1] == 0.0) and np.all(state[1] == [0.0, 5.0, 0.0, 0.0])
+    assert flags[0] == 0
+
+
+def test_jerk_ego_extras():
+    before = np.array([[0.0, -1.75, 0.0, 10.0]], np.float64)
+    after = before.copy()
+    after[0] = oracle.bicycle(0.0, -1.75, 0.0, 10.0, 4.5, -2.5, 0.1)
+    _, ego = oracle.rewards_world(before, [0], after, [0], [[-2.5, 0.1]], [[4.5, 1.9]],
+                                  np.zeros((1, 2)), [W_INF], STRAIGHT, jerk=[[-2.5, 2.0, 0.1]])
+    assert ego[0, 6] == pytest.approx(0.2) and ego[0, 7] == pytest.approx(-0.5)
+    assert ego[0, 8] == pytest.approx(0.5)
+    _, ego = oracle.rewards_world(before, [0], after, [0], [[-2.5, 0.1]], [[4.5, 1.9]],
+                                  np.zeros((1, 2)), [W_INF], STRAIGHT)
+    assert np.all(ego[0, 6:] == 0.0)

@@ -265,5 +265,16 @@ def actions(seed: int, step: int, n_agents: int, gid0: int = 0,
     return out
 
 
+# App. A's discrete action set: (longitudinal, lateral) jerk in m/s^3.
+JERK_TABLE = np.array([(jl, jt) for jl in (-15.0, -4.0, 0.0, 4.0) for jt in (-4.0, 0.0, 4.0)],
+                      np.float32)
+
+
+def jerk_actions(seed: int, step: int, n_agents: int) -> np.ndarray:
+    """Jerk actions [n_agents, 2] for one step: a uniform pick from the twelve per agent."""
+    rng = np.random.default_rng([seed, step, 12])
+    return JERK_TABLE[rng.integers(0, 12, n_agents)]
+
+
 def deg(x: float) -> float:
     return x * math.pi / 180.0
