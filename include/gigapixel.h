@@ -71,6 +71,15 @@ enum { GP_CLASS_BACKGROUND = 0, GP_CLASS_ROAD = 1, GP_CLASS_LANE_LINE = 2, GP_CL
 #define GP_OBS_AGENT_RADIUS 100.0f
 #define GP_OBS_ROADS 32          /* road-segment slots per agent */
 #define GP_OBS_ROAD_RADIUS 30.0f
+/* Ego-state width (gp_get_rewards) */
+#define GP_EGO_DIM 9
+
+/* Vehicle dynamics (gp_config.dynamics). */
+enum {
+    GP_DYN_DIRECT = 0,  /* actions are (acceleration m/s^2, steering angle rad) */
+    GP_DYN_JERK = 1     /* actions are (longitudinal, lateral jerk m/s^3); App. A's discrete set
+                           is {-15, -4, 0, 4} x {-4, 0, 4} */
+};
 
 /*
  * Worlds, as host arrays in CSR form over worlds; copied to the device at create time.
@@ -140,6 +149,7 @@ typedef struct gp_config {
     int32_t rewards;
     float lane_width;             /* lane width of the two-lane roads (default 3.5 m) */
     float v_limit;                /* speed limit of the overspeed term (default 30 m/s) */
+    int32_t dynamics;             /* GP_DYN_DIRECT (default) or GP_DYN_JERK */
 } gp_config;
 
 /* Fill `cfg` with the defaults above. */
@@ -166,6 +176,12 @@ gp_status gp_destroy(gp_handle *h);
  * agents get v = 0 and ignore later actions but stay in the scene.
  *   actions_dev  float [n_agents][2] device: acceleration (m/s^2), steering angle (rad);
  *                agents ordered by world, then by agent index within the world.
+ *                With GP_DYN_JERK: longitudinal and lateral jerk (m/s^3) of the
+ *                jerk-actuated bicycle (App. A "Action Space and Dynamics"): the jerks move
+ *                the actuator state a_lon in [-5, 3], a_lat in [-4, 4] m/s^2; the steering
+ *                angle tracks atan(0.6 L a_lat / max(v^2, 1)) at most 0.5 rad/s, |steer| <=
+ *                0.5 rad; the bicycle then runs on (a_lon, steer).  Halted agents' actuator
+ *                state is zeroed.
  * Returns GP_EDEVICE if a previous gp_get_status saw an error bit (until gp_clear_status).
  */
 gp_status gp_step(gp_handle *h, const float *actions_dev, void *stream);
@@ -214,11 +230,21 @@ gp_status gp_render_world(gp_handle *h, int32_t world, void *out_dev, void *dept
 /*
  * Agent state: state[n_agents][4] = x, y, yaw, v (float) and flags[n_agents] (uint8).
  * on_host = 1: host pointers (the call synchronises the stream); 0: device pointers.
- * gp_set_state also forks/resumes a simulation (e.g. teacher rollouts from a snapshot).
+ * gp_set_state also forks/resumes a simulation (e.g. teacher rollouts from a snapshot);
+ * it zeroes the jerk dynamics' actuator state (restore it with gp_set_dynamics after).
  */
 gp_status gp_get_state(gp_handle *h, float *state, uint8_t *flags, int on_host, void *stream);
 gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, int on_host,
                        void *stream);
+
+/*
+ * Actuator state of the jerk dynamics, dyn[n_agents][3] float = a_lon, a_lat (m/s^2),
+ * steering angle (rad); GP_ESTATE unless gp_config.dynamics = GP_DYN_JERK.  on_host as for
+ * gp_get_state.  gp_set_dynamics rejects non-finite host values (GP_EINVAL); device values
+ * are taken as given.
+ */
+gp_status gp_get_dynamics(gp_handle *h, float *dyn, int on_host, void *stream);
+gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *stream);
 
 /* Sizes of a handle. */
 typedef struct gp_info {
@@ -240,8 +266,11 @@ gp_status gp_get_info(gp_handle *h, gp_info *info);
  *   (|v| > v_limit); traffic-light (w6) and goal terms are 0 (no signals or goals).
  *   Accelerations are the bicycle's increments of the step (speed before any halt):
  *   a_lon = (v' - v) / dt, a_lat = v dyaw / dt; an agent halted before the step earns 0.
- * ego [n_agents][6] float: speed / v_max, a_lon / 10, a_lat / 10, L / 10, W / 5 (clipped to
- *   [-1, 1]) and the collision flag (0 or 1).
+ * ego [n_agents][GP_EGO_DIM] float: speed / v_max, a_lon / 10, a_lat / 10, L / 10, W / 5
+ *   (clipped to [-1, 1]) and the collision flag (0 or 1); then, with GP_DYN_JERK, the
+ *   post-step steering angle / 0.5 and the actuator accelerations a_lon / 5, a_lat / 4
+ *   (0 under GP_DYN_DIRECT).  With GP_DYN_JERK the reward's accelerations are those of the
+ *   bicycle driven by the resolved (a_lon, steer).
  * Either pointer may be NULL.  on_host != 0: host memory, synchronous; else device
  * memory, asynchronous on `stream`.
  */

@@ -21,6 +21,10 @@ OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8 = 0, 1, 2
 FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
+DYN_DIRECT, DYN_JERK = 0, 1
+EGO_DIM = 9
+# App. A's discrete action set for DYN_JERK: (longitudinal, lateral) jerk in m/s^3.
+JERK_ACTIONS = tuple((jl, jt) for jl in (-15.0, -4.0, 0.0, 4.0) for jt in (-4.0, 0.0, 4.0))
 
 TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,)),
                       ("prim", "<u4"), ("sub", "<u4")])
@@ -29,6 +33,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
+            "gp_get_dynamics", "gp_set_dynamics",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -59,7 +64,7 @@ class Config(ctypes.Structure):
                 ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("colour", (ctypes.c_float * 3) * 4),
                 ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
-                ("v_limit", ctypes.c_float)]
+                ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -105,6 +110,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_trace": [vp, vp, vp, vp],
         "gp_observe_vec": [vp, vp, vp, vp],
         "gp_set_reward_weights": [vp, vp, i32, vp],
+        "gp_get_dynamics": [vp, vp, i32, vp],
+        "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
         "gp_debug_dump_tris_noalloc": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -291,13 +298,24 @@ class Simulator:
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _stream(stream)))
         return a, r
 
+    def get_dynamics(self) -> np.ndarray:
+        """Jerk dynamics' actuator state float32 [n_agents, 3] = a_lon, a_lat, steer (host)."""
+        d = np.zeros((self.n_agents, 3), np.float32)
+        check(lib().gp_get_dynamics(self._h, _ptr(d), 1, _stream(None)))
+        return d
+
+    def set_dynamics(self, dyn) -> None:
+        d = np.ascontiguousarray(dyn, np.float32)
+        assert d.shape == (self.n_agents, 3)
+        check(lib().gp_set_dynamics(self._h, _ptr(d), 1, _stream(None)))
+
     def rewards(self, stream=None):
-        """(reward [n_agents], ego state [n_agents, 6]) of the last step, float32 on the
-        device (the handle must have been created with rewards = 1)."""
+        """(reward [n_agents], ego state [n_agents, EGO_DIM]) of the last step, float32 on
+        the device (the handle must have been created with rewards = 1)."""
         import torch
         dev = torch.device("cuda", self.device)
         r = torch.empty((self.n_agents,), dtype=torch.float32, device=dev)
-        e = torch.empty((self.n_agents, 6), dtype=torch.float32, device=dev)
+        e = torch.empty((self.n_agents, EGO_DIM), dtype=torch.float32, device=dev)
         check(lib().gp_get_rewards(self._h, _ptr(r), _ptr(e), 0, _stream(stream)))
         return r, e
 

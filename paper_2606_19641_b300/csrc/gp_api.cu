@@ -89,7 +89,8 @@ struct gp_handle {
     DevBuf<int2> items;
     DevBuf<DumpTri> dump;
     DevBuf<float> state_stage;
-    DevBuf<float> reward, ego, weights;  // per-step rewards: [n_agents], [n_agents][6], [n_agents][10]
+    DevBuf<float> reward, ego, weights;  // per-step rewards: [n_agents], [n_agents][GP_EGO_DIM], [n_agents][10]
+    DevBuf<float> jerk;                  // jerk dynamics' actuator state [n_agents][3]
     DevBuf<float2> acc;                  // previous-step accelerations
     DevBuf<uint8_t> flag_stage;
     Shape shape;
@@ -124,6 +125,8 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
     if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16 && c->output != GP_OUT_RGB_U8)
         return fail(GP_EINVAL, "output");
     if (c->rewards != 0 && c->rewards != 1) return fail(GP_EINVAL, "rewards must be 0 or 1");
+    if (c->dynamics != GP_DYN_DIRECT && c->dynamics != GP_DYN_JERK)
+        return fail(GP_EINVAL, "dynamics must be GP_DYN_DIRECT or GP_DYN_JERK");
     if (c->rewards && !(c->lane_width > 0.f && c->v_limit >= 0.f))
         return fail(GP_EINVAL, "lane_width must be positive, v_limit >= 0");
     if (c->output == GP_OUT_RGB_U8) {
@@ -307,6 +310,8 @@ StepParams step_params(gp_handle *h, const float *actions) {
     p.acc = h->acc.p;
     p.reward = h->reward.p;
     p.ego = h->ego.p;
+    p.dynamics = h->cfg.dynamics;
+    p.jerk = h->jerk.p;
     return p;
 }
 
@@ -514,6 +519,7 @@ void release_all(gp_handle *h) {
     h->ego.release();
     h->weights.release();
     h->acc.release();
+    h->jerk.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -560,6 +566,7 @@ gp_status gp_default_config(gp_config *c) {
     c->rewards = 0;
     c->lane_width = 3.5f;
     c->v_limit = 30.f;
+    c->dynamics = GP_DYN_DIRECT;
     const float col[4][3] = {{0.55f, 0.75f, 0.95f}, {0.33f, 0.33f, 0.35f}, {0.92f, 0.92f, 0.85f},
                              {0.15f, 0.35f, 0.85f}};
     std::memcpy(c->colour, col, sizeof col);
@@ -798,7 +805,7 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(flag_stage, fstage);
     {
         const size_t na = (size_t)std::max(1, h->n_agents);
-        std::vector<float> r0(na, 0.f), e0(6 * na, 0.f), w0(10 * na);
+        std::vector<float> r0(na, 0.f), e0(GP_EGO_DIM * na, 0.f), w0(10 * na), j0(3 * na, 0.f);
         const float inference[10] = {3.f, 3.f, 0.05f, 0.025f, 3.8e-3f, 2.5e-3f, 1.f, 2.5e-5f, 5e-3f, 0.f};
         for (size_t i = 0; i < na; ++i)
             for (int k = 0; k < 10; ++k) w0[10 * i + k] = inference[k];
@@ -807,6 +814,7 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         UP(ego, e0);
         UP(weights, w0);
         UP(acc, a0);
+        UP(jerk, j0);
     }
 #undef UP
 
@@ -977,6 +985,34 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
                         h->speed.p, h->flags.p, h->agent_box.p, n, 0, s));
     }
     if (n) CK(cudaMemsetAsync(h->acc.p, 0, sizeof(float2) * n, s));  // accelerations restart
+    if (n) CK(cudaMemsetAsync(h->jerk.p, 0, sizeof(float) * 3 * n, s));
+    return GP_OK;
+}
+
+gp_status gp_get_dynamics(gp_handle *h, float *dyn, int on_host, void *stream) {
+    if (!h || !dyn) return fail(GP_EINVAL, "null argument");
+    if (h->cfg.dynamics != GP_DYN_JERK) return fail(GP_ESTATE, "dynamics is not GP_DYN_JERK");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    if (n)
+        CK(cudaMemcpyAsync(dyn, h->jerk.p, sizeof(float) * 3 * n,
+                           on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
+gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *stream) {
+    if (!h || !dyn) return fail(GP_EINVAL, "null argument");
+    if (h->cfg.dynamics != GP_DYN_JERK) return fail(GP_ESTATE, "dynamics is not GP_DYN_JERK");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    if (on_host && !finite_all(dyn, 3 * n)) return fail(GP_EINVAL, "non-finite dynamics state");
+    if (n)
+        CK(cudaMemcpyAsync(h->jerk.p, dyn, sizeof(float) * 3 * n,
+                           on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
     return GP_OK;
 }
 
@@ -1011,7 +1047,7 @@ gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, v
     const size_t n = (size_t)h->n_agents;
     const cudaMemcpyKind k = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (reward && n) CK(cudaMemcpyAsync(reward, h->reward.p, sizeof(float) * n, k, s));
-    if (ego && n) CK(cudaMemcpyAsync(ego, h->ego.p, sizeof(float) * 6 * n, k, s));
+    if (ego && n) CK(cudaMemcpyAsync(ego, h->ego.p, sizeof(float) * GP_EGO_DIM * n, k, s));
     if (on_host) CK(cudaStreamSynchronize(s));
     return GP_OK;
 }

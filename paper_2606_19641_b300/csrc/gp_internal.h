@@ -43,7 +43,7 @@ struct StepParams {
     const float4 *box_dim;  // L, W, H, 0
     float *speed;           // [n_agents]
     uint8_t *flags;         // [n_agents]
-    const float2 *actions;  // [n_agents] accel, steer
+    const float2 *actions;  // [n_agents] accel, steer (jerk dynamics: j_lon, j_lat)
     const float4 *road_geo; // 2 per road quad (original order)
     const int *cell_off;    // CSR of road quads per grid cell
     const int *cell_quads;
@@ -55,7 +55,10 @@ struct StepParams {
     const float *weights;   // [n_agents][10]
     float2 *acc;            // [n_agents] previous a_lon, a_lat (updated)
     float *reward;          // [n_agents]
-    float *ego;             // [n_agents][6]
+    float *ego;             // [n_agents][GP_EGO_DIM]
+    // jerk-actuated dynamics (dynamics == GP_DYN_JERK): actuator state per agent
+    int dynamics;
+    float *jerk;            // [n_agents][3] a_lon, a_lat, steer (updated)
 };
 
 // Vectorized observations (gp_observe_vec).

@@ -3,7 +3,9 @@
 // Per world (App. A "Action Space and Dynamics", "Other Details"):
 //   1. every non-halted agent advances by a kinematic bicycle with wheelbase 0.6 L,
 //      centre reference point (l_r = l_f = 0.3 L), explicit Euler with the speed at the
-//      start of the step, then v += a dt clamped to [0, v_max];
+//      start of the step, then v += a dt clamped to [0, v_max]; under the jerk dynamics the
+//      action's jerks first move the actuator state (a_lon, a_lat, steer), which then gives
+//      the bicycle's acceleration and steering (jerk_actuate);
 //   2. footprint collisions: all pairs (agent, box) by the separating-axis test on the
 //      four box axes, strict overlap (touching is no collision);
 //   3. off-road: an agent whose footprint has a corner outside every road quad (boundary
@@ -94,6 +96,25 @@ __device__ bool lane_frame(const StepParams &p, const WorldInfo &wi, float px, f
     return true;
 }
 
+// Jerk-actuated control (App. A "Action Space and Dynamics"): the longitudinal and lateral
+// jerks move the accelerations, clipped to a_lon in [-5, 3] and |a_lat| <= 4 m/s^2; the
+// steering angle follows the curvature a_lat / max(v^2, 1) through tan(steer) = kappa 0.6 L,
+// limited to 0.5 rad/s of change and to |steer| <= 0.5 rad.  Returns the bicycle's
+// (acceleration, steering) and updates the state st = (a_lon, a_lat, steer).
+__device__ __forceinline__ float2 jerk_actuate(float2 jerk, float v, float L, float dt, float *st) {
+    const float a_lon = fminf(fmaxf(st[0] + jerk.x * dt, -5.f), 3.f);
+    const float a_lat = fminf(fmaxf(st[1] + jerk.y * dt, -4.f), 4.f);
+    const float v2 = fmaxf(v * v, 1.f);
+    float steer = atanf((a_lat / v2) * 0.6f * L);
+    const float step = 0.5f * dt;
+    steer = fmaxf(fminf(steer, st[2] + step), st[2] - step);
+    steer = fmaxf(fminf(steer, 0.5f), -0.5f);
+    st[0] = a_lon;
+    st[1] = a_lat;
+    st[2] = steer;
+    return make_float2(a_lon, steer);
+}
+
 // Reward terms of one agent's step (App. A reward table; inference weights by default) and
 // its ego state.  Accelerations are the bicycle's increments of the step (speed before any
 // halt); an agent halted before the step earns 0.  The traffic-light and goal terms are 0.
@@ -129,13 +150,18 @@ __device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, fl
     }
     p.acc[a] = make_float2(a_lon, a_lat);
     p.reward[a] = r;
-    float *e = p.ego + 6 * a;
+    float *e = p.ego + GP_EGO_DIM * a;
     e[0] = fmaxf(-1.f, fminf(1.f, v_after / p.vmax));
     e[1] = fmaxf(-1.f, fminf(1.f, a_lon / 10.f));
     e[2] = fmaxf(-1.f, fminf(1.f, a_lat / 10.f));
     e[3] = fmaxf(-1.f, fminf(1.f, L / 10.f));
     e[4] = fmaxf(-1.f, fminf(1.f, W / 5.f));
     e[5] = (fl1 & GP_FLAG_COLLIDED) ? 1.f : 0.f;
+    // jerk dynamics: steering angle and actuator accelerations, each over its limit
+    const float *js = p.dynamics ? p.jerk + 3 * a : nullptr;
+    e[6] = js ? js[2] / 0.5f : 0.f;
+    e[7] = js ? js[0] / 5.f : 0.f;
+    e[8] = js ? js[1] / 4.f : 0.f;
 }
 
 __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
@@ -161,6 +187,13 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
             v0 = v;
             if (!(fl & GP_FLAG_HALTED)) {
                 act = p.actions[a];
+                if (p.dynamics) {
+                    float st[3] = {p.jerk[3 * a], p.jerk[3 * a + 1], p.jerk[3 * a + 2]};
+                    act = jerk_actuate(act, v, dim.x, p.dt, st);
+                    p.jerk[3 * a] = st[0];
+                    p.jerk[3 * a + 1] = st[1];
+                    p.jerk[3 * a + 2] = st[2];
+                }
                 const float lr = 0.3f * dim.x;
                 const float beta = atanf(0.5f * tanf(act.y));
                 float sb, cb;
@@ -174,6 +207,7 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
                 v = fminf(fmaxf(v + act.x * p.dt, 0.f), p.vmax);
             } else {
                 v = 0.f;
+                if (p.dynamics) p.jerk[3 * a] = p.jerk[3 * a + 1] = p.jerk[3 * a + 2] = 0.f;
             }
             if (!isfinite(pose.x) || !isfinite(pose.y) || !isfinite(pose.z) || !isfinite(v))
                 atomicOr(p.status, GP_DEV_NONFINITE_STATE);

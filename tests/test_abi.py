@@ -56,6 +56,7 @@ def test_default_config_values(gp):
     assert c.hfov == pytest.approx(np.pi / 2) and c.dt == pytest.approx(0.1)
     assert c.cam_height == pytest.approx(1.5) and c.near_plane == pytest.approx(0.1)
     assert list(c.norm_mean) == [0.5] * 4 and list(c.norm_std) == [0.5] * 4
+    assert c.dynamics == gp.DYN_DIRECT and c.rewards == 0
 
 
 def _desc(gp, worlds):
@@ -97,6 +98,7 @@ def _good():
     (lambda w, c: setattr(c, "n_cams", 9), -4),
     (lambda w, c: setattr(c, "key_precision", 7), -1),
     (lambda w, c: setattr(c, "threads", 100), -1),
+    (lambda w, c: setattr(c, "dynamics", 2), -1),
     (lambda w, c: w.update(box_off=[0, 130], agents=[1], boxes=np.tile([1, 1, 0, 4, 2, 1.5, 0], (130, 1))), -4),
 ])
 def test_create_rejects_invalid_input_on_host(gp, mutate, status):
@@ -117,6 +119,8 @@ def test_null_handle_calls_fail_cleanly(gp):
     assert L.gp_render(None, None, None, None) == -1
     assert L.gp_destroy(None) == 0
     assert L.gp_get_info(None, None) == -1
+    assert L.gp_get_dynamics(None, None, 1, None) == -1
+    assert L.gp_set_dynamics(None, None, 1, None) == -1
 
 
 def test_fp16_primitive_limit(gp):

@@ -806,3 +806,100 @@ def test_observe_vec_matches_oracle(name, n_worlds):
           % (name, checked, skipped, compared_rows[0]))
     assert checked > 0.5 * (checked + skipped)
     assert compared_rows[0] > 1000
+
+
+# ---------------------------------------------------------------------------------------
+# Jerk-actuated dynamics (App. A "Action Space and Dynamics")
+# ---------------------------------------------------------------------------------------
+
+def _jerk_actions(n, step, seed):
+    return wg.jerk_actions(seed, step, n)
+
+
+@pytest.mark.parametrize("name,n_worlds,steps", [("tiny", 1, 15), ("uniform", 4, 25),
+                                                 ("ragged", 6, 20)])
+def test_jerk_dynamics_match_oracle(name, n_worlds, steps):
+    """One GPU step against one oracle step from the same pose, flags and actuator state;
+    rewards and the ego extras against the oracle on the resolved controls."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    sim, cfg = sim_for(worlds, wl, dynamics=gp.DYN_JERK, rewards=1)
+    na = worlds.n_agents
+    off = worlds.agent_offsets()
+    dims = np.zeros((na, 2), np.float64)
+    for w in range(worlds.n_worlds):
+        b0 = int(worlds.box_off[w])
+        dims[off[w]:off[w + 1]] = worlds.boxes[b0:b0 + (off[w + 1] - off[w]), 3:5]
+    acc = np.zeros((na, 2), np.float64)
+    saw_clip = saw_rate = False
+    for k in range(steps):
+        st0, fl0 = sim.get_state()
+        dy0 = sim.get_dynamics()
+        osim = oracle.Sim(worlds, jerk_dynamics=True)
+        osim.set_state(st0.astype(np.float64), fl0, dy0.astype(np.float64))
+        act = _jerk_actions(na, k, wl.seed)
+        sim.step(torch.from_numpy(act).cuda())
+        osim.step(act)
+        st1, fl1 = sim.get_state()
+        dy1 = sim.get_dynamics()
+        assert np.allclose(dy1, osim.jerk, atol=2e-5, rtol=0), "actuator state, step %d" % k
+        assert np.allclose(st1[:, 0:2], osim.state[:, 0:2], atol=2e-4, rtol=0)
+        dyaw = np.angle(np.exp(1j * (st1[:, 2].astype(np.float64) - osim.state[:, 2])))
+        assert np.all(np.abs(dyaw) < 2e-5)
+        assert np.allclose(st1[:, 3], osim.state[:, 3], atol=2e-5)
+        assert np.array_equal(fl1, osim.flags), "flags differ at step %d" % k
+        saw_clip |= bool((np.abs(dy1[:, 0] - 3.0) < 1e-6).any() or (np.abs(dy1[:, 0] + 5.0) < 1e-6).any())
+        saw_rate |= bool((np.abs(np.abs(dy1[:, 2] - dy0[:, 2]) - 0.05) < 1e-6).any())
+        # rewards / ego on the controls the actuator resolved (a_lon, steer)
+        r, e = sim.rewards()
+        torch.cuda.synchronize()
+        r, e = r.cpu().numpy(), e.cpu().numpy()
+        ctrl = np.stack([dy1[:, 0], dy1[:, 2]], 1).astype(np.float32)
+        for w in range(worlds.n_worlds):
+            a0, a1 = int(off[w]), int(off[w + 1])
+            road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
+            acc_w = np.ascontiguousarray(acc[a0:a1])
+            rr, ee = oracle.rewards_world(st0[a0:a1], fl0[a0:a1], st1[a0:a1], fl1[a0:a1],
+                                          ctrl[a0:a1], dims[a0:a1], acc_w,
+                                          np.tile(oracle.REWARD_WEIGHTS, (a1 - a0, 1)), road,
+                                          jerk=dy1[a0:a1])
+            acc[a0:a1] = acc_w
+            assert np.allclose(e[a0:a1], ee, atol=3e-5)
+            d = np.abs(r[a0:a1] - rr)
+            assert np.all((d <= 1e-4 + 1e-4 * np.abs(rr)) | (d <= oracle.REWARD_WEIGHTS[2] + 1e-4))
+    assert saw_clip and saw_rate  # the limits were exercised
+    assert sim.status() == 0
+
+
+def test_jerk_state_fork_and_reset():
+    """get/set of pose + actuator state replays a rollout exactly; set_state zeroes the
+    actuators; the calls are refused under direct control."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    sim, _ = sim_for(worlds, wl, dynamics=gp.DYN_JERK)
+    na = worlds.n_agents
+    for k in range(5):
+        sim.step(torch.from_numpy(_jerk_actions(na, k, 7)).cuda())
+    snap = sim.get_state(), sim.get_dynamics()
+    assert np.abs(snap[1]).max() > 0.1
+    outs = []
+    for _ in range(2):
+        sim.set_state(*snap[0])
+        assert np.all(sim.get_dynamics() == 0.0)
+        sim.set_dynamics(snap[1])
+        for k in range(5, 10):
+            sim.step(torch.from_numpy(_jerk_actions(na, k, 7)).cuda())
+        outs.append((sim.get_state()[0], sim.get_dynamics()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    bad = snap[1].copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(gp.GigapixelError):
+        sim.set_dynamics(bad)
+    direct, _ = sim_for(worlds, wl)
+    with pytest.raises(gp.GigapixelError) as e:
+        direct.get_dynamics()
+    assert e.value.status == gp.binding.GP_ESTATE
