@@ -79,13 +79,14 @@ def _lib():
                                       ctypes.c_double]
         lib.or_camera_tris.argtypes = [P(OrCam), ctypes.c_int32, c_f64p, ctypes.c_int32,
                                        ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
+                                       ctypes.c_int32, c_f64p,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
         lib.or_camera_tris.restype = ctypes.c_int64
         for fn in (lib.or_raster, lib.or_raster_bruteforce):
             fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
-                           ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, c_u64p, c_u8p,
-                           c_f32p, c_u16p]
+                           ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                           c_u64p, c_u8p, c_f32p, c_u16p]
         lib.or_f32_to_f16.argtypes = [ctypes.c_float]
         lib.or_f32_to_f16.restype = ctypes.c_uint16
         lib.or_f32_to_bf16.argtypes = [ctypes.c_float]
@@ -93,7 +94,7 @@ def _lib():
         lib.or_onehot_bf16.argtypes = [c_u8p, ctypes.c_int64, c_f32p, c_f32p, c_u16p]
         lib.or_trace_view.argtypes = [P(OrCam), ctypes.c_int32, c_f64p, ctypes.c_int32,
                                       ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
-                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int32, c_f64p, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, c_u8p, c_f32p, P(ctypes.c_uint32)]
         lib.or_observe_world.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p,
                                          ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
@@ -107,8 +108,8 @@ def _lib():
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, c_f64p, c_f64p, c_f64p]
         lib.or_shade_rgb.argtypes = [c_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
-                                     ctypes.c_uint32, c_f64p, c_f64p, c_f64p, ctypes.c_double,
-                                     c_u8p]
+                                     ctypes.c_uint32, ctypes.c_uint32, c_f64p, c_f64p, c_u8p,
+                                     c_f64p, c_f64p, c_f64p, ctypes.c_double, c_u8p]
         _lib_handle = lib
     return _lib_handle
 
@@ -204,20 +205,27 @@ class CamConfig:
                      self.line_z, self.guard)
 
 
+def _sph(sph) -> np.ndarray:
+    return _c(np.zeros((0, 4)) if sph is None else sph, np.float64).reshape(-1, 4)
+
+
 def camera_tris(cam: CamConfig, boxes6: np.ndarray, ego: int, road: np.ndarray,
                 line: np.ndarray, ax: float, ay: float, ayaw: float, cam_yaw: float = 0.0,
-                cap: Optional[int] = None) -> np.ndarray:
-    """FP64 scene triangles of one camera after clipping, snapping and back-face culling."""
+                cap: Optional[int] = None, sph=None) -> np.ndarray:
+    """FP64 scene triangles of one camera after clipping, snapping and back-face culling;
+    sph [n, 4] = signal spheres (x, y, z, r)."""
     b = _c(boxes6, np.float64).reshape(-1, 6)
     rd = _c(road, np.float32).reshape(-1, 8)
     ln = _c(line, np.float32).reshape(-1, 8)
+    sp = _sph(sph)
     lib = _lib()
     c = cam.c()
     if cap is None:
-        cap = 6 * (12 * b.shape[0] + 2 * rd.shape[0] + 2 * ln.shape[0]) + 16
+        cap = 6 * (12 * b.shape[0] + 2 * rd.shape[0] + 2 * ln.shape[0] + 64 * sp.shape[0]) + 16
     out = np.zeros(cap, TRI_DTYPE)
     n = lib.or_camera_tris(ctypes.byref(c), b.shape[0], _p(b, c_f64p), int(ego), rd.shape[0],
-                           _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), float(ax), float(ay),
+                           _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), sp.shape[0],
+                           _p(sp, c_f64p), float(ax), float(ay),
                            float(ayaw), float(cam_yaw), out.ctypes.data, cap)
     assert n <= cap
     return out[:n].copy()
@@ -239,17 +247,19 @@ class Traced:
 
 
 def trace_view(cam: CamConfig, boxes6: np.ndarray, ego: int, road: np.ndarray, line: np.ndarray,
-               ax: float, ay: float, ayaw: float, cam_yaw: float) -> Traced:
+               ax: float, ay: float, ayaw: float, cam_yaw: float, sph=None) -> Traced:
     """Ray-traced view (see or_trace_view)."""
     b = _c(boxes6, np.float64).reshape(-1, 6)
     rd = _c(road, np.float32).reshape(-1, 8)
     ln = _c(line, np.float32).reshape(-1, 8)
+    sp = _sph(sph)
     cls = np.zeros((cam.height, cam.width), np.uint8)
     dep = np.zeros((cam.height, cam.width), np.float32)
     pr = np.zeros((cam.height, cam.width), np.uint32)
     c = cam.c()
     _lib().or_trace_view(ctypes.byref(c), b.shape[0], _p(b, c_f64p), int(ego), rd.shape[0],
-                         _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), float(ax), float(ay),
+                         _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), sp.shape[0],
+                         _p(sp, c_f64p), float(ax), float(ay),
                          float(ayaw), float(cam_yaw), _p(cls, c_u8p), _p(dep, c_f32p),
                          pr.ctypes.data_as(P(ctypes.c_uint32)))
     return Traced(cls, dep, pr)
@@ -263,8 +273,9 @@ class Image:
 
 
 def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: int,
-           road_end: int, bruteforce: bool = False) -> Image:
-    """The raster rule on snapped triangles; box_end = 12 n_boxes, road_end = box_end + 2 n_road."""
+           road_end: int, bruteforce: bool = False, line_end: Optional[int] = None) -> Image:
+    """The raster rule on snapped triangles; box_end = 12 n_boxes, road_end = box_end + 2 n_road,
+    line_end = road_end + 2 n_line (ids from it on are signal spheres; None: no spheres)."""
     t = _c(tris, TRI_DTYPE)
     if key_f16 and len(t):
         assert int(t["prim"].max()) <= 0xFFFE, "FP16 keys hold 16-bit primitive ids"
@@ -273,8 +284,9 @@ def raster(tris: np.ndarray, width: int, height: int, key_f16: bool, box_end: in
     d32 = np.zeros((height, width), np.float32)
     d16 = np.zeros((height, width), np.uint16)
     fn = _lib().or_raster_bruteforce if bruteforce else _lib().or_raster
-    fn(t.ctypes.data, len(t), width, height, int(key_f16), box_end, road_end, _p(key, c_u64p),
-       _p(cls, c_u8p), _p(d32, c_f32p), _p(d16, c_u16p))
+    le = 0xFFFFFFFF if line_end is None else int(line_end)
+    fn(t.ctypes.data, len(t), width, height, int(key_f16), box_end, road_end, le,
+       _p(key, c_u64p), _p(cls, c_u8p), _p(d32, c_f32p), _p(d16, c_u16p))
     return Image(key, cls, d16 if key_f16 else d32)
 
 
@@ -344,6 +356,8 @@ def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weight
 RGB_COLOURS = ((0.55, 0.75, 0.95), (0.33, 0.33, 0.35), (0.92, 0.92, 0.85), (0.15, 0.35, 0.85))
 RGB_LIGHT = (0.3, 0.4, 0.866)
 RGB_AMBIENT = 0.35
+# Signal-sphere colours by state 0 red, 1 amber, 2 green, 3 off (readings).
+SIGNAL_COLOURS = ((0.9, 0.1, 0.1), (0.95, 0.7, 0.1), (0.1, 0.8, 0.3), (0.25, 0.25, 0.25))
 
 
 def unit(v) -> np.ndarray:
@@ -352,16 +366,22 @@ def unit(v) -> np.ndarray:
 
 
 def shade_rgb(key: np.ndarray, key_f16: bool, box_end: int, road_end: int, boxes6: np.ndarray,
-              colour=RGB_COLOURS, light=RGB_LIGHT, ambient: float = RGB_AMBIENT) -> np.ndarray:
+              colour=RGB_COLOURS, light=RGB_LIGHT, ambient: float = RGB_AMBIENT,
+              line_end: Optional[int] = None, sph=None, sph_state=None,
+              signal_colour=SIGNAL_COLOURS) -> np.ndarray:
     """uint8 [3, H, W] RGB observation from the raster's keys (see or_shade_rgb)."""
     k = _c(key, np.uint64)
     b = _c(boxes6, np.float64).reshape(-1, 6)
     col = _c(colour, np.float64).reshape(4, 3)
+    sc = _c(signal_colour, np.float64).reshape(4, 3)
+    sp = _sph(sph)
+    st = _c(np.zeros(sp.shape[0]) if sph_state is None else sph_state, np.uint8)
+    le = 0xFFFFFFFF if line_end is None else int(line_end)
     l = _c(unit(light), np.float64)
     out = np.zeros((3,) + k.shape, np.uint8)
-    _lib().or_shade_rgb(_p(k, c_u64p), k.size, int(key_f16), box_end, road_end,
-                        _p(b, c_f64p), _p(col, c_f64p), _p(l, c_f64p), float(ambient),
-                        _p(out, c_u8p))
+    _lib().or_shade_rgb(_p(k, c_u64p), k.size, int(key_f16), box_end, road_end, le,
+                        _p(b, c_f64p), _p(sp, c_f64p), _p(st, c_u8p), _p(col, c_f64p),
+                        _p(sc, c_f64p), _p(l, c_f64p), float(ambient), _p(out, c_u8p))
     return out
 
 
@@ -402,6 +422,8 @@ class Sim:
         self.flags = np.zeros(na, np.uint8)
         # jerk-dynamics actuator state a_lon, a_lat, steer (None under direct control)
         self.jerk = np.zeros((na, 3), np.float64) if jerk_dynamics else None
+        st = getattr(worlds, "signal_state", None)
+        self.signal_state = None if st is None else np.array(st, np.uint8)
         for w in range(worlds.n_worlds):
             b0 = int(worlds.box_off[w])
             a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
@@ -428,6 +450,15 @@ class Sim:
     def line(self, w: int) -> np.ndarray:
         return self.w.line[int(self.w.line_off[w]):int(self.w.line_off[w + 1])]
 
+    def signals(self, w: int):
+        """(spheres float64 [n, 4] x, y, z, r; states uint8 [n]) of world w."""
+        off = getattr(self.w, "signal_off", None)
+        if off is None:
+            return np.zeros((0, 4)), np.zeros(0, np.uint8)
+        s0, s1 = int(off[w]), int(off[w + 1])
+        return (self.w.signal[s0:s1].astype(np.float64),
+                np.asarray(self.signal_state[s0:s1], np.uint8))
+
     def step(self, actions: np.ndarray, worlds: Optional[Sequence[int]] = None) -> None:
         ws = range(self.w.n_worlds) if worlds is None else worlds
         for w in ws:
@@ -445,27 +476,35 @@ class Sim:
     def camera_tris(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> np.ndarray:
         a = int(self.agent_off[w]) + agent_local
         return camera_tris(cam, self.boxes6(w), agent_local, self.road(w), self.line(w),
-                           self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw)
+                           self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw,
+                           sph=self.signals(w)[0])
 
     def trace(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> Traced:
         a = int(self.agent_off[w]) + agent_local
         return trace_view(cam, self.boxes6(w), agent_local, self.road(w), self.line(w),
-                          self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw)
+                          self.state[a, 0], self.state[a, 1], self.state[a, 2], cam_yaw,
+                          sph=self.signals(w)[0])
 
     def prim_ranges(self, w: int):
         nb = int(self.w.box_off[w + 1] - self.w.box_off[w])
         nr = int(self.w.road_off[w + 1] - self.w.road_off[w])
         return 12 * nb, 12 * nb + 2 * nr
 
+    def line_end(self, w: int) -> int:
+        nl = int(self.w.line_off[w + 1] - self.w.line_off[w])
+        return self.prim_ranges(w)[1] + 2 * nl
+
     def render_rgb(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float,
                    key_f16: bool = False, **appearance) -> np.ndarray:
         """uint8 [3, H, W] RGB observation of one camera (FP64 pipeline)."""
         img = self.render(cam, w, agent_local, cam_yaw, key_f16)
         be, re = self.prim_ranges(w)
-        return shade_rgb(img.key, key_f16, be, re, self.boxes6(w), **appearance)
+        sp, st = self.signals(w)
+        return shade_rgb(img.key, key_f16, be, re, self.boxes6(w), line_end=self.line_end(w),
+                         sph=sp, sph_state=st, **appearance)
 
     def render(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float,
                key_f16: bool = False) -> Image:
         tris = self.camera_tris(cam, w, agent_local, cam_yaw)
         be, re = self.prim_ranges(w)
-        return raster(tris, cam.width, cam.height, key_f16, be, re)
+        return raster(tris, cam.width, cam.height, key_f16, be, re, line_end=self.line_end(w))

@@ -475,6 +475,51 @@ static v3 box_corner(const double *b, int k) {
 static const int BOX_FACES[6][4] = {
     {1, 3, 7, 5}, {0, 4, 6, 2}, {2, 6, 7, 3}, {0, 1, 5, 4}, {4, 5, 7, 6}, {0, 2, 3, 1}};
 
+/*
+ * Traffic-signal sphere (Sec. 3.1 / App. A: spheres are the world's third primitive, used
+ * for traffic lights).  Reading: a sphere of centre c and radius r is drawn as the convex
+ * polyhedron with vertices on it at latitudes th_i = -pi/2 + i pi/4 (i = 0..4) and
+ * longitudes ph_j = j pi/4 (j = 0..7): V(i, j) = c + r (cos th_i cos ph_j, cos th_i sin ph_j,
+ * sin th_i), the poles exactly (0, 0, -+1).  Quad q = 8 i + j (i = 0..3) has the corners
+ * V(i, j), V(i, j+1), V(i+1, j+1), V(i+1, j), counter-clockwise seen from outside; its
+ * triangles (q0 q1 q2) and (q0 q2 q3) are primitives 2 q and 2 q + 1 of the sphere (64 ids
+ * per sphere).  In the two pole bands one triangle of each quad is degenerate.
+ *   sp [4] = x, y, z, r
+ */
+static v3 sphere_vertex(const double *sp, int i, int j) {
+    const double th = -0.5 * M_PI + 0.25 * M_PI * i, ph = 0.25 * M_PI * (j % 8);
+    const double ct = (i == 0 || i == 4) ? 0.0 : cos(th);
+    const v3 v = {sp[0] + sp[3] * ct * cos(ph), sp[1] + sp[3] * ct * sin(ph), sp[2] + sp[3] * sin(th)};
+    return v;
+}
+
+static void sphere_quad(const double *sp, int q, v3 c[4]) {
+    const int i = q / 8, j = q % 8;
+    c[0] = sphere_vertex(sp, i, j);
+    c[1] = sphere_vertex(sp, i, j + 1);
+    c[2] = sphere_vertex(sp, i + 1, j + 1);
+    c[3] = sphere_vertex(sp, i + 1, j);
+}
+
+/* Outward unit normal of sphere quad q and its plane offset n . V (the plane through the
+ * quad's distinct corners). */
+static v3 sphere_face(const double *sp, int q, double *off) {
+    v3 c[4];
+    sphere_quad(sp, q, c);
+    /* three distinct corners: the south-pole band repeats corner 0 as corner 1 */
+    const v3 a = c[0], b = q < 8 ? c[2] : c[1], d = q < 8 ? c[3] : c[2];
+    const double ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const double wx = d.x - a.x, wy = d.y - a.y, wz = d.z - a.z;
+    double nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+    const double len = sqrt(nx * nx + ny * ny + nz * nz);
+    nx /= len;
+    ny /= len;
+    nz /= len;
+    *off = nx * a.x + ny * a.y + nz * a.z;
+    const v3 n = {nx, ny, nz};
+    return n;
+}
+
 typedef struct {
     double s, c;   /* sin, cos of camera yaw */
     double px, py, pz;
@@ -566,14 +611,16 @@ static int64_t emit_triangle(const or_cam *cfg, const camera *cm, v3 a, v3 b, v3
  *   boxes [n_boxes][6] x, y, yaw, L, W, H (current poses); box `ego` is skipped
  *   road/line quads [n][8]; roads at z = 0, lane lines at z = cfg->line_z
  *   agent pose (ax, ay, ayaw), camera yaw offset cam_yaw
+ *   signal spheres sph [n_sph][4] x, y, z, r (sphere_vertex)
  * Primitive ids: box b face-triangle t -> 12 b + t; road quad r triangle t ->
- * 12 n_boxes + 2 r + t; lane-line quad l triangle t -> 12 n_boxes + 2 n_road + 2 l + t.
+ * 12 n_boxes + 2 r + t; lane-line quad l triangle t -> 12 n_boxes + 2 n_road + 2 l + t;
+ * sphere s quad q triangle t -> 12 n_boxes + 2 n_road + 2 n_line + 64 s + 2 q + t.
  * Writes at most `cap` triangles; returns the number produced.
  */
 int64_t or_camera_tris(const or_cam *cfg, int32_t n_boxes, const double *boxes, int32_t ego,
                        int32_t n_road, const float *road, int32_t n_line, const float *line,
-                       double ax, double ay, double ayaw, double cam_yaw, or_tri *out,
-                       int64_t cap) {
+                       int32_t n_sph, const double *sph, double ax, double ay, double ayaw,
+                       double cam_yaw, or_tri *out, int64_t cap) {
     camera cm;
     double yaw = ayaw + cam_yaw;
     cm.s = sin(yaw);
@@ -615,6 +662,15 @@ int64_t or_camera_tris(const or_cam *cfg, int32_t n_boxes, const double *boxes, 
             n = emit_triangle(cfg, &cm, c[0], c[2], c[3], base + 2 * i + 1, out, n, cap);
         }
     }
+    const uint32_t sbase = (uint32_t)(12 * n_boxes + 2 * n_road + 2 * n_line);
+    for (int32_t s = 0; s < n_sph; ++s)
+        for (int q = 0; q < 32; ++q) {
+            v3 c[4];
+            sphere_quad(sph + 4 * s, q, c);
+            const uint32_t pr = sbase + (uint32_t)(64 * s + 2 * q);
+            n = emit_triangle(cfg, &cm, c[0], c[1], c[2], pr, out, n, cap);
+            n = emit_triangle(cfg, &cm, c[0], c[2], c[3], pr + 1, out, n, cap);
+        }
     return n;
 }
 
@@ -627,17 +683,21 @@ int64_t or_camera_tris(const or_cam *cfg, int32_t n_boxes, const double *boxes, 
  * x = (i + 1/2 - W/2) / f, y = (H/2 - j - 1/2) / f, so the ray parameter t is the view
  * depth z.  Nearest hit with t >= near among every box except the ego's (slab test in the
  * box frame, z from 0 to H), road quads on z = 0 and lane-line strips on z = line_z (plane
- * hit, point in quad with the boundary inside); ties go to the lower object (boxes by index,
- * then road quads, then lines).  Per pixel: class (0 background, 1 road, 2 lane line, 3 box),
- * reversed-Z depth near / t rounded to FP32 (0 background), and the hit's primitive id in
- * the raster's numbering -- box b's entry face f gives 12 b + 2 f (faces +x, -x, +y, -y, +z,
- * -z), road quad r gives 12 n_boxes + 2 r, line l gives 12 n_boxes + 2 n_road + 2 l --
- * or 0xFFFFFFFF on background, so the RGB shading applies unchanged.
+ * hit, point in quad with the boundary inside) and signal spheres (the polyhedron of
+ * sphere_vertex as the intersection of its 32 face half-spaces: entry at the largest
+ * entering-face parameter, the first such face on ties); ties go to the lower object
+ * (boxes by index, then road quads, then lines, then spheres).  Per pixel: class
+ * (0 background, 1 road, 2 lane line, 3 box, 4 signal), reversed-Z depth near / t rounded to
+ * FP32 (0 background), and the hit's primitive id in the raster's numbering -- box b's entry
+ * face f gives 12 b + 2 f (faces +x, -x, +y, -y, +z, -z), road quad r gives 12 n_boxes + 2 r,
+ * line l gives 12 n_boxes + 2 n_road + 2 l, sphere s's entry quad q the id of its
+ * non-degenerate triangle (2 q + 1 in the south-pole band, else 2 q) -- or 0xFFFFFFFF on
+ * background, so the RGB shading applies unchanged.
  */
 void or_trace_view(const or_cam *cfg, int32_t n_boxes, const double *boxes, int32_t ego,
                    int32_t n_road, const float *road, int32_t n_line, const float *line,
-                   double ax, double ay, double ayaw, double cam_yaw, uint8_t *cls, float *depth,
-                   uint32_t *prim) {
+                   int32_t n_sph, const double *sph, double ax, double ay, double ayaw,
+                   double cam_yaw, uint8_t *cls, float *depth, uint32_t *prim) {
     const double yaw = ayaw + cam_yaw;
     const double fx = cos(yaw), fy = sin(yaw);  /* forward */
     const double rx = sin(yaw), ry = -cos(yaw); /* right */
@@ -705,6 +765,34 @@ void or_trace_view(const or_cam *cfg, int32_t n_boxes, const double *boxes, int3
                             break;
                         }
                 }
+            }
+            for (int32_t s = 0; s < n_sph; ++s) {
+                double t0 = -INFINITY, t1 = INFINITY;
+                int face = -1, inside = 1;
+                for (int q = 0; q < 32 && inside; ++q) {
+                    double off;
+                    const v3 n = sphere_face(sph + 4 * s, q, &off);
+                    const double den = n.x * dx + n.y * dy + n.z * dz;
+                    const double num = off - (n.x * ax + n.y * ay + n.z * oz);
+                    if (den == 0.0) {
+                        if (num < 0.0) inside = 0;
+                        continue;
+                    }
+                    const double t = num / den;
+                    if (den < 0.0) {
+                        if (t > t0) {
+                            t0 = t;
+                            face = q;
+                        }
+                    } else if (t < t1) {
+                        t1 = t;
+                    }
+                }
+                if (!inside || face < 0 || t0 > t1 || t0 < cfg->near || !(t0 < best)) continue;
+                best = t0;
+                c = 4;
+                pr = (uint32_t)(12 * n_boxes + 2 * n_road + 2 * n_line + 64 * s + 2 * face +
+                                (face < 8 ? 1 : 0));
             }
             const int64_t pix = (int64_t)j * cfg->width + i;
             cls[pix] = (uint8_t)c;
@@ -820,13 +908,15 @@ static uint64_t pixel_key(const rtri *r, int64_t Xp, int64_t Yp, int key_f16) {
     return ((uint64_t)bits << 32) | (uint64_t)(0xFFFFFFFFu - r->prim);
 }
 
-/* Class of a primitive id: 3 vehicle/box, 1 road, 2 lane line. */
-static uint8_t prim_class(uint32_t prim, uint32_t box_end, uint32_t road_end) {
-    return prim < box_end ? 3 : (prim < road_end ? 1 : 2);
+/* Class of a primitive id: 3 vehicle/box, 1 road, 2 lane line, 4 signal sphere. */
+static uint8_t prim_class(uint32_t prim, uint32_t box_end, uint32_t road_end,
+                          uint32_t line_end) {
+    return prim < box_end ? 3 : (prim < road_end ? 1 : (prim < line_end ? 2 : 4));
 }
 
 static void resolve(const uint64_t *key, int64_t npx, int key_f16, uint32_t box_end,
-                    uint32_t road_end, uint8_t *cls, float *depth, uint16_t *depth16) {
+                    uint32_t road_end, uint32_t line_end, uint8_t *cls, float *depth,
+                    uint16_t *depth16) {
     for (int64_t p = 0; p < npx; ++p) {
         uint64_t k = key[p];
         uint8_t c = 0;
@@ -835,7 +925,7 @@ static void resolve(const uint64_t *key, int64_t npx, int key_f16, uint32_t box_
         if (k) {
             uint32_t prim = key_f16 ? (0xFFFFu - (uint32_t)(k & 0xFFFFu))
                                     : (0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
-            c = prim_class(prim, box_end, road_end);
+            c = prim_class(prim, box_end, road_end, line_end);
             if (key_f16) h = (uint16_t)(k >> 16);
             else {
                 uint32_t bits = (uint32_t)(k >> 32);
@@ -851,13 +941,14 @@ static void resolve(const uint64_t *key, int64_t npx, int key_f16, uint32_t box_
 /*
  * Rasterise snapped triangles into W x H.  Pixel (i, j) samples (16 i + 8, 16 j + 8).
  * Output per pixel: the max key (0 = background), the class (0 background, 1 road,
- * 2 lane line, 3 box) and the winner's depth (FP32 mode) or its binary16 bits (FP16 mode).
+ * 2 lane line, 3 box, 4 signal: ids from line_end on) and the winner's depth (FP32 mode) or
+ * its binary16 bits (FP16 mode).
  * The loop visits each triangle's snapped bounding box; or_raster_bruteforce visits every
  * pixel for every triangle and must give the same result.
  */
 void or_raster(const or_tri *tris, int64_t n, int32_t W, int32_t H, int32_t key_f16,
-               uint32_t box_end, uint32_t road_end, uint64_t *key, uint8_t *cls, float *depth,
-               uint16_t *depth16) {
+               uint32_t box_end, uint32_t road_end, uint32_t line_end, uint64_t *key,
+               uint8_t *cls, float *depth, uint16_t *depth16) {
     memset(key, 0, sizeof(uint64_t) * (size_t)W * (size_t)H);
     for (int64_t t = 0; t < n; ++t) {
         rtri r;
@@ -884,12 +975,12 @@ void or_raster(const or_tri *tris, int64_t n, int32_t W, int32_t H, int32_t key_
                 if (k > key[j * W + i]) key[j * W + i] = k;
             }
     }
-    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, cls, depth, depth16);
+    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, line_end, cls, depth, depth16);
 }
 
 void or_raster_bruteforce(const or_tri *tris, int64_t n, int32_t W, int32_t H, int32_t key_f16,
-                          uint32_t box_end, uint32_t road_end, uint64_t *key, uint8_t *cls,
-                          float *depth, uint16_t *depth16) {
+                          uint32_t box_end, uint32_t road_end, uint32_t line_end, uint64_t *key,
+                          uint8_t *cls, float *depth, uint16_t *depth16) {
     for (int32_t j = 0; j < H; ++j)
         for (int32_t i = 0; i < W; ++i) {
             uint64_t best = 0;
@@ -903,7 +994,7 @@ void or_raster_bruteforce(const or_tri *tris, int64_t n, int32_t W, int32_t H, i
             }
             key[(int64_t)j * W + i] = best;
         }
-    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, cls, depth, depth16);
+    resolve(key, (int64_t)W * H, key_f16, box_end, road_end, line_end, cls, depth, depth16);
 }
 
 /*
@@ -913,26 +1004,39 @@ void or_raster_bruteforce(const or_tri *tris, int64_t n, int32_t W, int32_t H, i
  *     base * (ambient + (1 - ambient) * max(0, n . l))
  * with base the winning primitive's class colour (all boxes share one colour), n its
  * outward unit normal in the world frame -- a box face's normal turned by the box's yaw,
- * +z for road and lane-line strips -- and l the unit direction towards the light (the same
- * light in every world).  Background pixels take the background colour unshaded.  Each
- * channel is quantised as rint(255 * clamp(v, 0, 1)) (round half to even).
+ * +z for road and lane-line strips, a signal sphere's face normal (sphere_face) -- and l
+ * the unit direction towards the light (the same light in every world).  A signal sphere's
+ * base colour is that of its state (0 red, 1 amber, 2 green, 3 off).  Background pixels take
+ * the background colour unshaded.  Each channel is quantised as rint(255 * clamp(v, 0, 1))
+ * (round half to even).
  *   key [npx]: the raster's per-pixel keys; boxes [n][6]: x, y, yaw, L, W, H of the world's
- *   boxes (post-step); colour [4][3]: classes 0 background, 1 road, 2 lane line, 3 box;
+ *   boxes (post-step); sph [n][4], sph_state [n]: its signal spheres; colour [4][3]: classes
+ *   0 background, 1 road, 2 lane line, 3 box; sig_colour [4][3]: signal states;
  *   light [3] unit -> rgb [3][npx]
  */
 void or_shade_rgb(const uint64_t *key, int64_t npx, int32_t key_f16, uint32_t box_end,
-                  uint32_t road_end, const double *boxes, const double *colour,
+                  uint32_t road_end, uint32_t line_end, const double *boxes, const double *sph,
+                  const uint8_t *sph_state, const double *colour, const double *sig_colour,
                   const double *light, double ambient, uint8_t *rgb) {
     for (int64_t p = 0; p < npx; ++p) {
         const uint64_t k = key[p];
         int cls = 0;
         double shade = 1.0;
+        const double *base = colour;
         if (k) {
             const uint32_t prim = key_f16 ? (0xFFFFu - (uint32_t)(k & 0xFFFFu))
                                           : (0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFu));
-            cls = prim_class(prim, box_end, road_end);
+            cls = prim_class(prim, box_end, road_end, line_end);
             double nx = 0.0, ny = 0.0, nz = 1.0;
-            if (cls == 3) {
+            if (cls == 4) {
+                const uint32_t s = (prim - line_end) / 64, q = ((prim - line_end) % 64) / 2;
+                double off;
+                const v3 n = sphere_face(sph + 4 * s, (int)q, &off);
+                nx = n.x;
+                ny = n.y;
+                nz = n.z;
+                base = sig_colour + 3 * sph_state[s];
+            } else if (cls == 3) {
                 const uint32_t b = prim / 12, face = (prim % 12) / 2;
                 const double c = cos(boxes[6 * b + 2]), sn = sin(boxes[6 * b + 2]);
                 switch (face) { /* +x, -x, +y, -y, +z, -z in the box frame */
@@ -948,8 +1052,9 @@ void or_shade_rgb(const uint64_t *key, int64_t npx, int32_t key_f16, uint32_t bo
             if (ndl < 0.0) ndl = 0.0;
             shade = ambient + (1.0 - ambient) * ndl;
         }
+        if (cls != 4) base = colour + 3 * cls;
         for (int ch = 0; ch < 3; ++ch) {
-            double v = colour[3 * cls + ch] * shade;
+            double v = base[ch] * shade;
             if (v < 0.0) v = 0.0;
             if (v > 1.0) v = 1.0;
             rgb[(int64_t)ch * npx + p] = (uint8_t)rint(255.0 * v);
@@ -959,7 +1064,8 @@ void or_shade_rgb(const uint64_t *key, int64_t npx, int32_t key_f16, uint32_t bo
 
 /*
  * Policy-input encoding: 4-channel one-hot of the class image, normalised per channel,
- * bfloat16, NCHW.  value(c) = bf16((onehot_c - mean_c) / std_c), computed in FP32.
+ * bfloat16, NCHW.  value(c) = bf16((onehot_c - mean_c) / std_c), computed in FP32.  Signal
+ * spheres (class 4) count as objects: channel 3, with the boxes.
  *   cls [n] -> out [4][n]
  */
 void or_onehot_bf16(const uint8_t *cls, int64_t n, const float *mean, const float *std_,
@@ -971,5 +1077,6 @@ void or_onehot_bf16(const uint8_t *cls, int64_t n, const float *mean, const floa
             val[c][hot] = or_f32_to_bf16(t);
         }
     for (int c = 0; c < 4; ++c)
-        for (int64_t p = 0; p < n; ++p) out[(int64_t)c * n + p] = val[c][cls[p] == c];
+        for (int64_t p = 0; p < n; ++p)
+            out[(int64_t)c * n + p] = val[c][cls[p] == c || (c == 3 && cls[p] == 4)];
 }

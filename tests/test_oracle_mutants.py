@@ -68,6 +68,16 @@ MUTANTS = {
                                       "double target = atan((a_lat / v2) * 0.3 * L);"),
     "jerk lateral unclipped": ("    if (a_lat > 4.0) a_lat = 4.0;\n", ""),
     "jerk halted state kept": ("            if (jerk_state) jerk_state[3 * i] = jerk_state[3 * i + 1] = jerk_state[3 * i + 2] = 0.0;\n", ""),
+    "sphere latitude step": ("const double th = -0.5 * M_PI + 0.25 * M_PI * i,", "const double th = -0.5 * M_PI + 0.24 * M_PI * i,"),
+    "sphere x and y swapped": ("const v3 v = {sp[0] + sp[3] * ct * cos(ph), sp[1] + sp[3] * ct * sin(ph),", "const v3 v = {sp[0] + sp[3] * ct * sin(ph), sp[1] + sp[3] * ct * cos(ph),"),
+    "sphere radius ignored in z": ("sp[2] + sp[3] * sin(th)};", "sp[2] + sin(th)};"),
+    "sphere face from wrong corners": ("const v3 a = c[0], b = q < 8 ? c[2] : c[1], d = q < 8 ? c[3] : c[2];", "const v3 a = c[0], b = c[1], d = c[2];"),
+    "trace sphere exit face": ("                    if (den < 0.0) {\n                        if (t > t0) {", "                    if (den > 0.0) {\n                        if (t > t0) {"),
+    "trace sphere id band": ("64 * s + 2 * face +\n                                (face < 8 ? 1 : 0));", "64 * s + 2 * face);"),
+    "signal drawn as box": ("return prim < box_end ? 3 : (prim < road_end ? 1 : (prim < line_end ? 2 : 4));", "return prim < box_end ? 3 : (prim < road_end ? 1 : (prim < line_end ? 2 : 3));"),
+    "signal colour ignores state": ("                base = sig_colour + 3 * sph_state[s];", "                base = sig_colour;"),
+    "signal one-hot channel": ("val[c][cls[p] == c || (c == 3 && cls[p] == 4)]", "val[c][cls[p] == c]"),
+    "sphere ids overlap lines": ("const uint32_t sbase = (uint32_t)(12 * n_boxes + 2 * n_road + 2 * n_line);", "const uint32_t sbase = (uint32_t)(12 * n_boxes + 2 * n_road);"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

@@ -34,12 +34,14 @@ def ego_box(x=0.0, y=0.0, yaw=0.0):
 
 
 def render_scene(cam, boxes, road=(), line=(), pose=(0.0, 0.0, 0.0), cam_yaw=0.0,
-                 key_f16=False, ego=0):
+                 key_f16=False, ego=0, sph=None):
     b = np.array(boxes, np.float64).reshape(-1, 6)
     rd = np.array(road, np.float32).reshape(-1, 8)
     ln = np.array(line, np.float32).reshape(-1, 8)
-    tris = oracle.camera_tris(cam, b, ego, rd, ln, pose[0], pose[1], pose[2], cam_yaw)
-    img = oracle.raster(tris, cam.width, cam.height, key_f16, 12 * len(b), 12 * len(b) + 2 * len(rd))
+    tris = oracle.camera_tris(cam, b, ego, rd, ln, pose[0], pose[1], pose[2], cam_yaw, sph=sph)
+    re = 12 * len(b) + 2 * len(rd)
+    img = oracle.raster(tris, cam.width, cam.height, key_f16, 12 * len(b), re,
+                        line_end=re + 2 * len(ln))
     return img, tris
 
 
@@ -1233,3 +1235,214 @@ def test_jerk_ego_extras():
     _, ego = oracle.rewards_world(before, [0], after, [0], [[-2.5, 0.1]], [[4.5, 1.9]],
                                   np.zeros((1, 2)), [W_INF], STRAIGHT)
     assert np.all(ego[0, 6:] == 0.0)
+
+
+# ---------------------------------------------------------------------------------------
+# Traffic-signal spheres (Sec. 3.1 / App. A third primitive): the drawn polyhedron lies
+# between its inscribed and circumscribed spheres; faces, depth and ids against an
+# independent ray/triangle intersection; shading against the faces' closed-form normals
+# ---------------------------------------------------------------------------------------
+
+SPH_IN = 0.8628  # inscribed-sphere radius of the 4 x 8 polyhedron, in units of r (below the exact 0.86286)
+
+
+def _rays(W, H, psi, jx=0.0, jy=0.0, hfov=math.pi / 2):
+    f = (W / 2) / math.tan(hfov / 2)
+    xv = ((np.arange(W) + 0.5 + jx - W / 2) / f)[None, :, None]
+    yv = (-(np.arange(H) + 0.5 + jy - H / 2) / f)[:, None, None]
+    right = np.array([math.sin(psi), -math.cos(psi), 0.0])
+    fwd = np.array([math.cos(psi), math.sin(psi), 0.0])
+    return np.broadcast_to(xv * right + yv * np.array([0.0, 0.0, 1.0]) + fwd, (H, W, 3))
+
+
+def _sphere_entry(O, D, c, R):
+    """Entry parameter of rays O + t D into the sphere (c, R); nan where they miss."""
+    oc = O - np.asarray(c, np.float64)
+    a = np.einsum("hwk,hwk->hw", D, D)
+    b = 2.0 * np.einsum("hwk,k->hw", D, oc)
+    cc = float(oc @ oc) - R * R
+    disc = b * b - 4 * a * cc
+    with np.errstate(invalid="ignore"):
+        return np.where(disc >= 0, (-b - np.sqrt(disc)) / (2 * a), np.nan)
+
+
+def _fmin(arrays):
+    out = arrays[0]
+    for a in arrays[1:]:
+        out = np.fmin(out, a)
+    return out
+
+
+def _sphere_mesh(c, r):
+    """The polyhedron's quads from its definition: [32, 4, 3] corners."""
+    def V(i, j):
+        th, ph = -math.pi / 2 + i * math.pi / 4, (j % 8) * math.pi / 4
+        ct = 0.0 if i in (0, 4) else math.cos(th)
+        return np.array([c[0] + r * ct * math.cos(ph), c[1] + r * ct * math.sin(ph), c[2] + r * math.sin(th)])
+    return np.array([[V(q // 8, q % 8), V(q // 8, q % 8 + 1), V(q // 8 + 1, q % 8 + 1), V(q // 8 + 1, q % 8)]
+                     for q in range(32)])
+
+
+def _mt_cast(O, D, quads):
+    """Nearest hit per ray over the quads' triangles (Moller-Trumbore): (t, quad, edge
+    margin = smallest barycentric coordinate), t = inf on a miss."""
+    H, W, _ = D.shape
+    best = np.full((H, W), np.inf)
+    bq = np.full((H, W), -1)
+    marg = np.zeros((H, W))
+    for q, c in enumerate(quads):
+        for tri in ((c[0], c[1], c[2]), (c[0], c[2], c[3])):
+            e1, e2 = tri[1] - tri[0], tri[2] - tri[0]
+            if np.linalg.norm(np.cross(e1, e2)) < 1e-12:
+                continue  # degenerate pole triangle
+            pv = np.cross(D, e2)
+            det = pv @ e1
+            with np.errstate(divide="ignore", invalid="ignore"):
+                inv = 1.0 / det
+                tv = O - tri[0]
+                u = np.einsum("hwk,k->hw", pv, tv) * inv
+                qv = np.cross(tv, e1)
+                v = (D @ qv) * inv
+                t = (qv @ e2) * inv
+            ok = (np.abs(det) > 1e-15) & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0) & (t < best)
+            best[ok], bq[ok] = t[ok], q
+            marg[ok] = np.minimum(np.minimum(u, v), 1 - u - v)[ok]
+    return best, bq, marg
+
+
+SPH_SCENE = dict(boxes=[ego_box()], sph=np.array([[5.0, 0.6, 2.0, 1.8], [12.0, -2.5, 1.2, 1.0],
+                                                   [7.0, -3.2, 4.2, 1.2]]))
+
+
+@pytest.mark.parametrize("W,H,yaw", [(48, 48, 0.0), (64, 40, 0.15), (40, 24, -0.2)])
+def test_signal_sphere_between_insphere_and_circumsphere(W, H, yaw):
+    cam = CamConfig(W, H)
+    sph = SPH_SCENE["sph"]
+    img, _ = render_scene(cam, SPH_SCENE["boxes"], cam_yaw=yaw, sph=sph)
+    tr = oracle.trace_view(cam, np.array(SPH_SCENE["boxes"], np.float64), 0, np.zeros((0, 8)),
+                           np.zeros((0, 8)), 0.0, 0.0, 0.0, yaw, sph=sph)
+    O = np.array([0.0, 0.0, 1.5])
+    D = _rays(W, H, yaw)
+    t_in = _fmin([_sphere_entry(O, D, s[:3], SPH_IN * s[3]) for s in sph])
+    t_out = _fmin([_sphere_entry(O, D, s[:3], s[3]) for s in sph])
+    inner, outer = np.isfinite(t_in), np.isfinite(t_out)
+    assert inner.sum() > 100
+    # ray tracing: exact containment
+    assert np.all(tr.cls[inner] == 4) and not np.any(tr.cls[~outer])
+    hit = tr.cls == 4
+    with np.errstate(divide="ignore"):
+        assert np.all(tr.depth[hit] <= 0.1 / t_out[hit] * (1 + 1e-6))
+        assert np.all(tr.depth[inner] >= 0.1 / t_in[inner] * (1 - 1e-6))
+    # raster: the same up to snapping (1/32 px per axis): use spheres 3 % apart
+    t_in2 = _fmin([_sphere_entry(O, D, s[:3], 0.97 * SPH_IN * s[3]) for s in sph])
+    t_out2 = _fmin([_sphere_entry(O, D, s[:3], 1.03 * s[3]) for s in sph])
+    assert np.all(img.cls[np.isfinite(t_in2)] == 4) and not np.any(img.cls[~np.isfinite(t_out2)])
+    near = np.isfinite(t_in2)
+    assert np.all(img.depth[near] >= 0.1 / t_in2[near] * (1 - 1e-3))
+    assert np.all(img.depth[near] <= 0.1 / t_out2[near] * (1 + 1e-3))
+
+
+@pytest.mark.parametrize("W,H,yaw", [(48, 48, 0.0), (56, 32, 0.1)])
+def test_signal_faces_against_ray_triangle_intersection(W, H, yaw):
+    """Trace: every ray class, depth and entry quad as Moller-Trumbore on the mesh; raster:
+    the drawn quad at every pixel whose neighbourhood (+-1/16 px) hits one quad only."""
+    cam = CamConfig(W, H)
+    sph = SPH_SCENE["sph"]
+    quads = np.concatenate([_sphere_mesh(s[:3], s[3]) for s in sph])
+    O = np.array([0.0, 0.0, 1.5])
+    t, q, marg = _mt_cast(O, _rays(W, H, yaw), quads)
+    tr = oracle.trace_view(cam, np.array(SPH_SCENE["boxes"], np.float64), 0, np.zeros((0, 8)),
+                           np.zeros((0, 8)), 0.0, 0.0, 0.0, yaw, sph=sph)
+    hit = np.isfinite(t)
+    assert np.array_equal(tr.cls == 4, hit)
+    assert np.allclose(tr.depth[hit], (0.1 / t[hit]).astype(np.float32), rtol=1e-6)
+    base = 12  # one box, no ground quads
+    rel = tr.prim[hit].astype(np.int64) - base
+    clear = marg[hit] > 1e-6
+    assert np.array_equal((rel // 64 * 32 + rel % 64 // 2)[clear], q[hit][clear])
+    img, _ = render_scene(cam, SPH_SCENE["boxes"], cam_yaw=yaw, sph=sph)
+    same = hit.copy()
+    for jx, jy in ((1 / 16, 0), (-1 / 16, 0), (0, 1 / 16), (0, -1 / 16)):
+        _, qj, _ = _mt_cast(O, _rays(W, H, yaw, jx, jy), quads)
+        same &= qj == q
+    assert same.sum() > 200
+    full = 0xFFFFFFFF
+    prim = full - (img.key & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    rel = prim[same] - base
+    assert np.all(img.cls[same] == 4)
+    assert np.array_equal(rel // 64 * 32 + rel % 64 // 2, q[same])
+    # a pole-band quad has one drawn triangle: the trace reports that triangle's id
+    pole = same & clear_map(hit, clear) & ((q % 32 < 8) | (q % 32 >= 24))
+    assert pole.sum() >= 5
+    assert np.array_equal(prim[pole], tr.prim[pole].astype(np.int64))
+
+
+def test_signal_prim_ids_follow_lane_lines():
+    cam = CamConfig(48, 48)
+    road = [rect_quad(1.0, 30.0, -4.0, 4.0), rect_quad(30.0, 60.0, -4.0, 4.0)]
+    line = [rect_quad(1.0, 60.0, -0.1, 0.1)]
+    boxes = [ego_box(), [20.0, 5.0, 0.3, 4.5, 1.9, 1.6]]
+    sph = np.array([[9.0, 0.0, 3.0, 0.8], [16.0, 1.0, 3.5, 0.8]])
+    _, tris = render_scene(cam, boxes, road, line, sph=sph)
+    _, plain = render_scene(cam, boxes, road, line)
+    base = 12 * 2 + 2 * 2 + 2 * 1
+    # the spheres add ids [base, base + 128) only; every other triangle is unchanged
+    assert np.array_equal(tris[tris["prim"] < base], plain)
+    sp = tris["prim"][tris["prim"] >= base].astype(np.int64) - base
+    assert set(sp // 64) == {0, 1} and sp.max() < 128
+    # the same spheres without ground quads: the same triangles, ids shifted by the 6
+    # ground ids only
+    _, bare = render_scene(cam, boxes, sph=sph)
+    _, bare_plain = render_scene(cam, boxes)
+    a, b = tris[len(plain):], bare[len(bare_plain):]
+    assert len(a) == len(b) > 30
+    assert np.array_equal(a["X"], b["X"]) and np.array_equal(a["Y"], b["Y"])
+    assert np.array_equal(a["prim"].astype(np.int64) - base, b["prim"].astype(np.int64) - 24)
+
+
+def clear_map(hit, clear):
+    m = np.zeros(hit.shape, bool)
+    m[hit] = clear
+    return m
+
+
+def _face_normal(q):
+    """Closed form: a band quad is a planar isosceles trapezoid whose normal lies in the
+    meridian plane of its middle longitude, perpendicular to the line joining the midpoints
+    of its two horizontal edges."""
+    i, j = divmod(q, 8)
+    th0, th1 = -math.pi / 2 + i * math.pi / 4, -math.pi / 2 + (i + 1) * math.pi / 4
+    ph = (j + 0.5) * math.pi / 4
+    drho = math.cos(math.pi / 8) * (math.cos(th1) - math.cos(th0))
+    dz = math.sin(th1) - math.sin(th0)
+    n = np.array([dz * math.cos(ph), dz * math.sin(ph), -drho])
+    return n / np.linalg.norm(n)
+
+
+@pytest.mark.parametrize("state", [0, 1, 2, 3])
+def test_signal_shading_uses_state_colour_and_face_normal(state):
+    nb, nr, nl = 1, 2, 1
+    line_end = 12 * nb + 2 * nr + 2 * nl
+    sph = np.array([[0.0, 0.0, 4.0, 0.5], [3.0, 0.0, 4.0, 0.5]])
+    states = np.array([3 - state, state], np.uint8)
+    prims = line_end + 64 + np.arange(64)  # every triangle of the second sphere
+    key = ((np.uint64(1) << np.uint64(40)) | (np.uint64(0xFFFFFFFF) - prims.astype(np.uint64)))
+    rgb = oracle.shade_rgb(key[None, :], False, 12 * nb, 12 * nb + 2 * nr,
+                           np.array([ego_box()], np.float64), line_end=line_end, sph=sph,
+                           sph_state=states)
+    l = oracle.unit(oracle.RGB_LIGHT)
+    for t in range(64):
+        n = _face_normal(t // 2)
+        shade = oracle.RGB_AMBIENT + (1 - oracle.RGB_AMBIENT) * max(0.0, float(n @ l))
+        want = [round(255 * min(1.0, max(0.0, c * shade))) for c in oracle.SIGNAL_COLOURS[state]]
+        assert list(rgb[:, 0, t]) == pytest.approx(want, abs=1), t
+
+
+def test_signal_class_and_onehot_channel():
+    cls = np.array([0, 1, 2, 3, 4], np.uint8)
+    oh = oracle.onehot_bf16(cls)
+    hot, cold = oracle.f32_to_bf16_bits([1.0])[0], oracle.f32_to_bf16_bits([-1.0])[0]
+    assert list(oh[3]) == [cold, cold, cold, hot, hot]
+    assert list(oh[0]) == [hot, cold, cold, cold, cold]
+    img, _ = render_scene(CamConfig(32, 32), [ego_box()], sph=np.array([[6.0, 0.0, 1.5, 1.0]]))
+    assert (img.cls == 4).sum() > 10 and set(np.unique(img.cls)) == {0, 4}

@@ -13,6 +13,9 @@ Layout of a batch of worlds (all host numpy arrays, CSR over worlds):
 * ``boxes``    float32 [n_boxes, 7] x, y, yaw, L, W, H, v0
 * ``road_off`` int32 [n_worlds+1], ``road`` float32 [n_road, 8] road-surface quads
 * ``line_off`` int32 [n_worlds+1], ``line`` float32 [n_line, 8] lane-line strips
+* ``signal_off`` int32 [n_worlds+1], ``signal`` float32 [n_signal, 4] traffic-signal
+  spheres (x, y, z, radius), ``signal_state`` uint8 [n_signal] (0 red, 1 amber, 2 green,
+  3 off)
 
 Quads are four (x, y) corners, counter-clockwise seen from above.
 """
@@ -116,6 +119,7 @@ class Workload:
     dt: float = 0.1
     hfov_deg: float = 90.0
     cam_height: float = 1.5
+    signals: int = 0                 # traffic-signal spheres per world
 
     @property
     def n_cams(self) -> int:
@@ -144,13 +148,13 @@ WORKLOADS = {
     # front, front-left, front-right (read as +-60 deg), rear -- at its two training
     # resolutions, shaded RGB with one directional light.
     "paper_rig_210x126": Workload(
-        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 210x126 RGB",
+        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 8 signals, 210x126 RGB",
         256, (32, 32), (500, 500), 32, 210, 126, cam_yaw_deg=(0.0, 60.0, -60.0, 180.0),
-        precision="f16", output="rgb_u8", steps=10, seed=1005),
+        precision="f16", output="rgb_u8", steps=10, seed=1005, signals=8),
     "paper_rig_434x252": Workload(
-        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 434x252 RGB",
+        "paper rig: 256 worlds x 32 agents x 4 cameras (0, +-60, 180 deg), 8 signals, 434x252 RGB",
         256, (32, 32), (500, 500), 32, 434, 252, cam_yaw_deg=(0.0, 60.0, -60.0, 180.0),
-        precision="f16", output="rgb_u8", steps=10, seed=1006),
+        precision="f16", output="rgb_u8", steps=10, seed=1006, signals=8),
 }
 
 
@@ -163,6 +167,15 @@ class Worlds:
     road: np.ndarray
     line_off: np.ndarray
     line: np.ndarray
+    signal_off: Optional[np.ndarray] = None
+    signal: Optional[np.ndarray] = None
+    signal_state: Optional[np.ndarray] = None
+
+    def __post_init__(self):
+        if self.signal_off is None:
+            self.signal_off = np.zeros(self.n_worlds + 1, np.int32)
+            self.signal = np.zeros((0, 4), np.float32)
+            self.signal_state = np.zeros(0, np.uint8)
 
     @property
     def n_worlds(self) -> int:
@@ -177,10 +190,12 @@ class Worlds:
         b0, b1 = int(self.box_off[w]), int(self.box_off[w + 1])
         r0, r1 = int(self.road_off[w]), int(self.road_off[w + 1])
         l0, l1 = int(self.line_off[w]), int(self.line_off[w + 1])
+        s0, s1 = int(self.signal_off[w]), int(self.signal_off[w + 1])
         return Worlds(np.array([0, b1 - b0], np.int32), self.agent_count[w:w + 1].copy(),
                       self.boxes[b0:b1].copy(), np.array([0, r1 - r0], np.int32),
                       self.road[r0:r1].copy(), np.array([0, l1 - l0], np.int32),
-                      self.line[l0:l1].copy())
+                      self.line[l0:l1].copy(), np.array([0, s1 - s0], np.int32),
+                      self.signal[s0:s1].copy(), self.signal_state[s0:s1].copy())
 
     def agent_offsets(self) -> np.ndarray:
         off = np.zeros(self.n_worlds + 1, np.int64)
@@ -248,11 +263,37 @@ def workload_counts(wl: Workload):
     return ag, bx, sg
 
 
+def add_signals(worlds: Worlds, per_world: int, seed: int, height: float = 5.0,
+                radius: float = 0.4) -> Worlds:
+    """Place ``per_world`` traffic-signal spheres over each world's road: each hangs
+    ``height`` m above the centroid of a road quad drawn uniformly (seeded per world), in a
+    uniformly drawn state red / amber / green.  Worlds without road get none."""
+    sig, st, counts = [], [], []
+    for w in range(worlds.n_worlds):
+        r0, r1 = int(worlds.road_off[w]), int(worlds.road_off[w + 1])
+        k = per_world if r1 > r0 else 0
+        rng = np.random.default_rng([seed, w, 7])
+        q = worlds.road[r0 + rng.integers(0, max(r1 - r0, 1), size=k)].reshape(k, 4, 2)
+        c = q.astype(np.float64).mean(axis=1)
+        sig.append(np.column_stack([c, np.full(k, height), np.full(k, radius)]))
+        st.append(rng.integers(0, 3, size=k))
+        counts.append(k)
+    worlds.signal_off = np.zeros(worlds.n_worlds + 1, np.int32)
+    np.cumsum(counts, out=worlds.signal_off[1:])
+    worlds.signal = np.ascontiguousarray(np.concatenate(sig) if sig else np.zeros((0, 4)),
+                                         np.float32).reshape(-1, 4)
+    worlds.signal_state = np.ascontiguousarray(np.concatenate(st) if st else np.zeros(0), np.uint8)
+    return worlds
+
+
 def make_workload(wl: Workload, n_worlds: Optional[int] = None) -> Worlds:
     """Worlds of a workload; ``n_worlds`` takes only the first worlds (same seeds)."""
     ag, bx, sg = workload_counts(wl)
     n = wl.n_worlds if n_worlds is None else n_worlds
-    return make_worlds(n, ag[:n], bx[:n], sg[:n], wl.seed)
+    worlds = make_worlds(n, ag[:n], bx[:n], sg[:n], wl.seed)
+    if wl.signals:
+        add_signals(worlds, wl.signals, wl.seed)
+    return worlds
 
 
 def actions(seed: int, step: int, n_agents: int, gid0: int = 0,
