@@ -58,14 +58,18 @@ enum {
     GP_DEV_INJECTED = 1u << 31        /* set by gp_debug_inject_status */
 };
 
-/* Pixel classes of the class image / one-hot channels. */
-enum { GP_CLASS_BACKGROUND = 0, GP_CLASS_ROAD = 1, GP_CLASS_LANE_LINE = 2, GP_CLASS_VEHICLE = 3 };
+/* Pixel classes of the class image / one-hot channels (signals share channel 3). */
+enum { GP_CLASS_BACKGROUND = 0, GP_CLASS_ROAD = 1, GP_CLASS_LANE_LINE = 2, GP_CLASS_VEHICLE = 3,
+       GP_CLASS_SIGNAL = 4 };
+/* Traffic-signal states (gp_world_desc.signal_state, gp_set_signal_states). */
+enum { GP_SIGNAL_RED = 0, GP_SIGNAL_AMBER = 1, GP_SIGNAL_GREEN = 2, GP_SIGNAL_OFF = 3 };
 
 /* Limits (GP_ELIMIT beyond them). */
 #define GP_MAX_CAMS 8            /* cameras per agent */
 #define GP_MAX_BOXES 128         /* boxes (agents + static) per world */
 #define GP_MAX_QUADS 32767       /* road + lane-line quads per world */
 #define GP_MAX_WIDTH 512         /* image width and height */
+#define GP_MAX_SIGNALS 32        /* traffic-signal spheres per world */
 /* Vectorized observations (gp_observe_vec) */
 #define GP_OBS_AGENTS 16         /* surrounding-agent slots per agent */
 #define GP_OBS_AGENT_RADIUS 100.0f
@@ -93,9 +97,17 @@ enum {
  *                          seen from above, on the ground plane z = 0 (class road)
  *   line_off/line          lane-line strips [n][8], same layout, at z = lane_line_z
  *                          (class lane line)
+ *   signal_off/signal      traffic-signal spheres [n][4]: centre x, y, z and radius > 0
+ *                          (class signal); NULL signal_off = none.  A sphere is drawn as
+ *                          the polyhedron with vertices on it at latitudes -90, -45, 0, 45,
+ *                          90 deg and longitudes k 45 deg: quad q = 8 i + j (band i = 0..3
+ *                          from the south pole, sector j) with corners (i, j), (i, j+1),
+ *                          (i+1, j+1), (i+1, j), split into (q0 q1 q2), (q0 q2 q3)
+ *   signal_state[n]        GP_SIGNAL_* state of each sphere (RGB colour); NULL = all red
  * Primitive ids of a world (used for the depth tie-break): box b face triangle t ->
  * 12 b + t; road quad r triangle t -> 12 n_boxes + 2 r + t; lane-line quad l triangle t ->
- * 12 n_boxes + 2 n_road + 2 l + t.
+ * 12 n_boxes + 2 n_road + 2 l + t; signal s quad q triangle t -> 12 n_boxes + 2 n_road +
+ * 2 n_line + 64 s + 2 q + t.
  */
 typedef struct gp_world_desc {
     int32_t n_worlds;
@@ -106,6 +118,9 @@ typedef struct gp_world_desc {
     const float *road;
     const int32_t *line_off;
     const float *line;
+    const int32_t *signal_off;
+    const float *signal;
+    const uint8_t *signal_state;
 } gp_world_desc;
 
 /*
@@ -150,6 +165,9 @@ typedef struct gp_config {
     float lane_width;             /* lane width of the two-lane roads (default 3.5 m) */
     float v_limit;                /* speed limit of the overspeed term (default 30 m/s) */
     int32_t dynamics;             /* GP_DYN_DIRECT (default) or GP_DYN_JERK */
+    float signal_colour[4][3];    /* RGB in 0..1 of signal states red, amber, green, off
+                                     (defaults 0.9 0.1 0.1 / 0.95 0.7 0.1 / 0.1 0.8 0.3 /
+                                     0.25 0.25 0.25); shaded like every surface */
 } gp_config;
 
 /* Fill `cfg` with the defaults above. */
@@ -244,6 +262,13 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
  * are taken as given.
  */
 gp_status gp_get_dynamics(gp_handle *h, float *dyn, int on_host, void *stream);
+
+/*
+ * Traffic-signal states state[n_signals] (uint8, GP_SIGNAL_*; signals ordered by world),
+ * seen by the next render in RGB output.  on_host as for gp_get_state; host values above
+ * GP_SIGNAL_OFF are rejected (GP_EINVAL), device values are taken modulo 4.
+ */
+gp_status gp_set_signal_states(gp_handle *h, const uint8_t *state, int on_host, void *stream);
 gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *stream);
 
 /* Sizes of a handle. */

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libgigapixel.so")
 GP_OK, GP_EINVAL, GP_ENOMEM, GP_ECUDA, GP_ELIMIT, GP_EDEVICE, GP_ESTATE = 0, -1, -2, -3, -4, -5, -6
 KEY_F32, KEY_F16 = 0, 1
 OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8 = 0, 1, 2
+CLASS_SIGNAL = 4
+SIGNAL_RED, SIGNAL_AMBER, SIGNAL_GREEN, SIGNAL_OFF = 0, 1, 2, 3
 FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
@@ -33,7 +35,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
-            "gp_get_dynamics", "gp_set_dynamics",
+            "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -48,7 +50,10 @@ class WorldDesc(ctypes.Structure):
                 ("road_off", ctypes.POINTER(ctypes.c_int32)),
                 ("road", ctypes.POINTER(ctypes.c_float)),
                 ("line_off", ctypes.POINTER(ctypes.c_int32)),
-                ("line", ctypes.POINTER(ctypes.c_float))]
+                ("line", ctypes.POINTER(ctypes.c_float)),
+                ("signal_off", ctypes.POINTER(ctypes.c_int32)),
+                ("signal", ctypes.POINTER(ctypes.c_float)),
+                ("signal_state", ctypes.POINTER(ctypes.c_uint8))]
 
 
 class Config(ctypes.Structure):
@@ -64,7 +69,8 @@ class Config(ctypes.Structure):
                 ("light_dir", ctypes.c_float * 3), ("ambient", ctypes.c_float),
                 ("colour", (ctypes.c_float * 3) * 4),
                 ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
-                ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32)]
+                ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32),
+                ("signal_colour", (ctypes.c_float * 3) * 4)]
 
 
 class Info(ctypes.Structure):
@@ -111,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_observe_vec": [vp, vp, vp, vp],
         "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_get_dynamics": [vp, vp, i32, vp],
+        "gp_set_signal_states": [vp, vp, i32, vp],
         "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -153,10 +160,11 @@ def default_config(**kw) -> Config:
             arr = getattr(c, k)
             for i, y in enumerate(v):
                 arr[i] = y
-        elif k == "colour":
+        elif k in ("colour", "signal_colour"):
+            arr = getattr(c, k)
             for i, row in enumerate(v):
                 for j, y in enumerate(row):
-                    c.colour[i][j] = y
+                    arr[i][j] = y
         else:
             setattr(c, k, v)
     return c
@@ -197,6 +205,12 @@ class Simulator:
         desc.road = arr(worlds.road, np.float32, ctypes.c_float)
         desc.line_off = arr(worlds.line_off, np.int32, ctypes.c_int32)
         desc.line = arr(worlds.line, np.float32, ctypes.c_float)
+        sig_off = getattr(worlds, "signal_off", None)
+        if sig_off is not None:
+            desc.signal_off = arr(sig_off, np.int32, ctypes.c_int32)
+            desc.signal = arr(worlds.signal, np.float32, ctypes.c_float)
+            desc.signal_state = arr(worlds.signal_state, np.uint8, ctypes.c_uint8)
+        self.n_signals = 0 if sig_off is None else int(sig_off[-1])
         self.config = config
         self.device = device
         self._h = None
@@ -297,6 +311,17 @@ class Simulator:
         r = torch.empty((self.n_agents, 32, 8), dtype=torch.float32, device=dev)
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _stream(stream)))
         return a, r
+
+    def set_signal_states(self, states) -> None:
+        """Traffic-signal states uint8 [n_signals] (0 red, 1 amber, 2 green, 3 off): host
+        array, or a device tensor."""
+        if isinstance(states, np.ndarray):
+            s = np.ascontiguousarray(states, np.uint8)
+            assert s.shape == (self.n_signals,)
+            check(lib().gp_set_signal_states(self._h, _ptr(s), 1, _stream(None)))
+        else:
+            assert tuple(states.shape) == (self.n_signals,) and states.is_contiguous()
+            check(lib().gp_set_signal_states(self._h, _ptr(states), 0, _stream(None)))
 
     def get_dynamics(self) -> np.ndarray:
         """Jerk dynamics' actuator state float32 [n_agents, 3] = a_lon, a_lat, steer (host)."""

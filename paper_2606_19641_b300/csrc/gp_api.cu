@@ -74,12 +74,13 @@ struct GraphKey {
 struct gp_handle {
     int device = 0, sms = 148;
     gp_config cfg{};
-    int n_worlds = 0, n_agents = 0, n_boxes = 0, n_views = 0;
+    int n_worlds = 0, n_agents = 0, n_boxes = 0, n_views = 0, n_signals = 0;
     int max_cl = 1;  // most culling clusters in one world
     std::vector<WorldInfo> worlds_h;
     std::vector<int> world_item_begin, world_item_count;
     DevBuf<WorldInfo> worlds;
-    DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo;
+    DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo, sig;
+    DevBuf<uint8_t> sig_state;
     DevBuf<float> speed;
     DevBuf<uint8_t> flags;
     DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, counter,
@@ -134,7 +135,7 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
                           (double)c->light_dir[1] * c->light_dir[1] +
                           (double)c->light_dir[2] * c->light_dir[2];
         if (!(l2 > 1e-12) || !finite_all(c->light_dir, 3) || !(c->ambient >= 0.f && c->ambient <= 1.f) ||
-            !finite_all(&c->colour[0][0], 12))
+            !finite_all(&c->colour[0][0], 12) || !finite_all(&c->signal_colour[0][0], 12))
             return fail(GP_EINVAL, "RGB appearance: light_dir non-zero, ambient in 0..1, finite colours");
     }
     if (c->threads < 0 || c->threads > 1024 || c->threads % 32 || c->band_rows < 0 ||
@@ -157,13 +158,29 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
         if (na < 0 || na > nb) return fail(GP_EINVAL, "agent_count must be in [0, boxes]");
         if (nb > GP_MAX_BOXES) return fail(GP_ELIMIT, "more than 128 boxes in a world");
         if (nr + nl > GP_MAX_QUADS) return fail(GP_ELIMIT, "more than 32767 quads in a world");
-        const long long prims = 12LL * nb + 2LL * (nr + nl);
+        const int ns = d->signal_off ? d->signal_off[w + 1] - d->signal_off[w] : 0;
+        if (ns < 0) return fail(GP_EINVAL, "CSR offsets must be non-decreasing");
+        if (ns > GP_MAX_SIGNALS) return fail(GP_ELIMIT, "more than 32 signals in a world");
+        const long long prims = 12LL * nb + 2LL * (nr + nl) + 64LL * ns;
         if (c->key_precision == GP_KEY_F16 && prims > 65535)
             return fail(GP_ELIMIT, "FP16 keys hold at most 65535 primitive ids per world");
     }
     const size_t nb = d->box_off[nw], nr = d->road_off[nw], nl = d->line_off[nw];
     if ((nb && !d->boxes) || (nr && !d->road) || (nl && !d->line))
         return fail(GP_EINVAL, "null geometry array");
+    // ground-quad codes of the render kernel keep bits 30..31 free
+    if (nr + nl >= (size_t)1 << 29) return fail(GP_ELIMIT, "more than 2^29 quads in the batch");
+    if (d->signal_off) {
+        if (d->signal_off[0] != 0) return fail(GP_EINVAL, "CSR offsets must start at 0");
+        const size_t ns = d->signal_off[nw];
+        if (ns && !d->signal) return fail(GP_EINVAL, "null geometry array");
+        if (!finite_all(d->signal, ns * 4)) return fail(GP_EINVAL, "non-finite geometry");
+        for (size_t s = 0; s < ns; ++s) {
+            if (!(d->signal[4 * s + 3] > 0.f)) return fail(GP_EINVAL, "signal radius must be positive");
+            if (d->signal_state && d->signal_state[s] > GP_SIGNAL_OFF)
+                return fail(GP_EINVAL, "signal state must be 0..3");
+        }
+    }
     if (!finite_all(d->boxes, nb * 7) || !finite_all(d->road, nr * 8) || !finite_all(d->line, nl * 8))
         return fail(GP_EINVAL, "non-finite geometry");
     for (size_t b = 0; b < nb; ++b)
@@ -265,7 +282,10 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
         p.light[2] = n > 0 ? (float)(l2 / n) : 1.f;
         p.ambient = c.ambient;
         std::memcpy(p.colour, c.colour, sizeof(p.colour));
+        std::memcpy(p.sig_colour, c.signal_colour, sizeof(p.sig_colour));
     }
+    p.sig = h->sig.p;
+    p.sig_state = h->sig_state.p;
     p.out = out;
     p.depth = depth;
     p.view_mod = 0;
@@ -339,7 +359,8 @@ void build_items(gp_handle *h, int band_rows, std::vector<int2> &items) {
     for (int w = 0; w < h->n_worlds; ++w) order[w] = w;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const WorldInfo &A = h->worlds_h[a], &B = h->worlds_h[b];
-        return (long long)A.n_cl * 16 + A.n_boxes > (long long)B.n_cl * 16 + B.n_boxes;
+        return (long long)A.n_cl * 16 + A.n_boxes + 5 * A.n_sig >
+               (long long)B.n_cl * 16 + B.n_boxes + 5 * B.n_sig;
     });
     items.clear();
     items.reserve((size_t)h->n_views * nb);
@@ -520,6 +541,8 @@ void release_all(gp_handle *h) {
     h->weights.release();
     h->acc.release();
     h->jerk.release();
+    h->sig.release();
+    h->sig_state.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -570,6 +593,9 @@ gp_status gp_default_config(gp_config *c) {
     const float col[4][3] = {{0.55f, 0.75f, 0.95f}, {0.33f, 0.33f, 0.35f}, {0.92f, 0.92f, 0.85f},
                              {0.15f, 0.35f, 0.85f}};
     std::memcpy(c->colour, col, sizeof col);
+    const float sig[4][3] = {{0.9f, 0.1f, 0.1f}, {0.95f, 0.7f, 0.1f}, {0.1f, 0.8f, 0.3f},
+                             {0.25f, 0.25f, 0.25f}};
+    std::memcpy(c->signal_colour, sig, sizeof sig);
     for (int k = 0; k < 4; ++k) {
         c->norm_mean[k] = 0.5f;
         c->norm_std[k] = 0.5f;
@@ -631,6 +657,9 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         const int l0 = d->line_off[w], nl = d->line_off[w + 1] - l0;
         wi.box_end = 12u * wi.n_boxes;
         wi.road_end = wi.box_end + 2u * nr;
+        wi.line_end = wi.road_end + 2u * nl;
+        wi.sig_begin = d->signal_off ? d->signal_off[w] : 0;
+        wi.n_sig = d->signal_off ? d->signal_off[w + 1] - d->signal_off[w] : 0;
         wi.road_begin = (int)road_geo.size() / 2;
         wi.n_road = nr;
         float bx0 = 1e30f, by0 = 1e30f, bx1 = -1e30f, by1 = -1e30f;
@@ -794,6 +823,19 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(line_geo, line_geo);
     UP(lcell_off, lcell_off);
     UP(lcell_quads, lcell_quads);
+    {
+        const size_t ns = d->signal_off ? (size_t)d->signal_off[nw] : 0;
+        std::vector<float4> sig(std::max<size_t>(ns, 1), make_float4(0.f, 0.f, 0.f, 1.f));
+        std::vector<uint8_t> sst(std::max<size_t>(ns, 1), 0);
+        for (size_t s = 0; s < ns; ++s) {
+            const float *q = d->signal + 4 * s;
+            sig[s] = make_float4(q[0], q[1], q[2], q[3]);
+            sst[s] = d->signal_state ? d->signal_state[s] : (uint8_t)GP_SIGNAL_RED;
+        }
+        h->n_signals = (int)ns;
+        UP(sig, sig);
+        UP(sig_state, sst);
+    }
     std::vector<int> one(1, 0);
     UP(counter, one);
     UP(dump_count, one);
@@ -986,6 +1028,21 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     }
     if (n) CK(cudaMemsetAsync(h->acc.p, 0, sizeof(float2) * n, s));  // accelerations restart
     if (n) CK(cudaMemsetAsync(h->jerk.p, 0, sizeof(float) * 3 * n, s));
+    return GP_OK;
+}
+
+gp_status gp_set_signal_states(gp_handle *h, const uint8_t *state, int on_host, void *stream) {
+    if (!h || !state) return fail(GP_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_signals;
+    if (on_host)
+        for (size_t i = 0; i < n; ++i)
+            if (state[i] > GP_SIGNAL_OFF) return fail(GP_EINVAL, "signal state must be 0..3");
+    if (n)
+        CK(cudaMemcpyAsync(h->sig_state.p, state, n,
+                           on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
     return GP_OK;
 }
 

@@ -14,6 +14,8 @@ constexpr int kMaxBoxes = GP_MAX_BOXES;
 constexpr int kClusterQuads = 32;  // quads per culling cluster = one quad per lane of a warp
 constexpr int kMaxClustersPerWorld = 4096;
 constexpr int kMaxBandRows = 128;  // rows per screen band (raster records pack band-relative rows)
+constexpr int kMaxSignals = GP_MAX_SIGNALS;
+constexpr int kSignalQuads = 32;   // faces of a signal polyhedron = one setup unit
 
 // Per-world table (device).
 struct WorldInfo {
@@ -26,7 +28,9 @@ struct WorldInfo {
     int lcell_begin;             // the same grid over lane-line quads
     int gnx, gny;
     float gx0, gy0, ginv;        // grid origin and inverse cell size
+    int sig_begin, n_sig;        // traffic-signal spheres
     uint32_t box_end, road_end;  // primitive-id class boundaries: box < box_end <= road < road_end
+    uint32_t line_end;           // <= line < line_end <= signal
 };
 
 // A culling cluster: up to kClusterQuads ground quads of one grid cell.
@@ -103,6 +107,9 @@ struct RenderParams {
     int key_f16, out_mode;
     float light[3], ambient;  // RGB output: unit direction towards the light, ambient term
     float colour[4][3];       // RGB output: class colours in [0, 1]
+    float sig_colour[4][3];   // RGB output: signal colours by state
+    const float4 *sig;        // signal spheres: x, y, z, r
+    const uint8_t *sig_state; // their states
     void *out;
     void *depth;
     int view_mod;            // 0, or write view v at slot v % view_mod (tuning scratch)

@@ -33,6 +33,7 @@
 // fixed IEEE FP32 operation sequence (explicit _rn intrinsics), so identical snapped
 // triangles give bit-identical keys on any implementation that follows the same sequence.
 #include <algorithm>
+#include <cmath>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -67,15 +68,32 @@ __device__ __forceinline__ int vtx_y(int xy) { return xy >> 16; }
 struct Cam {
     float px, py, s, c;  // camera position and yaw sin/cos
     int by0, by1;        // band rows, inclusive
-    uint32_t box_end, road_end;
+    uint32_t box_end, road_end, line_end;
+    int sig_begin;       // the world's first signal sphere
     int box_begin, ego, cl_begin;
     float gtx, gty;      // guard-band planes |x| <= gtx z, |y| <= gty z
     float vl, vt, vb;    // band edges widened by 1/4 px: |x| <= vl z, vb z <= y <= vt z
 };
 
 struct Smem {
-    size_t keys, tris, rowoff, map, clipscratch, vq0, vpre, vnq, visbox, clipq, total;
+    size_t keys, tris, rowoff, map, clipscratch, vq0, vpre, vnq, visbox, vissig, clipq, total;
 };
+
+// Traffic-signal polyhedron (4 latitude bands x 8 longitude sectors, vertices on the
+// sphere): cos/sin of the latitudes -90..90 deg (poles exact) and longitudes 0..315 deg;
+// per face q = 8 i + j the outward unit normal (xyz) and the plane's distance from the
+// centre in radii (w).  Filled by render_configure.
+__constant__ float c_lat_c[5], c_lat_s[5], c_lon_c[8], c_lon_s[8];
+__constant__ float4 c_sig_face[kSignalQuads];
+
+// Vertex (i, j) of a signal sphere (x, y, z, r); one rounding order for every caller, so
+// the triangles of a face and their clipped pieces share exact corners.
+__device__ __forceinline__ void sig_vertex(float4 sp, int i, int j, float &x, float &y, float &z) {
+    const float rc = __fmul_rn(sp.w, c_lat_c[i]);
+    x = __fadd_rn(sp.x, __fmul_rn(rc, c_lon_c[j & 7]));
+    y = __fadd_rn(sp.y, __fmul_rn(rc, c_lon_s[j & 7]));
+    z = __fadd_rn(sp.z, __fmul_rn(sp.w, c_lat_s[i]));
+}
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -114,6 +132,8 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     o += (size_t)max_cl;
     s.visbox = o;
     o += kMaxBoxes;
+    s.vissig = o;
+    o += kMaxSignals;
     o = align_up(o, 16);
     s.clipq = o;
     o += (size_t)kClipQueue * 4;
@@ -523,7 +543,7 @@ __device__ __forceinline__ int group_exclusive_max(int v, int *s_warp, const Gro
 
 // Block state of the setup side (the whole block, or the producer warps).
 struct Shared {
-    int item, resv, next_unit, npend, nvcl, nvbox, cq_n, nvq;
+    int item, resv, next_unit, npend, nvcl, nvbox, nvsig, cq_n, nvq;
 };
 
 // Rasterise a batch of n triangles into the key buffer of the band of rows by0..by1 (all
@@ -611,6 +631,7 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
 
 // World-space vertices and primitive id of a source triangle.
 //   code bit 31 set: box triangle, bits 4..11 local box index, bits 0..3 face triangle
+//   code bit 30 set: signal triangle, bits 6..10 local signal index, bits 0..5 2 q + t
 //   otherwise: quad (cluster order) << 1 | triangle
 __device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm, uint32_t code,
                                            float vx[3], float vy[3], float vz[3],
@@ -626,6 +647,15 @@ __device__ __forceinline__ void source_tri(const RenderParams &p, const Cam &cm,
 #pragma unroll
         for (int i = 0; i < 3; ++i) box_corner(pose, dim, s, c, k[i], vx[i], vy[i], vz[i]);
         prim = 12u * b + t;
+    } else if (code & 0x40000000u) {
+        const int sg = (code >> 6) & 31, q = (code >> 1) & 31, t = code & 1;
+        const float4 sp = p.sig[cm.sig_begin + sg];
+        const int i = q >> 3, j = q & 7;
+        // quad corners (i, j) (i, j+1) (i+1, j+1) (i+1, j); triangles (0 1 2), (0 2 3)
+        sig_vertex(sp, i, j, vx[0], vy[0], vz[0]);
+        sig_vertex(sp, t ? i + 1 : i, j + 1, vx[1], vy[1], vz[1]);
+        sig_vertex(sp, i + 1, t ? j : j + 1, vx[2], vy[2], vz[2]);
+        prim = cm.line_end + 64u * sg + 2u * q + t;
     } else {
         const int q = code >> 1, t = code & 1;
         const float4 g0 = p.quad_geo[2 * q], g1 = p.quad_geo[2 * q + 1];
@@ -767,6 +797,7 @@ __device__ __forceinline__ int cas_reserve(int *counter, int n, int cap) {
 
 // World-space corners of a source quad and the primitive id of its first triangle.
 //   code bit 31 set: box face, bits 4..11 local box index, bits 0..3 face index
+//   code bit 30 set: signal face, bits 5..9 local signal index, bits 0..4 face q
 //   otherwise: ground quad index (cluster order)
 // The quad's triangles are (q0 q1 q2) and (q0 q2 q3), primitive ids prim0 and prim0 + 1.
 __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm, uint32_t code,
@@ -786,6 +817,15 @@ __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm
         box_corner(pose, dim, s, c, k2, qx[2], qy[2], qz[2]);
         box_corner(pose, dim, s, c, k3, qx[3], qy[3], qz[3]);
         prim0 = 12u * b + 2u * face;
+    } else if (code & 0x40000000u) {
+        const int sg = (code >> 5) & 31, q = code & 31;
+        const float4 sp = p.sig[cm.sig_begin + sg];
+        const int i = q >> 3, j = q & 7;
+        sig_vertex(sp, i, j, qx[0], qy[0], qz[0]);
+        sig_vertex(sp, i, j + 1, qx[1], qy[1], qz[1]);
+        sig_vertex(sp, i + 1, j + 1, qx[2], qy[2], qz[2]);
+        sig_vertex(sp, i + 1, j, qx[3], qy[3], qz[3]);
+        prim0 = cm.line_end + 64u * sg + 2u * q;
     } else {
         const float4 g0 = p.quad_geo[2 * code], g1 = p.quad_geo[2 * code + 1];
         prim0 = p.quad_prim[code];
@@ -802,15 +842,16 @@ __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm
     }
 }
 
-// One setup unit: 32 quads (box faces, or the visible clusters' ground quads packed back to
-// back), one per lane, two triangles each
+// One setup unit: 32 quads (box faces, the 32 faces of one signal sphere, or the visible
+// clusters' ground quads packed back to back), one per lane, two triangles each
 // (warp-uniform call).  Returns false if the clip queue or the batch has no room;
 // `clips_queued` tells the retry (after a flush) whether this unit's clip jobs are already
 // queued.
 __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
                            uint32_t *clipq, const int *vq0, const int *vpre, int nvcl, int nvq,
-                           const unsigned char *visbox, int view, int unit, int n_box_units,
-                           int nbox_items, bool clips_done, bool &clips_queued) {
+                           const unsigned char *visbox, const unsigned char *vissig, int view,
+                           int unit, int n_box_units, int nbox_items, int n_sig_units,
+                           bool clips_done, bool &clips_queued) {
     const int lane = threadIdx.x & 31;
     uint32_t qcode = 0, tcode = 0;  // quad code; triangle-code base for the clip queue
     bool valid;
@@ -822,10 +863,15 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
             qcode = 0x80000000u | (b << 4) | face;
             tcode = 0x80000000u | (b << 4) | (2u * face);
         }
+    } else if (unit < n_box_units + n_sig_units) {
+        const uint32_t sg = vissig[unit - n_box_units];
+        valid = true;
+        qcode = 0x40000000u | (sg << 5) | (uint32_t)lane;
+        tcode = 0x40000000u | (sg << 6) | (2u * lane);
     } else {
         // the visible clusters' quads, packed 32 per unit: find this lane's cluster (the
         // last one whose first packed index is <= gq)
-        const int gq = (unit - n_box_units) * 32 + lane;
+        const int gq = (unit - n_box_units - n_sig_units) * 32 + lane;
         valid = gq < nvq;
         int lo = 0, hi = nvcl - 1;
         while (lo < hi) {
@@ -915,27 +961,36 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
     return true;
 }
 
-// Class of an inverted primitive id (0 = nothing covered): 3 box, 1 road, 2 lane line.
+// Class of an inverted primitive id (0 = nothing covered): 3 box, 1 road, 2 lane line,
+// 4 signal.
 __device__ __forceinline__ uint32_t class_of_low(uint32_t low, uint32_t full, const Cam &cm) {
     if (!low) return 0;
     const uint32_t prim = full - low;
-    return prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : 2u);
+    return prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : (prim < cm.line_end ? 2u : 4u));
 }
 
 // RGB observation of one pixel, 8 bits per channel in bytes 0..2 (App. A: one directional
 // light, a colour per instance): class colour x (ambient + (1 - ambient) max(0, n . l)), n
 // the winning surface's outward normal -- a box face's normal turned by the box yaw, +z for
-// the ground strips -- and the background unshaded; each channel rint(255 clamp(v, 0, 1)).
+// the ground strips, a signal face's normal (signals take their state's colour) -- and the
+// background unshaded; each channel rint(255 clamp(v, 0, 1)).
 // low = inverted primitive id (0 = background), full = the id's all-ones value.
 __device__ __forceinline__ uint32_t shade_rgb(const RenderParams &p, const Cam &cm, uint32_t low,
                                               uint32_t full) {
-    uint32_t cls = 0;
+    uint32_t cls = 0, state = 0;
     float shade = 1.f;
     if (low) {
         const uint32_t prim = full - low;
-        cls = prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : 2u);
+        cls = prim < cm.box_end ? 3u : (prim < cm.road_end ? 1u : (prim < cm.line_end ? 2u : 4u));
         float nx = 0.f, ny = 0.f, nz = 1.f;
-        if (cls == 3u) {
+        if (cls == 4u) {
+            const uint32_t rel = prim - cm.line_end;
+            const float4 fn = c_sig_face[(rel & 63u) >> 1];
+            nx = fn.x;
+            ny = fn.y;
+            nz = fn.z;
+            state = p.sig_state[cm.sig_begin + (rel >> 6)] & 3u;
+        } else if (cls == 3u) {
             const uint32_t b = prim / 12u, face = (prim % 12u) >> 1;
             float sn, c;
             sincosf(p.box_pose[cm.box_begin + b].z, &sn, &c);
@@ -950,9 +1005,10 @@ __device__ __forceinline__ uint32_t shade_rgb(const RenderParams &p, const Cam &
     uint32_t rgb = 0;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-        const float base = cls == 0u ? p.colour[0][ch]
-                                     : (cls == 1u ? p.colour[1][ch]
-                                                  : (cls == 2u ? p.colour[2][ch] : p.colour[3][ch]));
+        const float base = cls == 4u ? p.sig_colour[state][ch]
+                                     : (cls == 0u ? p.colour[0][ch]
+                                                  : (cls == 1u ? p.colour[1][ch]
+                                                               : (cls == 2u ? p.colour[2][ch] : p.colour[3][ch])));
         const float v = fminf(fmaxf(base * shade, 0.f), 1.f);
         rgb |= (uint32_t)__float2int_rn(255.f * v) << (8 * ch);
     }
@@ -979,11 +1035,14 @@ __device__ __forceinline__ void store_classes(const RenderParams &p, const Cam &
                        (((q[2] >> sh) & 0xFFu) << 16) | (((q[3] >> sh) & 0xFFu) << 24));
         }
     } else {
+        // signals (class 4) share the object channel 3 with the boxes
+        const uint32_t o[4] = {c[0] == 4u ? 3u : c[0], c[1] == 4u ? 3u : c[1], c[2] == 4u ? 3u : c[2],
+                               c[3] == 4u ? 3u : c[3]};
         for (int ch = 0; ch < 4; ++ch) {
-            const uint32_t lo = (uint32_t)p.onehot[ch][c[0] == (uint32_t)ch] |
-                                ((uint32_t)p.onehot[ch][c[1] == (uint32_t)ch] << 16);
-            const uint32_t hi = (uint32_t)p.onehot[ch][c[2] == (uint32_t)ch] |
-                                ((uint32_t)p.onehot[ch][c[3] == (uint32_t)ch] << 16);
+            const uint32_t lo = (uint32_t)p.onehot[ch][o[0] == (uint32_t)ch] |
+                                ((uint32_t)p.onehot[ch][o[1] == (uint32_t)ch] << 16);
+            const uint32_t hi = (uint32_t)p.onehot[ch][o[2] == (uint32_t)ch] |
+                                ((uint32_t)p.onehot[ch][o[3] == (uint32_t)ch] << 16);
             __stcs((uint2 *)((uint16_t *)p.out + (slot * 4 + ch) * plane + px), make_uint2(lo, hi));
         }
     }
@@ -1052,6 +1111,8 @@ __device__ __forceinline__ void view_cam(const RenderParams &p, int view, Cam &c
     cm.cl_begin = wi.cl_begin;
     cm.box_end = wi.box_end;
     cm.road_end = wi.road_end;
+    cm.line_end = wi.line_end;
+    cm.sig_begin = wi.sig_begin;
     const float4 pose = p.box_pose[wi.box_begin + cm.ego];
     cm.px = pose.x;
     cm.py = pose.y;
@@ -1091,8 +1152,9 @@ struct TraceBox {
 };
 
 // Ray-traced class (0 background) and, on a hit, primitive id and view depth t of pixel (i, j).
+// ts: the world's signal spheres as (camera - centre, radius), radius < 0 if culled.
 __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int i, int j,
-                           const TraceBox *tb, uint32_t &prim, float &t_hit) {
+                           const TraceBox *tb, const float4 *ts, uint32_t &prim, float &t_hit) {
     const float x = ((float)i + 0.5f - 0.5f * (float)p.W) / p.f;
     const float y = (0.5f * (float)p.H - (float)j - 0.5f) / p.f;
     // right = (sin psi, -cos psi, 0), up = +z, forward = (cos psi, sin psi, 0)
@@ -1162,6 +1224,42 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
             }
         }
     }
+    // signal spheres: the polyhedron as the intersection of its face half-spaces (entry at
+    // the largest entering-face parameter, the first such face on ties), after a reject
+    // against the circumscribed sphere
+    const float dd = dx * dx + dy * dy + dz * dz;
+    for (int sg = 0; sg < wi.n_sig; ++sg) {
+        const float4 S = ts[sg];
+        if (S.w < 0.f) continue;
+        const float b = S.x * dx + S.y * dy + S.z * dz;
+        const float c0 = S.x * S.x + S.y * S.y + S.z * S.z - S.w * S.w * 1.0001f - 1e-6f;
+        if (b * b < dd * c0) continue;  // the ray's line misses the circumsphere
+        float t0 = -INFINITY, t1 = INFINITY;
+        int face = -1;
+        bool inside = true;
+        for (int q = 0; q < kSignalQuads; ++q) {
+            const float4 F = c_sig_face[q];
+            const float den = F.x * dx + F.y * dy + F.z * dz;
+            const float num = F.w * S.w - (F.x * S.x + F.y * S.y + F.z * S.z);
+            if (den == 0.f) {
+                if (num < 0.f) inside = false;
+                continue;
+            }
+            const float t = num / den;
+            if (den < 0.f) {
+                if (t > t0) {
+                    t0 = t;
+                    face = q;
+                }
+            } else {
+                t1 = fminf(t1, t);
+            }
+        }
+        if (!inside || face < 0 || t0 > t1 || t0 < p.near_plane || !(t0 < best)) continue;
+        best = t0;
+        cls = 4;
+        prim = wi.line_end + 64u * (uint32_t)sg + 2u * (uint32_t)face + (face < 8 ? 1u : 0u);
+    }
     t_hit = best;
     return cls;
 }
@@ -1170,6 +1268,7 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
 // encode (class / one-hot / RGB, and FP32 depth or its binary16 bits).
 __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
     __shared__ TraceBox tb[kMaxBoxes];
+    __shared__ float4 ts[kMaxSignals];
     const int view = p.trace_view0 + (int)blockIdx.y;
     const long long plane = (long long)p.H * p.W;
     const int px0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -1200,6 +1299,16 @@ __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
         if (b == cm.ego || culled) B.hl = -1.f;
         tb[b] = B;
     }
+    for (int sg = threadIdx.x; sg < wi.n_sig; sg += blockDim.x) {
+        const float4 sp = p.sig[wi.sig_begin + sg];
+        const float ox = cm.px - sp.x, oy = cm.py - sp.y, oz = p.cam_h - sp.z;
+        // the same frustum test on the sphere's footprint circle
+        const float fwd = -(ox * cm.c + oy * cm.s), side = -ox * cm.s + oy * cm.c;
+        const float nrm = sqrtf(1.f + p.tx * p.tx);
+        const bool culled = fwd + sp.w < p.near_plane || (side + p.tx * fwd) < -sp.w * nrm ||
+                            (p.tx * fwd - side) < -sp.w * nrm;
+        ts[sg] = make_float4(ox, oy, oz, culled ? -1.f : sp.w);
+    }
     __syncthreads();
     if (px0 >= plane) return;
     const uint32_t full = p.key_f16 ? 0xFFFFu : 0xFFFFFFFFu;
@@ -1210,7 +1319,7 @@ __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
         const int pix = px0 + k, j = pix / p.W, i = pix - j * p.W;
         uint32_t prim;
         float t;
-        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, prim, t);
+        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, ts, prim, t);
         low[k] = c[k] ? full - prim : 0u;
         d[k] = c[k] ? __fdiv_rn(p.near_plane, t) : 0.f;
     }
@@ -1240,6 +1349,8 @@ __device__ __forceinline__ void make_cam(const RenderParams &p, int item, Cam &c
     cm.cl_begin = wi.cl_begin;
     cm.box_end = wi.box_end;
     cm.road_end = wi.road_end;
+    cm.line_end = wi.line_end;
+    cm.sig_begin = wi.sig_begin;
     const float4 pose = p.box_pose[wi.box_begin + cm.ego];
     cm.px = pose.x;
     cm.py = pose.y;
@@ -1267,6 +1378,7 @@ __device__ __forceinline__ int next_item(const RenderParams &p, Shared &sh, int 
         sh.npend = 0;
         sh.nvcl = 0;
         sh.nvbox = 0;
+        sh.nvsig = 0;
         sh.cq_n = 0;
     }
     g.sync();
@@ -1279,7 +1391,7 @@ struct SetupMem {
     uint32_t *clipq;
     float *clipscratch;
     int *vq0, *vpre;
-    unsigned char *vnq, *visbox;
+    unsigned char *vnq, *visbox, *vissig;
 };
 
 // Cull, set up and clip one (view, band) work item on group g.  Kept triangles fill the
@@ -1321,6 +1433,17 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
         const int k = warp_append(keep, &sh.nvbox);
         if (keep) m.visbox[k] = (unsigned char)b;
     }
+    for (int base = 0; base < wi.n_sig; base += g.nt) {
+        const int sg = base + g.tid;
+        bool keep = false;
+        if (sg < wi.n_sig) {
+            const float4 sp = p.sig[wi.sig_begin + sg];
+            const float h = sp.w * 1.0001f + 1e-4f;
+            keep = aabb_visible(p, cm, sp.x, sp.y, h, h, sp.z - h, sp.z + h);
+        }
+        const int k = warp_append(keep, &sh.nvsig);
+        if (keep) m.vissig[k] = (unsigned char)sg;
+    }
     g.sync();
     // packed positions of the visible clusters' quads (warp 0 scans the counts)
     if (g.warp() == 0) {
@@ -1347,7 +1470,8 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
     const int nbox_items = sh.nvbox * 6;  // one box face (two triangles) per lane
     const int n_box_units = (nbox_items + 31) / 32;
     const int nvcl = sh.nvcl, nvq = sh.nvq;
-    const int n_units = n_box_units + (nvq + 31) / 32;
+    const int n_sig_units = sh.nvsig;  // one signal sphere (32 faces) per unit
+    const int n_units = n_box_units + n_sig_units + (nvq + 31) / 32;
     int pend = -1;            // unit this warp could not place (warp-uniform)
     bool pend_clips = false;  // its clip jobs are already queued
     for (;;) {
@@ -1365,8 +1489,9 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
             }
             if (u >= n_units) break;
             bool queued = false;
-            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vpre, nvcl, nvq, m.visbox, view,
-                            u, n_box_units, nbox_items, done_clips, queued)) {
+            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vpre, nvcl, nvq, m.visbox,
+                            m.vissig, view, u, n_box_units, nbox_items, n_sig_units, done_clips,
+                            queued)) {
                 pend = u;
                 pend_clips = queued;
                 if ((g.tid & 31) == 0) atomicAdd(&sh.npend, 1);
@@ -1425,7 +1550,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     unsigned short *map = (unsigned short *)(smem + L.map);
     SetupMem m{tris, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
                (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
-               smem + L.visbox};
+               smem + L.visbox, smem + L.vissig};
 
     for (int b = g.tid; b < (F32 ? 2 : 1) * p.band_rows * p.W; b += g.nt) keys[b] = 0;
 
@@ -1454,8 +1579,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
 
 // What a raster batch of the pipelined kernel carries besides its triangles.
 struct BatchMeta {
-    int n, view, by0, by1, box_begin;
-    uint32_t box_end, road_end;
+    int n, view, by0, by1, box_begin, sig_begin;
+    uint32_t box_end, road_end, line_end;
     int flags;  // kBatchLast: the item's last batch (encode after it); kBatchEnd: no more work
 };
 constexpr int kBatchLast = 1, kBatchEnd = 2;
@@ -1547,7 +1672,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
         const Group g{(int)threadIdx.x, nprod, 1};
         SetupMem m{tris0, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
                    (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
-               smem + L.visbox};
+               smem + L.visbox, smem + L.vissig};
         Cam cm;
         WorldInfo wi;
         int view = 0;
@@ -1558,8 +1683,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             g.sync();
             const int b = s & 1;
             if (g.tid == 0) {
-                meta[b] = BatchMeta{sh.resv, view, cm.by0, cm.by1, cm.box_begin, cm.box_end,
-                                    cm.road_end, last ? kBatchLast : 0};
+                meta[b] = BatchMeta{sh.resv, view, cm.by0, cm.by1, cm.box_begin, cm.sig_begin,
+                                    cm.box_end, cm.road_end, cm.line_end, last ? kBatchLast : 0};
                 sh.resv = 0;
             }
             mbar_arrive(&bars[b]);  // release: this thread's records (and thread 0's meta)
@@ -1612,6 +1737,8 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
                 cm.box_begin = mt.box_begin;
                 cm.box_end = mt.box_end;
                 cm.road_end = mt.road_end;
+                cm.line_end = mt.line_end;
+                cm.sig_begin = mt.sig_begin;
                 if (F32) encode_f32(p, cm, (unsigned long long *)keys, mt.view, g);
                 else encode_f16(p, cm, keys, mt.view, g);
                 g.sync();
@@ -1640,6 +1767,50 @@ size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri
     return smem_layout(W, band_rows, key_f16, threads, tri_cap, max_cl, prod_warps).total;
 }
 
+// The signal polyhedron's tables, computed in double on the host and rounded once.
+static cudaError_t upload_signal_tables() {
+    const double pi = 3.14159265358979323846;
+    float lat_c[5], lat_s[5], lon_c[8], lon_s[8];
+    double V[5][8][3];
+    for (int i = 0; i < 5; ++i) {
+        const double th = -0.5 * pi + 0.25 * pi * i;
+        const double ct = (i == 0 || i == 4) ? 0.0 : std::cos(th), st = std::sin(th);
+        lat_c[i] = (float)ct;
+        lat_s[i] = (float)st;
+        for (int j = 0; j < 8; ++j) {
+            const double ph = 0.25 * pi * j;
+            V[i][j][0] = ct * std::cos(ph);
+            V[i][j][1] = ct * std::sin(ph);
+            V[i][j][2] = st;
+        }
+    }
+    for (int j = 0; j < 8; ++j) {
+        lon_c[j] = (float)std::cos(0.25 * pi * j);
+        lon_s[j] = (float)std::sin(0.25 * pi * j);
+    }
+    float4 face[kSignalQuads];
+    for (int q = 0; q < kSignalQuads; ++q) {
+        const int i = q / 8, j = q % 8, j1 = (j + 1) % 8;
+        // three distinct corners of the face: the south-pole band's corners 0 and 1 coincide
+        const double *a = V[i][j];
+        const double *b = i == 0 ? V[i + 1][j1] : V[i][j1];
+        const double *c = i == 0 ? V[i + 1][j] : V[i + 1][j1];
+        const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (double &x : n) x /= len;
+        face[q] = make_float4((float)n[0], (float)n[1], (float)n[2],
+                              (float)(n[0] * a[0] + n[1] * a[1] + n[2] * a[2]));
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(c_lat_c, lat_c, sizeof lat_c)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_lat_s, lat_s, sizeof lat_s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_lon_c, lon_c, sizeof lon_c)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_lon_s, lon_s, sizeof lon_s)) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(c_sig_face, face, sizeof face);
+}
+
 cudaError_t render_configure(size_t max_smem) {
     const void *fns[4] = {(const void *)render_kernel<true>, (const void *)render_kernel<false>,
                           (const void *)render_kernel_ws<true>, (const void *)render_kernel_ws<false>};
@@ -1648,7 +1819,7 @@ cudaError_t render_configure(size_t max_smem) {
                                              (int)max_smem);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return upload_signal_tables();
 }
 
 static const void *render_fn(int key_f16, int prod_warps) {

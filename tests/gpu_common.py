@@ -46,11 +46,12 @@ def oracle_raster_of(worlds, cfg, view, tris):
     w, _, _ = view_loc(worlds, cfg, view)
     nb = int(worlds.box_off[w + 1] - worlds.box_off[w])
     nr = int(worlds.road_off[w + 1] - worlds.road_off[w])
+    nl = int(worlds.line_off[w + 1] - worlds.line_off[w])
     t = np.zeros(len(tris), oracle.TRI_DTYPE)
     for k in ("X", "Y", "d", "prim", "sub"):
         t[k] = tris[k]
     return oracle.raster(t, int(cfg.width), int(cfg.height), bool(cfg.key_precision), 12 * nb,
-                         12 * nb + 2 * nr)
+                         12 * nb + 2 * nr, line_end=12 * nb + 2 * nr + 2 * nl)
 
 
 def gpu_view(cfg, out, depth, view):
