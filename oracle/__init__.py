@@ -100,6 +100,8 @@ def _lib():
                                          ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                          ctypes.c_double, c_f64p, c_f64p, c_f64p]
+        lib.or_observe_signals.argtypes = [ctypes.c_int32, c_f64p, ctypes.c_int32, c_f64p, c_u8p,
+                                           ctypes.c_int32, ctypes.c_double, c_f64p, c_f64p]
         lib.or_lane_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, c_f32p,
                                       ctypes.c_double, c_f64p, c_f64p]
         lib.or_lane_frame.restype = ctypes.c_int
@@ -315,6 +317,21 @@ def observe_world(boxes6, speed, road, line, K=OBS_AGENTS, r_agents=OBS_AGENT_RA
                             _p(rd, c_f32p), ln.shape[0], _p(ln, c_f32p), K, float(r_agents), M,
                             float(r_roads), _p(ao, c_f64p), _p(ro, c_f64p), _p(scratch, c_f64p))
     return ao, ro
+
+
+OBS_SIGNALS, OBS_SIGNAL_RADIUS = 4, 50.0
+
+
+def observe_signals(boxes6, n_agents, sph, state, S=OBS_SIGNALS, r_sig=OBS_SIGNAL_RADIUS):
+    """Traffic controls of O_vec for a world's agents: [n_agents, S, 8] (or_observe_signals)."""
+    b = _c(boxes6, np.float64).reshape(-1, 6)
+    sp = _sph(sph)
+    st = _c(np.zeros(sp.shape[0]) if state is None else state, np.uint8)
+    out = np.zeros((n_agents, S, 8), np.float64)
+    scratch = np.zeros(2 * max(1, sp.shape[0]), np.float64)
+    _lib().or_observe_signals(n_agents, _p(b, c_f64p), sp.shape[0], _p(sp, c_f64p), _p(st, c_u8p),
+                              S, float(r_sig), _p(out, c_f64p), _p(scratch, c_f64p))
+    return out
 
 
 def lane_frame(px: float, py: float, road: np.ndarray, lane_w: float = LANE_WIDTH):

@@ -439,6 +439,45 @@ void or_observe_world(int32_t n_boxes, int32_t n_agents, const double *boxes, co
     }
 }
 
+/*
+ * Traffic controls of O_vec (App. A "Observations": the vectorized observation also holds
+ * traffic-control states).  Reading: per agent i the signal spheres s whose centre is
+ * within r_sig of c_i on the ground plane, nearest first (ties to the lower index), at
+ * most S; slot = [1, x / r_sig, y / r_sig (ego frame, x forward, y left), z_s / 10,
+ * 1[red], 1[amber], 1[green], 1[off]]; unused slots zero.
+ *   boxes [n_agents..][6]; sph [n_sph][4] x, y, z, r; state [n_sph] -> out [n_agents][S][8]
+ */
+void or_observe_signals(int32_t n_agents, const double *boxes, int32_t n_sph, const double *sph,
+                        const uint8_t *state, int32_t S, double r_sig, double *out,
+                        double *scratch /* >= 2 * n_sph */) {
+    for (int32_t i = 0; i < n_agents; ++i) {
+        const double *bi = boxes + 6 * i;
+        const double c = cos(bi[2]), sn = sin(bi[2]);
+        double *so = out + (int64_t)i * S * 8;
+        memset(so, 0, sizeof(double) * S * 8);
+        int32_t n = 0;
+        for (int32_t s = 0; s < n_sph; ++s) {
+            const double d = hypot(sph[4 * s] - bi[0], sph[4 * s + 1] - bi[1]);
+            if (d <= r_sig) {
+                scratch[2 * n] = d;
+                scratch[2 * n + 1] = s;
+                ++n;
+            }
+        }
+        qsort(scratch, (size_t)n, 2 * sizeof(double), cmp_key);
+        for (int32_t k = 0; k < n && k < S; ++k) {
+            const int32_t s = (int32_t)scratch[2 * k + 1];
+            const double dx = sph[4 * s] - bi[0], dy = sph[4 * s + 1] - bi[1];
+            double *o = so + 8 * k;
+            o[0] = 1.0;
+            o[1] = (dx * c + dy * sn) / r_sig;
+            o[2] = (-dx * sn + dy * c) / r_sig;
+            o[3] = sph[4 * s + 2] / 10.0;
+            o[4 + (state[s] & 3)] = 1.0;
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------------------
  * Geometry: camera, scene triangles, clipping, projection, snapping (FP64)
  * ------------------------------------------------------------------------------------ */

@@ -78,6 +78,9 @@ MUTANTS = {
     "signal colour ignores state": ("                base = sig_colour + 3 * sph_state[s];", "                base = sig_colour;"),
     "signal one-hot channel": ("val[c][cls[p] == c || (c == 3 && cls[p] == 4)]", "val[c][cls[p] == c]"),
     "sphere ids overlap lines": ("const uint32_t sbase = (uint32_t)(12 * n_boxes + 2 * n_road + 2 * n_line);", "const uint32_t sbase = (uint32_t)(12 * n_boxes + 2 * n_road);"),
+    "ovec signal lateral sign": ("            o[2] = (-dx * sn + dy * c) / r_sig;", "            o[2] = (dx * sn - dy * c) / r_sig;"),
+    "ovec signal state slot": ("            o[4 + (state[s] & 3)] = 1.0;", "            o[4 + ((state[s] + 1) & 3)] = 1.0;"),
+    "ovec signal radius": ("            if (d <= r_sig) {", "            if (d < r_sig) {"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

@@ -1446,3 +1446,27 @@ def test_signal_class_and_onehot_channel():
     assert list(oh[0]) == [hot, cold, cold, cold, cold]
     img, _ = render_scene(CamConfig(32, 32), [ego_box()], sph=np.array([[6.0, 0.0, 1.5, 1.0]]))
     assert (img.cls == 4).sum() > 10 and set(np.unique(img.cls)) == {0, 4}
+
+
+def test_ovec_signals_frame_order_and_state():
+    # ego at the origin facing +y: world +y is ego-forward (x), world -x is ego-left (y)
+    boxes = np.array([[0.0, 0.0, math.pi / 2, 4.5, 1.9, 1.5]])
+    sph = [[-10.0, 0.0, 5.0, 0.4],    # 10 m left, red
+           [0.0, 30.0, 4.0, 0.4],     # 30 m ahead, green
+           [10.0, 0.0, 6.0, 0.4],     # 10 m right, amber: ties with signal 0, higher index
+           [0.0, -50.0, 5.0, 0.4],    # exactly at the radius: included
+           [0.0, 50.001, 5.0, 0.4],   # just outside
+           [3.0, 4.0, 5.0, 0.4]]      # 5 m: the nearest, off
+    st = [0, 2, 1, 0, 0, 3]
+    o = oracle.observe_signals(boxes, 1, sph, st)[0]
+    assert o.shape == (4, 8)
+    # order: 5 m (index 5), 10 m (index 0 before 2), then 30 m; the 50 m one is 5th
+    want = [[1, 4 / 50, -3 / 50, 0.5, 0, 0, 0, 1],
+            [1, 0.0, 10 / 50, 0.5, 1, 0, 0, 0],
+            [1, 0.0, -10 / 50, 0.6, 0, 1, 0, 0],
+            [1, 30 / 50, 0.0, 0.4, 0, 0, 1, 0]]
+    assert np.allclose(o, want, atol=1e-12)
+    # with fewer candidates the 50 m signal appears and the rest stays zero
+    o2 = oracle.observe_signals(boxes, 1, [sph[3], sph[4]], [2, 1])[0]
+    assert np.allclose(o2[0], [1, -1.0, 0.0, 0.5, 0, 0, 1, 0], atol=1e-12)
+    assert not o2[1:].any()
