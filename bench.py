@@ -416,17 +416,18 @@ def main():
             "render_gbs": algo_bytes / (tr_ms / 1e3) / 1e9,
             "render_frac_of_measured_hbm": algo_bytes / (tr_ms / 1e3) / 1e9 / peak,
             "note": "one ray per pixel: box slabs, lane-line and road plane hits via the grid"}
-        # vectorized observations O_vec of every agent (16 agent + 32 road slots)
-        ga, gr = sim.observe_vec()
+        # vectorized observations O_vec of every agent (16 agent, 32 road, 4 signal slots)
+        obs = sim.observe_vec(stream=stream)
         barrier()
         eo = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         eo[0].record(stream)
         for k in range(10):
-            sim.observe_vec()
+            sim.observe_vec(stream=stream, out=obs)
         eo[1].record(stream)
         barrier()
         extras["observe_vec"] = {"ms_per_call": maxred(eo[0].elapsed_time(eo[1])) / 10,
-                                 "agents": n_agents, "slots_per_agent": [16, 32]}
+                                 "agents": n_agents, "slots_per_agent": [16, 32, 4],
+                                 "note": "one warp per agent, nearest-K by warp sort/merge"}
         # the same batch with the reward terms and ego state computed in every step
         sim_w = Simulator(worlds, config_for(wl_rank, rewards=1, autotune=1), device=local)
         extras["with_rewards"] = graph_rate(sim_w, worlds, wl_rank, 20)

@@ -75,6 +75,8 @@ enum { GP_SIGNAL_RED = 0, GP_SIGNAL_AMBER = 1, GP_SIGNAL_GREEN = 2, GP_SIGNAL_OF
 #define GP_OBS_AGENT_RADIUS 100.0f
 #define GP_OBS_ROADS 32          /* road-segment slots per agent */
 #define GP_OBS_ROAD_RADIUS 30.0f
+#define GP_OBS_SIGNALS 4         /* traffic-signal slots per agent */
+#define GP_OBS_SIGNAL_RADIUS 50.0f
 /* Ego-state width (gp_get_rewards) */
 #define GP_EGO_DIM 9
 
@@ -311,8 +313,7 @@ gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host,
 
 /*
  * Vectorized observations O_vec of every agent from the current state (App. A
- * "Observations"; the synthetic worlds have no traffic controls).  Ego frame: x forward,
- * y left.
+ * "Observations"), one warp per agent.  Ego frame: x forward, y left.
  *   agents_dev  float [n_agents][GP_OBS_AGENTS][8]: the other boxes (agents and static
  *               boxes) within GP_OBS_AGENT_RADIUS, nearest first (ties to the lower index);
  *               slot = [1, x / R, y / R, L / 10, W / 5, cos dth, sin dth, (v_j - v_i) / 30]
@@ -321,9 +322,14 @@ gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host,
  *               with midpoint within GP_OBS_ROAD_RADIUS, nearest first (ties: roads before
  *               lines, then lower index), found through the world's spatial grid;
  *               slot = [1, x / R, y / R, length / R, cos dphi, sin dphi, 1[road], 1[line]]
- * Unused slots are zero.  Either pointer may be NULL; both 16-byte aligned.  Asynchronous.
+ *   signals_dev float [n_agents][GP_OBS_SIGNALS][8]: the traffic-signal spheres with
+ *               centre within GP_OBS_SIGNAL_RADIUS on the ground plane, nearest first
+ *               (ties to the lower index); slot = [1, x / R, y / R, z / 10, 1[red],
+ *               1[amber], 1[green], 1[off]] (traffic controls)
+ * Unused slots are zero.  Any pointer may be NULL; all 16-byte aligned.  Asynchronous.
  */
-gp_status gp_observe_vec(gp_handle *h, float *agents_dev, float *roads_dev, void *stream);
+gp_status gp_observe_vec(gp_handle *h, float *agents_dev, float *roads_dev, float *signals_dev,
+                         void *stream);
 
 /* Read (synchronously) / clear the device status word; set bits for tests. */
 gp_status gp_get_status(gp_handle *h, uint32_t *bits);

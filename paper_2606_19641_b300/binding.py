@@ -114,7 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_debug_inject_status": [vp, u32],
         "gp_get_rewards": [vp, vp, vp, i32, vp],
         "gp_trace": [vp, vp, vp, vp],
-        "gp_observe_vec": [vp, vp, vp, vp],
+        "gp_observe_vec": [vp, vp, vp, vp, vp],
         "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_get_dynamics": [vp, vp, i32, vp],
         "gp_set_signal_states": [vp, vp, i32, vp],
@@ -303,14 +303,17 @@ class Simulator:
         """Ray-traced render of every camera into the same tensors as render()."""
         check(lib().gp_trace(self._h, _ptr(out), _ptr(depth), _stream(stream)))
 
-    def observe_vec(self, stream=None):
-        """(agents [n_agents, 16, 8], roads [n_agents, 32, 8]) float32 O_vec on the device."""
+    def observe_vec(self, stream=None, out=None):
+        """(agents [n_agents, 16, 8], roads [n_agents, 32, 8], signals [n_agents, 4, 8])
+        float32 O_vec on the device (into `out`, a tuple of such tensors, if given)."""
         import torch
-        dev = torch.device("cuda", self.device)
-        a = torch.empty((self.n_agents, 16, 8), dtype=torch.float32, device=dev)
-        r = torch.empty((self.n_agents, 32, 8), dtype=torch.float32, device=dev)
-        check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _stream(stream)))
-        return a, r
+        if out is None:
+            dev = torch.device("cuda", self.device)
+            out = tuple(torch.empty((self.n_agents, k, 8), dtype=torch.float32, device=dev)
+                        for k in (16, 32, 4))
+        a, r, s = out
+        check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
+        return a, r, s
 
     def set_signal_states(self, states) -> None:
         """Traffic-signal states uint8 [n_signals] (0 red, 1 amber, 2 green, 3 off): host

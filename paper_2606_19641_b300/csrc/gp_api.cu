@@ -83,8 +83,8 @@ struct gp_handle {
     DevBuf<uint8_t> sig_state;
     DevBuf<float> speed;
     DevBuf<uint8_t> flags;
-    DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, counter,
-        dump_count;
+    DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, seg_off,
+        seg_list, counter, dump_count;
     DevBuf<Cluster> clusters;
     DevBuf<uint32_t> quad_prim, status;
     DevBuf<int2> items;
@@ -551,6 +551,8 @@ void release_all(gp_handle *h) {
     h->line_geo.release();
     h->lcell_off.release();
     h->lcell_quads.release();
+    h->seg_off.release();
+    h->seg_list.release();
     h->counter.release();
     h->dump_count.release();
     h->clusters.release();
@@ -640,7 +642,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     std::vector<Cluster> clusters;
     std::vector<float4> quad_geo, road_geo, line_geo;
     std::vector<uint32_t> quad_prim;
-    std::vector<int> cell_off(1, 0), cell_quads, lcell_off(1, 0), lcell_quads;
+    std::vector<int> cell_off(1, 0), cell_quads, lcell_off(1, 0), lcell_quads, seg_off(1, 0),
+        seg_list;
     h->worlds_h.resize(nw);
     for (int w = 0; w < nw; ++w) {
         WorldInfo wi{};
@@ -719,6 +722,25 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, cell_off, cell_quads);
         wi.lcell_begin = (int)lcell_off.size() - 1;
         build_cells(d->line + 8 * (size_t)l0, nl, wi.line_begin, lcell_off, lcell_quads);
+        // each road/line segment once, in the cell of its centre-line midpoint (the same
+        // FP32 expressions as the observation kernel's, so both agree on the cell)
+        {
+            wi.scell_begin = (int)seg_off.size() - 1;
+            std::vector<std::vector<int>> cells((size_t)wi.gnx * wi.gny);
+            for (int s = 0; s < nr + nl; ++s) {
+                const float *q = s < nr ? d->road + 8 * (size_t)(r0 + s) : d->line + 8 * (size_t)(l0 + s - nr);
+                const float ax = 0.5f * (q[0] + q[6]), ay = 0.5f * (q[1] + q[7]);
+                const float bx = 0.5f * (q[2] + q[4]), by = 0.5f * (q[3] + q[5]);
+                const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by);
+                const int cx = std::min(wi.gnx - 1, std::max(0, (int)std::floor((mx - wi.gx0) * wi.ginv)));
+                const int cy = std::min(wi.gny - 1, std::max(0, (int)std::floor((my - wi.gy0) * wi.ginv)));
+                cells[(size_t)cy * wi.gnx + cx].push_back(s);
+            }
+            for (auto &cl : cells) {
+                seg_list.insert(seg_list.end(), cl.begin(), cl.end());
+                seg_off.push_back((int)seg_list.size());
+            }
+        }
         // culling clusters: quads bucketed by the 16 m cell of their centroid, chunks of 16
         {
             const float cc = 16.f;
@@ -823,6 +845,9 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(line_geo, line_geo);
     UP(lcell_off, lcell_off);
     UP(lcell_quads, lcell_quads);
+    if (seg_list.empty()) seg_list.push_back(0);
+    UP(seg_off, seg_off);
+    UP(seg_list, seg_list);
     {
         const size_t ns = d->signal_off ? (size_t)d->signal_off[nw] : 0;
         std::vector<float4> sig(std::max<size_t>(ns, 1), make_float4(0.f, 0.f, 0.f, 1.f));
@@ -1073,26 +1098,29 @@ gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *str
     return GP_OK;
 }
 
-gp_status gp_observe_vec(gp_handle *h, float *agents, float *roads, void *stream) {
+gp_status gp_observe_vec(gp_handle *h, float *agents, float *roads, float *signals, void *stream) {
     if (!h) return fail(GP_EINVAL, "null handle");
-    if ((agents && !aligned16(agents)) || (roads && !aligned16(roads)))
+    if ((agents && !aligned16(agents)) || (roads && !aligned16(roads)) ||
+        (signals && !aligned16(signals)))
         return fail(GP_EINVAL, "outputs must be 16-byte aligned");
     CK(cudaSetDevice(h->device));
     ObsParams p{};
     p.worlds = h->worlds.p;
-    p.n_worlds = h->n_worlds;
+    p.agent_world = h->agent_world.p;
+    p.n_agents = h->n_agents;
     p.box_pose = h->box_pose.p;
     p.box_dim = h->box_dim.p;
     p.speed = h->speed.p;
     p.road_geo = h->road_geo.p;
     p.line_geo = h->line_geo.p;
-    p.cell_off = h->cell_off.p;
-    p.cell_quads = h->cell_quads.p;
-    p.lcell_off = h->lcell_off.p;
-    p.lcell_quads = h->lcell_quads.p;
+    p.seg_off = h->seg_off.p;
+    p.seg_list = h->seg_list.p;
+    p.sig = h->sig.p;
+    p.sig_state = h->sig_state.p;
     p.agents_out = agents;
     p.roads_out = roads;
-    CK(launch_obs(p, 8 * h->sms, (cudaStream_t)stream));
+    p.signals_out = signals;
+    CK(launch_obs(p, (cudaStream_t)stream));
     return GP_OK;
 }
 

@@ -26,6 +26,8 @@ struct WorldInfo {
     int line_begin, n_line;      // lane-line quads in original order (ray tracing)
     int cell_begin;              // off-road grid: cells [cell_begin, cell_begin + gnx*gny)
     int lcell_begin;             // the same grid over lane-line quads
+    int scell_begin;             // the same grid listing each road/line segment once, in the
+                                 // cell of its centre-line midpoint (ids: road r, n_road + line l)
     int gnx, gny;
     float gx0, gy0, ginv;        // grid origin and inverse cell size
     int sig_begin, n_sig;        // traffic-signal spheres
@@ -68,15 +70,19 @@ struct StepParams {
 // Vectorized observations (gp_observe_vec).
 struct ObsParams {
     const WorldInfo *worlds;
-    int n_worlds;
+    const int *agent_world;
+    int n_agents;
     const float4 *box_pose, *box_dim;
     const float *speed;
     const float4 *road_geo, *line_geo;
-    const int *cell_off, *cell_quads, *lcell_off, *lcell_quads;
-    float *agents_out;  // [n_agents][GP_OBS_AGENTS][8] or null
-    float *roads_out;   // [n_agents][GP_OBS_ROADS][8] or null
+    const int *seg_off, *seg_list;  // midpoint grid (WorldInfo::scell_begin)
+    const float4 *sig;
+    const uint8_t *sig_state;
+    float *agents_out;   // [n_agents][GP_OBS_AGENTS][8] or null
+    float *roads_out;    // [n_agents][GP_OBS_ROADS][8] or null
+    float *signals_out;  // [n_agents][GP_OBS_SIGNALS][8] or null
 };
-cudaError_t launch_obs(const ObsParams &p, int max_blocks, cudaStream_t s);
+cudaError_t launch_obs(const ObsParams &p, cudaStream_t s);
 
 // Snapped triangle as dumped for parity checks (matches gp_debug_dump_tris records).
 struct DumpTri {

@@ -762,24 +762,38 @@ def _sure_limit(d, cap, radius, eps):
 
 
 def _rows(x, scale, limit):
-    """Valid slots nearer than limit, as a set: rows sorted by their rounded features
-    (near-equal distances may order differently in FP32 and FP64)."""
+    """Valid slots nearer than limit (near-equal distances may order differently in FP32
+    and FP64, so they are compared as sets with _same_rows)."""
     v = x[x[:, 0] > 0]
-    v = v[np.hypot(v[:, 1], v[:, 2]) * scale < limit]
-    return v[np.lexsort(np.round(v, 3).T[::-1])]
+    return v[np.hypot(v[:, 1], v[:, 2]) * scale < limit]
 
 
-@pytest.mark.parametrize("name,n_worlds", [("uniform", 3), ("ragged", 4)])
+def _same_rows(a, b, atol):
+    """a and b hold the same rows up to atol, in any order (a one-to-one matching)."""
+    if a.shape != b.shape:
+        return False
+    used = np.zeros(len(b), bool)
+    for r in a:
+        hit = np.flatnonzero(~used & np.all(np.abs(b - r) <= atol, axis=1))
+        if len(hit) == 0:
+            return False
+        used[hit[0]] = True
+    return True
+
+
+@pytest.mark.parametrize("name,n_worlds", [("uniform", 3), ("ragged", 4), ("paper_rig_210x126", 3)])
 def test_observe_vec_matches_oracle(name, n_worlds):
     import torch
     wl = wg.WORKLOADS[name]
     worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    if wl.signals:
+        wg.add_signals(worlds, 24, wl.seed, height=5.0)  # denser: more than 4 in range
     sim, cfg = sim_for(worlds, wl)
     for k in range(3):
         sim.step(torch_actions(worlds, k, wl.seed)[0])
-    ga, gr = sim.observe_vec()
+    ga, gr, gs = sim.observe_vec()
     torch.cuda.synchronize()
-    ga, gr = ga.cpu().numpy(), gr.cpu().numpy()
+    ga, gr, gs = ga.cpu().numpy(), gr.cpu().numpy(), gs.cpu().numpy()
     st, fl = sim.get_state()
     osim = oracle_sim(worlds, sim)
     off = worlds.agent_offsets()
@@ -792,6 +806,18 @@ def test_observe_vec_matches_oracle(name, n_worlds):
         sp[:a1 - a0] = st[a0:a1, 3]
         road, line = osim.road(w), osim.line(w)
         oa, orr = oracle.observe_world(b, sp, road, line, n_agents=a1 - a0)
+        sph, sst = osim.signals(w)
+        osg = oracle.observe_signals(b, a1 - a0, sph, sst)
+        for i in range(a1 - a0):
+            ds = np.hypot(sph[:, 0] - b[i, 0], sph[:, 1] - b[i, 1])
+            ls, _ = _sure_limit(ds, 4, 50.0, 1e-3)
+            ra, rb = _rows(gs[a0 + i], 50.0, ls), _rows(osg[i], 50.0, ls)
+            assert _same_rows(ra, rb, 2e-5), "signals, agent %d" % (a0 + i)
+            compared_rows[0] += len(ra)
+        if wl.signals:
+            assert (gs[a0:a1, :, 0] > 0).sum() > 2 * (a1 - a0)
+        else:
+            assert not gs[a0:a1].any()
         segs = np.concatenate([road, line]).astype(np.float64).reshape(-1, 4, 2)
         mid = 0.25 * (segs[:, 0] + segs[:, 3] + segs[:, 1] + segs[:, 2])
         for i in range(a1 - a0):
@@ -803,7 +829,7 @@ def test_observe_vec_matches_oracle(name, n_worlds):
             skipped += int(not full)
             for g, o, scale, lim in ((ga[a0 + i], oa[i], 100.0, la), (gr[a0 + i], orr[i], 30.0, lr)):
                 ra, rb = _rows(g, scale, lim), _rows(o, scale, lim)
-                assert ra.shape == rb.shape and np.allclose(ra, rb, atol=2e-5), "agent %d" % (a0 + i)
+                assert _same_rows(ra, rb, 2e-5), "agent %d" % (a0 + i)
                 compared_rows[0] += len(ra)
                 # nearest first: the GPU's slot distances are non-decreasing
                 v = g[g[:, 0] > 0]
