@@ -681,7 +681,7 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
             }
         }
         // off-road grid: 8 m cells over the bounding box of the road and lane-line quads; a
-        // quad is listed in every cell its bounding box touches (widened by one cell), so any
+        // quad is listed in every cell its bounding box touches (widened by 1 mm), so any
         // point inside it finds it.  A second CSR over the same cells lists the lane lines.
         const float cs = 8.f;
         if (nr + nl == 0) {
@@ -705,10 +705,14 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
                     qy0 = std::min(qy0, q[2 * k + 1]);
                     qy1 = std::max(qy1, q[2 * k + 1]);
                 }
-                const int cx0 = std::max(0, (int)std::floor((qx0 - bx0) / cs) - 1);
-                const int cx1 = std::min(wi.gnx - 1, (int)std::floor((qx1 - bx0) / cs) + 1);
-                const int cy0 = std::max(0, (int)std::floor((qy0 - by0) / cs) - 1);
-                const int cy1 = std::min(wi.gny - 1, (int)std::floor((qy1 - by0) / cs) + 1);
+                // the cells of the bounding box widened by 1 mm: a point that passes the FP32
+                // containment test lies within rounding of the box, and the kernels' cell
+                // index floor((p - origin) * ginv) is monotone in p
+                const float eps = 1e-3f;
+                const int cx0 = std::max(0, (int)std::floor((qx0 - eps - bx0) * wi.ginv));
+                const int cx1 = std::min(wi.gnx - 1, (int)std::floor((qx1 + eps - bx0) * wi.ginv));
+                const int cy0 = std::max(0, (int)std::floor((qy0 - eps - by0) * wi.ginv));
+                const int cy1 = std::min(wi.gny - 1, (int)std::floor((qy1 + eps - by0) * wi.ginv));
                 for (int cy = cy0; cy <= cy1; ++cy)
                     for (int cx = cx0; cx <= cx1; ++cx)
                         cells[(size_t)cy * wi.gnx + cx].push_back(index_base + r);

@@ -1152,9 +1152,11 @@ struct TraceBox {
 };
 
 // Ray-traced class (0 background) and, on a hit, primitive id and view depth t of pixel (i, j).
-// ts: the world's signal spheres as (camera - centre, radius), radius < 0 if culled.
+// blist[0, nb): the boxes that can appear in this block's rows, in index order; ts: the
+// world's signal spheres as (camera - centre, radius), radius < 0 if culled.
 __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int i, int j,
-                           const TraceBox *tb, const float4 *ts, uint32_t &prim, float &t_hit) {
+                           const TraceBox *tb, const unsigned char *blist, int nb,
+                           const float4 *ts, uint32_t &prim, float &t_hit) {
     const float x = ((float)i + 0.5f - 0.5f * (float)p.W) / p.f;
     const float y = (0.5f * (float)p.H - (float)j - 0.5f) / p.f;
     // right = (sin psi, -cos psi, 0), up = +z, forward = (cos psi, sin psi, 0)
@@ -1163,9 +1165,9 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
     float best = INFINITY;
     int cls = 0;
     prim = 0xFFFFFFFFu;
-    for (int b = 0; b < wi.n_boxes; ++b) {
+    for (int k = 0; k < nb; ++k) {
+        const int b = blist[k];
         const TraceBox B = tb[b];
-        if (B.hl < 0.f) continue;
         const float cs = B.cs, sn = B.sn;
         const float o[3] = {B.ox, B.oy, oz};
         const float d[3] = {cs * dx + sn * dy, -sn * dx + cs * dy, dz};
@@ -1269,14 +1271,21 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
 __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
     __shared__ TraceBox tb[kMaxBoxes];
     __shared__ float4 ts[kMaxSignals];
+    __shared__ unsigned char blist[kMaxBoxes];
+    __shared__ int wcount[4];
     const int view = p.trace_view0 + (int)blockIdx.y;
     const long long plane = (long long)p.H * p.W;
     const int px0 = 4 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     Cam cm;
     WorldInfo wi;
     view_cam(p, view, cm, wi);
+    // this block's pixel rows
+    const long long first = 4LL * blockIdx.x * blockDim.x;
+    const int row0 = (int)(first / p.W);
+    const int row1 = (int)(min(first + 4LL * blockDim.x, (long long)p.H * p.W) - 1) / p.W;
     // the world's boxes in index order (ties keep going to the lower index), each once per
     // block: yaw sin/cos and the camera in the box frame
+    bool keep = false;
     for (int b = threadIdx.x; b < wi.n_boxes; b += blockDim.x) {
         const float4 bp = p.box_pose[wi.box_begin + b];
         const float4 bd = p.box_dim[wi.box_begin + b];
@@ -1298,6 +1307,26 @@ __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
                             (p.tx * fwd - side) < -rad * nrm;
         if (b == cm.ego || culled) B.hl = -1.f;
         tb[b] = B;
+        keep = B.hl >= 0.f;
+        if (keep) {
+            // rows the box can cover: its corners' projected rows when all lie beyond the
+            // near plane (else every row), widened by a pixel for rounding
+            float jlo = INFINITY, jhi = -INFINITY;
+            bool behind = false;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float lx = (k & 1) ? B.hl : -B.hl, ly = (k & 2) ? B.hw : -B.hw;
+                const float wx = bp.x + B.cs * lx - B.sn * ly - cm.px;
+                const float wy = bp.y + B.sn * lx + B.cs * ly - cm.py;
+                const float z = wx * cm.c + wy * cm.s;
+                const float yv = ((k & 4) ? B.h : 0.f) - p.cam_h;
+                behind |= !(z > p.near_plane);
+                const float j = 0.5f * (float)p.H - p.f * yv / z - 0.5f;
+                jlo = fminf(jlo, j);
+                jhi = fmaxf(jhi, j);
+            }
+            keep = behind || (jhi + 1.f >= (float)row0 && jlo - 1.f <= (float)row1);
+        }
     }
     for (int sg = threadIdx.x; sg < wi.n_sig; sg += blockDim.x) {
         const float4 sp = p.sig[wi.sig_begin + sg];
@@ -1309,6 +1338,17 @@ __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
                             (p.tx * fwd - side) < -sp.w * nrm;
         ts[sg] = make_float4(ox, oy, oz, culled ? -1.f : sp.w);
     }
+    // compact the kept boxes, in index order (one box per thread: n_boxes <= blockDim)
+    const unsigned int kb = __ballot_sync(0xffffffffu, keep);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wcount[warp] = __popc(kb);
+    __syncthreads();
+    int pos = 0, nbk = 0;
+    for (int w = 0; w < 4; ++w) {
+        pos += w < warp ? wcount[w] : 0;
+        nbk += wcount[w];
+    }
+    if (keep) blist[pos + __popc(kb & ((1u << lane) - 1u))] = (unsigned char)threadIdx.x;
     __syncthreads();
     if (px0 >= plane) return;
     const uint32_t full = p.key_f16 ? 0xFFFFu : 0xFFFFFFFFu;
@@ -1319,7 +1359,7 @@ __global__ void __launch_bounds__(128) trace_kernel(RenderParams p) {
         const int pix = px0 + k, j = pix / p.W, i = pix - j * p.W;
         uint32_t prim;
         float t;
-        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, ts, prim, t);
+        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, blist, nbk, ts, prim, t);
         low[k] = c[k] ? full - prim : 0u;
         d[k] = c[k] ? __fdiv_rn(p.near_plane, t) : 0.f;
     }
