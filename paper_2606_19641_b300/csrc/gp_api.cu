@@ -693,29 +693,46 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         wi.ginv = 1.f / cs;
         wi.gnx = std::max(1, (int)std::ceil((bx1 - bx0) / cs) + 1);
         wi.gny = std::max(1, (int)std::ceil((by1 - by0) / cs) + 1);
-        auto build_cells = [&](const float *quads, int n, int index_base, std::vector<int> &off,
-                               std::vector<int> &list) {
-            std::vector<std::vector<int>> cells((size_t)wi.gnx * wi.gny);
+        // A quad is listed in every cell it overlaps, widened by 1 mm: per row of cells, the
+        // x-extent of the quad within the row's y-band.  A point that passes the kernels'
+        // FP32 containment test lies within rounding (far below 1 mm) of the quad, and their
+        // cell index floor((p - origin) * ginv) is monotone in p, so it finds the quad.
+        auto build_cells = [&](const float *quads, int n, int index_base, float ginv, int gnx,
+                               int gny, std::vector<int> &off, std::vector<int> &list) {
+            std::vector<std::vector<int>> cells((size_t)gnx * gny);
+            const double eps = 1e-3, cell = 1.0 / ginv;
             for (int r = 0; r < n; ++r) {
                 const float *q = quads + 8 * (size_t)r;
-                float qx0 = q[0], qx1 = q[0], qy0 = q[1], qy1 = q[1];
+                double qy0 = q[1], qy1 = q[1];
                 for (int k = 1; k < 4; ++k) {
-                    qx0 = std::min(qx0, q[2 * k]);
-                    qx1 = std::max(qx1, q[2 * k]);
-                    qy0 = std::min(qy0, q[2 * k + 1]);
-                    qy1 = std::max(qy1, q[2 * k + 1]);
+                    qy0 = std::min(qy0, (double)q[2 * k + 1]);
+                    qy1 = std::max(qy1, (double)q[2 * k + 1]);
                 }
-                // the cells of the bounding box widened by 1 mm: a point that passes the FP32
-                // containment test lies within rounding of the box, and the kernels' cell
-                // index floor((p - origin) * ginv) is monotone in p
-                const float eps = 1e-3f;
-                const int cx0 = std::max(0, (int)std::floor((qx0 - eps - bx0) * wi.ginv));
-                const int cx1 = std::min(wi.gnx - 1, (int)std::floor((qx1 + eps - bx0) * wi.ginv));
-                const int cy0 = std::max(0, (int)std::floor((qy0 - eps - by0) * wi.ginv));
-                const int cy1 = std::min(wi.gny - 1, (int)std::floor((qy1 + eps - by0) * wi.ginv));
-                for (int cy = cy0; cy <= cy1; ++cy)
+                const int cy0 = std::max(0, (int)std::floor(((float)(qy0 - eps) - by0) * ginv));
+                const int cy1 = std::min(gny - 1, (int)std::floor(((float)(qy1 + eps) - by0) * ginv));
+                for (int cy = cy0; cy <= cy1; ++cy) {
+                    const double ya = by0 + cy * cell - eps, yb = by0 + (cy + 1) * cell + eps;
+                    double xa = INFINITY, xb = -INFINITY;
+                    for (int k = 0; k < 4; ++k) {
+                        const double x0 = q[2 * k], y0 = q[2 * k + 1];
+                        const double x1 = q[(2 * k + 2) % 8], y1 = q[(2 * k + 3) % 8];
+                        if (y0 >= ya && y0 <= yb) {
+                            xa = std::min(xa, x0);
+                            xb = std::max(xb, x0);
+                        }
+                        for (const double yc : {ya, yb})
+                            if ((y0 - yc) * (y1 - yc) < 0.0) {
+                                const double x = x0 + (x1 - x0) * (yc - y0) / (y1 - y0);
+                                xa = std::min(xa, x);
+                                xb = std::max(xb, x);
+                            }
+                    }
+                    if (!(xa <= xb)) continue;  // the quad misses this row's band
+                    const int cx0 = std::max(0, (int)std::floor(((float)(xa - eps) - bx0) * ginv));
+                    const int cx1 = std::min(gnx - 1, (int)std::floor(((float)(xb + eps) - bx0) * ginv));
                     for (int cx = cx0; cx <= cx1; ++cx)
-                        cells[(size_t)cy * wi.gnx + cx].push_back(index_base + r);
+                        cells[(size_t)cy * gnx + cx].push_back(index_base + r);
+                }
             }
             for (auto &cl : cells) {
                 list.insert(list.end(), cl.begin(), cl.end());
@@ -723,9 +740,19 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
             }
         };
         wi.cell_begin = (int)cell_off.size() - 1;
-        build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, cell_off, cell_quads);
+        build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.ginv, wi.gnx, wi.gny, cell_off,
+                    cell_quads);
+        // lane-line strips are thin: a finer grid (2 m cells, at most 256 per side) keeps
+        // their per-cell lists short for the ray tracer's lookups
+        {
+            const float lcs = std::max(2.f, std::max(bx1 - bx0, by1 - by0) / 255.f);
+            wi.lginv = 1.f / lcs;
+            wi.lgnx = std::max(1, (int)std::ceil((bx1 - bx0) / lcs) + 1);
+            wi.lgny = std::max(1, (int)std::ceil((by1 - by0) / lcs) + 1);
+        }
         wi.lcell_begin = (int)lcell_off.size() - 1;
-        build_cells(d->line + 8 * (size_t)l0, nl, wi.line_begin, lcell_off, lcell_quads);
+        build_cells(d->line + 8 * (size_t)l0, nl, wi.line_begin, wi.lginv, wi.lgnx, wi.lgny,
+                    lcell_off, lcell_quads);
         // each road/line segment once, in the cell of its centre-line midpoint (the same
         // FP32 expressions as the observation kernel's, so both agree on the cell)
         {

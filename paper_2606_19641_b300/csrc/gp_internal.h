@@ -25,7 +25,9 @@ struct WorldInfo {
     int road_begin, n_road;      // road quads in original order (off-road test)
     int line_begin, n_line;      // lane-line quads in original order (ray tracing)
     int cell_begin;              // off-road grid: cells [cell_begin, cell_begin + gnx*gny)
-    int lcell_begin;             // the same grid over lane-line quads
+    int lcell_begin;             // a finer grid over lane-line quads (same origin)
+    int lgnx, lgny;
+    float lginv;
     int scell_begin;             // the same grid listing each road/line segment once, in the
                                  // cell of its centre-line midpoint (ids: road r, n_road + line l)
     int gnx, gny;

@@ -1134,10 +1134,11 @@ __device__ __forceinline__ bool quad_contains(float px, float py, float4 g0, flo
 // -1 if none.  A cell lists its quads in increasing index order, so the first that contains
 // the point is the one.
 __device__ int ground_quad(const WorldInfo &wi, float px, float py, const int *off,
-                           const int *list, int cell_base, const float4 *geo) {
-    const float fx = floorf((px - wi.gx0) * wi.ginv), fy = floorf((py - wi.gy0) * wi.ginv);
-    if (!(fx >= 0.f && fy >= 0.f && fx < (float)wi.gnx && fy < (float)wi.gny)) return -1;
-    const int cell = cell_base + (int)fy * wi.gnx + (int)fx;
+                           const int *list, int cell_base, float ginv, int gnx, int gny,
+                           const float4 *geo) {
+    const float fx = floorf((px - wi.gx0) * ginv), fy = floorf((py - wi.gy0) * ginv);
+    if (!(fx >= 0.f && fy >= 0.f && fx < (float)gnx && fy < (float)gny)) return -1;
+    const int cell = cell_base + (int)fy * gnx + (int)fx;
     for (int q = off[cell]; q < off[cell + 1]; ++q) {
         const int r = list[q];
         if (quad_contains(px, py, geo[2 * r], geo[2 * r + 1])) return r;
@@ -1207,7 +1208,8 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
         bool line_hit = false;
         if (tl >= p.near_plane && tl < best) {
             const int q = ground_quad(wi, cm.px + tl * dx, cm.py + tl * dy, p.lcell_off,
-                                      p.lcell_quads, wi.lcell_begin, p.line_geo);
+                                      p.lcell_quads, wi.lcell_begin, wi.lginv, wi.lgnx, wi.lgny,
+                                      p.line_geo);
             if (q >= 0) {
                 best = tl;
                 cls = 2;
@@ -1218,7 +1220,8 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
         const float tr = -oz / dz;
         if (!line_hit && tr >= p.near_plane && tr < best) {
             const int q = ground_quad(wi, cm.px + tr * dx, cm.py + tr * dy, p.cell_off,
-                                      p.cell_quads, wi.cell_begin, p.road_geo);
+                                      p.cell_quads, wi.cell_begin, wi.ginv, wi.gnx, wi.gny,
+                                      p.road_geo);
             if (q >= 0) {
                 best = tr;
                 cls = 1;
