@@ -368,7 +368,8 @@ def main():
                 "render_kernel_ms": rms, "render_gbs": rb / (rms / 1e3) / 1e9,
                 "render_frac_of_measured_hbm": rb / (rms / 1e3) / 1e9 / peaks()[0],
                 "cameras": sim2.n_views, "band_rows": sim2.info.band_rows,
-                "threads": sim2.info.threads, "tri_capacity": sim2.info.tri_capacity}
+                "threads": sim2.info.threads, "tri_capacity": sim2.info.tri_capacity,
+                "planes_written": "the output tensor only (no depth plane)"}
 
     if not args.no_extras:
         # plain per-world path: one step launch and one render launch per world, no graph
