@@ -108,7 +108,8 @@ def _lib():
         lib.or_rewards_world.argtypes = [ctypes.c_int32, c_f64p, c_u8p, c_f64p, c_u8p, c_f32p,
                                          c_f64p, c_f64p, c_f64p, ctypes.c_int32, c_f32p,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_double, c_f64p, c_f64p, c_f64p]
+                                         ctypes.c_double, c_f64p, ctypes.c_int32, c_f64p, c_u8p,
+                                         c_f64p, c_f64p]
         lib.or_shade_rgb.argtypes = [c_u64p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                      ctypes.c_uint32, ctypes.c_uint32, c_f64p, c_f64p, c_u8p,
                                      c_f64p, c_f64p, c_f64p, ctypes.c_double, c_u8p]
@@ -344,7 +345,8 @@ def lane_frame(px: float, py: float, road: np.ndarray, lane_w: float = LANE_WIDT
 
 
 def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weights, road,
-                  lane_w=LANE_WIDTH, v_lim=30.0, dt=0.1, vmax=30.0, jerk=None):
+                  lane_w=LANE_WIDTH, v_lim=30.0, dt=0.1, vmax=30.0, jerk=None, sph=None,
+                  sph_state=None):
     """Per-agent reward and ego state [n, 9] of one step (see or_rewards_world); `acc`
     [n, 2] (previous accelerations) is updated in place; `jerk` [n, 3] is the post-step
     jerk-dynamics state (a_lon, a_lat, steer) or None under direct control."""
@@ -360,10 +362,13 @@ def rewards_world(before, fl_before, after, fl_after, actions, dims, acc, weight
     reward = np.zeros(n, np.float64)
     ego = np.zeros((n, 9), np.float64)
     jk = None if jerk is None else _c(jerk, np.float64).reshape(n, 3)
+    sp = _sph(sph)
+    st = _c(np.zeros(sp.shape[0]) if sph_state is None else sph_state, np.uint8)
     _lib().or_rewards_world(n, _p(b, c_f64p), _p(fb, c_u8p), _p(a, c_f64p), _p(fa, c_u8p),
                             _p(act, c_f32p), _p(dm, c_f64p), _p(acc, c_f64p), _p(w, c_f64p),
                             rd.shape[0], _p(rd, c_f32p), float(lane_w), float(v_lim), float(dt),
                             float(vmax), None if jk is None else _p(jk, c_f64p),
+                            sp.shape[0], _p(sp, c_f64p), _p(st, c_u8p),
                             _p(reward, c_f64p), _p(ego, c_f64p))
     return reward, ego
 

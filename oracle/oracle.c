@@ -276,8 +276,11 @@ int or_lane_frame(double px, double py, int32_t n_road, const float *road, doubl
  *   - theta_f in [0, pi] is the heading's misalignment with the lane of the post-step
  *     position (or_lane_frame) and x_f the lateral offset from its centre line; the lane
  *     terms are 0 off the road;
- *   - the traffic-light and goal terms are 0: the synthetic worlds have no signals or
- *     goals; an agent halted before the step earns 0 and has zero accelerations;
+ *   - red-light violation: a signal controls the road quad of smallest index that
+ *     contains its centre (none if no quad does); an agent violates when its centre moves
+ *     during the step from outside a red signal's quad to inside it (boundary inside);
+ *   - the goal term is 0: the synthetic worlds have no goals; an agent halted before the
+ *     step earns 0 and has zero accelerations;
  *   - ego state: v'' / v_max (v'' the post-step speed), a_lon / 10, a_lat / 10, L / 10,
  *     W / 5 (each clipped to [-1, 1]) and the collision flag (0 or 1); under the jerk
  *     dynamics also the post-step steering angle / 0.5, and the actuator accelerations
@@ -286,14 +289,16 @@ int or_lane_frame(double px, double py, int32_t n_road, const float *road, doubl
  *   (under the jerk dynamics: the resolved a_lon and steer of the step); dims [n][2] L, W;
  *   acc [n][2] previous a_lon, a_lat (overwritten with this step's); weights [n][10]
  *   collision, off-road, comfort, alignment, centering, velocity, traffic light, time,
- *   reverse, overspeed; jerk [n][3] post-step a_lon, a_lat, steer or NULL
+ *   reverse, overspeed; jerk [n][3] post-step a_lon, a_lat, steer or NULL; signals
+ *   sph [n_sig][4] x, y, z, r with states sig_state [n_sig] (0 = red)
  *   -> reward [n], ego [n][9]
  */
 void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
                       const double *after, const uint8_t *fl_after, const float *actions,
                       const double *dims, double *acc, const double *weights, int32_t n_road,
                       const float *road, double lane_w, double v_lim, double dt, double vmax,
-                      const double *jerk, double *reward, double *ego) {
+                      const double *jerk, int32_t n_sig, const double *sph,
+                      const uint8_t *sig_state, double *reward, double *ego) {
     for (int32_t i = 0; i < n; ++i) {
         const double *w = weights + 10 * i;
         double a_lon = 0.0, a_lat = 0.0, r = 0.0;
@@ -324,6 +329,17 @@ void or_rewards_world(int32_t n, const double *before, const uint8_t *fl_before,
             if (fabs(vn) > 0.0 || a_lon != 0.0 || a_lat != 0.0) r -= w[7] * dt;
             if (vn < 0.0) r -= w[8] * dt;
             if (fabs(vn) > v_lim) r -= w[9];
+            for (int32_t s = 0; s < n_sig; ++s) {
+                if (sig_state[s] != 0) continue;
+                int32_t q = 0;
+                while (q < n_road && !or_point_in_quad(sph[4 * s], sph[4 * s + 1], road + 8 * q)) ++q;
+                if (q == n_road) continue;
+                if (!or_point_in_quad(before[4 * i], before[4 * i + 1], road + 8 * q) &&
+                    or_point_in_quad(after[4 * i], after[4 * i + 1], road + 8 * q)) {
+                    r -= w[6];
+                    break;
+                }
+            }
         }
         acc[2 * i] = a_lon;
         acc[2 * i + 1] = a_lat;

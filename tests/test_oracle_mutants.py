@@ -81,6 +81,9 @@ MUTANTS = {
     "ovec signal lateral sign": ("            o[2] = (-dx * sn + dy * c) / r_sig;", "            o[2] = (dx * sn - dy * c) / r_sig;"),
     "ovec signal state slot": ("            o[4 + (state[s] & 3)] = 1.0;", "            o[4 + ((state[s] + 1) & 3)] = 1.0;"),
     "ovec signal radius": ("            if (d <= r_sig) {", "            if (d < r_sig) {"),
+    "red light fires on leaving": ("                if (!or_point_in_quad(before[4 * i], before[4 * i + 1], road + 8 * q) &&\n                    or_point_in_quad(after[4 * i], after[4 * i + 1], road + 8 * q)) {", "                if (or_point_in_quad(before[4 * i], before[4 * i + 1], road + 8 * q) &&\n                    !or_point_in_quad(after[4 * i], after[4 * i + 1], road + 8 * q)) {"),
+    "red light any state": ("                if (sig_state[s] != 0) continue;", "                if (sig_state[s] > 1) continue;"),
+    "red light counted per signal": ("                    r -= w[6];\n                    break;", "                    r -= w[6];"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

@@ -1470,3 +1470,35 @@ def test_ovec_signals_frame_order_and_state():
     o2 = oracle.observe_signals(boxes, 1, [sph[3], sph[4]], [2, 1])[0]
     assert np.allclose(o2[0], [1, -1.0, 0.0, 0.5, 0, 0, 1, 0], atol=1e-12)
     assert not o2[1:].any()
+
+
+def test_red_light_violation_term():
+    """Reward table, traffic-light row: -w6 when the agent's centre enters, during the
+    step, the road quad controlled by a red signal (the quad of smallest index under the
+    signal's centre); nothing for green/amber/off, for staying inside, for leaving, or for
+    a signal over no road."""
+    road = [rect_quad(-100.0, 0.0, -3.5, 3.5), rect_quad(0.0, 100.0, -3.5, 3.5)]
+    over_b = [[50.0, 0.0, 5.0, 0.4]]
+    w = [list(W_INF)]
+
+    def r_of(x0, x1, state, sph=over_b, fl_before=0):
+        before = np.array([[x0, -1.75, 0.0, 10.0]])
+        after = np.array([[x1, -1.75, 0.0, 10.0]])
+        r, _ = oracle.rewards_world(before, [fl_before], after, [fl_before], [[0.0, 0.0]],
+                                    [[4.5, 1.9]], np.zeros((1, 2)), w, road, sph=sph,
+                                    sph_state=state)
+        return float(r[0])
+    base = r_of(-0.5, 0.5, [2])
+    assert r_of(-0.5, 0.5, [0]) == pytest.approx(base - W_INF[6], abs=1e-15)
+    for st in ([1], [2], [3]):
+        assert r_of(-0.5, 0.5, st) == base
+    assert r_of(0.5, 1.5, [0]) == r_of(0.5, 1.5, [2])      # already inside
+    assert r_of(0.5, -0.5, [0]) == r_of(0.5, -0.5, [2])    # leaving
+    assert r_of(-0.5, 0.0, [0]) == pytest.approx(r_of(-0.5, 0.0, [2]) - W_INF[6])  # edge is inside
+    assert r_of(-0.5, 0.5, [0], sph=[[50.0, 40.0, 5.0, 0.4]]) == base  # over no road
+    two = over_b + [[60.0, 1.0, 5.0, 0.4]]
+    assert r_of(-0.5, 0.5, [0, 0], sph=two) == pytest.approx(base - W_INF[6])  # counted once
+    # the signal controls the quad of smallest index under it: over quad A it fires on entering A
+    assert r_of(0.5, -0.5, [0], sph=[[-50.0, 0.0, 5.0, 0.4]]) == pytest.approx(
+        r_of(0.5, -0.5, [2], sph=[[-50.0, 0.0, 5.0, 0.4]]) - W_INF[6])
+    assert r_of(-0.5, 0.5, [0], fl_before=4 | 1) == 0.0  # halted agents earn nothing
