@@ -290,7 +290,8 @@ gp_status gp_get_info(gp_handle *h, gp_info *info);
  *   + 1[|jerk_lon| > 5 or |jerk_lat| > 5]), lane alignment, lane centering and velocity
  *   (w3..w5, from the lane frame of the road quad of smallest index under the agent,
  *   right-hand traffic, 0 off the road), time -w7 dt, reverse -w8 dt, overspeed -w9
- *   (|v| > v_limit); traffic-light (w6) and goal terms are 0 (no signals or goals).
+ *   (|v| > v_limit), red-light violation -w6 (the agent's centre enters, during the step,
+ *   the road quad of smallest index under a red signal's centre); the goal term is 0.
  *   Accelerations are the bicycle's increments of the step (speed before any halt):
  *   a_lon = (v' - v) / dt, a_lat = v dyaw / dt; an agent halted before the step earns 0.
  * ego [n_agents][GP_EGO_DIM] float: speed / v_max, a_lon / 10, a_lat / 10, L / 10, W / 5

@@ -81,6 +81,7 @@ struct gp_handle {
     DevBuf<WorldInfo> worlds;
     DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo, sig;
     DevBuf<uint8_t> sig_state;
+    DevBuf<int> sig_quad;  // road quad (road_geo index) each signal controls, -1 if none
     DevBuf<float> speed;
     DevBuf<uint8_t> flags;
     DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, seg_off,
@@ -332,6 +333,9 @@ StepParams step_params(gp_handle *h, const float *actions) {
     p.ego = h->ego.p;
     p.dynamics = h->cfg.dynamics;
     p.jerk = h->jerk.p;
+    p.sig = h->sig.p;
+    p.sig_state = h->sig_state.p;
+    p.sig_quad = h->sig_quad.p;
     return p;
 }
 
@@ -543,6 +547,7 @@ void release_all(gp_handle *h) {
     h->jerk.release();
     h->sig.release();
     h->sig_state.release();
+    h->sig_quad.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -883,14 +888,36 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         const size_t ns = d->signal_off ? (size_t)d->signal_off[nw] : 0;
         std::vector<float4> sig(std::max<size_t>(ns, 1), make_float4(0.f, 0.f, 0.f, 1.f));
         std::vector<uint8_t> sst(std::max<size_t>(ns, 1), 0);
+        std::vector<int> sq(std::max<size_t>(ns, 1), -1);
         for (size_t s = 0; s < ns; ++s) {
             const float *q = d->signal + 4 * s;
             sig[s] = make_float4(q[0], q[1], q[2], q[3]);
             sst[s] = d->signal_state ? d->signal_state[s] : (uint8_t)GP_SIGNAL_RED;
         }
+        // the road quad each signal controls: the one of smallest index under its centre
+        for (int w = 0; w < nw && d->signal_off; ++w) {
+            const WorldInfo &wi = h->worlds_h[w];
+            for (int s = d->signal_off[w]; s < d->signal_off[w + 1]; ++s) {
+                const float px = d->signal[4 * s], py = d->signal[4 * s + 1];
+                for (int r = 0; r < wi.n_road; ++r) {
+                    const float *q = d->road + 8 * (size_t)(d->road_off[w] + r);
+                    bool in = true;
+                    for (int k = 0; k < 4 && in; ++k) {
+                        const int n = (k + 1) & 3;
+                        in = (q[2 * n] - q[2 * k]) * (py - q[2 * k + 1]) -
+                                 (q[2 * n + 1] - q[2 * k + 1]) * (px - q[2 * k]) >= 0.f;
+                    }
+                    if (in) {
+                        sq[s] = wi.road_begin + r;
+                        break;
+                    }
+                }
+            }
+        }
         h->n_signals = (int)ns;
         UP(sig, sig);
         UP(sig_state, sst);
+        UP(sig_quad, sq);
     }
     std::vector<int> one(1, 0);
     UP(counter, one);

@@ -67,6 +67,10 @@ struct StepParams {
     // jerk-actuated dynamics (dynamics == GP_DYN_JERK): actuator state per agent
     int dynamics;
     float *jerk;            // [n_agents][3] a_lon, a_lat, steer (updated)
+    // traffic signals for the red-light term: centre, state, controlled road quad (-1: none)
+    const float4 *sig;
+    const uint8_t *sig_state;
+    const int *sig_quad;
 };
 
 // Vectorized observations (gp_observe_vec).

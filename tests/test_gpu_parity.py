@@ -604,14 +604,20 @@ def test_rgb_rejects_bad_appearance():
 # Rewards and ego state (App. A reward table and observations)
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,n_worlds,steps", [("uniform", 4, 12), ("ragged", 6, 10)])
+@pytest.mark.parametrize("name,n_worlds,steps", [("uniform", 4, 12), ("ragged", 6, 10),
+                                                 ("paper_rig_210x126", 3, 12)])
 def test_rewards_match_oracle(name, n_worlds, steps):
     """Per-step rewards and ego states against the oracle evaluated on the GPU's own
-    before/after states and flags; random per-agent weights from the table's ranges."""
+    before/after states and flags; random per-agent weights from the table's ranges.  The
+    signal worlds hang 32 red signals per world so that the red-light term fires."""
     import torch
     wl = wg.WORKLOADS[name]
     worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    if wl.signals:
+        wg.add_signals(worlds, 32, wl.seed, height=5.0)
+        worlds.signal_state[:] = 0
     sim, cfg = sim_for(worlds, wl, rewards=1)
+    red_fired = 0
     na = worlds.n_agents
     rng = np.random.default_rng(5)
     lo = np.array([0, 0, 0, 2.5e-4, 2.5e-4, 0, 0, 0, 2.5e-4, 0])
@@ -638,9 +644,18 @@ def test_rewards_match_oracle(name, n_worlds, steps):
         for w in range(worlds.n_worlds):
             a0, a1 = int(off[w]), int(off[w + 1])
             road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
+            s0, s1 = int(worlds.signal_off[w]), int(worlds.signal_off[w + 1])
+            sph, sst = worlds.signal[s0:s1], worlds.signal_state[s0:s1]
             acc_w = np.ascontiguousarray(acc[a0:a1])
+            acc_g = acc_w.copy()
             rr, ee = oracle.rewards_world(st0[a0:a1], fl0[a0:a1], st1[a0:a1], fl1[a0:a1],
-                                          act[a0:a1], dims[a0:a1], acc_w, weights[a0:a1], road)
+                                          act[a0:a1], dims[a0:a1], acc_w, weights[a0:a1], road,
+                                          sph=sph, sph_state=sst)
+            if s1 > s0:
+                rg, _ = oracle.rewards_world(st0[a0:a1], fl0[a0:a1], st1[a0:a1], fl1[a0:a1],
+                                             act[a0:a1], dims[a0:a1], acc_g, weights[a0:a1], road,
+                                             sph=sph, sph_state=np.full(s1 - s0, 2, np.uint8))
+                red_fired += int((np.abs(rg - rr) > 0).sum())
             acc[a0:a1] = acc_w
             d = np.abs(r[a0:a1] - rr)
             n_bad += int((d > 1e-4 + 1e-4 * np.abs(rr)).sum())
@@ -652,6 +667,9 @@ def test_rewards_match_oracle(name, n_worlds, steps):
             seen_collision |= bool((fl1[a0:a1] & 1).any())
     assert n_bad <= 0.005 * n_total
     assert sim.status() == 0
+    if wl.signals:
+        print("red-light violations in the oracle: %d" % red_fired)
+        assert red_fired > 0
 
 
 def test_rewards_off_by_default_and_weights_validated():
