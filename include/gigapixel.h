@@ -258,6 +258,15 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
                        void *stream);
 
 /*
+ * Episode reset: the agents of every world w with mask[w] != 0 (every world if mask is
+ * NULL) return to their initial pose and speed from gp_create_worlds, with clear flags and
+ * zero previous-step accelerations and actuator state; other worlds are untouched.
+ *   mask  uint8 [n_worlds]; on_host != 0: host memory (synchronous), else device memory
+ *         (asynchronous on `stream`, so it can follow a device-side "done" test).
+ */
+gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *stream);
+
+/*
  * Actuator state of the jerk dynamics, dyn[n_agents][3] float = a_lon, a_lat (m/s^2),
  * steering angle (rad); GP_ESTATE unless gp_config.dynamics = GP_DYN_JERK.  on_host as for
  * gp_get_state.  gp_set_dynamics rejects non-finite host values (GP_EINVAL); device values

@@ -35,7 +35,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
-            "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states",
+            "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_set_reward_weights": [vp, vp, i32, vp],
         "gp_get_dynamics": [vp, vp, i32, vp],
         "gp_set_signal_states": [vp, vp, i32, vp],
+        "gp_reset_worlds": [vp, vp, i32, vp],
         "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -314,6 +315,20 @@ class Simulator:
         a, r, s = out
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
         return a, r, s
+
+    def reset_worlds(self, mask=None, stream=None) -> None:
+        """Return the agents of the worlds selected by mask (uint8/bool [n_worlds], host
+        array or device tensor; None = all) to their initial state."""
+        if mask is None:
+            check(lib().gp_reset_worlds(self._h, None, 1, _stream(stream)))
+        elif isinstance(mask, np.ndarray):
+            m = np.ascontiguousarray(mask, np.uint8)
+            assert m.shape == (self.info.n_worlds,)
+            check(lib().gp_reset_worlds(self._h, _ptr(m), 1, _stream(stream)))
+        else:
+            assert tuple(mask.shape) == (self.info.n_worlds,) and mask.is_contiguous()
+            assert mask.element_size() == 1, "mask must be uint8 or bool"
+            check(lib().gp_reset_worlds(self._h, _ptr(mask), 0, _stream(stream)))
 
     def set_signal_states(self, states) -> None:
         """Traffic-signal states uint8 [n_signals] (0 red, 1 amber, 2 green, 3 off): host

@@ -82,7 +82,8 @@ struct gp_handle {
     DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo, sig;
     DevBuf<uint8_t> sig_state;
     DevBuf<int> sig_quad;  // road quad (road_geo index) each signal controls, -1 if none
-    DevBuf<float> speed;
+    DevBuf<float> speed, speed0;
+    DevBuf<float4> pose0;  // initial poses and speeds (gp_reset_worlds)
     DevBuf<uint8_t> flags;
     DevBuf<int> agent_world, agent_box, cell_off, cell_quads, lcell_off, lcell_quads, seg_off,
         seg_list, counter, dump_count;
@@ -94,7 +95,7 @@ struct gp_handle {
     DevBuf<float> reward, ego, weights;  // per-step rewards: [n_agents], [n_agents][GP_EGO_DIM], [n_agents][10]
     DevBuf<float> jerk;                  // jerk dynamics' actuator state [n_agents][3]
     DevBuf<float2> acc;                  // previous-step accelerations
-    DevBuf<uint8_t> flag_stage;
+    DevBuf<uint8_t> flag_stage, world_stage;  // host-copy staging: per agent, per world
     Shape shape;
     uint16_t onehot[4][2];
     cudaStream_t capture_stream = nullptr;
@@ -540,6 +541,8 @@ void release_all(gp_handle *h) {
     h->quad_geo.release();
     h->road_geo.release();
     h->speed.release();
+    h->speed0.release();
+    h->pose0.release();
     h->reward.release();
     h->ego.release();
     h->weights.release();
@@ -567,6 +570,7 @@ void release_all(gp_handle *h) {
     h->dump.release();
     h->state_stage.release();
     h->flag_stage.release();
+    h->world_stage.release();
 }
 
 }  // namespace
@@ -866,8 +870,10 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     } while (0)
     UP(worlds, h->worlds_h);
     UP(box_pose, pose);
+    UP(pose0, pose);
     UP(box_dim, dim);
     UP(speed, speed);
+    UP(speed0, speed);
     std::vector<uint8_t> zeros(h->n_agents, 0);
     UP(flags, zeros);
     UP(agent_world, agent_world);
@@ -928,6 +934,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(state_stage, stage);
     std::vector<uint8_t> fstage(std::max(1, h->n_agents), 0);
     UP(flag_stage, fstage);
+    std::vector<uint8_t> wstage(std::max(1, nw), 0);
+    UP(world_stage, wstage);
     {
         const size_t na = (size_t)std::max(1, h->n_agents);
         std::vector<float> r0(na, 0.f), e0(GP_EGO_DIM * na, 0.f), w0(10 * na), j0(3 * na, 0.f);
@@ -1111,6 +1119,31 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     }
     if (n) CK(cudaMemsetAsync(h->acc.p, 0, sizeof(float2) * n, s));  // accelerations restart
     if (n) CK(cudaMemsetAsync(h->jerk.p, 0, sizeof(float) * 3 * n, s));
+    return GP_OK;
+}
+
+gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *stream) {
+    if (!h) return fail(GP_EINVAL, "null handle");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ResetParams p{};
+    p.n_agents = h->n_agents;
+    p.mask = mask;
+    if (mask && on_host) {
+        if (h->n_worlds) CK(cudaMemcpyAsync(h->world_stage.p, mask, h->n_worlds, cudaMemcpyHostToDevice, s));
+        p.mask = h->world_stage.p;
+    }
+    p.agent_world = h->agent_world.p;
+    p.agent_box = h->agent_box.p;
+    p.pose0 = h->pose0.p;
+    p.speed0 = h->speed0.p;
+    p.pose = h->box_pose.p;
+    p.speed = h->speed.p;
+    p.flags = h->flags.p;
+    p.acc = h->acc.p;
+    p.jerk = h->jerk.p;
+    CK(launch_reset(p, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
     return GP_OK;
 }
 

@@ -151,6 +151,21 @@ size_t render_smem_bytes(int W, int band_rows, int key_f16, int threads, int tri
                          int prod_warps);
 
 cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
+
+// Episode reset of selected worlds (gp_reset_worlds).
+struct ResetParams {
+    int n_agents;
+    const uint8_t *mask;  // [n_worlds] or null = all
+    const int *agent_world, *agent_box;
+    const float4 *pose0;  // initial box poses
+    const float *speed0;  // initial agent speeds
+    float4 *pose;
+    float *speed;
+    uint8_t *flags;
+    float2 *acc;
+    float *jerk;
+};
+cudaError_t launch_reset(const ResetParams &p, cudaStream_t s);
 cudaError_t launch_state(float *state, uint8_t *flags, float4 *pose, float *speed, uint8_t *fl,
                          const int *agent_box, int n, int to_state, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t smem,

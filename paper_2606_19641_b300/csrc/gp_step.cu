@@ -321,7 +321,28 @@ __global__ void state_kernel(float *state, uint8_t *flags, float4 *pose, float *
     }
 }
 
+// Episode reset: the agents of every world whose mask byte is non-zero (every world if
+// mask is null) get their initial pose and speed back, with clear flags, zero previous-step
+// accelerations and zero actuator state.
+__global__ void reset_kernel(ResetParams p) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= p.n_agents) return;
+    if (p.mask && !p.mask[p.agent_world[a]]) return;
+    const int b = p.agent_box[a];
+    p.pose[b] = p.pose0[b];
+    p.speed[a] = p.speed0[a];
+    p.flags[a] = 0;
+    p.acc[a] = make_float2(0.f, 0.f);
+    p.jerk[3 * a] = p.jerk[3 * a + 1] = p.jerk[3 * a + 2] = 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_reset(const ResetParams &p, cudaStream_t s) {
+    if (p.n_agents <= 0) return cudaSuccess;
+    reset_kernel<<<(p.n_agents + 255) / 256, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s) {
     if (p.n_worlds <= 0) return cudaSuccess;

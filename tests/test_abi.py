@@ -121,6 +121,8 @@ def test_null_handle_calls_fail_cleanly(gp):
     assert L.gp_get_info(None, None) == -1
     assert L.gp_get_dynamics(None, None, 1, None) == -1
     assert L.gp_set_dynamics(None, None, 1, None) == -1
+    assert L.gp_reset_worlds(None, None, 1, None) == -1
+    assert L.gp_set_signal_states(None, None, 1, None) == -1
 
 
 def test_fp16_primitive_limit(gp):

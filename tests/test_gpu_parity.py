@@ -1088,3 +1088,43 @@ def test_signal_limits_validated():
     worlds.signal[0, 3] = 0.0
     with pytest.raises(gp.GigapixelError):
         sim_for(worlds, wl)
+
+
+def test_reset_worlds():
+    """Episode reset: the selected worlds' agents get their initial state back exactly
+    (pose, speed, clear flags, zero actuator state); the others are untouched."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    sim, _ = sim_for(worlds, wl, dynamics=gp.DYN_JERK)
+    na = worlds.n_agents
+    st_init, fl_init = sim.get_state()
+    off = worlds.agent_offsets()
+    # the initial state is the descriptor's
+    for w in range(3):
+        b0, a0, a1 = int(worlds.box_off[w]), int(off[w]), int(off[w + 1])
+        bx = worlds.boxes[b0:b0 + (a1 - a0)]
+        assert np.array_equal(st_init[a0:a1, :3], bx[:, :3]) and np.array_equal(st_init[a0:a1, 3], bx[:, 6])
+    for k in range(8):
+        sim.step(torch.from_numpy(wg.jerk_actions(3, k, na)).cuda())
+    st1, fl1 = sim.get_state()
+    dy1 = sim.get_dynamics()
+    assert not np.array_equal(st1, st_init) and np.abs(dy1).max() > 0
+    sim.reset_worlds(np.array([0, 1, 0], np.uint8))
+    st2, fl2 = sim.get_state()
+    dy2 = sim.get_dynamics()
+    a0, a1 = int(off[1]), int(off[2])
+    assert np.array_equal(st2[a0:a1], st_init[a0:a1]) and not fl2[a0:a1].any()
+    assert not dy2[a0:a1].any()
+    keep = np.ones(na, bool)
+    keep[a0:a1] = False
+    assert np.array_equal(st2[keep], st1[keep]) and np.array_equal(fl2[keep], fl1[keep])
+    assert np.array_equal(dy2[keep], dy1[keep])
+    # device mask, every world
+    sim.reset_worlds(torch.ones(3, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    st3, fl3 = sim.get_state()
+    assert np.array_equal(st3, st_init) and not fl3.any() and not sim.get_dynamics().any()
+    sim.reset_worlds()
+    assert sim.status() == 0
