@@ -11,6 +11,7 @@ Prints one JSON line (rank 0).  Under torchrun every rank simulates its own worl
 data-path collective; weak scaling); timings are max-reduced over ranks.
 """
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -213,6 +214,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the 3-camera resolution sweep 64..512 (extra minutes)")
     ap.add_argument("--shape", default="",
                     help="pin the render launch shape ROWS,THREADS,TRI_CAP instead of autotuning "
                          "(for profiler captures that must skip a known number of launches)")
@@ -442,6 +445,15 @@ def main():
         extras["ragged_precision_256x144"] = graph_rate(sim_r, worlds_r, wl_r, 5)
         extras["ragged_precision_256x144"]["workload"] = wl_r.name
         sim_r.close()
+        # the ragged batch at 128x128 on the precision path (FP16 key, BF16 one-hot NCHW)
+        wl_c = rank_workload(wg.WORKLOADS["ragged"], rank)
+        worlds_c = wg.make_workload(wl_c)
+        sim_c = Simulator(worlds_c, config_for(wl_c, autotune=1, key_precision=1, output=1),
+                          device=local)
+        extras["ragged_precision_128x128"] = graph_rate(sim_c, worlds_c, wl_c, 5)
+        extras["ragged_precision_128x128"]["workload"] = wl_c.name + ", f16 key, bf16 one-hot"
+        sim_c.close()
+        del worlds_c
         # the paper's observation rig: 4 cameras (0, +-60, 180 deg) at 434x252, shaded RGB
         wl_g = rank_workload(wg.WORKLOADS["paper_rig_434x252"], rank)
         worlds_g = wg.make_workload(wl_g)
@@ -452,6 +464,21 @@ def main():
             extras["paper_rig_434x252_rgb"]["cameras"] * wl_g.width * wl_g.height /
             (extras["paper_rig_434x252_rgb"]["ms_per_step"] / 1e3) / 1e6)
         sim_g.close()
+
+    if args.sweep and not args.no_extras:
+        # resolution sweep: 3 cameras (0, +-60 deg), 64 boxes, 1000 segments per world
+        # (about three minutes with the autotuner at every size, so only on request)
+        wl_s0 = rank_workload(wg.WORKLOADS["sweep"], rank)
+        worlds_s = wg.make_workload(wl_s0)
+        sweep = {}
+        for res in (64, 128, 256, 512):
+            wl_s = dataclasses.replace(wl_s0, width=res, height=res)
+            sim_s = Simulator(worlds_s, config_for(wl_s, autotune=1), device=local)
+            r = graph_rate(sim_s, worlds_s, wl_s, 5)
+            r["mpix_per_s"] = r["cameras"] * res * res / (r["ms_per_step"] / 1e3) / 1e6
+            sweep["%dx%d" % (res, res)] = r
+            sim_s.close()
+        extras["sweep_3cam_class_u8"] = sweep
 
     cpu = None
     if rank == 0:
