@@ -358,7 +358,9 @@ __device__ __forceinline__ void row_span(const TriRec &T, int row, int &lo, int 
 
 // Depth test of one fragment: the key's maximum wins per pixel -- FP32 mode one 64-bit key
 // (FP32 depth bits << 32 | inverted id), FP16 mode one 32-bit key (binary16 depth bits << 16
-// | inverted id) -- so the nearest surface wins and ties go to the smaller primitive id.
+// | inverted id) -- so the nearest surface wins and ties go to the smaller primitive id.  The
+// shared-memory atomic is issued unconditionally (its result is unused): reading the key
+// first to skip losing fragments cost about 2 % more time.
 // Depth is a * g + inner, clamped to >= 0, g the pixel centre's offset (1/16 px) from the
 // triangle's vertex 0.
 template <bool F32>
@@ -369,11 +371,11 @@ __device__ __forceinline__ void depth_test(void *keys, int ko, int g, float a, f
     if (F32) {
         unsigned long long *rk = (unsigned long long *)keys + ko;
         const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | low;
-        if (key > *rk) atomicMax(rk, key);
+        atomicMax(rk, key);
     } else {
         unsigned int *rk = (unsigned int *)keys + ko;
         const unsigned int key = key16(d, low);
-        if (key > *rk) atomicMax(rk, key);
+        atomicMax(rk, key);
     }
 }
 
