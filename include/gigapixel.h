@@ -77,6 +77,24 @@ enum { GP_SIGNAL_RED = 0, GP_SIGNAL_AMBER = 1, GP_SIGNAL_GREEN = 2, GP_SIGNAL_OF
 #define GP_OBS_ROAD_RADIUS 30.0f
 #define GP_OBS_SIGNALS 4         /* traffic-signal slots per agent */
 #define GP_OBS_SIGNAL_RADIUS 50.0f
+/* Render counters (gp_config.stats = 1, read with gp_get_render_stats), summed over
+ * every render launch since the last reset; a triangle spanning several screen bands is
+ * set up once per band. */
+enum {
+    GP_STAT_ITEMS = 0,          /* (view, band) work items */
+    GP_STAT_CLUSTERS = 1,       /* culling clusters visible in an item's band */
+    GP_STAT_BOXES = 2,          /* boxes visible in an item's band */
+    GP_STAT_SIGNALS = 3,        /* signal spheres visible in an item's band */
+    GP_STAT_QUADS = 4,          /* quads set up (visible clusters' quads, box faces, sphere faces) */
+    GP_STAT_TRIS_KEPT = 5,      /* triangles kept without clipping */
+    GP_STAT_TRIS_CLIPPED = 6,   /* triangles sent to near/guard-band clipping */
+    GP_STAT_TRIS_FROM_CLIP = 7, /* triangles kept out of clipping */
+    GP_STAT_BATCHES = 8,        /* raster batches */
+    GP_STAT_ROW_ITEMS = 9,      /* (triangle, row) raster items */
+    GP_STAT_FRAGMENTS = 10,     /* covered (triangle, pixel) pairs depth-tested */
+    GP_STAT_COUNT = 16
+};
+
 /* Ego-state width (gp_get_rewards) */
 #define GP_EGO_DIM 9
 
@@ -167,6 +185,7 @@ typedef struct gp_config {
     float lane_width;             /* lane width of the two-lane roads (default 3.5 m) */
     float v_limit;                /* speed limit of the overspeed term (default 30 m/s) */
     int32_t dynamics;             /* GP_DYN_DIRECT (default) or GP_DYN_JERK */
+    int32_t stats;                /* 1: count GP_STAT_* events in every render (default 0) */
     float signal_colour[4][3];    /* RGB in 0..1 of signal states red, amber, green, off
                                      (defaults 0.9 0.1 0.1 / 0.95 0.7 0.1 / 0.1 0.8 0.3 /
                                      0.25 0.25 0.25); shaded like every surface */
@@ -265,6 +284,13 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
  *         (asynchronous on `stream`, so it can follow a device-side "done" test).
  */
 gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *stream);
+
+/*
+ * Render counters out[GP_STAT_COUNT] (host, uint64) summed since create or the last reset
+ * (reset != 0 clears them after reading).  Synchronises the device.  GP_ESTATE unless
+ * gp_config.stats = 1.
+ */
+gp_status gp_get_render_stats(gp_handle *h, uint64_t *out, int reset);
 
 /*
  * Actuator state of the jerk dynamics, dyn[n_agents][3] float = a_lon, a_lat (m/s^2),

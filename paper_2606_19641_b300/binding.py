@@ -24,6 +24,8 @@ FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
 DYN_DIRECT, DYN_JERK = 0, 1
+STAT_NAMES = ("items", "clusters", "boxes", "signals", "quads", "tris_kept", "tris_clipped",
+              "tris_from_clip", "batches", "row_items", "fragments")
 EGO_DIM = 9
 # App. A's discrete action set for DYN_JERK: (longitudinal, lateral) jerk in m/s^3.
 JERK_ACTIONS = tuple((jl, jt) for jl in (-15.0, -4.0, 0.0, 4.0) for jt in (-4.0, 0.0, 4.0))
@@ -36,6 +38,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
+            "gp_get_render_stats",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -70,7 +73,7 @@ class Config(ctypes.Structure):
                 ("colour", (ctypes.c_float * 3) * 4),
                 ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
                 ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32),
-                ("signal_colour", (ctypes.c_float * 3) * 4)]
+                ("stats", ctypes.c_int32), ("signal_colour", (ctypes.c_float * 3) * 4)]
 
 
 class Info(ctypes.Structure):
@@ -119,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_get_dynamics": [vp, vp, i32, vp],
         "gp_set_signal_states": [vp, vp, i32, vp],
         "gp_reset_worlds": [vp, vp, i32, vp],
+        "gp_get_render_stats": [vp, vp, i32],
         "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -315,6 +319,12 @@ class Simulator:
         a, r, s = out
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
         return a, r, s
+
+    def render_stats(self, reset: bool = False) -> dict:
+        """GP_STAT_* render counters since create or the last reset (config stats = 1)."""
+        c = np.zeros(16, np.uint64)
+        check(lib().gp_get_render_stats(self._h, _ptr(c), int(reset)))
+        return {k: int(c[i]) for i, k in enumerate(STAT_NAMES)}
 
     def reset_worlds(self, mask=None, stream=None) -> None:
         """Return the agents of the worlds selected by mask (uint8/bool [n_worlds], host

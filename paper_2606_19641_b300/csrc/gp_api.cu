@@ -14,11 +14,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gp_internal.h"
 
 using namespace gpk;
 
 namespace {
+
+// NVTX range over a public call (visible in a timeline tool; free when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 thread_local std::string g_err;
 
@@ -81,7 +91,8 @@ struct gp_handle {
     DevBuf<WorldInfo> worlds;
     DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo, sig;
     DevBuf<uint8_t> sig_state;
-    DevBuf<int> sig_quad;  // road quad (road_geo index) each signal controls, -1 if none
+    DevBuf<int> sig_quad;
+    DevBuf<unsigned long long> stats;  // GP_STAT_* counters (gp_config.stats)  // road quad (road_geo index) each signal controls, -1 if none
     DevBuf<float> speed, speed0;
     DevBuf<float4> pose0;  // initial poses and speeds (gp_reset_worlds)
     DevBuf<uint8_t> flags;
@@ -128,6 +139,7 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
     if (c->output != GP_OUT_CLASS_U8 && c->output != GP_OUT_ONEHOT_BF16 && c->output != GP_OUT_RGB_U8)
         return fail(GP_EINVAL, "output");
     if (c->rewards != 0 && c->rewards != 1) return fail(GP_EINVAL, "rewards must be 0 or 1");
+    if (c->stats != 0 && c->stats != 1) return fail(GP_EINVAL, "stats must be 0 or 1");
     if (c->dynamics != GP_DYN_DIRECT && c->dynamics != GP_DYN_JERK)
         return fail(GP_EINVAL, "dynamics must be GP_DYN_DIRECT or GP_DYN_JERK");
     if (c->rewards && !(c->lane_width > 0.f && c->v_limit >= 0.f))
@@ -305,6 +317,7 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     p.wait_ns = 2000000000ull;  // 2 s: far beyond any legitimate handoff
     p.debug_stall = 0;
     p.status = h->status.p;
+    p.stats = h->cfg.stats ? h->stats.p : nullptr;
     p.dump_view = -1;
     return p;
 }
@@ -551,6 +564,7 @@ void release_all(gp_handle *h) {
     h->sig.release();
     h->sig_state.release();
     h->sig_quad.release();
+    h->stats.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -624,6 +638,7 @@ gp_status gp_destroy(gp_handle *h) {
 
 gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int device,
                            gp_handle **out) {
+    NvtxRange range("gp_create_worlds");
     if (!out) return fail(GP_EINVAL, "null out handle");
     *out = nullptr;
     gp_status st = validate(d, cfg);
@@ -925,6 +940,10 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         UP(sig_state, sst);
         UP(sig_quad, sq);
     }
+    {
+        std::vector<unsigned long long> z(GP_STAT_COUNT, 0ull);
+        UP(stats, z);
+    }
     std::vector<int> one(1, 0);
     UP(counter, one);
     UP(dump_count, one);
@@ -977,7 +996,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         gp_destroy(h);
         return fail(GP_ECUDA, "stream create");
     }
-    if (cudaDeviceSynchronize() != cudaSuccess) {
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemset(h->stats.p, 0, sizeof(unsigned long long) * GP_STAT_COUNT) != cudaSuccess) {
         gp_destroy(h);
         return fail(GP_ECUDA, "create: device error");
     }
@@ -986,6 +1006,7 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
 }
 
 gp_status gp_step(gp_handle *h, const float *actions, void *stream) {
+    NvtxRange range("gp_step");
     if (!h) return fail(GP_EINVAL, "null handle");
     if (!actions) return fail(GP_EINVAL, "actions_dev is null");
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
@@ -995,6 +1016,7 @@ gp_status gp_step(gp_handle *h, const float *actions, void *stream) {
 }
 
 gp_status gp_render(gp_handle *h, void *out, void *depth, void *stream) {
+    NvtxRange range("gp_render");
     if (!h) return fail(GP_EINVAL, "null handle");
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
@@ -1006,6 +1028,7 @@ gp_status gp_render(gp_handle *h, void *out, void *depth, void *stream) {
 
 gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *depth,
                          void *stream) {
+    NvtxRange range("gp_step_render");
     if (!h) return fail(GP_EINVAL, "null handle");
     if (!actions) return fail(GP_EINVAL, "actions_dev is null");
     gp_status st = check_out(out, depth);
@@ -1055,6 +1078,7 @@ gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions, void 
 }
 
 gp_status gp_trace(gp_handle *h, void *out, void *depth, void *stream) {
+    NvtxRange range("gp_trace");
     if (!h) return fail(GP_EINVAL, "null handle");
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
@@ -1119,6 +1143,16 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     }
     if (n) CK(cudaMemsetAsync(h->acc.p, 0, sizeof(float2) * n, s));  // accelerations restart
     if (n) CK(cudaMemsetAsync(h->jerk.p, 0, sizeof(float) * 3 * n, s));
+    return GP_OK;
+}
+
+gp_status gp_get_render_stats(gp_handle *h, uint64_t *out, int reset) {
+    if (!h || !out) return fail(GP_EINVAL, "null argument");
+    if (!h->cfg.stats) return fail(GP_ESTATE, "stats are off (gp_config.stats = 0)");
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(out, h->stats.p, sizeof(uint64_t) * GP_STAT_COUNT, cudaMemcpyDeviceToHost));
+    if (reset) CK(cudaMemset(h->stats.p, 0, sizeof(uint64_t) * GP_STAT_COUNT));
     return GP_OK;
 }
 
@@ -1190,6 +1224,7 @@ gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *str
 }
 
 gp_status gp_observe_vec(gp_handle *h, float *agents, float *roads, float *signals, void *stream) {
+    NvtxRange range("gp_observe_vec");
     if (!h) return fail(GP_EINVAL, "null handle");
     if ((agents && !aligned16(agents)) || (roads && !aligned16(roads)) ||
         (signals && !aligned16(signals)))

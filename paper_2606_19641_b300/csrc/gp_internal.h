@@ -139,6 +139,7 @@ struct RenderParams {
     int debug_stall;         // pipelined kernel: producers publish nothing (timeout test)
     uint32_t *status;
 
+    unsigned long long *stats;  // GP_STAT_* counters, or null (off)
     int dump_view;           // -1 = off
     DumpTri *dump;
     int *dump_count;

@@ -550,7 +550,7 @@ struct Shared {
 
 // Rasterise a batch of n triangles into the key buffer of the band of rows by0..by1 (all
 // threads of group g call; ends with a group barrier).
-template <bool F32>
+template <bool F32, bool ST>
 __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys, TriRec *tris,
                       int *rowoff, unsigned short *map, int *s_warp, const Group &g) {
     n = min(n, p.tri_cap);
@@ -566,7 +566,13 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
         rowoff[t] = run;
         run += tri_items(tris[t].span);
     }
-    if (tid == 0) rowoff[n] = total;
+    if (tid == 0) {
+        rowoff[n] = total;
+        if (ST && p.stats) {
+            atomicAdd(&p.stats[GP_STAT_BATCHES], 1ull);
+            atomicAdd(&p.stats[GP_STAT_ROW_ITEMS], (unsigned long long)total);
+        }
+    }
     g.sync();
 
     const int chunk = nt * kItemsPerThread;
@@ -624,6 +630,11 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
                         low = T.low;
                     }
                 }
+            }
+            if (ST && p.stats) {
+                const int fr = __reduce_add_sync(0xffffffffu, cnt);
+                if ((tid & 31) == 0 && fr)
+                    atomicAdd(&p.stats[GP_STAT_FRAGMENTS], (unsigned long long)fr);
             }
             warp_fragments<F32>(cnt, kofs, gx0, a, inner, low, keys);
         }
@@ -685,6 +696,7 @@ __device__ __forceinline__ void empty_rec(TriRec &r) { r.span = 1u; }  // i0 = 1
 // and the segment compacts the outputs through shared scratch.  The polygon is then
 // fan-triangulated from its first vertex, one fan triangle per lane, into slots[6 j ..).
 // Called by all threads of group grp for jobs [0, njobs) of `jobs`.
+template <bool ST>
 __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const uint32_t *jobs,
                           int njobs, TriRec *slots, float *scratch, const Group &grp) {
     const int lane = grp.tid & 31, warp = grp.warp(), nw = grp.nw();
@@ -772,15 +784,22 @@ __device__ void clip_jobs(const RenderParams &p, const Cam &cm, int view, const 
                            __shfl_sync(0xffffffffu, Y, s2)};
         const float td[3] = {__shfl_sync(0xffffffffu, d, seg0), __shfl_sync(0xffffffffu, d, s1),
                              __shfl_sync(0xffffffffu, d, s2)};
+        bool built = false;
         if (active && gl < 6) {
             TriRec &r = slots[6 * job + gl];
             int i0, i1, j0, j1;
             if (n >= 3 && gl + 2 < n && tri_bbox(p, cm, tX, tY, i0, i1, j0, j1)) {
                 build_rec(r, tX, tY, td, prim, p.key_f16, i0, i1, j0, j1, cm.by0);
                 if (view == p.dump_view) dump_tri(p, tX, tY, td, prim, (uint32_t)gl);
+                built = true;
             } else {
                 empty_rec(r);
             }
+        }
+        if (ST && p.stats) {
+            const unsigned int b = __ballot_sync(0xffffffffu, built);
+            if ((threadIdx.x & 31) == 0 && b)
+                atomicAdd(&p.stats[GP_STAT_TRIS_FROM_CLIP], (unsigned long long)__popc(b));
         }
     }
 }
@@ -849,6 +868,7 @@ __device__ __forceinline__ void source_quad(const RenderParams &p, const Cam &cm
 // (warp-uniform call).  Returns false if the clip queue or the batch has no room;
 // `clips_queued` tells the retry (after a flush) whether this unit's clip jobs are already
 // queued.
+template <bool ST>
 __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, TriRec *tris,
                            uint32_t *clipq, const int *vq0, const int *vpre, int nvcl, int nvq,
                            const unsigned char *visbox, const unsigned char *vissig, int view,
@@ -938,6 +958,7 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
         if (qb < 0) return false;
         if (clip0) clipq[qb + __popc(c0 & lt)] = tcode;
         if (clip1) clipq[qb + n0 + __popc(c1 & lt)] = tcode + 1u;
+        if (ST && p.stats && lane == 0) atomicAdd(&p.stats[GP_STAT_TRIS_CLIPPED], (unsigned long long)nc);
     }
     clips_queued = true;
     if (!(k0 | k1)) return true;
@@ -946,6 +967,7 @@ __device__ bool setup_unit(const RenderParams &p, const Cam &cm, Shared &sh, Tri
     if (lane == 0) base = cas_reserve(&sh.resv, nk, p.tri_cap);
     base = __shfl_sync(0xffffffffu, base, 0);
     if (base < 0) return false;
+    if (ST && p.stats && lane == 0) atomicAdd(&p.stats[GP_STAT_TRIS_KEPT], (unsigned long long)nk);
     if (keep0) {
         const int tX[3] = {X[0], X[1], X[2]}, tY[3] = {Y[0], Y[1], Y[2]};
         const float td[3] = {d[0], d[1], d[2]};
@@ -1444,7 +1466,7 @@ struct SetupMem {
 // full, and once with last = true when the item is done (that batch may be empty) -- and
 // returns the batch to fill next, or nullptr to abandon the item; all threads of g call it
 // after a group barrier, and it ends with one.  Returns false if the item was abandoned.
-template <class Emit>
+template <bool ST, class Emit>
 __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int view,
                              Shared &sh, SetupMem &m, const Group &g, Emit &emit) {
     // 1. cull clusters and boxes against the band frustum
@@ -1509,6 +1531,13 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
         if (lane == 0) sh.nvq = run;
     }
     g.sync();
+    if (ST && p.stats && g.tid == 0) {
+        atomicAdd(&p.stats[GP_STAT_ITEMS], 1ull);
+        atomicAdd(&p.stats[GP_STAT_CLUSTERS], (unsigned long long)sh.nvcl);
+        atomicAdd(&p.stats[GP_STAT_BOXES], (unsigned long long)sh.nvbox);
+        atomicAdd(&p.stats[GP_STAT_SIGNALS], (unsigned long long)sh.nvsig);
+        atomicAdd(&p.stats[GP_STAT_QUADS], (unsigned long long)(sh.nvq + 6 * sh.nvbox + 32 * sh.nvsig));
+    }
 
     // 2. setup: warps pull units until the units run out or the batch is full; then the
     //    batch is handed over; repeat until every unit is placed.
@@ -1534,7 +1563,7 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
             }
             if (u >= n_units) break;
             bool queued = false;
-            if (!setup_unit(p, cm, sh, m.tris, m.clipq, m.vq0, m.vpre, nvcl, nvq, m.visbox,
+            if (!setup_unit<ST>(p, cm, sh, m.tris, m.clipq, m.vq0, m.vpre, nvcl, nvq, m.visbox,
                             m.vissig, view, u, n_box_units, nbox_items, n_sig_units, done_clips,
                             queued)) {
                 pend = u;
@@ -1555,7 +1584,7 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
                 continue;
             }
             const int take = min(nq, room);
-            clip_jobs(p, cm, view, m.clipq + (nq - take), take, m.tris + rv, m.clipscratch, g);
+            clip_jobs<ST>(p, cm, view, m.clipq + (nq - take), take, m.tris + rv, m.clipscratch, g);
             g.sync();
             if (g.tid == 0) {
                 sh.cq_n = nq - take;
@@ -1582,7 +1611,7 @@ __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldIn
 
 // One block does everything for its items: setup, then raster of each full batch, then
 // the encode of the band.
-template <bool F32>
+template <bool F32, bool ST>
 __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
@@ -1604,7 +1633,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     int view = 0;
     auto emit = [&](bool last) -> TriRec * {
         const int n = sh.resv;
-        if (n > 0) flush<F32>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, s_warp, g);
+        if (n > 0) flush<F32, ST>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, s_warp, g);
         if (g.tid == 0) sh.resv = 0;
         g.sync();
         if (last) {  // 3. encode and store the band
@@ -1618,7 +1647,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
         const int item = next_item(p, sh, iter, g);
         if (item >= p.n_items) break;
         make_cam(p, item, cm, wi, view);
-        produce_item(p, cm, wi, view, sh, m, g, emit);
+        produce_item<ST>(p, cm, wi, view, sh, m, g, emit);
     }
 }
 
@@ -1687,7 +1716,7 @@ __device__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned lon
 // own hardware barrier (1 producers, 2 consumers).  Every handoff wait is bounded (p.wait_ns):
 // on a timeout the side records it, sets GP_DEV_PIPELINE_TIMEOUT and leaves as a whole, and
 // the other side then times out too.
-template <bool F32>
+template <bool F32, bool ST>
 __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
@@ -1748,7 +1777,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             const int item = next_item(p, sh, iter, g);
             if (item >= p.n_items) break;
             make_cam(p, item, cm, wi, view);
-            if (!produce_item(p, cm, wi, view, sh, m, g, emit)) {
+            if (!produce_item<ST>(p, cm, wi, view, sh, m, g, emit)) {
                 ok = false;
                 break;
             }
@@ -1772,7 +1801,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             const BatchMeta mt = meta[b];
             if (mt.flags & kBatchEnd) break;
             if (mt.n > 0)
-                flush<F32>(p, mt.by0, mt.by1, mt.n, keys, tris0 + (size_t)b * p.tri_cap, rowoff,
+                flush<F32, ST>(p, mt.by0, mt.by1, mt.n, keys, tris0 + (size_t)b * p.tri_cap, rowoff,
                            map, s_warp, g);
             mbar_arrive(&bars[2 + b]);  // release: this thread is done reading buffer b
             if (mt.flags & kBatchLast) {
@@ -1857,8 +1886,11 @@ static cudaError_t upload_signal_tables() {
 }
 
 cudaError_t render_configure(size_t max_smem) {
-    const void *fns[4] = {(const void *)render_kernel<true>, (const void *)render_kernel<false>,
-                          (const void *)render_kernel_ws<true>, (const void *)render_kernel_ws<false>};
+    // the ST = true instances count GP_STAT_* events (gp_config.stats)
+    const void *fns[8] = {(const void *)render_kernel<true, false>, (const void *)render_kernel<false, false>,
+                          (const void *)render_kernel_ws<true, false>, (const void *)render_kernel_ws<false, false>,
+                          (const void *)render_kernel<true, true>, (const void *)render_kernel<false, true>,
+                          (const void *)render_kernel_ws<true, true>, (const void *)render_kernel_ws<false, true>};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)max_smem);
@@ -1869,8 +1901,8 @@ cudaError_t render_configure(size_t max_smem) {
 
 static const void *render_fn(int key_f16, int prod_warps) {
     if (prod_warps > 0)
-        return key_f16 ? (const void *)render_kernel_ws<false> : (const void *)render_kernel_ws<true>;
-    return key_f16 ? (const void *)render_kernel<false> : (const void *)render_kernel<true>;
+        return key_f16 ? (const void *)render_kernel_ws<false, false> : (const void *)render_kernel_ws<true, false>;
+    return key_f16 ? (const void *)render_kernel<false, false> : (const void *)render_kernel<true, false>;
 }
 
 int render_occupancy(int key_f16, int threads, size_t smem, int prod_warps) {
@@ -1884,11 +1916,23 @@ cudaError_t launch_render(const RenderParams &p, int blocks, int threads, size_t
                           cudaStream_t s) {
     if (p.n_items <= 0) return cudaSuccess;
     if (p.prod_warps > 0) {
-        if (p.key_f16) render_kernel_ws<false><<<blocks, threads, smem, s>>>(p);
-        else render_kernel_ws<true><<<blocks, threads, smem, s>>>(p);
+        if (p.stats) {
+            if (p.key_f16) render_kernel_ws<false, true><<<blocks, threads, smem, s>>>(p);
+            else render_kernel_ws<true, true><<<blocks, threads, smem, s>>>(p);
+        } else if (p.key_f16) {
+            render_kernel_ws<false, false><<<blocks, threads, smem, s>>>(p);
+        } else {
+            render_kernel_ws<true, false><<<blocks, threads, smem, s>>>(p);
+        }
     } else {
-        if (p.key_f16) render_kernel<false><<<blocks, threads, smem, s>>>(p);
-        else render_kernel<true><<<blocks, threads, smem, s>>>(p);
+        if (p.stats) {
+            if (p.key_f16) render_kernel<false, true><<<blocks, threads, smem, s>>>(p);
+            else render_kernel<true, true><<<blocks, threads, smem, s>>>(p);
+        } else if (p.key_f16) {
+            render_kernel<false, false><<<blocks, threads, smem, s>>>(p);
+        } else {
+            render_kernel<true, false><<<blocks, threads, smem, s>>>(p);
+        }
     }
     return cudaGetLastError();
 }

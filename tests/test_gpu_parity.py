@@ -1128,3 +1128,39 @@ def test_reset_worlds():
     assert np.array_equal(st3, st_init) and not fl3.any() and not sim.get_dynamics().any()
     sim.reset_worlds()
     assert sim.status() == 0
+
+
+def test_render_stats_counters():
+    """GP_STAT_* counters of one render against what the GPU's own triangles imply: one item
+    per (view, band), the kept triangles equal the records rasterised, and the fragments
+    equal the covered (triangle, pixel) pairs of the raster rule."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl, stats=1)
+    out, depth = sim.alloc_outputs()
+    sim.render_stats(reset=True)
+    sim.render(out, depth)
+    st = sim.render_stats(reset=True)
+    bands = -(-int(cfg.height) // int(sim.info.band_rows))
+    assert st["items"] == sim.n_views * bands
+    n_rec = frags = 0
+    be = 12 * int(worlds.box_off[1])
+    re = be + 2 * int(worlds.road_off[1])
+    for v in range(sim.n_views):
+        tris = sim.dump_tris(v, out, depth)
+        n_rec += len(tris)
+        for t in dedupe(tris):
+            one = np.zeros(1, oracle.TRI_DTYPE)
+            for k in ("X", "Y", "d", "prim", "sub"):
+                one[k] = t[k]
+            frags += int((oracle.raster(one, int(cfg.width), int(cfg.height), False, be, re).key != 0).sum())
+    print("render stats:", st)
+    assert st["tris_kept"] + st["tris_from_clip"] == n_rec
+    assert st["fragments"] == frags
+    assert st["row_items"] >= st["tris_kept"] and st["batches"] >= 1 and st["quads"] > 0
+    direct, _ = sim_for(worlds, wl)
+    with pytest.raises(gp.GigapixelError) as e:
+        direct.render_stats()
+    assert e.value.status == gp.binding.GP_ESTATE
