@@ -15,6 +15,9 @@ constexpr int kClusterQuads = 32;  // quads per culling cluster = one quad per l
 constexpr int kMaxClustersPerWorld = 4096;
 constexpr int kMaxBandRows = 128;  // rows per screen band (raster records pack band-relative rows)
 constexpr int kMaxSignals = GP_MAX_SIGNALS;
+// The ray-tracing kernel (128 threads, four warps) stages one box per thread and compacts
+// them with one ballot per warp.
+static_assert(kMaxBoxes <= 128, "trace_kernel keeps at most one box per thread");
 constexpr int kSignalQuads = 32;   // faces of a signal polyhedron = one setup unit
 
 // Per-world table (device).
