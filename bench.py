@@ -414,9 +414,20 @@ def main():
         et[1].record(stream)
         barrier()
         tr_ms = maxred(et[0].elapsed_time(et[1])) / tr_steps
+        # step + trace replayed from one graph per step (gp_step_trace)
+        for k in range(2):
+            sim.step_trace(act, out, depth, stream=stream)
+        barrier()
+        et[0].record(stream)
+        for k in range(tr_steps):
+            sim.step_trace(act, out, depth, stream=stream)
+        et[1].record(stream)
+        barrier()
+        st_ms = maxred(et[0].elapsed_time(et[1])) / tr_steps
         extras["ray_traced"] = {
             "trace_kernel_ms": tr_ms,
-            "agent_steps_per_s_step_plus_trace": job_rate(total_agents, 1, tr_ms + stepk_ms),
+            "agent_steps_per_s_step_plus_trace": job_rate(total_agents, 1, st_ms),
+            "ms_per_step_graph": st_ms,
             "render_gbs": algo_bytes / (tr_ms / 1e3) / 1e9,
             "render_frac_of_measured_hbm": algo_bytes / (tr_ms / 1e3) / 1e9 / peak,
             "note": "one ray per pixel: box slabs, lane-line and road plane hits via the grid"}

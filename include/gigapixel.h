@@ -252,11 +252,14 @@ gp_status gp_trace(gp_handle *h, void *out_dev, void *depth_dev, void *stream);
 
 /*
  * gp_step followed by gp_render, replayed from a CUDA graph (captured on the first call
- * for this (actions, out, depth) pointer triple; up to 4 triples are cached).  The
- * pointers must stay valid while their graph is cached (until gp_destroy).
+ * for this (actions, out, depth) pointer triple; up to 4 graphs are cached, shared with
+ * gp_step_trace).  The pointers must stay valid while their graph is cached (until
+ * gp_destroy).  gp_step_trace is the same with gp_trace as the renderer.
  */
 gp_status gp_step_render(gp_handle *h, const float *actions_dev, void *out_dev,
                          void *depth_dev, void *stream);
+gp_status gp_step_trace(gp_handle *h, const float *actions_dev, void *out_dev,
+                        void *depth_dev, void *stream);
 
 /*
  * Per-world path: step or render one world only (one launch each), writing the world's

@@ -34,7 +34,7 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
                       ("prim", "<u4"), ("sub", "<u4")])
 
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render", "gp_trace",
-            "gp_step_render", "gp_step_world", "gp_render_world", "gp_get_state",
+            "gp_step_render", "gp_step_trace", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_step": [vp, vp, vp],
         "gp_render": [vp, vp, vp, vp],
         "gp_step_render": [vp, vp, vp, vp, vp],
+        "gp_step_trace": [vp, vp, vp, vp, vp],
         "gp_step_world": [vp, i32, vp, vp],
         "gp_render_world": [vp, i32, vp, vp, vp],
         "gp_get_state": [vp, vp, vp, ctypes.c_int, vp],
@@ -271,6 +272,11 @@ class Simulator:
     def step_render(self, actions, out, depth=None, stream=None) -> None:
         check(lib().gp_step_render(self._h, _ptr(actions), _ptr(out), _ptr(depth),
                                    _stream(stream)))
+
+    def step_trace(self, actions, out, depth=None, stream=None) -> None:
+        """One step then the ray-traced render, replayed from a CUDA graph."""
+        check(lib().gp_step_trace(self._h, _ptr(actions), _ptr(out), _ptr(depth),
+                                  _stream(stream)))
 
     def step_world(self, world: int, actions, stream=None) -> None:
         check(lib().gp_step_world(self._h, world, _ptr(actions), _stream(stream)))

@@ -72,7 +72,9 @@ struct Shape {
 
 struct GraphKey {
     const void *a, *o, *d;
+    int backend;  // 0: step + raster, 1: step + ray tracing
     bool operator<(const GraphKey &k) const {
+        if (backend != k.backend) return backend < k.backend;
         if (a != k.a) return a < k.a;
         if (o != k.o) return o < k.o;
         return d < k.d;
@@ -1026,16 +1028,17 @@ gp_status gp_render(gp_handle *h, void *out, void *depth, void *stream) {
     return GP_OK;
 }
 
-gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *depth,
-                         void *stream) {
-    NvtxRange range("gp_step_render");
+// One step followed by one render (backend 0: raster, 1: ray tracing), replayed from a
+// CUDA graph cached per (backend, actions, out, depth).
+static gp_status step_then_render(gp_handle *h, const float *actions, void *out, void *depth,
+                                  void *stream, int backend) {
     if (!h) return fail(GP_EINVAL, "null handle");
     if (!actions) return fail(GP_EINVAL, "actions_dev is null");
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
-    GraphKey key{actions, out, depth};
+    GraphKey key{actions, out, depth, backend};
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (h->graphs.size() >= 4) {
@@ -1045,7 +1048,11 @@ gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *de
         cudaStream_t cs = h->capture_stream;
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e1 = launch_step(step_params(h, actions), 8 * h->sms, cs);
-        cudaError_t e2 = e1 == cudaSuccess ? enqueue_render(h, render_params(h, out, depth), cs) : e1;
+        cudaError_t e2 = e1;
+        if (e1 == cudaSuccess)
+            e2 = backend ? (h->n_views ? launch_trace(render_params(h, out, depth), h->n_views, cs)
+                                       : cudaSuccess)
+                         : enqueue_render(h, render_params(h, out, depth), cs);
         cudaGraph_t g = nullptr;
         cudaError_t e3 = cudaStreamEndCapture(cs, &g);
         if (e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -1062,6 +1069,18 @@ gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *de
     }
     CK(cudaGraphLaunch(it->second, (cudaStream_t)stream));
     return GP_OK;
+}
+
+gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *depth,
+                         void *stream) {
+    NvtxRange range("gp_step_render");
+    return step_then_render(h, actions, out, depth, stream, 0);
+}
+
+gp_status gp_step_trace(gp_handle *h, const float *actions, void *out, void *depth,
+                        void *stream) {
+    NvtxRange range("gp_step_trace");
+    return step_then_render(h, actions, out, depth, stream, 1);
 }
 
 gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions, void *stream) {

@@ -1164,3 +1164,31 @@ def test_render_stats_counters():
     with pytest.raises(gp.GigapixelError) as e:
         direct.render_stats()
     assert e.value.status == gp.binding.GP_ESTATE
+
+
+def test_step_trace_graph_matches_direct_calls():
+    """The step + ray-tracing graph gives the same images and states as the direct calls,
+    and shares the graph cache with the raster graph."""
+    import torch
+    wl = wg.WORKLOADS["paper_rig_210x126"]
+    worlds = wg.make_workload(wl, n_worlds=2)
+    a, cfg = sim_for(worlds, wl)
+    b, _ = sim_for(worlds, wl)
+    oa, da = a.alloc_outputs()
+    ob, db = b.alloc_outputs()
+    oc, dc = b.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(3):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        a.step(act)
+        a.trace(oa, da)
+        b.step_trace(act, ob, db)
+        torch.cuda.synchronize()
+        assert torch.equal(oa, ob) and torch.equal(da.view(torch.int16), db.view(torch.int16))
+    # both graph kinds on the same pointers are distinct cache entries
+    a.step(act)
+    a.render(oa, da)
+    b.step_render(act, oc, dc)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, oc)
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
