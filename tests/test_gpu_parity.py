@@ -1130,7 +1130,8 @@ def test_reset_worlds():
     assert sim.status() == 0
 
 
-def test_render_stats_counters():
+@pytest.mark.parametrize("shape", [dict(), dict(producer_warps=2)], ids=["default", "pipelined"])
+def test_render_stats_counters(shape):
     """GP_STAT_* counters of one render against what the GPU's own triangles imply: one item
     per (view, band), the kept triangles equal the records rasterised, and the fragments
     equal the covered (triangle, pixel) pairs of the raster rule."""
@@ -1138,7 +1139,7 @@ def test_render_stats_counters():
     import paper_2606_19641_b300 as gp
     wl = wg.WORKLOADS["tiny"]
     worlds = wg.make_workload(wl)
-    sim, cfg = sim_for(worlds, wl, stats=1)
+    sim, cfg = sim_for(worlds, wl, stats=1, **shape)
     out, depth = sim.alloc_outputs()
     sim.render_stats(reset=True)
     sim.render(out, depth)
