@@ -435,7 +435,8 @@ def onehot_bf16(cls: np.ndarray, mean=(0.5,) * 4, std=(0.5,) * 4) -> np.ndarray:
 class Sim:
     """Oracle simulation of a batch of worlds: FP64 agent state, latched flags."""
 
-    def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0, jerk_dynamics: bool = False):
+    def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0, jerk_dynamics: bool = False,
+                 episode_steps: int = 0):
         self.w = worlds
         self.dt, self.vmax = dt, vmax
         na = worlds.n_agents
@@ -452,6 +453,12 @@ class Sim:
             bx = worlds.boxes[b0:b0 + (a1 - a0)].astype(np.float64)
             self.state[a0:a1, 0:3] = bx[:, 0:3]
             self.state[a0:a1, 3] = bx[:, 6]
+        # episodes (App. A "Other Details": episodes end after a fixed time): after
+        # episode_steps steps a world's agents return to their initial state with only the
+        # done flag (8) set; 0 = never
+        self.episode_steps = episode_steps
+        self.ep = np.zeros(worlds.n_worlds, np.int64)
+        self.state0 = self.state.copy()
 
     def set_state(self, state, flags, jerk=None) -> None:
         self.state[:] = np.asarray(state, np.float64)
@@ -487,13 +494,21 @@ class Sim:
             a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
             b = self.boxes6(w)
             st = np.ascontiguousarray(self.state[a0:a1])
-            fl = np.ascontiguousarray(self.flags[a0:a1])
+            fl = np.ascontiguousarray(self.flags[a0:a1] & ~np.uint8(8))
             jk = None if self.jerk is None else np.ascontiguousarray(self.jerk[a0:a1])
             step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax, jk)
             self.state[a0:a1] = st
             self.flags[a0:a1] = fl
             if jk is not None:
                 self.jerk[a0:a1] = jk
+            if self.episode_steps:
+                self.ep[w] += 1
+                if self.ep[w] >= self.episode_steps:
+                    self.ep[w] = 0
+                    self.state[a0:a1] = self.state0[a0:a1]
+                    self.flags[a0:a1] = 8
+                    if self.jerk is not None:
+                        self.jerk[a0:a1] = 0.0
 
     def camera_tris(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> np.ndarray:
         a = int(self.agent_off[w]) + agent_local

@@ -1502,3 +1502,21 @@ def test_red_light_violation_term():
     assert r_of(0.5, -0.5, [0], sph=[[-50.0, 0.0, 5.0, 0.4]]) == pytest.approx(
         r_of(0.5, -0.5, [2], sph=[[-50.0, 0.0, 5.0, 0.4]]) - W_INF[6])
     assert r_of(-0.5, 0.5, [0], fl_before=4 | 1) == 0.0  # halted agents earn nothing
+
+
+def test_episode_end_returns_worlds_to_their_start():
+    """A world's agents are back at the descriptor's poses and speeds, with only the done
+    flag, exactly every episode_steps steps; other steps keep moving."""
+    import worldgen as wg
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim = oracle.Sim(worlds, episode_steps=3)
+    b0 = worlds.boxes[:worlds.n_agents]
+    start = np.column_stack([b0[:, 0:3], b0[:, 6]]).astype(np.float64)
+    assert np.array_equal(sim.state, start)
+    for k in range(7):
+        sim.step(wg.actions(wl.seed, k, worlds.n_agents))
+        if (k + 1) % 3 == 0:
+            assert np.array_equal(sim.state, start) and np.all(sim.flags == 8)
+        else:
+            assert not np.array_equal(sim.state, start) and not np.any(sim.flags & 8)
