@@ -48,7 +48,8 @@ enum { GP_KEY_F32 = 0, GP_KEY_F16 = 1 };
 /* Image encoding written by gp_render. */
 enum { GP_OUT_CLASS_U8 = 0, GP_OUT_ONEHOT_BF16 = 1, GP_OUT_RGB_U8 = 2 };
 /* Per-agent flag bits (latched for the lifetime of the handle or until gp_set_state). */
-enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4 };
+enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4,
+       GP_FLAG_DONE = 8 /* set for one step: the world's episode ended and it was reset */ };
 /* Device status bits (sticky until gp_clear_status). */
 enum {
     GP_DEV_NONFINITE_STATE = 1u << 0, /* an agent's state became NaN/inf */
@@ -186,6 +187,9 @@ typedef struct gp_config {
     float v_limit;                /* speed limit of the overspeed term (default 30 m/s) */
     int32_t dynamics;             /* GP_DYN_DIRECT (default) or GP_DYN_JERK */
     int32_t stats;                /* 1: count GP_STAT_* events in every render (default 0) */
+    int32_t episode_steps;        /* > 0: after this many steps of a world its agents return to
+                                     their initial state, flags = GP_FLAG_DONE (default 0 =
+                                     never; 200 is the paper's 20 s at dt = 0.1 s) */
     float signal_colour[4][3];    /* RGB in 0..1 of signal states red, amber, green, off
                                      (defaults 0.9 0.1 0.1 / 0.95 0.7 0.1 / 0.1 0.8 0.3 /
                                      0.25 0.25 0.25); shaded like every surface */
@@ -273,7 +277,8 @@ gp_status gp_render_world(gp_handle *h, int32_t world, void *out_dev, void *dept
  * Agent state: state[n_agents][4] = x, y, yaw, v (float) and flags[n_agents] (uint8).
  * on_host = 1: host pointers (the call synchronises the stream); 0: device pointers.
  * gp_set_state also forks/resumes a simulation (e.g. teacher rollouts from a snapshot);
- * it zeroes the jerk dynamics' actuator state (restore it with gp_set_dynamics after).
+ * it zeroes the jerk dynamics' actuator state (restore it with gp_set_dynamics after) and
+ * leaves the per-world episode step counters alone (gp_reset_worlds restarts them).
  */
 gp_status gp_get_state(gp_handle *h, float *state, uint8_t *flags, int on_host, void *stream);
 gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, int on_host,
@@ -282,7 +287,8 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
 /*
  * Episode reset: the agents of every world w with mask[w] != 0 (every world if mask is
  * NULL) return to their initial pose and speed from gp_create_worlds, with clear flags and
- * zero previous-step accelerations and actuator state; other worlds are untouched.
+ * zero previous-step accelerations and actuator state, and the world's episode step
+ * counter restarts; other worlds are untouched.
  *   mask  uint8 [n_worlds]; on_host != 0: host memory (synchronous), else device memory
  *         (asynchronous on `stream`, so it can follow a device-side "done" test).
  */

@@ -20,7 +20,7 @@ KEY_F32, KEY_F16 = 0, 1
 OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8 = 0, 1, 2
 CLASS_SIGNAL = 4
 SIGNAL_RED, SIGNAL_AMBER, SIGNAL_GREEN, SIGNAL_OFF = 0, 1, 2, 3
-FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED = 1, 2, 4
+FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED, FLAG_DONE = 1, 2, 4, 8
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
 DYN_DIRECT, DYN_JERK = 0, 1
@@ -73,7 +73,8 @@ class Config(ctypes.Structure):
                 ("colour", (ctypes.c_float * 3) * 4),
                 ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
                 ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32),
-                ("stats", ctypes.c_int32), ("signal_colour", (ctypes.c_float * 3) * 4)]
+                ("stats", ctypes.c_int32), ("episode_steps", ctypes.c_int32),
+                ("signal_colour", (ctypes.c_float * 3) * 4)]
 
 
 class Info(ctypes.Structure):

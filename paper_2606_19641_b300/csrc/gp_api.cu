@@ -94,7 +94,8 @@ struct gp_handle {
     DevBuf<float4> box_pose, box_dim, quad_geo, road_geo, line_geo, sig;
     DevBuf<uint8_t> sig_state;
     DevBuf<int> sig_quad;
-    DevBuf<unsigned long long> stats;  // GP_STAT_* counters (gp_config.stats)  // road quad (road_geo index) each signal controls, -1 if none
+    DevBuf<unsigned long long> stats;  // GP_STAT_* counters (gp_config.stats)
+    DevBuf<int> ep_counter;            // per-world episode step counter  // road quad (road_geo index) each signal controls, -1 if none
     DevBuf<float> speed, speed0;
     DevBuf<float4> pose0;  // initial poses and speeds (gp_reset_worlds)
     DevBuf<uint8_t> flags;
@@ -142,6 +143,7 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
         return fail(GP_EINVAL, "output");
     if (c->rewards != 0 && c->rewards != 1) return fail(GP_EINVAL, "rewards must be 0 or 1");
     if (c->stats != 0 && c->stats != 1) return fail(GP_EINVAL, "stats must be 0 or 1");
+    if (c->episode_steps < 0) return fail(GP_EINVAL, "episode_steps must be >= 0");
     if (c->dynamics != GP_DYN_DIRECT && c->dynamics != GP_DYN_JERK)
         return fail(GP_EINVAL, "dynamics must be GP_DYN_DIRECT or GP_DYN_JERK");
     if (c->rewards && !(c->lane_width > 0.f && c->v_limit >= 0.f))
@@ -352,6 +354,10 @@ StepParams step_params(gp_handle *h, const float *actions) {
     p.sig = h->sig.p;
     p.sig_state = h->sig_state.p;
     p.sig_quad = h->sig_quad.p;
+    p.episode_steps = h->cfg.episode_steps;
+    p.ep_counter = h->ep_counter.p;
+    p.pose0 = h->pose0.p;
+    p.speed0 = h->speed0.p;
     return p;
 }
 
@@ -567,6 +573,7 @@ void release_all(gp_handle *h) {
     h->sig_state.release();
     h->sig_quad.release();
     h->stats.release();
+    h->ep_counter.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -945,6 +952,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     {
         std::vector<unsigned long long> z(GP_STAT_COUNT, 0ull);
         UP(stats, z);
+        std::vector<int> ep(std::max(1, nw), 0);
+        UP(ep_counter, ep);
     }
     std::vector<int> one(1, 0);
     UP(counter, one);
@@ -1181,6 +1190,8 @@ gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *
     cudaStream_t s = (cudaStream_t)stream;
     ResetParams p{};
     p.n_agents = h->n_agents;
+    p.n_worlds = h->n_worlds;
+    p.ep_counter = h->ep_counter.p;
     p.mask = mask;
     if (mask && on_host) {
         if (h->n_worlds) CK(cudaMemcpyAsync(h->world_stage.p, mask, h->n_worlds, cudaMemcpyHostToDevice, s));

@@ -74,6 +74,11 @@ struct StepParams {
     const float4 *sig;
     const uint8_t *sig_state;
     const int *sig_quad;
+    // fixed-length episodes (episode_steps > 0): per-world step counter, initial state
+    int episode_steps;
+    int *ep_counter;       // [n_worlds]
+    const float4 *pose0;   // [n_boxes]
+    const float *speed0;   // [n_agents]
 };
 
 // Vectorized observations (gp_observe_vec).
@@ -158,7 +163,8 @@ cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
 
 // Episode reset of selected worlds (gp_reset_worlds).
 struct ResetParams {
-    int n_agents;
+    int n_agents, n_worlds;
+    int *ep_counter;      // [n_worlds] episode step counters (zeroed for reset worlds)
     const uint8_t *mask;  // [n_worlds] or null = all
     const int *agent_world, *agent_box;
     const float4 *pose0;  // initial box poses

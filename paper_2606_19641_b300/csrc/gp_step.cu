@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
         const float x0 = pose.x, y0 = pose.y;  // centre before the step (red-light term)
         if (tid < wi.n_agents) {
             const int a = wi.agent_begin + tid;
-            fl = p.flags[a];
+            fl = p.flags[a] & ~GP_FLAG_DONE;  // the done flag lasts one step
             fl0 = fl;
             v = p.speed[a];
             v0 = v;
@@ -297,6 +297,27 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
                 agent_reward(p, wi, a, x0, y0, pose.x, pose.y, pose.z, v, v0, act, dim.x, dim.y, fl0,
                              fl);
         }
+        if (p.episode_steps > 0) {
+            // end of the world's episode: its agents return to their initial state (the
+            // step's rewards stand); the done flag marks it for one step
+            __shared__ int s_done;
+            __syncthreads();
+            if (tid == 0) {
+                int *c = p.ep_counter + p.world_begin + wl;
+                const int n = *c + 1 >= p.episode_steps ? 0 : *c + 1;
+                *c = n;
+                s_done = n == 0;
+            }
+            __syncthreads();
+            if (s_done && tid < na) {
+                const int a = wi.agent_begin + tid;
+                p.box_pose[wi.box_begin + tid] = p.pose0[wi.box_begin + tid];
+                p.speed[a] = p.speed0[a];
+                p.flags[a] = GP_FLAG_DONE;
+                p.acc[a] = make_float2(0.f, 0.f);
+                if (p.dynamics) p.jerk[3 * a] = p.jerk[3 * a + 1] = p.jerk[3 * a + 2] = 0.f;
+            }
+        }
         __syncthreads();
     }
 }
@@ -326,6 +347,7 @@ __global__ void state_kernel(float *state, uint8_t *flags, float4 *pose, float *
 // accelerations and zero actuator state.
 __global__ void reset_kernel(ResetParams p) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < p.n_worlds && (!p.mask || p.mask[a])) p.ep_counter[a] = 0;
     if (a >= p.n_agents) return;
     if (p.mask && !p.mask[p.agent_world[a]]) return;
     const int b = p.agent_box[a];
@@ -339,8 +361,9 @@ __global__ void reset_kernel(ResetParams p) {
 }  // namespace
 
 cudaError_t launch_reset(const ResetParams &p, cudaStream_t s) {
-    if (p.n_agents <= 0) return cudaSuccess;
-    reset_kernel<<<(p.n_agents + 255) / 256, 256, 0, s>>>(p);
+    const int n = p.n_agents > p.n_worlds ? p.n_agents : p.n_worlds;
+    if (n <= 0) return cudaSuccess;
+    reset_kernel<<<(n + 255) / 256, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

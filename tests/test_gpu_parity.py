@@ -1193,3 +1193,40 @@ def test_step_trace_graph_matches_direct_calls():
     torch.cuda.synchronize()
     assert torch.equal(oa, oc)
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
+
+
+def test_fixed_length_episodes():
+    """episode_steps: every world returns to its start with the done flag after exactly that
+    many steps, matching the oracle from the same state; gp_reset_worlds restarts a world's
+    count."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    sim, _ = sim_for(worlds, wl, episode_steps=4)
+    osim = oracle.Sim(worlds, episode_steps=4)
+    start, _ = sim.get_state()
+    for k in range(9):
+        st0, fl0 = sim.get_state()
+        osim.set_state(st0.astype(np.float64), fl0)
+        act_t, act = torch_actions(worlds, k, wl.seed)
+        sim.step(act_t)
+        osim.step(act)
+        st1, fl1 = sim.get_state()
+        assert np.array_equal(fl1, osim.flags), "flags, step %d" % k
+        assert np.allclose(st1, osim.state, atol=2e-4)
+        if (k + 1) % 4 == 0:
+            assert np.all(fl1 == gp.FLAG_DONE) and np.array_equal(st1, start)
+        else:
+            assert not np.any(fl1 & gp.FLAG_DONE)
+    # one step into the third episode; restart world 1: its episode now ends 4 steps later
+    sim.reset_worlds(np.array([0, 1, 0], np.uint8))
+    off = worlds.agent_offsets()
+    a0, a1 = int(off[1]), int(off[2])
+    for k in range(4):
+        sim.step(torch_actions(worlds, 20 + k, wl.seed)[0])
+        fl = sim.get_state()[1]
+        other = np.ones(len(fl), bool)
+        other[a0:a1] = False
+        assert np.all(fl[other] == gp.FLAG_DONE) == (k == 2)
+        assert np.all(fl[a0:a1] == gp.FLAG_DONE) == (k == 3)
