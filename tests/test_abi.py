@@ -75,6 +75,10 @@ def _desc(gp, worlds):
     d.road = arr(worlds["road"], np.float32, ctypes.c_float)
     d.line_off = arr(worlds["line_off"], np.int32, ctypes.c_int32)
     d.line = arr(worlds["line"], np.float32, ctypes.c_float)
+    if "signal_off" in worlds:
+        d.signal_off = arr(worlds["signal_off"], np.int32, ctypes.c_int32)
+        d.signal = arr(worlds["signal"], np.float32, ctypes.c_float)
+        d.signal_state = arr(worlds["signal_state"], np.uint8, ctypes.c_uint8)
     return d, keep
 
 
@@ -99,6 +103,13 @@ def _good():
     (lambda w, c: setattr(c, "key_precision", 7), -1),
     (lambda w, c: setattr(c, "threads", 100), -1),
     (lambda w, c: setattr(c, "dynamics", 2), -1),
+    (lambda w, c: setattr(c, "stats", 2), -1),
+    (lambda w, c: setattr(c, "episode_steps", -1), -1),
+    (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, 0, 5, 0.0]], signal_state=[0]), -1),
+    (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, 0, 5, 0.4]], signal_state=[4]), -1),
+    (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, np.nan, 5, 0.4]], signal_state=[0]), -1),
+    (lambda w, c: w.update(signal_off=[0, 33], signal=np.tile([0, 0, 5, 0.4], (33, 1)),
+                           signal_state=np.zeros(33)), -4),
     (lambda w, c: w.update(box_off=[0, 130], agents=[1], boxes=np.tile([1, 1, 0, 4, 2, 1.5, 0], (130, 1))), -4),
 ])
 def test_create_rejects_invalid_input_on_host(gp, mutate, status):
