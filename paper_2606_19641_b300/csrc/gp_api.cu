@@ -775,10 +775,10 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         wi.cell_begin = (int)cell_off.size() - 1;
         build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.ginv, wi.gnx, wi.gny, cell_off,
                     cell_quads);
-        // lane-line strips are thin: a finer grid (2 m cells, at most 256 per side) keeps
+        // lane-line strips are thin: a finer grid (1 m cells, at most 256 per side) keeps
         // their per-cell lists short for the ray tracer's lookups
         {
-            const float lcs = std::max(2.f, std::max(bx1 - bx0, by1 - by0) / 255.f);
+            const float lcs = std::max(1.f, std::max(bx1 - bx0, by1 - by0) / 255.f);
             wi.lginv = 1.f / lcs;
             wi.lgnx = std::max(1, (int)std::ceil((bx1 - bx0) / lcs) + 1);
             wi.lgny = std::max(1, (int)std::ceil((by1 - by0) / lcs) + 1);

@@ -1207,7 +1207,8 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
                 if (o[k] < lo[k] || o[k] > hi[k]) inside = false;
                 continue;
             }
-            float ta = (lo[k] - o[k]) / d[k], tb = (hi[k] - o[k]) / d[k];
+            const float rd = __frcp_rn(d[k]);  // one reciprocal, two products
+            float ta = (lo[k] - o[k]) * rd, tb = (hi[k] - o[k]) * rd;
             int fa = 2 * k + 1;  // entering through the low side: face -k
             if (ta > tb) {
                 const float tt = ta;
