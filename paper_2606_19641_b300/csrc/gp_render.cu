@@ -1275,7 +1275,7 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
                 if (num < 0.f) inside = false;
                 continue;
             }
-            const float t = num / den;
+            const float t = num * __frcp_rn(den);
             if (den < 0.f) {
                 if (t > t0) {
                     t0 = t;
