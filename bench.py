@@ -186,19 +186,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def profiled_traffic(shape):
-    """DRAM bytes per render launch from the committed ncu summary, if that capture was taken
-    of the current render source at the same launch shape; else None."""
+def profiled_traffic(shape, kernel="render_kernel"):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, if that capture was
+    taken of the current render source at the same launch shape; else None."""
     import hashlib
     import re
     here = os.path.dirname(os.path.abspath(__file__))
     try:
-        text = open(os.path.join(here, "profiles", "render_kernel_uniform_128x128.md")).read()
+        text = open(os.path.join(here, "profiles", kernel + "_uniform_128x128.md")).read()
         src = open(os.path.join(here, "paper_2606_19641_b300", "csrc", "gp_render.cu"), "rb").read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch: (\d+) \(render source sha256 ([0-9a-f]+), "
-                  r"shape ([0-9,]+)\)", text)
+                  r"shape ([0-9a-z,]+)\)", text)
     if not m or m.group(3) != shape:
         return None
     if hashlib.sha256(src).hexdigest()[:len(m.group(2))] != m.group(2):
@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--backend", default="raster", choices=["raster", "trace"],
+                    help="renderer of the timed step: the rasteriser (default) or the ray tracer")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the 3-camera resolution sweep 64..512 (extra minutes)")
     ap.add_argument("--shape", default="",
@@ -264,10 +266,14 @@ def main():
     def maxred(x):
         return reduce_over_ranks(x, "max", world, "cuda")
 
+    trace = args.backend == "trace"
+    step_render = sim.step_trace if trace else sim.step_render
+    render = sim.trace if trace else sim.render
+
     # warm-up (graph capture happens on the first replay)
     for k in range(args.warmup):
         act.copy_(acts[k])
-        sim.step_render(act, out, depth)
+        step_render(act, out, depth)
     barrier()
 
     # --- timed: graph replays of step+render, L2 evicted between steps (not timed) ---
@@ -279,7 +285,7 @@ def main():
             act.copy_(acts[args.warmup + k])
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            sim.step_render(act, out, depth)
+            step_render(act, out, depth)
             ev[k][1].record(stream)
         barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -298,7 +304,7 @@ def main():
         evr[k][0].record(stream)
         sim.step(act)
         evr[k][1].record(stream)
-        sim.render(out, depth)
+        render(out, depth)
         evr[k][2].record(stream)
     barrier()
     render_ms = statistics.mean(b.elapsed_time(c) for a, b, c in evr)
@@ -309,9 +315,11 @@ def main():
     peak, peak_kind = peaks()
     achieved = algo_bytes / (render_ms / 1e3) / 1e9
     shape_s = "%d,%d,%d" % (sim.info.band_rows, sim.info.threads, sim.info.tri_capacity)
+    kernel = "trace_kernel" if trace else "render_kernel"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(shape_s),
-                "kernel": "render_kernel",
+                "frac": achieved / peak,
+                "traffic": profiled_traffic("trace" if trace else shape_s, kernel),
+                "kernel": kernel,
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
                 "avg_launch_ms": render_ms, "frac_of_nominal_8tbs": achieved / 8000.0}
 
@@ -330,7 +338,7 @@ def main():
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         act.copy_(h_acts[k], non_blocking=True)
-        sim.step_render(act, out, depth)
+        step_render(act, out, depth)
         sim.get_state_device(d_state, d_flags)
         h_state.copy_(d_state, non_blocking=True)
         h_flags.copy_(d_flags, non_blocking=True)
@@ -507,7 +515,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(wl, wl.n_worlds), "worlds_per_gpu": worlds.n_worlds,
                        "cameras_per_gpu": sim.n_views, "resolution": "%dx%d" % (wl.width, wl.height),
-                       "output": "uint8 class + fp32 depth", "launch": "CUDA graph: step + render",
+                       "output": "uint8 class + fp32 depth",
+                       "renderer": "ray tracer (gp_step_trace)" if trace else "rasteriser",
+                       "launch": "CUDA graph: step + %s" % ("trace" if trace else "render"),
                        "l2": "2x L2 buffer written between timed steps (outside the events); each "
                              "step also writes %.0f MB of images" % (out_bytes / 1e6),
                        "band_rows": sim.info.band_rows, "threads": sim.info.threads,
