@@ -102,6 +102,10 @@ def _lib():
                                          ctypes.c_double, c_f64p, c_f64p, c_f64p]
         lib.or_observe_signals.argtypes = [ctypes.c_int32, c_f64p, ctypes.c_int32, c_f64p, c_u8p,
                                            ctypes.c_int32, ctypes.c_double, c_f64p, c_f64p]
+        lib.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.or_splitmix64.restype = ctypes.c_uint64
+        lib.or_conditioning.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, c_f64p, c_f64p]
         lib.or_lane_frame.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, c_f32p,
                                       ctypes.c_double, c_f64p, c_f64p]
         lib.or_lane_frame.restype = ctypes.c_int
@@ -320,6 +324,20 @@ def observe_world(boxes6, speed, road, line, K=OBS_AGENTS, r_agents=OBS_AGENT_RA
     return ao, ro
 
 
+def splitmix64(seed: int, n: int) -> int:
+    """n-th output (n >= 1) of the SplitMix64 stream seeded with `seed`."""
+    return int(_lib().or_splitmix64(seed & (2**64 - 1), n & (2**64 - 1)))
+
+
+def conditioning(seed: int, world: int, episode: int, agent: int):
+    """(reward weights [10], normalised conditioning vector [12]) of one agent and episode
+    (see or_conditioning)."""
+    w = np.zeros(10, np.float64)
+    c = np.zeros(12, np.float64)
+    _lib().or_conditioning(seed & (2**64 - 1), world, episode, agent, _p(w, c_f64p), _p(c, c_f64p))
+    return w, c
+
+
 OBS_SIGNALS, OBS_SIGNAL_RADIUS = 4, 50.0
 
 
@@ -436,7 +454,7 @@ class Sim:
     """Oracle simulation of a batch of worlds: FP64 agent state, latched flags."""
 
     def __init__(self, worlds, dt: float = 0.1, vmax: float = 30.0, jerk_dynamics: bool = False,
-                 episode_steps: int = 0):
+                 episode_steps: int = 0, conditioning_seed: Optional[int] = None):
         self.w = worlds
         self.dt, self.vmax = dt, vmax
         na = worlds.n_agents
@@ -459,6 +477,15 @@ class Sim:
         self.episode_steps = episode_steps
         self.ep = np.zeros(worlds.n_worlds, np.int64)
         self.state0 = self.state.copy()
+        # reward conditioning: per-agent weights and normalised vector, redrawn at every
+        # episode start (episode index per world counts the restarts)
+        self.cond_seed = conditioning_seed
+        self.episode_index = np.zeros(worlds.n_worlds, np.int64)
+        self.weights = np.tile(np.array(REWARD_WEIGHTS, np.float64), (na, 1))
+        self.cond = np.zeros((na, 12), np.float64)
+        if conditioning_seed is not None:
+            for w in range(worlds.n_worlds):
+                self._draw(w)
 
     def set_state(self, state, flags, jerk=None) -> None:
         self.state[:] = np.asarray(state, np.float64)
@@ -504,11 +531,31 @@ class Sim:
             if self.episode_steps:
                 self.ep[w] += 1
                 if self.ep[w] >= self.episode_steps:
-                    self.ep[w] = 0
-                    self.state[a0:a1] = self.state0[a0:a1]
+                    self._restart(w)
                     self.flags[a0:a1] = 8
-                    if self.jerk is not None:
-                        self.jerk[a0:a1] = 0.0
+
+    def _draw(self, w: int) -> None:
+        a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
+        for i in range(a1 - a0):
+            self.weights[a0 + i], self.cond[a0 + i] = conditioning(
+                self.cond_seed, w, int(self.episode_index[w]), i)
+
+    def _restart(self, w: int) -> None:
+        """A new episode of world w: initial state, clear flags, next conditioning draw."""
+        a0, a1 = int(self.agent_off[w]), int(self.agent_off[w + 1])
+        self.ep[w] = 0
+        self.state[a0:a1] = self.state0[a0:a1]
+        self.flags[a0:a1] = 0
+        if self.jerk is not None:
+            self.jerk[a0:a1] = 0.0
+        self.episode_index[w] += 1
+        if self.cond_seed is not None:
+            self._draw(w)
+
+    def reset_worlds(self, mask=None) -> None:
+        for w in range(self.w.n_worlds):
+            if mask is None or mask[w]:
+                self._restart(w)
 
     def camera_tris(self, cam: CamConfig, w: int, agent_local: int, cam_yaw: float) -> np.ndarray:
         a = int(self.agent_off[w]) + agent_local

@@ -456,6 +456,43 @@ void or_observe_world(int32_t n_boxes, int32_t n_agents, const double *boxes, co
 }
 
 /*
+ * SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+ * OOPSLA 2014; the 64-bit variant as published with xoroshiro): the n-th output (n >= 1) of
+ * the stream seeded with s is mix(s + n * 0x9E3779B97F4A7C15), mix the variant-13 finaliser.
+ */
+uint64_t or_splitmix64(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/*
+ * Reward conditioning (App. A "Reward Functions and Reward Conditioning", Table "Reward
+ * terms", training distribution): at every episode start each agent's twelve coefficients
+ * are drawn independently and uniformly from the table's ranges; the policy sees them
+ * normalised to [-1, 1].  Readings: coefficient k of agent i (index within its world) of
+ * world w in episode e uses u = top 24 bits of SplitMix64 output n = 1 + (w << 40 | e << 20 |
+ * i << 4 | k) of the stream seeded with `seed`, scaled by 2^-24; value = lo + (hi - lo) u,
+ * normalised 2 u - 1.  Coefficients 0..9 are the reward weights (collision .. overspeed);
+ * 10 and 11 (goal radius, goal speed tolerance) are only observed (no goals here).
+ *   -> w10 [10], c12 [12]
+ */
+static const double COND_LO[12] = {0.0, 0.0, 0.0, 2.5e-4, 2.5e-4, 0.0, 0.0, 0.0, 2.5e-4, 0.0, 2.0, 1.0};
+static const double COND_HI[12] = {3.0, 3.0, 0.05, 2.5e-2, 7.5e-3, 5e-3, 1.0, 5e-5, 7.5e-3, 1.0, 12.0, 5.0};
+
+void or_conditioning(uint64_t seed, uint32_t world, uint32_t episode, uint32_t agent, double *w10,
+                     double *c12) {
+    for (int k = 0; k < 12; ++k) {
+        const uint64_t c = ((uint64_t)world << 40) | ((uint64_t)(episode & 0xFFFFFu) << 20) |
+                           ((uint64_t)(agent & 0xFFFFu) << 4) | (uint64_t)k;
+        const double u = (double)(or_splitmix64(seed, c + 1) >> 40) / 16777216.0;
+        if (k < 10) w10[k] = COND_LO[k] + (COND_HI[k] - COND_LO[k]) * u;
+        c12[k] = 2.0 * u - 1.0;
+    }
+}
+
+/*
  * Traffic controls of O_vec (App. A "Observations": the vectorized observation also holds
  * traffic-control states).  Reading: per agent i the signal spheres s whose centre is
  * within r_sig of c_i on the ground plane, nearest first (ties to the lower index), at

@@ -84,6 +84,8 @@ MUTANTS = {
     "red light fires on leaving": ("                if (!or_point_in_quad(before[4 * i], before[4 * i + 1], road + 8 * q) &&\n                    or_point_in_quad(after[4 * i], after[4 * i + 1], road + 8 * q)) {", "                if (or_point_in_quad(before[4 * i], before[4 * i + 1], road + 8 * q) &&\n                    !or_point_in_quad(after[4 * i], after[4 * i + 1], road + 8 * q)) {"),
     "red light any state": ("                if (sig_state[s] != 0) continue;", "                if (sig_state[s] > 1) continue;"),
     "red light counted per signal": ("                    r -= w[6];\n                    break;", "                    r -= w[6];"),
+    "splitmix mix constant": ("    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "    z = (z ^ (z >> 27)) * 0x94D049BB133111EDull;"),
+    "conditioning range swapped": ("static const double COND_HI[12] = {3.0, 3.0, 0.05,", "static const double COND_HI[12] = {3.0, 3.0, 0.5,"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

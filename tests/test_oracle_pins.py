@@ -1520,3 +1520,39 @@ def test_episode_end_returns_worlds_to_their_start():
             assert np.array_equal(sim.state, start) and np.all(sim.flags == 8)
         else:
             assert not np.array_equal(sim.state, start) and not np.any(sim.flags & 8)
+
+
+def test_splitmix64_known_outputs():
+    # the first outputs of the SplitMix64 stream seeded with 0, as published with the
+    # generator; the n-th output depends only on (seed, n)
+    assert [oracle.splitmix64(0, n) for n in (1, 2, 3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert oracle.splitmix64(12345, 7) == oracle.splitmix64(12345, 7)
+    assert oracle.splitmix64(12345, 7) != oracle.splitmix64(12346, 7)
+
+
+def test_reward_conditioning_ranges_and_normalisation():
+    lo = np.array([0, 0, 0, 2.5e-4, 2.5e-4, 0, 0, 0, 2.5e-4, 0, 2, 1], np.float64)  # Table "Reward terms"
+    hi = np.array([3, 3, 0.05, 2.5e-2, 7.5e-3, 5e-3, 1, 5e-5, 7.5e-3, 1, 12, 5], np.float64)
+    cs = []
+    for w in range(3):
+        for e in range(3):
+            for i in range(40):
+                wt, c = oracle.conditioning(99, w, e, i)
+                assert np.all(c >= -1.0) and np.all(c < 1.0)
+                assert np.allclose(wt, lo[:10] + (hi[:10] - lo[:10]) * (c[:10] + 1) / 2, rtol=1e-12)
+                assert np.all((c + 1) * 2 ** 23 == np.round((c + 1) * 2 ** 23))  # 24-bit uniforms
+                cs.append(c)
+    cs = np.array(cs)
+    assert abs(cs.mean()) < 0.02 and abs(cs.var() - 1 / 3) < 0.02  # U(-1, 1)
+    assert len({tuple(c) for c in cs}) == len(cs)  # every (world, episode, agent) differs
+    # the oracle's episode restarts redraw: episode 0 at start, 1 after the first restart
+    import worldgen as wg
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim = oracle.Sim(worlds, episode_steps=2, conditioning_seed=5)
+    assert np.allclose(sim.cond[3], oracle.conditioning(5, 0, 0, 3)[1])
+    for k in range(2):
+        sim.step(wg.actions(wl.seed, k, worlds.n_agents))
+    assert np.allclose(sim.cond[3], oracle.conditioning(5, 0, 1, 3)[1])
+    assert np.allclose(sim.weights[3], oracle.conditioning(5, 0, 1, 3)[0])
