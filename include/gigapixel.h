@@ -190,6 +190,11 @@ typedef struct gp_config {
     int32_t episode_steps;        /* > 0: after this many steps of a world its agents return to
                                      their initial state, flags = GP_FLAG_DONE (default 0 =
                                      never; 200 is the paper's 20 s at dt = 0.1 s) */
+    int32_t reward_conditioning;  /* 1: draw every agent's twelve reward coefficients from the
+                                     reward table's training distribution at each episode start
+                                     (App. A reward conditioning); 0 (default): the weights of
+                                     gp_set_reward_weights / the inference column */
+    uint32_t conditioning_seed;   /* seed of those draws (default 0) */
     float signal_colour[4][3];    /* RGB in 0..1 of signal states red, amber, green, off
                                      (defaults 0.9 0.1 0.1 / 0.95 0.7 0.1 / 0.1 0.8 0.3 /
                                      0.25 0.25 0.25); shaded like every surface */
@@ -300,6 +305,18 @@ gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *
  * gp_config.stats = 1.
  */
 gp_status gp_get_render_stats(gp_handle *h, uint64_t *out, int reset);
+
+/*
+ * Reward conditioning vector cond[n_agents][12] (float): the agent's twelve coefficients of
+ * its current episode normalised to [-1, 1] -- collision, off-road, comfort, alignment,
+ * centering, velocity, traffic light, time, reverse, overspeed (the reward weights in use),
+ * goal radius, goal speed tolerance (observed only).  Coefficient k of the agent with index i
+ * in world w, episode e (0 at create, +1 at every restart) is lo_k + (hi_k - lo_k) u, u the
+ * top 24 bits of output 1 + (w << 40 | e << 20 | i << 4 | k) of the SplitMix64 stream seeded
+ * with conditioning_seed, times 2^-24; the normalised value is 2 u - 1.  GP_ESTATE unless
+ * gp_config.reward_conditioning = 1.  on_host as for gp_get_state.
+ */
+gp_status gp_get_conditioning(gp_handle *h, float *cond, int on_host, void *stream);
 
 /*
  * Actuator state of the jerk dynamics, dyn[n_agents][3] float = a_lon, a_lat (m/s^2),

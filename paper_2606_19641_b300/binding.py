@@ -38,7 +38,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
-            "gp_get_render_stats",
+            "gp_get_render_stats", "gp_get_conditioning",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -74,6 +74,7 @@ class Config(ctypes.Structure):
                 ("rewards", ctypes.c_int32), ("lane_width", ctypes.c_float),
                 ("v_limit", ctypes.c_float), ("dynamics", ctypes.c_int32),
                 ("stats", ctypes.c_int32), ("episode_steps", ctypes.c_int32),
+                ("reward_conditioning", ctypes.c_int32), ("conditioning_seed", ctypes.c_uint32),
                 ("signal_colour", (ctypes.c_float * 3) * 4)]
 
 
@@ -125,6 +126,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_set_signal_states": [vp, vp, i32, vp],
         "gp_reset_worlds": [vp, vp, i32, vp],
         "gp_get_render_stats": [vp, vp, i32],
+        "gp_get_conditioning": [vp, vp, i32, vp],
         "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -326,6 +328,12 @@ class Simulator:
         a, r, s = out
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
         return a, r, s
+
+    def conditioning(self) -> np.ndarray:
+        """Reward conditioning vectors float32 [n_agents, 12] in [-1, 1] (host copy)."""
+        c = np.zeros((self.n_agents, 12), np.float32)
+        check(lib().gp_get_conditioning(self._h, _ptr(c), 1, _stream(None)))
+        return c
 
     def render_stats(self, reset: bool = False) -> dict:
         """GP_STAT_* render counters since create or the last reset (config stats = 1)."""

@@ -95,7 +95,9 @@ struct gp_handle {
     DevBuf<uint8_t> sig_state;
     DevBuf<int> sig_quad;
     DevBuf<unsigned long long> stats;  // GP_STAT_* counters (gp_config.stats)
-    DevBuf<int> ep_counter;            // per-world episode step counter  // road quad (road_geo index) each signal controls, -1 if none
+    DevBuf<int> ep_counter;            // per-world episode step counter
+    DevBuf<int> ep_index;              // per-agent episodes started (conditioning draws)
+    DevBuf<float> cond;                // per-agent conditioning vector [n_agents][12]  // road quad (road_geo index) each signal controls, -1 if none
     DevBuf<float> speed, speed0;
     DevBuf<float4> pose0;  // initial poses and speeds (gp_reset_worlds)
     DevBuf<uint8_t> flags;
@@ -144,6 +146,8 @@ gp_status validate(const gp_world_desc *d, const gp_config *c) {
     if (c->rewards != 0 && c->rewards != 1) return fail(GP_EINVAL, "rewards must be 0 or 1");
     if (c->stats != 0 && c->stats != 1) return fail(GP_EINVAL, "stats must be 0 or 1");
     if (c->episode_steps < 0) return fail(GP_EINVAL, "episode_steps must be >= 0");
+    if (c->reward_conditioning != 0 && c->reward_conditioning != 1)
+        return fail(GP_EINVAL, "reward_conditioning must be 0 or 1");
     if (c->dynamics != GP_DYN_DIRECT && c->dynamics != GP_DYN_JERK)
         return fail(GP_EINVAL, "dynamics must be GP_DYN_DIRECT or GP_DYN_JERK");
     if (c->rewards && !(c->lane_width > 0.f && c->v_limit >= 0.f))
@@ -356,8 +360,36 @@ StepParams step_params(gp_handle *h, const float *actions) {
     p.sig_quad = h->sig_quad.p;
     p.episode_steps = h->cfg.episode_steps;
     p.ep_counter = h->ep_counter.p;
+    p.conditioning = h->cfg.reward_conditioning;
+    p.cond_seed = h->cfg.conditioning_seed;
+    p.ep_index = h->ep_index.p;
+    p.cond = h->cond.p;
     p.pose0 = h->pose0.p;
     p.speed0 = h->speed0.p;
+    return p;
+}
+
+ResetParams reset_params(gp_handle *h) {
+    ResetParams p{};
+    p.n_agents = h->n_agents;
+    p.n_worlds = h->n_worlds;
+    p.ep_counter = h->ep_counter.p;
+    p.worlds = h->worlds.p;
+    p.conditioning = h->cfg.reward_conditioning;
+    p.cond_seed = h->cfg.conditioning_seed;
+    p.ep_index = h->ep_index.p;
+    p.weights = h->weights.p;
+    p.cond = h->cond.p;
+    p.mask = nullptr;
+    p.agent_world = h->agent_world.p;
+    p.agent_box = h->agent_box.p;
+    p.pose0 = h->pose0.p;
+    p.speed0 = h->speed0.p;
+    p.pose = h->box_pose.p;
+    p.speed = h->speed.p;
+    p.flags = h->flags.p;
+    p.acc = h->acc.p;
+    p.jerk = h->jerk.p;
     return p;
 }
 
@@ -574,6 +606,8 @@ void release_all(gp_handle *h) {
     h->sig_quad.release();
     h->stats.release();
     h->ep_counter.release();
+    h->ep_index.release();
+    h->cond.release();
     h->flags.release();
     h->agent_world.release();
     h->agent_box.release();
@@ -954,6 +988,10 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         UP(stats, z);
         std::vector<int> ep(std::max(1, nw), 0);
         UP(ep_counter, ep);
+        std::vector<int> ei(std::max(1, h->n_agents), 0);
+        UP(ep_index, ei);
+        std::vector<float> c0(12 * (size_t)std::max(1, h->n_agents), 0.f);
+        UP(cond, c0);
     }
     std::vector<int> one(1, 0);
     UP(counter, one);
@@ -1006,6 +1044,14 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
         gp_destroy(h);
         return fail(GP_ECUDA, "stream create");
+    }
+    if (h->cfg.reward_conditioning) {  // episode 0's conditioning draws
+        ResetParams rp = reset_params(h);
+        rp.draw_only = 1;
+        if (launch_reset(rp, 0) != cudaSuccess) {
+            gp_destroy(h);
+            return fail(GP_ECUDA, "create: conditioning draw");
+        }
     }
     if (cudaDeviceSynchronize() != cudaSuccess ||
         cudaMemset(h->stats.p, 0, sizeof(unsigned long long) * GP_STAT_COUNT) != cudaSuccess) {
@@ -1174,6 +1220,20 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
     return GP_OK;
 }
 
+gp_status gp_get_conditioning(gp_handle *h, float *cond, int on_host, void *stream) {
+    if (!h || !cond) return fail(GP_EINVAL, "null argument");
+    if (!h->cfg.reward_conditioning)
+        return fail(GP_ESTATE, "reward conditioning is off (gp_config.reward_conditioning = 0)");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    if (n)
+        CK(cudaMemcpyAsync(cond, h->cond.p, sizeof(float) * 12 * n,
+                           on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
 gp_status gp_get_render_stats(gp_handle *h, uint64_t *out, int reset) {
     if (!h || !out) return fail(GP_EINVAL, "null argument");
     if (!h->cfg.stats) return fail(GP_ESTATE, "stats are off (gp_config.stats = 0)");
@@ -1188,24 +1248,12 @@ gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *
     if (!h) return fail(GP_EINVAL, "null handle");
     CK(cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
-    ResetParams p{};
-    p.n_agents = h->n_agents;
-    p.n_worlds = h->n_worlds;
-    p.ep_counter = h->ep_counter.p;
+    ResetParams p = reset_params(h);
     p.mask = mask;
     if (mask && on_host) {
         if (h->n_worlds) CK(cudaMemcpyAsync(h->world_stage.p, mask, h->n_worlds, cudaMemcpyHostToDevice, s));
         p.mask = h->world_stage.p;
     }
-    p.agent_world = h->agent_world.p;
-    p.agent_box = h->agent_box.p;
-    p.pose0 = h->pose0.p;
-    p.speed0 = h->speed0.p;
-    p.pose = h->box_pose.p;
-    p.speed = h->speed.p;
-    p.flags = h->flags.p;
-    p.acc = h->acc.p;
-    p.jerk = h->jerk.p;
     CK(launch_reset(p, s));
     if (on_host) CK(cudaStreamSynchronize(s));
     return GP_OK;

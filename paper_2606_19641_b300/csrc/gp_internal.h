@@ -63,7 +63,7 @@ struct StepParams {
     // per-step reward terms and ego state (only if rewards != 0)
     int rewards;
     float lane_w, vlim;
-    const float *weights;   // [n_agents][10]
+    float *weights;         // [n_agents][10] (redrawn at episode starts with conditioning)
     float2 *acc;            // [n_agents] previous a_lon, a_lat (updated)
     float *reward;          // [n_agents]
     float *ego;             // [n_agents][GP_EGO_DIM]
@@ -79,6 +79,11 @@ struct StepParams {
     int *ep_counter;       // [n_worlds]
     const float4 *pose0;   // [n_boxes]
     const float *speed0;   // [n_agents]
+    // reward conditioning: coefficients redrawn at every episode start
+    int conditioning;
+    unsigned long long cond_seed;
+    int *ep_index;         // [n_agents] episodes started so far
+    float *cond;           // [n_agents][12] normalised coefficients
 };
 
 // Vectorized observations (gp_observe_vec).
@@ -164,7 +169,14 @@ cudaError_t launch_step(const StepParams &p, int max_blocks, cudaStream_t s);
 // Episode reset of selected worlds (gp_reset_worlds).
 struct ResetParams {
     int n_agents, n_worlds;
+    int draw_only;        // 1: draw the current episode's conditioning, change nothing else
     int *ep_counter;      // [n_worlds] episode step counters (zeroed for reset worlds)
+    const WorldInfo *worlds;
+    int conditioning;
+    unsigned long long cond_seed;
+    int *ep_index;        // [n_agents]
+    float *weights;       // [n_agents][10]
+    float *cond;          // [n_agents][12]
     const uint8_t *mask;  // [n_worlds] or null = all
     const int *agent_world, *agent_box;
     const float4 *pose0;  // initial box poses

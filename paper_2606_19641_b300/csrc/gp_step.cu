@@ -96,6 +96,35 @@ __device__ bool lane_frame(const StepParams &p, const WorldInfo &wi, float px, f
     return true;
 }
 
+// Reward conditioning (App. A "Reward Functions and Reward Conditioning", Table "Reward
+// terms", training distribution): coefficient k of the agent with index i in world w, in
+// its episode e, is lo_k + (hi_k - lo_k) u with u the top 24 bits of output
+// n = 1 + (w << 40 | e << 20 | i << 4 | k) of the SplitMix64 stream seeded with `seed`
+// (the stream's n-th output is its finaliser applied to seed + n * golden gamma), scaled by
+// 2^-24; the policy sees 2 u - 1.  Coefficients 0..9 are the reward weights, 10..11 the goal
+// radius and goal speed tolerance (observed only).
+__device__ __forceinline__ uint32_t splitmix_top24(unsigned long long seed, unsigned long long n) {
+    unsigned long long z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (uint32_t)((z ^ (z >> 31)) >> 40);
+}
+
+__device__ __forceinline__ void draw_conditioning(unsigned long long seed, int world, int episode,
+                                                  int agent, float *w10, float *c12) {
+    const float lo[12] = {0.f, 0.f, 0.f, 2.5e-4f, 2.5e-4f, 0.f, 0.f, 0.f, 2.5e-4f, 0.f, 2.f, 1.f};
+    const float hi[12] = {3.f, 3.f, 0.05f, 2.5e-2f, 7.5e-3f, 5e-3f, 1.f, 5e-5f, 7.5e-3f, 1.f, 12.f, 5.f};
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const unsigned long long c = ((unsigned long long)world << 40) |
+                                     ((unsigned long long)(episode & 0xFFFFF) << 20) |
+                                     ((unsigned long long)(agent & 0xFFFF) << 4) | (unsigned long long)k;
+        const float u = (float)splitmix_top24(seed, c + 1) * (1.f / 16777216.f);
+        if (k < 10) w10[k] = lo[k] + (hi[k] - lo[k]) * u;
+        c12[k] = 2.f * u - 1.f;
+    }
+}
+
 // Jerk-actuated control (App. A "Action Space and Dynamics"): the longitudinal and lateral
 // jerks move the accelerations, clipped to a_lon in [-5, 3] and |a_lat| <= 4 m/s^2; the
 // steering angle follows the curvature a_lat / max(v^2, 1) through tan(steer) = kappa 0.6 L,
@@ -316,6 +345,10 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
                 p.flags[a] = GP_FLAG_DONE;
                 p.acc[a] = make_float2(0.f, 0.f);
                 if (p.dynamics) p.jerk[3 * a] = p.jerk[3 * a + 1] = p.jerk[3 * a + 2] = 0.f;
+                const int e = ++p.ep_index[a];
+                if (p.conditioning)
+                    draw_conditioning(p.cond_seed, p.world_begin + wl, e, tid, p.weights + 10 * a,
+                                      p.cond + 12 * a);
             }
         }
         __syncthreads();
@@ -347,9 +380,24 @@ __global__ void state_kernel(float *state, uint8_t *flags, float4 *pose, float *
 // accelerations and zero actuator state.
 __global__ void reset_kernel(ResetParams p) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p.draw_only) {
+        if (a < p.n_agents && p.conditioning) {
+            const int w = p.agent_world[a];
+            draw_conditioning(p.cond_seed, w, p.ep_index[a], a - p.worlds[w].agent_begin,
+                              p.weights + 10 * a, p.cond + 12 * a);
+        }
+        return;
+    }
     if (a < p.n_worlds && (!p.mask || p.mask[a])) p.ep_counter[a] = 0;
     if (a >= p.n_agents) return;
     if (p.mask && !p.mask[p.agent_world[a]]) return;
+    {
+        const int w = p.agent_world[a];
+        const int e = ++p.ep_index[a];
+        if (p.conditioning)
+            draw_conditioning(p.cond_seed, w, e, a - p.worlds[w].agent_begin, p.weights + 10 * a,
+                              p.cond + 12 * a);
+    }
     const int b = p.agent_box[a];
     p.pose[b] = p.pose0[b];
     p.speed[a] = p.speed0[a];

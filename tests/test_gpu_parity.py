@@ -1230,3 +1230,52 @@ def test_fixed_length_episodes():
         other[a0:a1] = False
         assert np.all(fl[other] == gp.FLAG_DONE) == (k == 2)
         assert np.all(fl[a0:a1] == gp.FLAG_DONE) == (k == 3)
+
+
+def test_reward_conditioning():
+    """Conditioning vectors drawn at create, at every episode restart and at gp_reset_worlds
+    equal the oracle's draws; the rewards use the drawn weights."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    sim, _ = sim_for(worlds, wl, rewards=1, episode_steps=3, reward_conditioning=1,
+                     conditioning_seed=11)
+    osim = oracle.Sim(worlds, episode_steps=3, conditioning_seed=11)
+    first = osim.cond.copy()
+    assert np.array_equal(sim.conditioning(), osim.cond.astype(np.float32))
+    off = worlds.agent_offsets()
+    dims = np.zeros((worlds.n_agents, 2), np.float64)
+    for w in range(worlds.n_worlds):
+        b0 = int(worlds.box_off[w])
+        dims[off[w]:off[w + 1]] = worlds.boxes[b0:b0 + (off[w + 1] - off[w]), 3:5]
+    acc = np.zeros((worlds.n_agents, 2), np.float64)
+    for k in range(5):
+        st0, fl0 = sim.get_state()
+        weights = osim.weights.copy()
+        act_t, act = torch_actions(worlds, k, wl.seed)
+        sim.step(act_t)
+        osim.set_state(st0.astype(np.float64), fl0)
+        osim.step(act)
+        st1, fl1 = sim.get_state()
+        assert np.array_equal(sim.conditioning(), osim.cond.astype(np.float32)), "step %d" % k
+        if k == 2:  # the episode restarts: rewards are on the pre-restart state, not kept here
+            acc[:] = 0.0
+            continue
+        r = sim.rewards()[0].cpu().numpy()
+        for w in range(worlds.n_worlds):
+            a0, a1 = int(off[w]), int(off[w + 1])
+            road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
+            acc_w = np.ascontiguousarray(acc[a0:a1])
+            rr, _ = oracle.rewards_world(st0[a0:a1], fl0[a0:a1] & 7, st1[a0:a1], fl1[a0:a1],
+                                         act[a0:a1], dims[a0:a1], acc_w, weights[a0:a1], road)
+            acc[a0:a1] = acc_w
+            d = np.abs(r[a0:a1] - rr)
+            assert np.all((d <= 1e-4 + 1e-4 * np.abs(rr)) | (d <= weights[a0:a1, 2] + 1e-4))
+    assert not np.array_equal(osim.cond, first)  # redrawn at the restart
+    sim.reset_worlds(np.array([0, 1, 0], np.uint8))
+    osim.reset_worlds([0, 1, 0])
+    assert np.array_equal(sim.conditioning(), osim.cond.astype(np.float32))
+    direct, _ = sim_for(worlds, wl)
+    with pytest.raises(gp.GigapixelError):
+        direct.conditioning()
