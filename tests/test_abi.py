@@ -105,6 +105,7 @@ def _good():
     (lambda w, c: setattr(c, "dynamics", 2), -1),
     (lambda w, c: setattr(c, "stats", 2), -1),
     (lambda w, c: setattr(c, "episode_steps", -1), -1),
+    (lambda w, c: setattr(c, "reward_conditioning", 3), -1),
     (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, 0, 5, 0.0]], signal_state=[0]), -1),
     (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, 0, 5, 0.4]], signal_state=[4]), -1),
     (lambda w, c: w.update(signal_off=[0, 1], signal=[[0, np.nan, 5, 0.4]], signal_state=[0]), -1),
@@ -133,6 +134,8 @@ def test_null_handle_calls_fail_cleanly(gp):
     assert L.gp_get_dynamics(None, None, 1, None) == -1
     assert L.gp_set_dynamics(None, None, 1, None) == -1
     assert L.gp_reset_worlds(None, None, 1, None) == -1
+    assert L.gp_get_conditioning(None, None, 1, None) == -1
+    assert L.gp_get_render_stats(None, None, 0) == -1
     assert L.gp_set_signal_states(None, None, 1, None) == -1
 
 
