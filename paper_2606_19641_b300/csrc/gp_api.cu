@@ -1102,12 +1102,17 @@ static gp_status step_then_render(gp_handle *h, const float *actions, void *out,
         }
         cudaStream_t cs = h->capture_stream;
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = launch_step(step_params(h, actions), 8 * h->sms, cs);
+        StepParams sp = step_params(h, actions);
+        if (!backend && h->n_worlds > 0) sp.render_counter = h->counter.p;  // no memset node
+        cudaError_t e1 = launch_step(sp, 8 * h->sms, cs);
         cudaError_t e2 = e1;
         if (e1 == cudaSuccess)
             e2 = backend ? (h->n_views ? launch_trace(render_params(h, out, depth), h->n_views, cs)
                                        : cudaSuccess)
-                         : enqueue_render(h, render_params(h, out, depth), cs);
+                         : (sp.render_counter
+                                ? launch_render(render_params(h, out, depth), h->shape.blocks,
+                                                h->shape.threads, h->shape.smem, cs)
+                                : enqueue_render(h, render_params(h, out, depth), cs));
         cudaGraph_t g = nullptr;
         cudaError_t e3 = cudaStreamEndCapture(cs, &g);
         if (e2 != cudaSuccess || e3 != cudaSuccess) {

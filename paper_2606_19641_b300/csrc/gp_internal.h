@@ -84,6 +84,7 @@ struct StepParams {
     unsigned long long cond_seed;
     int *ep_index;         // [n_agents] episodes started so far
     float *cond;           // [n_agents][12] normalised coefficients
+    int *render_counter;   // non-null: zeroed for the render launch that follows (graphs)
 };
 
 // Vectorized observations (gp_observe_vec).

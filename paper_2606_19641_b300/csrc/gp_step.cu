@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
     __shared__ Footprint fp[kMaxBoxes];
     __shared__ unsigned int sflag[kMaxBoxes];
     const int tid = threadIdx.x;
+    // the render launched after this step in the same graph takes its work items from this
+    // counter (saves a memset node between the two kernels)
+    if (p.render_counter && blockIdx.x == 0 && tid == 0) *p.render_counter = 0;
 
     for (int wl = blockIdx.x; wl < p.n_worlds; wl += gridDim.x) {
         const WorldInfo wi = p.worlds[p.world_begin + wl];
