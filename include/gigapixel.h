@@ -325,14 +325,15 @@ gp_status gp_get_conditioning(gp_handle *h, float *cond, int on_host, void *stre
  * are taken as given.
  */
 gp_status gp_get_dynamics(gp_handle *h, float *dyn, int on_host, void *stream);
+gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *stream);
 
 /*
  * Traffic-signal states state[n_signals] (uint8, GP_SIGNAL_*; signals ordered by world),
- * seen by the next render in RGB output.  on_host as for gp_get_state; host values above
- * GP_SIGNAL_OFF are rejected (GP_EINVAL), device values are taken modulo 4.
+ * seen from the next call on: RGB colours, the red-light reward term and the traffic
+ * controls of O_vec.  on_host as for gp_get_state; host values above GP_SIGNAL_OFF are
+ * rejected (GP_EINVAL), device values are taken modulo 4.
  */
 gp_status gp_set_signal_states(gp_handle *h, const uint8_t *state, int on_host, void *stream);
-gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *stream);
 
 /* Sizes of a handle. */
 typedef struct gp_info {
