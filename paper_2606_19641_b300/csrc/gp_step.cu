@@ -181,7 +181,7 @@ __device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, fl
         // red-light violation: the centre enters a red signal's road quad during the step
         for (int s = 0; s < wi.n_sig; ++s) {
             const int q = p.sig_quad[wi.sig_begin + s];
-            if (q < 0 || p.sig_state[wi.sig_begin + s] != GP_SIGNAL_RED) continue;
+            if (q < 0 || (p.sig_state[wi.sig_begin + s] & 3) != GP_SIGNAL_RED) continue;
             const float4 g0 = p.road_geo[2 * q], g1 = p.road_geo[2 * q + 1];
             if (!in_quad(px0, py0, g0, g1) && in_quad(px, py, g0, g1)) {
                 r -= w[6];
