@@ -90,18 +90,42 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
+def _run_mutant(name, workdir):
+    """Compile the oracle with one planted mistake and run the pins against it; returns the
+    pins' exit status and the end of their output."""
     src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
     a, b = MUTANTS[name]
-    assert a in src, "mutation site not found: " + name
-    c = tmp_path / "mut.c"
-    so = tmp_path / "mut.so"
-    c.write_text(src.replace(a, b, 1))
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
-                           str(c), "-lm"])
-    env = dict(os.environ, ORACLE_SO=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x",
+    if a not in src:
+        return None, "mutation site not found: " + name
+    d = os.path.join(workdir, "m%d" % sorted(MUTANTS).index(name))
+    os.makedirs(d, exist_ok=True)
+    c, so = os.path.join(d, "mut.c"), os.path.join(d, "mut.so")
+    with open(c, "w") as fh:
+        fh.write(src.replace(a, b, 1))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, c,
+                           "-lm"])
+    env = dict(os.environ, ORACLE_SO=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, "pins did not catch mutant %r:\n%s" % (name, r.stdout[-2000:])
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """Every mutant's pin run, several at a time (each is an independent process); under
+    pytest-xdist the workers already run in parallel, so each test runs its own."""
+    import concurrent.futures
+    if os.environ.get("PYTEST_XDIST_WORKER"):
+        return None
+    work = str(tmp_path_factory.mktemp("mutants"))
+    names = sorted(MUTANTS)
+    with concurrent.futures.ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
+        return dict(zip(names, ex.map(lambda n: _run_mutant(n, work), names)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, mutant_results, tmp_path):
+    rc, out = mutant_results[name] if mutant_results is not None else _run_mutant(name, str(tmp_path))
+    assert rc is not None, out
+    assert rc != 0, "pins did not catch mutant %r:\n%s" % (name, out)
