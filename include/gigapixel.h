@@ -373,6 +373,8 @@ gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, v
  * accelerations to 0.
  */
 gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host, void *stream);
+/* The weights in use, [n_agents][10] (after conditioning draws too); on_host as above. */
+gp_status gp_get_reward_weights(gp_handle *h, float *weights, int on_host, void *stream);
 
 /*
  * Vectorized observations O_vec of every agent from the current state (App. A

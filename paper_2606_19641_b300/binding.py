@@ -38,7 +38,7 @@ EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "g
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
-            "gp_get_render_stats", "gp_get_conditioning",
+            "gp_get_render_stats", "gp_get_conditioning", "gp_get_reward_weights",
             "gp_debug_inject_status", "gp_debug_stall_pipeline", "gp_debug_dump_tris",
             "gp_debug_dump_tris_noalloc",
             "gp_last_error")
@@ -127,6 +127,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_reset_worlds": [vp, vp, i32, vp],
         "gp_get_render_stats": [vp, vp, i32],
         "gp_get_conditioning": [vp, vp, i32, vp],
+        "gp_get_reward_weights": [vp, vp, i32, vp],
         "gp_set_dynamics": [vp, vp, i32, vp],
         "gp_debug_stall_pipeline": [vp, vp, vp, i64, vp],
         "gp_debug_dump_tris": [vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp],
@@ -328,6 +329,12 @@ class Simulator:
         a, r, s = out
         check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
         return a, r, s
+
+    def reward_weights(self) -> np.ndarray:
+        """Reward weights in use, float32 [n_agents, 10] (host copy)."""
+        w = np.zeros((self.n_agents, 10), np.float32)
+        check(lib().gp_get_reward_weights(self._h, _ptr(w), 1, _stream(None)))
+        return w
 
     def conditioning(self) -> np.ndarray:
         """Reward conditioning vectors float32 [n_agents, 12] in [-1, 1] (host copy)."""

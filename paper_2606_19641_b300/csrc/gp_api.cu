@@ -1361,6 +1361,18 @@ gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host,
     return GP_OK;
 }
 
+gp_status gp_get_reward_weights(gp_handle *h, float *weights, int on_host, void *stream) {
+    if (!h || !weights) return fail(GP_EINVAL, "null argument");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)h->n_agents;
+    if (n)
+        CK(cudaMemcpyAsync(weights, h->weights.p, sizeof(float) * 10 * n,
+                           on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    if (on_host) CK(cudaStreamSynchronize(s));
+    return GP_OK;
+}
+
 gp_status gp_get_info(gp_handle *h, gp_info *info) {
     if (!h || !info) return fail(GP_EINVAL, "null argument");
     info->n_worlds = h->n_worlds;

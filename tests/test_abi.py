@@ -135,6 +135,7 @@ def test_null_handle_calls_fail_cleanly(gp):
     assert L.gp_set_dynamics(None, None, 1, None) == -1
     assert L.gp_reset_worlds(None, None, 1, None) == -1
     assert L.gp_get_conditioning(None, None, 1, None) == -1
+    assert L.gp_get_reward_weights(None, None, 1, None) == -1
     assert L.gp_get_render_stats(None, None, 0) == -1
     assert L.gp_set_signal_states(None, None, 1, None) == -1
 

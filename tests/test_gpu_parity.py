@@ -1244,6 +1244,7 @@ def test_reward_conditioning():
     osim = oracle.Sim(worlds, episode_steps=3, conditioning_seed=11)
     first = osim.cond.copy()
     assert np.array_equal(sim.conditioning(), osim.cond.astype(np.float32))
+    assert np.allclose(sim.reward_weights(), osim.weights, rtol=1e-6, atol=1e-12)
     off = worlds.agent_offsets()
     dims = np.zeros((worlds.n_agents, 2), np.float64)
     for w in range(worlds.n_worlds):
@@ -1276,6 +1277,7 @@ def test_reward_conditioning():
     sim.reset_worlds(np.array([0, 1, 0], np.uint8))
     osim.reset_worlds([0, 1, 0])
     assert np.array_equal(sim.conditioning(), osim.cond.astype(np.float32))
+    assert np.allclose(sim.reward_weights(), osim.weights, rtol=1e-6, atol=1e-12)
     direct, _ = sim_for(worlds, wl)
     with pytest.raises(gp.GigapixelError):
         direct.conditioning()
