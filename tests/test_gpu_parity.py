@@ -745,6 +745,44 @@ def test_trace_matches_oracle(name, n_worlds, output):
     assert mism <= 1e-3 * total
 
 
+def test_full_size_uniform_trace_sampled():
+    """The full uniform batch (256 worlds x 32 agents, 128x128, class + FP32 depth) ray
+    traced in the benchmark's launch configuration (step + trace replayed from one graph):
+    sampled views agree with the oracle's FP64 ray tracer except on grazing rays; every view
+    keeps the class/depth invariants."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl, autotune=1, key_precision=gp.KEY_F32)
+    out, depth = sim.alloc_outputs()
+    act = torch.empty((worlds.n_agents, 2), device="cuda")
+    for k in range(3):
+        act.copy_(torch_actions(worlds, k, wl.seed)[0])
+        sim.step_trace(act, out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    assert int(out.max()) <= 3
+    assert torch.equal(out > 0, depth > 0)
+    osim = oracle_sim(worlds, sim)
+    cam = cam_config(cfg)
+    rng = np.random.default_rng(5)
+    views = sorted(rng.choice(sim.n_views, 4, replace=False).tolist())
+    mism = total = 0
+    for v in views:
+        w, a, c = view_loc(worlds, cfg, v)
+        tr = osim.trace(cam, w, a, float(np.float32(cfg.cam_yaw[c])))
+        go, gd = gpu_view(cfg, out, depth, v)
+        bad = go != tr.cls
+        mism += int(bad.sum())
+        total += bad.size
+        both = ~bad & (go != 0)
+        assert np.allclose(gd.view(np.float32)[both], tr.depth[both], rtol=2e-5)
+    print("trace uniform full size: %d of %d pixels differ" % (mism, total))
+    assert mism <= 1e-3 * total
+
+
+
 def test_trace_and_raster_agree_away_from_silhouettes():
     """Both backends render the same scene: they may differ only along edges."""
     import torch
