@@ -13,7 +13,9 @@
  * Conventions for every entry point:
  *  - Device pointers are raw CUDA device addresses on the handle's device, contiguous, in
  *    the layout stated at each call.  The library never frees or keeps a caller pointer
- *    after a call returns (except inside a captured graph, see gp_step_render).
+ *    after a call returns (except inside a captured graph, see gp_step_render).  Pointers
+ *    that the handle's GPU cannot address (pageable host memory, another GPU's memory)
+ *    return GP_EINVAL before any launch; the sizes behind a pointer cannot be checked.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All work
  *    is enqueued asynchronously on it; the call returns before the GPU finishes.  Calls on
  *    one handle must be ordered (one stream, or caller-side events).

@@ -267,26 +267,71 @@ class Simulator:
             d = torch.empty((i.n_views, i.height, i.width), dtype=dt, device=dev)
         return out, d
 
+    def _dev(self, t, dtype, numel: int, name: str) -> int:
+        """Address of a device tensor the library will read or write, after checking that it
+        is a contiguous tensor on this simulator's GPU with the dtype and element count of the
+        layout the call expects (a host array or a short buffer would otherwise reach a
+        kernel).  None passes through as a null pointer, which the library checks itself."""
+        import torch
+        if t is None:
+            return 0
+        if not isinstance(t, torch.Tensor):
+            raise GigapixelError(GP_EINVAL, "%s: expected a torch tensor on cuda:%d, got %s"
+                                 % (name, self.device, type(t).__name__))
+        if t.device.type != "cuda" or t.device.index != self.device:
+            raise GigapixelError(GP_EINVAL, "%s: tensor on %s, the simulator is on cuda:%d"
+                                 % (name, t.device, self.device))
+        if t.dtype != dtype:
+            raise GigapixelError(GP_EINVAL, "%s: dtype %s, expected %s" % (name, t.dtype, dtype))
+        if not t.is_contiguous():
+            raise GigapixelError(GP_EINVAL, "%s: tensor is not contiguous" % name)
+        if t.numel() != numel:
+            raise GigapixelError(GP_EINVAL, "%s: %d elements (shape %s), expected %d"
+                                 % (name, t.numel(), tuple(t.shape), numel))
+        return t.data_ptr()
+
+    def _actions(self, actions) -> int:
+        import torch
+        return self._dev(actions, torch.float32, 2 * self.n_agents, "actions")
+
+    def _images(self, out, depth):
+        """(out, depth) addresses checked against the configured output layout."""
+        import torch
+        i = self.info
+        px = i.n_views * i.height * i.width
+        if i.output == OUT_CLASS_U8:
+            od, on = torch.uint8, px
+        elif i.output == OUT_RGB_U8:
+            od, on = torch.uint8, 3 * px
+        else:
+            od, on = torch.bfloat16, 4 * px
+        dd = torch.float32 if i.key_precision == KEY_F32 else torch.float16
+        return self._dev(out, od, on, "out"), self._dev(depth, dd, px, "depth")
+
     def step(self, actions, stream=None) -> None:
-        check(lib().gp_step(self._h, _ptr(actions), _stream(stream)))
+        check(lib().gp_step(self._h, self._actions(actions), _stream(stream)))
 
     def render(self, out, depth=None, stream=None) -> None:
-        check(lib().gp_render(self._h, _ptr(out), _ptr(depth), _stream(stream)))
+        o, d = self._images(out, depth)
+        check(lib().gp_render(self._h, o, d, _stream(stream)))
 
     def step_render(self, actions, out, depth=None, stream=None) -> None:
-        check(lib().gp_step_render(self._h, _ptr(actions), _ptr(out), _ptr(depth),
-                                   _stream(stream)))
+        a = self._actions(actions)
+        o, d = self._images(out, depth)
+        check(lib().gp_step_render(self._h, a, o, d, _stream(stream)))
 
     def step_trace(self, actions, out, depth=None, stream=None) -> None:
         """One step then the ray-traced render, replayed from a CUDA graph."""
-        check(lib().gp_step_trace(self._h, _ptr(actions), _ptr(out), _ptr(depth),
-                                  _stream(stream)))
+        a = self._actions(actions)
+        o, d = self._images(out, depth)
+        check(lib().gp_step_trace(self._h, a, o, d, _stream(stream)))
 
     def step_world(self, world: int, actions, stream=None) -> None:
-        check(lib().gp_step_world(self._h, world, _ptr(actions), _stream(stream)))
+        check(lib().gp_step_world(self._h, world, self._actions(actions), _stream(stream)))
 
     def render_world(self, world: int, out, depth=None, stream=None) -> None:
-        check(lib().gp_render_world(self._h, world, _ptr(out), _ptr(depth), _stream(stream)))
+        o, d = self._images(out, depth)
+        check(lib().gp_render_world(self._h, world, o, d, _stream(stream)))
 
     def get_state(self):
         """(state float32 [n_agents, 4] = x, y, yaw, v; flags uint8 [n_agents]) on the host."""
@@ -316,7 +361,8 @@ class Simulator:
 
     def trace(self, out, depth=None, stream=None) -> None:
         """Ray-traced render of every camera into the same tensors as render()."""
-        check(lib().gp_trace(self._h, _ptr(out), _ptr(depth), _stream(stream)))
+        o, d = self._images(out, depth)
+        check(lib().gp_trace(self._h, o, d, _stream(stream)))
 
     def observe_vec(self, stream=None, out=None):
         """(agents [n_agents, 16, 8], roads [n_agents, 32, 8], signals [n_agents, 4, 8])
@@ -327,7 +373,11 @@ class Simulator:
             out = tuple(torch.empty((self.n_agents, k, 8), dtype=torch.float32, device=dev)
                         for k in (16, 32, 4))
         a, r, s = out
-        check(lib().gp_observe_vec(self._h, _ptr(a), _ptr(r), _ptr(s), _stream(stream)))
+        n = self.n_agents
+        pa = self._dev(a, torch.float32, n * 16 * 8, "agents")
+        pr = self._dev(r, torch.float32, n * 32 * 8, "roads")
+        ps = self._dev(s, torch.float32, n * 4 * 8, "signals")
+        check(lib().gp_observe_vec(self._h, pa, pr, ps, _stream(stream)))
         return a, r, s
 
     def reward_weights(self) -> np.ndarray:

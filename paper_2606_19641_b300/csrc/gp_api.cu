@@ -402,6 +402,35 @@ gp_status check_out(void *out, void *depth) {
     return GP_OK;
 }
 
+// Can kernels on the handle's GPU address p?  Device memory of that GPU, managed memory and
+// mapped pinned host memory qualify; pageable host memory and another GPU's memory do not
+// (a kernel touching them would fault), so they are refused before any launch.  Null passes.
+gp_status check_reach(const gp_handle *h, const void *p, const char *what) {
+    if (!p) return GP_OK;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GP_EINVAL, std::string(what) + ": not a CUDA-addressable pointer (" +
+                                   cudaGetErrorString(e) + ")");
+    }
+    if (a.type == cudaMemoryTypeUnregistered)
+        return fail(GP_EINVAL, std::string(what) + " is pageable host memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != h->device)
+        return fail(GP_EINVAL, std::string(what) + " is on another GPU");
+    if (a.type == cudaMemoryTypeHost && !a.devicePointer)
+        return fail(GP_EINVAL, std::string(what) + " is pinned host memory without a device mapping");
+    return GP_OK;
+}
+
+gp_status check_reach(const gp_handle *h, const void *actions, const void *out,
+                      const void *depth) {
+    gp_status st = check_reach(h, actions, "actions_dev");
+    if (st == GP_OK) st = check_reach(h, out, "out_dev");
+    if (st == GP_OK) st = check_reach(h, depth, "depth_dev");
+    return st;
+}
+
 cudaError_t enqueue_render(gp_handle *h, const RenderParams &p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(h->counter.p, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -1068,6 +1097,8 @@ gp_status gp_step(gp_handle *h, const float *actions, void *stream) {
     if (!actions) return fail(GP_EINVAL, "actions_dev is null");
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
+    gp_status st = check_reach(h, actions, nullptr, nullptr);
+    if (st != GP_OK) return st;
     CK(launch_step(step_params(h, actions), 8 * h->sms, (cudaStream_t)stream));
     return GP_OK;
 }
@@ -1079,6 +1110,8 @@ gp_status gp_render(gp_handle *h, void *out, void *depth, void *stream) {
     if (st != GP_OK) return st;
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
+    st = check_reach(h, nullptr, out, depth);
+    if (st != GP_OK) return st;
     CK(enqueue_render(h, render_params(h, out, depth), (cudaStream_t)stream));
     return GP_OK;
 }
@@ -1096,6 +1129,9 @@ static gp_status step_then_render(gp_handle *h, const float *actions, void *out,
     GraphKey key{actions, out, depth, backend};
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
+        // checked once per pointer triple: replays of a cached graph reuse the same pointers
+        st = check_reach(h, actions, out, depth);
+        if (st != GP_OK) return st;
         if (h->graphs.size() >= 4) {
             cudaGraphExecDestroy(h->graphs.begin()->second);
             h->graphs.erase(h->graphs.begin());
@@ -1149,6 +1185,8 @@ gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions, void 
     if (!actions) return fail(GP_EINVAL, "actions_dev is null");
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
+    gp_status st = check_reach(h, actions, nullptr, nullptr);
+    if (st != GP_OK) return st;
     StepParams p = step_params(h, actions);
     p.world_begin = world;
     p.n_worlds = 1;
@@ -1163,6 +1201,8 @@ gp_status gp_trace(gp_handle *h, void *out, void *depth, void *stream) {
     if (st != GP_OK) return st;
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
+    st = check_reach(h, nullptr, out, depth);
+    if (st != GP_OK) return st;
     if (h->n_views) CK(launch_trace(render_params(h, out, depth), h->n_views, (cudaStream_t)stream));
     return GP_OK;
 }
@@ -1174,6 +1214,8 @@ gp_status gp_render_world(gp_handle *h, int32_t world, void *out, void *depth, v
     if (st != GP_OK) return st;
     if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
     CK(cudaSetDevice(h->device));
+    st = check_reach(h, nullptr, out, depth);
+    if (st != GP_OK) return st;
     RenderParams p = render_params(h, out, depth);
     p.item_begin = h->world_item_begin[world];
     p.n_items = h->world_item_count[world];
@@ -1313,6 +1355,10 @@ gp_status gp_observe_vec(gp_handle *h, float *agents, float *roads, float *signa
         (signals && !aligned16(signals)))
         return fail(GP_EINVAL, "outputs must be 16-byte aligned");
     CK(cudaSetDevice(h->device));
+    gp_status st = check_reach(h, agents, "agents_dev");
+    if (st == GP_OK) st = check_reach(h, roads, "roads_dev");
+    if (st == GP_OK) st = check_reach(h, signals, "signals_dev");
+    if (st != GP_OK) return st;
     ObsParams p{};
     p.worlds = h->worlds.p;
     p.agent_world = h->agent_world.p;

@@ -148,3 +148,21 @@ def test_fp16_primitive_limit(gp):
     d, keep = _desc(gp, w)
     h = ctypes.c_void_p()
     assert gp.lib().gp_create_worlds(ctypes.byref(d), ctypes.byref(c), 0, ctypes.byref(h)) == -4
+
+
+def test_binding_rejects_host_buffers_before_any_call(gp):
+    """The Python layer hands the library raw addresses, so a host array or a tensor on
+    another device must be refused before it could reach a kernel."""
+    import types
+    import torch
+    sim = gp.Simulator.__new__(gp.Simulator)
+    sim.device = 0
+    sim.info = types.SimpleNamespace(n_agents=4, n_views=4, height=8, width=8,
+                                     output=gp.OUT_CLASS_U8, key_precision=gp.KEY_F32)
+    for bad in (np.zeros((4, 2), np.float32), torch.zeros((4, 2)), [0.0] * 8):
+        with pytest.raises(gp.GigapixelError) as e:
+            sim._actions(bad)
+        assert e.value.status == gp.GP_EINVAL
+    with pytest.raises(gp.GigapixelError):
+        sim._images(torch.zeros((4, 8, 8), dtype=torch.uint8), None)
+    assert sim._actions(None) == 0  # a null pointer is the library's to reject

@@ -588,6 +588,73 @@ def test_paper_rig_rgb(size, key):
     assert int(out[:, 2].float().mean()) > 0
 
 
+def test_binding_checks_tensor_layouts():
+    """Tensors of the wrong dtype, size or strides are refused before any launch, and the
+    simulator keeps working afterwards."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl)
+    out, depth = sim.alloc_outputs()
+    act = torch_actions(worlds, 0, wl.seed)[0]
+    bad = [
+        (act.double(), out, depth),                      # actions dtype
+        (act[:-1], out, depth),                          # short actions
+        (act.t().contiguous().t(), out, depth),          # actions not contiguous
+        (act, out.float(), depth),                       # class image dtype
+        (act, out[:-1], depth),                          # one view short
+        (act, out, depth.half()),                        # depth dtype for FP32 keys
+        (act, out, depth.transpose(1, 2)),               # depth not contiguous
+    ]
+    for a, o, d in bad:
+        with pytest.raises(gp.GigapixelError) as e:
+            sim.step_render(a, o, d)
+        assert e.value.status == gp.binding.GP_EINVAL
+    with pytest.raises(gp.GigapixelError):
+        sim.observe_vec(out=(torch.empty((sim.n_agents, 16, 8), device="cuda"),
+                             torch.empty((sim.n_agents, 31, 8), device="cuda"),
+                             torch.empty((sim.n_agents, 4, 8), device="cuda")))
+    sim.step_render(act, out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    check_t3(sim, cfg, worlds, [0, sim.n_views - 1], out, depth)
+
+
+def test_library_refuses_unreachable_pointers():
+    """Through the C ABI itself (no binding checks): a pageable host buffer handed to the
+    step, render, trace and O_vec calls returns GP_EINVAL before any launch.  The runtime is
+    first asked how it classifies the buffer; the calls are only made if it reports
+    unregistered host memory, which the library refuses."""
+    import torch
+    from cuda.bindings import runtime as rt
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["tiny"]
+    worlds = wg.make_workload(wl)
+    sim, cfg = sim_for(worlds, wl)
+    host = np.zeros(16 << 20, np.uint8)  # larger than any output of this workload
+    err, attr = rt.cudaPointerGetAttributes(host.ctypes.data)
+    assert err == rt.cudaError_t.cudaSuccess
+    assert attr.type == rt.cudaMemoryType.cudaMemoryTypeUnregistered
+    out, depth = sim.alloc_outputs()
+    act = torch_actions(worlds, 0, wl.seed)[0]
+    L, h, hp = gp.lib(), sim._h, host.ctypes.data
+    assert L.gp_step(h, hp, None) == gp.binding.GP_EINVAL
+    assert L.gp_step_world(h, 0, hp, None) == gp.binding.GP_EINVAL
+    assert L.gp_render(h, hp, depth.data_ptr(), None) == gp.binding.GP_EINVAL
+    assert L.gp_render(h, out.data_ptr(), hp, None) == gp.binding.GP_EINVAL
+    assert L.gp_render_world(h, 0, hp, None, None) == gp.binding.GP_EINVAL
+    assert L.gp_trace(h, hp, None, None) == gp.binding.GP_EINVAL
+    assert L.gp_step_render(h, act.data_ptr(), hp, None, None) == gp.binding.GP_EINVAL
+    assert L.gp_step_trace(h, hp, out.data_ptr(), None, None) == gp.binding.GP_EINVAL
+    assert "pageable host memory" in L.gp_last_error().decode()
+    assert L.gp_observe_vec(h, hp, None, None, None) == gp.binding.GP_EINVAL
+    sim.step_render(act, out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    check_t3(sim, cfg, worlds, [0], out, depth)
+
+
 def test_rgb_rejects_bad_appearance():
     import paper_2606_19641_b300 as gp
     wl = wg.WORKLOADS["paper_rig_210x126"]
