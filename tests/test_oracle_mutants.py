@@ -90,24 +90,63 @@ MUTANTS = {
 }
 
 
+# Mistakes in the oracle's Python batch driver (episodes, resets, conditioning draws); the
+# C library is left intact for these.
+PY_MUTANTS = {
+    "episode ends a step late": ("if self.ep[w] >= self.episode_steps:",
+                                 "if self.ep[w] > self.episode_steps:"),
+    "done flag kept into the next step": (
+        "fl = np.ascontiguousarray(self.flags[a0:a1] & ~np.uint8(8))",
+        "fl = np.ascontiguousarray(self.flags[a0:a1])"),
+    "restart keeps actuators": ("            self.jerk[a0:a1] = 0.0\n        self.episode_index[w] += 1",
+                                "            pass\n        self.episode_index[w] += 1"),
+    "restart keeps the episode index": ("        self.episode_index[w] += 1\n", ""),
+    "draw keyed by batch agent index": ("self.cond_seed, w, int(self.episode_index[w]), i)",
+                                        "self.cond_seed, w, int(self.episode_index[w]), a0 + i)"),
+    "reset ignores the mask": ("if mask is None or mask[w]:", "if True:"),
+    "restart from world 0's start": ("self.state[a0:a1] = self.state0[a0:a1]",
+                                     "self.state[a0:a1] = self.state0[:a1 - a0]"),
+    "restart keeps the episode clock": ("        self.ep[w] = 0\n", ""),
+}
+ALL = sorted(MUTANTS) + sorted("py: " + k for k in PY_MUTANTS)
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+
 def _run_mutant(name, workdir):
-    """Compile the oracle with one planted mistake and run the pins against it; returns the
-    pins' exit status and the end of their output."""
-    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
-    a, b = MUTANTS[name]
-    if a not in src:
-        return None, "mutation site not found: " + name
-    d = os.path.join(workdir, "m%d" % sorted(MUTANTS).index(name))
+    """Plant one mistake in a copy of the oracle (its C source, or for "py: " names its Python
+    driver) and run the pins against it; returns the pins' exit status and the end of their
+    output."""
+    d = os.path.join(workdir, "m%d" % ALL.index(name))
     os.makedirs(d, exist_ok=True)
-    c, so = os.path.join(d, "mut.c"), os.path.join(d, "mut.so")
-    with open(c, "w") as fh:
-        fh.write(src.replace(a, b, 1))
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, c,
-                           "-lm"])
+    if name.startswith("py: "):
+        import oracle
+        so = oracle.build()  # the intact C library
+        src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+        a, b = PY_MUTANTS[name[4:]]
+        if a not in src:
+            return None, "mutation site not found: " + name
+        pkg = os.path.join(d, "oracle")
+        os.makedirs(pkg, exist_ok=True)
+        with open(os.path.join(pkg, "__init__.py"), "w") as fh:
+            fh.write(src.replace(a, b, 1))
+        # import the mutated package first, so the pins' own import finds it loaded
+        cmd = [sys.executable, "-c",
+               "import sys; sys.path.insert(0, %r); import oracle; "
+               "assert oracle.__file__.startswith(%r); import pytest; "
+               "sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', %r]))" % (d, d, PINS)]
+    else:
+        src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+        a, b = MUTANTS[name]
+        if a not in src:
+            return None, "mutation site not found: " + name
+        c, so = os.path.join(d, "mut.c"), os.path.join(d, "mut.so")
+        with open(c, "w") as fh:
+            fh.write(src.replace(a, b, 1))
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", so,
+                               c, "-lm"])
+        cmd = [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", PINS]
     env = dict(os.environ, ORACLE_SO=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
-                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
 
 
@@ -119,13 +158,14 @@ def mutant_results(tmp_path_factory):
     if os.environ.get("PYTEST_XDIST_WORKER"):
         return None
     work = str(tmp_path_factory.mktemp("mutants"))
-    names = sorted(MUTANTS)
+    names = ALL
     with concurrent.futures.ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
         return dict(zip(names, ex.map(lambda n: _run_mutant(n, work), names)))
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+@pytest.mark.parametrize("name", ALL)
 def test_pins_catch_mutant(name, mutant_results, tmp_path):
     rc, out = mutant_results[name] if mutant_results is not None else _run_mutant(name, str(tmp_path))
     assert rc is not None, out
     assert rc != 0, "pins did not catch mutant %r:\n%s" % (name, out)
+    assert " failed" in out, "the pins did not run to a failure for %r:\n%s" % (name, out)

@@ -1556,3 +1556,41 @@ def test_reward_conditioning_ranges_and_normalisation():
         sim.step(wg.actions(wl.seed, k, worlds.n_agents))
     assert np.allclose(sim.cond[3], oracle.conditioning(5, 0, 1, 3)[1])
     assert np.allclose(sim.weights[3], oracle.conditioning(5, 0, 1, 3)[0])
+
+
+def test_reset_worlds_by_mask_and_per_world_draws():
+    """A masked reset returns only the chosen worlds to their own start (state, cleared
+    flags, actuators, episode clock) and redraws their conditioning for the next episode;
+    each world's draws are keyed by its own index and its agents' local indices."""
+    import worldgen as wg
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    off = worlds.agent_offsets()
+    sim = oracle.Sim(worlds, jerk_dynamics=True, episode_steps=50, conditioning_seed=21)
+    start = sim.state.copy()
+    for w in range(3):
+        for i in range(int(off[w + 1] - off[w])):
+            wt, c = oracle.conditioning(21, w, 0, i)
+            assert np.array_equal(sim.cond[off[w] + i], c)
+            assert np.array_equal(sim.weights[off[w] + i], wt)
+    for k in range(4):
+        sim.step(wg.jerk_actions(wl.seed, k, worlds.n_agents))
+    a0, a1 = int(off[1]), int(off[2])
+    assert np.any(sim.jerk[a0:a1]) and not np.array_equal(sim.state[a0:a1], start[a0:a1])
+    before = sim.state.copy(), sim.flags.copy(), sim.jerk.copy(), sim.cond.copy()
+    sim.reset_worlds([0, 1, 0])
+    assert np.array_equal(sim.state[a0:a1], start[a0:a1])
+    assert not np.any(sim.flags[a0:a1]) and not np.any(sim.jerk[a0:a1])
+    assert list(sim.ep) == [4, 0, 4] and list(sim.episode_index) == [0, 1, 0]
+    for i in range(a1 - a0):
+        assert np.array_equal(sim.cond[a0 + i], oracle.conditioning(21, 1, 1, i)[1])
+    keep = np.r_[0:a0, a1:worlds.n_agents]
+    for now, then in zip((sim.state, sim.flags, sim.jerk, sim.cond), before):
+        assert np.array_equal(now[keep], then[keep])
+    # the reset world runs its next episode from the start: one step from a fresh
+    # simulator with the same draw gives the same state
+    fresh = oracle.Sim(worlds, jerk_dynamics=True)
+    act = wg.jerk_actions(wl.seed, 9, worlds.n_agents)
+    sim.step(act)
+    fresh.step(act)
+    assert np.array_equal(sim.state[a0:a1], fresh.state[a0:a1])
