@@ -107,6 +107,13 @@ PY_MUTANTS = {
     "restart from world 0's start": ("self.state[a0:a1] = self.state0[a0:a1]",
                                      "self.state[a0:a1] = self.state0[:a1 - a0]"),
     "restart keeps the episode clock": ("        self.ep[w] = 0\n", ""),
+    "agents drawn at their start poses": ("        b[: a1 - a0, 0:3] = self.state[a0:a1, 0:3]\n", ""),
+    "every world reads world 0's signals": ("        s0, s1 = int(off[w]), int(off[w + 1])",
+                                             "        s0, s1 = int(off[0]), int(off[1])"),
+    "every world takes world 0's actions": ("actions[a0:a1], self.road(w)",
+                                            "actions[:a1 - a0], self.road(w)"),
+    "initial speed from box height": ("self.state[a0:a1, 3] = bx[:, 6]",
+                                      "self.state[a0:a1, 3] = bx[:, 5]"),
 }
 ALL = sorted(MUTANTS) + sorted("py: " + k for k in PY_MUTANTS)
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")

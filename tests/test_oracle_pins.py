@@ -1594,3 +1594,44 @@ def test_reset_worlds_by_mask_and_per_world_draws():
     sim.step(act)
     fresh.step(act)
     assert np.array_equal(sim.state[a0:a1], fresh.state[a0:a1])
+
+
+def test_batch_driver_keeps_worlds_apart():
+    """The batch driver gives each world its own agents' actions, draws agents at their
+    current poses and reads each world's own signals: world 1 with zero actions goes
+    straight at constant speed (the bicycle's closed form) while world 0 steers; an agent
+    moved in front of another's camera is the box under the image centre; every signal of
+    a world hangs over one of that world's road quads."""
+    import worldgen as wg
+    wl = wg.WORKLOADS["paper_rig_210x126"]
+    worlds = wg.make_workload(wl, n_worlds=3)
+    off = worlds.agent_offsets()
+    sim = oracle.Sim(worlds)
+    a0, a1 = int(off[1]), int(off[2])
+    act = wg.actions(wl.seed, 0, worlds.n_agents).copy()
+    act[a0:a1] = 0.0
+    before = sim.state.copy()
+    sim.step(act)
+    b, s, ok = before[a0:a1], sim.state[a0:a1], sim.flags[a0:a1] == 0
+    assert ok.sum() >= 10
+    assert np.allclose(s[ok, 0], b[ok, 0] + 0.1 * b[ok, 3] * np.cos(b[ok, 2]), rtol=0, atol=1e-12)
+    assert np.allclose(s[ok, 1], b[ok, 1] + 0.1 * b[ok, 3] * np.sin(b[ok, 2]), rtol=0, atol=1e-12)
+    assert np.array_equal(s[ok, 2:4], b[ok, 2:4])
+    # agent 1 of world 0 parked 6 m in front of agent 0, same heading
+    st = sim.state.copy()
+    x, y, yaw = st[0, 0:3]
+    st[1, 0:3] = (x + 6.0 * np.cos(yaw), y + 6.0 * np.sin(yaw), yaw)
+    sim.set_state(st, np.zeros_like(sim.flags))
+    cam = oracle.CamConfig(wl.width, wl.height, math.radians(wl.hfov_deg), wl.cam_height)
+    img = sim.render(cam, 0, 0, 0.0)
+    f = 0.5 * wl.width / math.tan(0.5 * cam.hfov)
+    row = int(0.5 * wl.height + f * 0.5 / 6.0)  # 1.0 m above the ground, 6 m ahead
+    col = wl.width // 2
+    prim = 0xFFFFFFFF - (int(img.key[row, col]) & 0xFFFFFFFF)
+    assert img.cls[row, col] == 3 and 12 <= prim < 24  # one of agent 1's 12 triangles
+    for w in range(3):
+        sph, _ = sim.signals(w)
+        road = sim.road(w)
+        assert len(sph) == 8
+        for c in sph:
+            assert any(oracle.point_in_quad(c[0], c[1], q) for q in road)
