@@ -375,7 +375,13 @@ gp_status gp_get_rewards(gp_handle *h, float *reward, float *ego, int on_host, v
  * accelerations to 0.
  */
 gp_status gp_set_reward_weights(gp_handle *h, const float *weights, int on_host, void *stream);
-/* The weights in use, [n_agents][10] (after conditioning draws too); on_host as above. */
+/*
+ * Copies the weights in use, float [n_agents][10] in the order above, into the caller's
+ * buffer: those last set by gp_set_reward_weights, or with reward_conditioning the ones
+ * drawn at each world's latest episode start.  on_host != 0: host memory, the call waits
+ * for `stream`; else device memory, asynchronous on `stream`.  GP_EINVAL for a null handle
+ * or buffer.
+ */
 gp_status gp_get_reward_weights(gp_handle *h, float *weights, int on_host, void *stream);
 
 /*
