@@ -1531,9 +1531,33 @@ def test_splitmix64_known_outputs():
     assert oracle.splitmix64(12345, 7) != oracle.splitmix64(12346, 7)
 
 
+REWARD_TERMS = ("collision", "offroad", "comfort", "alignment", "centering", "velocity",
+                "traffic_light", "time", "reverse", "overspeed", "goal_radius",
+                "goal_speed_tolerance")
+
+
+def reward_table():
+    """(lo, hi, inference) arrays of the twelve coefficients, from the golden table."""
+    g = read_golden("reward_table.txt")
+    assert list(g) == list(REWARD_TERMS)
+    t = np.array([g[k] for k in REWARD_TERMS], np.float64)
+    return t[:, 0], t[:, 1], t[:, 2]
+
+
+def test_reward_table_golden():
+    """The oracle's default weights are the table's inference column, and its conditioning
+    draws fill each coefficient's training range (uniform on [lo, hi))."""
+    lo, hi, inf = reward_table()
+    assert np.array_equal(np.array(oracle.REWARD_WEIGHTS, np.float64), inf[:10])
+    draws = np.array([oracle.conditioning(3, w, 0, i)[1] for w in range(4) for i in range(250)])
+    vals = lo + (hi - lo) * (draws + 1) / 2
+    assert np.all(vals >= lo) and np.all(vals < hi)
+    span = hi - lo
+    assert np.all(vals.min(axis=0) - lo < 0.01 * span) and np.all(hi - vals.max(axis=0) < 0.01 * span)
+
+
 def test_reward_conditioning_ranges_and_normalisation():
-    lo = np.array([0, 0, 0, 2.5e-4, 2.5e-4, 0, 0, 0, 2.5e-4, 0, 2, 1], np.float64)  # Table "Reward terms"
-    hi = np.array([3, 3, 0.05, 2.5e-2, 7.5e-3, 5e-3, 1, 5e-5, 7.5e-3, 1, 12, 5], np.float64)
+    lo, hi, _ = reward_table()
     cs = []
     for w in range(3):
         for e in range(3):
