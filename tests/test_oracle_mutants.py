@@ -86,6 +86,10 @@ MUTANTS = {
     "red light counted per signal": ("                    r -= w[6];\n                    break;", "                    r -= w[6];"),
     "splitmix mix constant": ("    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "    z = (z ^ (z >> 27)) * 0x94D049BB133111EDull;"),
     "conditioning range swapped": ("static const double COND_HI[12] = {3.0, 3.0, 0.05,", "static const double COND_HI[12] = {3.0, 3.0, 0.5,"),
+    "ovec road radius doubled": ("            if (d <= r_roads) {", "            if (d <= 2.0 * r_roads) {"),
+    "ovec road heading unrotated": ("            o[4] = cos(phi - bi[2]);", "            o[4] = cos(phi);"),
+    "ovec road type swapped": ("            o[6] = s < n_road ? 1.0 : 0.0;", "            o[6] = s < n_road ? 0.0 : 1.0;"),
+    "ovec road length unscaled": ("            o[3] = len / r_roads;", "            o[3] = len;"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 
