@@ -90,6 +90,13 @@ MUTANTS = {
     "ovec road heading unrotated": ("            o[4] = cos(phi - bi[2]);", "            o[4] = cos(phi);"),
     "ovec road type swapped": ("            o[6] = s < n_road ? 1.0 : 0.0;", "            o[6] = s < n_road ? 0.0 : 1.0;"),
     "ovec road length unscaled": ("            o[3] = len / r_roads;", "            o[3] = len;"),
+    "bf16 truncates": ("    x += 0x7FFFu + ((x >> 16) & 1u);\n", ""),
+    "bf16 ties away from even": ("    x += 0x7FFFu + ((x >> 16) & 1u);", "    x += 0x8000u;"),
+    "f16 subnormal truncated": ("    if (rem > half || (rem == half && (h & 1u))) ++h;\n    return (uint16_t)(sign | h);\n}",
+                                "    return (uint16_t)(sign | h);\n}"),
+    "f16 overflow threshold": ("if (ax >= 0x477FF000u) return", "if (ax >= 0x477FE000u) return"),
+    "onehot mean subtracted twice": ("float t = ((float)hot - mean[c]) / std_[c];",
+                                     "float t = ((float)hot - 2.0f * mean[c]) / std_[c];"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 
