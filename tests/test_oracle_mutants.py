@@ -97,6 +97,11 @@ MUTANTS = {
     "f16 overflow threshold": ("if (ax >= 0x477FF000u) return", "if (ax >= 0x477FE000u) return"),
     "onehot mean subtracted twice": ("float t = ((float)hot - mean[c]) / std_[c];",
                                      "float t = ((float)hot - 2.0f * mean[c]) / std_[c];"),
+    "snap to whole pixels": ("        X[i] = (int32_t)rint(16.0 * xs);", "        X[i] = 16 * (int32_t)rint(xs);"),
+    "snap truncates": ("        Y[i] = (int32_t)rint(16.0 * ys);", "        Y[i] = (int32_t)(16.0 * ys);"),
+    "depth is view z": ("        d[i] = (float)(cfg->near / poly[i].z);", "        d[i] = (float)(poly[i].z);"),
+    "fan from the wrong corner": ("        int i0 = 0, i1 = k, i2 = k + 1;", "        int i0 = k, i1 = 0, i2 = k + 1;"),
+    "one clip plane skipped": ("    for (int k = 0; k < 5 && m >= 3; ++k) {", "    for (int k = 0; k < 4 && m >= 3; ++k) {"),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

@@ -1659,3 +1659,45 @@ def test_batch_driver_keeps_worlds_apart():
         assert len(sph) == 8
         for c in sph:
             assert any(oracle.point_in_quad(c[0], c[1], q) for q in road)
+
+
+def test_unclipped_vertices_are_snapped_pinhole_projections():
+    """With nothing clipped, every triangle vertex is a box corner's pinhole projection
+    (x right, y up, z forward; x_px = W/2 + f x / z, y_px = H/2 - f y / z, f = (W/2) /
+    tan(hfov/2)) rounded half-to-even to 1/16 px."""
+    cam = CamConfig(128, 96)
+    f = 0.5 * cam.width / math.tan(0.5 * cam.hfov)
+    for box in ([20.0, 1.3, 0.4, 4.5, 1.9, 1.6], [13.0, -2.2, -1.1, 4.2, 1.8, 1.5]):
+        _, tris = render_scene(cam, [box], ego=-1)
+        assert len(tris) >= 4
+        bx, by, yaw, L, W, H = box
+        snapped, frac = set(), []
+        for sl in (-0.5, 0.5):
+            for sw in (-0.5, 0.5):
+                cx = bx + sl * L * math.cos(yaw) - sw * W * math.sin(yaw)
+                cy = by + sl * L * math.sin(yaw) + sw * W * math.cos(yaw)
+                for cz in (0.0, H):
+                    xr, yu, zf = -cy, cz - cam.cam_height, cx  # camera at the origin, yaw 0
+                    xs = 0.5 * cam.width + f * xr / zf
+                    ys = 0.5 * cam.height - f * yu / zf
+                    snapped.add((int(np.rint(16 * xs)), int(np.rint(16 * ys))))
+                    frac += [(16 * xs) % 1.0, (16 * ys) % 1.0]
+        assert any(0.5 < q < 1.0 for q in frac)  # some corner rounds up
+        for t in tris:
+            for i in range(3):
+                assert (int(t["X"][i]), int(t["Y"][i])) in snapped
+
+
+def test_guard_band_clips_near_tall_and_wide_boxes():
+    """A box too tall and too wide for the guard band, 2 m ahead: clipping against all four
+    guard planes keeps every snapped coordinate within 4x the viewport half-extent."""
+    cam = CamConfig(64, 64)
+    _, tris = render_scene(cam, [[2.5, 0.0, 0.0, 1.0, 30.0, 12.0]], ego=-1)
+    assert len(tris) > 0
+    X, Y = tris["X"].astype(np.int64), tris["Y"].astype(np.int64)
+    assert np.all(np.abs(X - 8 * 64) <= 4 * 8 * 64 + 1)
+    assert np.all(np.abs(Y - 8 * 64) <= 4 * 8 * 64 + 1)
+    # each of the four guard lines is reached
+    lim = 4 * 8 * 64
+    assert (X - 8 * 64).min() <= -lim + 1 and (X - 8 * 64).max() >= lim - 1
+    assert (Y - 8 * 64).min() <= -lim + 1
