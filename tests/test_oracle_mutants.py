@@ -102,6 +102,12 @@ MUTANTS = {
     "depth is view z": ("        d[i] = (float)(cfg->near / poly[i].z);", "        d[i] = (float)(poly[i].z);"),
     "fan from the wrong corner": ("        int i0 = 0, i1 = k, i2 = k + 1;", "        int i0 = k, i1 = 0, i2 = k + 1;"),
     "one clip plane skipped": ("    for (int k = 0; k < 5 && m >= 3; ++k) {", "    for (int k = 0; k < 4 && m >= 3; ++k) {"),
+    "second agent of a pair not flagged": ("                if (j < n_agents) flags[j] |= OR_COLLIDED;\n", ""),
+    "off-road needs every corner out": ("            if (!inside) {\n                flags[i] |= OR_OFFROAD;\n                break;",
+                                        "            if (!inside && k == 3) {\n                flags[i] |= OR_OFFROAD;\n                break;"),
+    "halt keeps off-road agents moving": ("        if (flags[i] & (OR_COLLIDED | OR_OFFROAD)) {", "        if (flags[i] & OR_COLLIDED) {"),
+    "lane frame from the quad's last match": ("        if (!or_point_in_quad(px, py, q)) continue;", "        if (!or_point_in_quad(px, py, q) || r + 1 < n_road) continue;"),
+    "lane direction normalised by x only": ("        dy /= len;\n", ""),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
 }
 

@@ -1701,3 +1701,41 @@ def test_guard_band_clips_near_tall_and_wide_boxes():
     lim = 4 * 8 * 64
     assert (X - 8 * 64).min() <= -lim + 1 and (X - 8 * 64).max() >= lim - 1
     assert (Y - 8 * 64).min() <= -lim + 1
+
+
+def test_lane_frame_takes_the_smallest_index_quad():
+    """Where road quads overlap (a junction), the lane frame comes from the containing quad
+    of smallest index; a point in only the later quad takes that quad's frame."""
+    east = rect_quad(-20.0, 20.0, -3.5, 3.5)                       # runs along +x
+    north = [3.5, -20.0, 3.5, 20.0, -3.5, 20.0, -3.5, -20.0]       # runs along +y
+    # (-1, -1) lies in both: the right half of the east-running quad, the left half (against
+    # the quad's direction) of the north-running one
+    for first, second, want in ((east, north, 0.0), (north, east, -0.5 * math.pi)):
+        road = np.array([first, second], np.float32)
+        d, _ = oracle.lane_frame(-1.0, -1.0, road)
+        assert math.cos(d - want) == pytest.approx(1.0, abs=1e-9)
+    road = np.array([east, north], np.float32)
+    d, _ = oracle.lane_frame(1.0, 10.0, road)  # only in the north-running quad
+    assert math.cos(d - 0.5 * math.pi) == pytest.approx(1.0, abs=1e-9)
+
+
+def test_offroad_when_any_single_corner_leaves_the_road():
+    """An agent (4 x 2 m at the origin, at rest) is off the road as soon as any one of its
+    four footprint corners lies outside every road quad, whichever corner it is."""
+    for sx in (-1.0, 1.0):
+        for sy in (-1.0, 1.0):
+            # two quads covering the footprint except the corner (2 sx, 1 sy)
+            road = np.array([rect_quad(-3.0, 3.0, -3.0, 0.5) if sy > 0 else rect_quad(-3.0, 3.0, -0.5, 3.0),
+                             rect_quad(-3.0, 0.0, 0.0, 3.0) if sx > 0 else rect_quad(0.0, 3.0, 0.0, 3.0)],
+                            np.float32)
+            if sy < 0:
+                road[1] = rect_quad(-3.0, 0.0, -3.0, 0.0) if sx > 0 else rect_quad(0.0, 3.0, -3.0, 0.0)
+            covered = [any(oracle.point_in_quad(2 * ax, ay, q) for q in road)
+                       for ax in (-1, 1) for ay in (-1, 1)]
+            assert sum(covered) == 3 and not any(
+                oracle.point_in_quad(2 * sx, sy, q) for q in road)
+            state = np.zeros((1, 4), np.float64)
+            flags = np.zeros(1, np.uint8)
+            boxes = np.array([[0.0, 0.0, 0.0, 4.0, 2.0, 1.5]], np.float64)
+            oracle.step_world(boxes, state, flags, np.zeros((1, 2), np.float32), road)
+            assert flags[0] & 2, (sx, sy)
