@@ -68,15 +68,16 @@ def _lib():
         lib.or_jerk_bicycle.argtypes = [c_f64p, c_f64p, c_f64p, c_f64p] + [ctypes.c_double] * 3 + \
             [c_f64p, ctypes.c_double, ctypes.c_double]
         lib.or_step_world_jerk.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p, c_u8p,
-                                           c_f32p, ctypes.c_int32, c_f32p, ctypes.c_double,
-                                           ctypes.c_double, c_f64p]
+                                           c_f32p, ctypes.c_int32, c_f32p, ctypes.c_int32,
+                                           c_f64p, c_u8p, ctypes.c_double, ctypes.c_double,
+                                           c_f64p]
         lib.or_obb_overlap.argtypes = [c_f64p, c_f64p]
         lib.or_obb_overlap.restype = ctypes.c_int
         lib.or_point_in_quad.argtypes = [ctypes.c_double, ctypes.c_double, c_f32p]
         lib.or_point_in_quad.restype = ctypes.c_int
         lib.or_step_world.argtypes = [ctypes.c_int32, ctypes.c_int32, c_f64p, c_f64p, c_u8p,
-                                      c_f32p, ctypes.c_int32, c_f32p, ctypes.c_double,
-                                      ctypes.c_double]
+                                      c_f32p, ctypes.c_int32, c_f32p, ctypes.c_int32, c_f64p,
+                                      c_u8p, ctypes.c_double, ctypes.c_double]
         lib.or_camera_tris.argtypes = [P(OrCam), ctypes.c_int32, c_f64p, ctypes.c_int32,
                                        ctypes.c_int32, c_f32p, ctypes.c_int32, c_f32p,
                                        ctypes.c_int32, c_f64p,
@@ -168,29 +169,35 @@ def point_in_quad(px: float, py: float, quad: Sequence[float]) -> bool:
 
 def step_world(boxes6: np.ndarray, state: np.ndarray, flags: np.ndarray, actions: np.ndarray,
                road: np.ndarray, dt: float = 0.1, vmax: float = 30.0,
-               jerk: Optional[np.ndarray] = None) -> None:
+               jerk: Optional[np.ndarray] = None, sph=None, sph_state=None) -> None:
     """One step of one world in place (App. A dynamics + infractions + halt).
 
-    boxes6 float64 [n_boxes, 6]; state float64 [n_agents, 4]; flags uint8 [n_agents];
-    actions float32 [n_agents, 2] (accel, steer; or j_lon, j_lat when `jerk` is given);
-    road float32 [n_road, 8]; jerk float64 [n_agents, 3] (a_lon, a_lat, steer), updated.
+    boxes6 float64 [n_boxes, 6]; state float64 [n_agents, 4]; flags uint8 [n_agents]
+    (1 collided, 2 off-road, 4 halted, 16 red-light violation); actions float32
+    [n_agents, 2] (accel, steer; or j_lon, j_lat when `jerk` is given); road float32
+    [n_road, 8]; jerk float64 [n_agents, 3] (a_lon, a_lat, steer), updated; sph [n_sig, 4]
+    signal spheres x, y, z, r with states sph_state [n_sig] (0 red; None = all red).
     """
     assert boxes6.dtype == np.float64 and boxes6.flags.c_contiguous
     assert state.dtype == np.float64 and state.flags.c_contiguous
     assert flags.dtype == np.uint8 and flags.flags.c_contiguous
     act = _c(actions, np.float32)
     rd = _c(road, np.float32).reshape(-1, 8)
+    sp = _sph(sph)
+    st = _c(np.zeros(sp.shape[0]) if sph_state is None else sph_state, np.uint8)
+    assert st.shape == (sp.shape[0],)
     if jerk is None:
         _lib().or_step_world(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p),
                              _p(state, c_f64p), _p(flags, c_u8p), _p(act, c_f32p), rd.shape[0],
-                             _p(rd, c_f32p), float(dt), float(vmax))
+                             _p(rd, c_f32p), sp.shape[0], _p(sp, c_f64p), _p(st, c_u8p),
+                             float(dt), float(vmax))
     else:
         assert jerk.dtype == np.float64 and jerk.flags.c_contiguous
         assert jerk.shape == (state.shape[0], 3)
         _lib().or_step_world_jerk(boxes6.shape[0], state.shape[0], _p(boxes6, c_f64p),
                                   _p(state, c_f64p), _p(flags, c_u8p), _p(act, c_f32p),
-                                  rd.shape[0], _p(rd, c_f32p), float(dt), float(vmax),
-                                  _p(jerk, c_f64p))
+                                  rd.shape[0], _p(rd, c_f32p), sp.shape[0], _p(sp, c_f64p),
+                                  _p(st, c_u8p), float(dt), float(vmax), _p(jerk, c_f64p))
 
 
 # ---------------------------------------------------------------------------------------
@@ -512,8 +519,8 @@ class Sim:
         if off is None:
             return np.zeros((0, 4)), np.zeros(0, np.uint8)
         s0, s1 = int(off[w]), int(off[w + 1])
-        return (self.w.signal[s0:s1].astype(np.float64),
-                np.asarray(self.signal_state[s0:s1], np.uint8))
+        st = np.zeros(s1 - s0, np.uint8) if self.signal_state is None else self.signal_state[s0:s1]
+        return self.w.signal[s0:s1].astype(np.float64), np.asarray(st, np.uint8)
 
     def step(self, actions: np.ndarray, worlds: Optional[Sequence[int]] = None) -> None:
         ws = range(self.w.n_worlds) if worlds is None else worlds
@@ -523,7 +530,9 @@ class Sim:
             st = np.ascontiguousarray(self.state[a0:a1])
             fl = np.ascontiguousarray(self.flags[a0:a1] & ~np.uint8(8))
             jk = None if self.jerk is None else np.ascontiguousarray(self.jerk[a0:a1])
-            step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax, jk)
+            sp, ss = self.signals(w)
+            step_world(b, st, fl, actions[a0:a1], self.road(w), self.dt, self.vmax, jk,
+                       sph=sp, sph_state=ss)
             self.state[a0:a1] = st
             self.flags[a0:a1] = fl
             if jk is not None:

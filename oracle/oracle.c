@@ -38,7 +38,7 @@
  * Dynamics (App. A "Action Space and Dynamics"; "Other Details")
  * ------------------------------------------------------------------------------------ */
 
-enum { OR_COLLIDED = 1, OR_OFFROAD = 2, OR_HALTED = 4 };
+enum { OR_COLLIDED = 1, OR_OFFROAD = 2, OR_HALTED = 4, OR_RED_LIGHT = 16 };
 
 static double wrap_pi(double a) {
     /* to (-pi, pi] */
@@ -151,37 +151,55 @@ int or_point_in_quad(double px, double py, const float *q) {
  * One simulation step of one world, in place.
  *   boxes  [n_boxes][6]  x, y, yaw, L, W, H  (rows of agents are overwritten from state)
  *   state  [n_agents][4] x, y, yaw, v        (FP64)
- *   flags  [n_agents]    bit0 collided, bit1 off-road, bit2 halted (all latched)
+ *   flags  [n_agents]    bit0 collided, bit1 off-road, bit2 halted, bit4 red-light
+ *                        violation (all latched)
  *   actions[n_agents][2] accel (m/s^2), steer (rad)
  *   road   [n_road][8]   road-surface quads
+ *   sph    [n_sig][4]    traffic-signal spheres x, y, z, r; sig_state [n_sig] (0 = red)
  * Order: move every non-halted agent; then flag collisions among all pairs that contain
- * an agent; then flag agents with a footprint corner outside every road quad; then halt
- * every flagged agent (v = 0).  Halted agents stay in place and stay in the scene.
+ * an agent; then flag agents with a footprint corner outside every road quad; then flag
+ * red-light violations (a halted agent does not move, so it cannot enter a quad); then
+ * halt every flagged agent (v = 0).  Halted agents stay in
+ * place and stay in the scene (App. A "Other Details": a collision, an off-road departure
+ * or a red-light violation halts the agent in place, velocity zeroed).
+ * Red-light violation (reading): a signal controls the road quad of smallest index that
+ * contains its centre (none if no quad does); an agent that moved this step violates when
+ * its centre went from outside a red signal's quad to inside it (boundary inside).
  */
 static void step_world_impl(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
                             uint8_t *flags, const float *actions, int32_t n_road,
-                            const float *road, double dt, double vmax, double *jerk_state);
+                            const float *road, int32_t n_sig, const double *sph,
+                            const uint8_t *sig_state, double dt, double vmax,
+                            double *jerk_state);
 
 void or_step_world(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
                    uint8_t *flags, const float *actions, int32_t n_road, const float *road,
-                   double dt, double vmax) {
-    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, dt, vmax, 0);
+                   int32_t n_sig, const double *sph, const uint8_t *sig_state, double dt,
+                   double vmax) {
+    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, n_sig, sph,
+                    sig_state, dt, vmax, 0);
 }
 
 /* The same step with the jerk-actuated bicycle: actions are (j_lon, j_lat) in m/s^3 and
  * jerk_state [n_agents][3] (a_lon, a_lat, steer) is updated for moving agents. */
 void or_step_world_jerk(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
                         uint8_t *flags, const float *actions, int32_t n_road, const float *road,
-                        double dt, double vmax, double *jerk_state) {
-    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, dt, vmax,
-                    jerk_state);
+                        int32_t n_sig, const double *sph, const uint8_t *sig_state, double dt,
+                        double vmax, double *jerk_state) {
+    step_world_impl(n_boxes, n_agents, boxes, state, flags, actions, n_road, road, n_sig, sph,
+                    sig_state, dt, vmax, jerk_state);
 }
 
 static void step_world_impl(int32_t n_boxes, int32_t n_agents, double *boxes, double *state,
                             uint8_t *flags, const float *actions, int32_t n_road,
-                            const float *road, double dt, double vmax, double *jerk_state) {
+                            const float *road, int32_t n_sig, const double *sph,
+                            const uint8_t *sig_state, double dt, double vmax,
+                            double *jerk_state) {
+    double *before = (double *)malloc(sizeof(double) * 2 * (size_t)(n_agents > 0 ? n_agents : 1));
     for (int32_t i = 0; i < n_agents; ++i) {
         double *s = state + 4 * i;
+        before[2 * i] = s[0];
+        before[2 * i + 1] = s[1];
         if (!(flags[i] & OR_HALTED)) {
             if (jerk_state)
                 or_jerk_bicycle(&s[0], &s[1], &s[2], &s[3], boxes[6 * i + 3], actions[2 * i],
@@ -224,7 +242,21 @@ static void step_world_impl(int32_t n_boxes, int32_t n_agents, double *boxes, do
         }
     }
     for (int32_t i = 0; i < n_agents; ++i) {
-        if (flags[i] & (OR_COLLIDED | OR_OFFROAD)) {
+        for (int32_t s = 0; s < n_sig; ++s) {
+            if (sig_state[s] != 0) continue;
+            int32_t q = 0;
+            while (q < n_road && !or_point_in_quad(sph[4 * s], sph[4 * s + 1], road + 8 * q)) ++q;
+            if (q == n_road) continue;
+            if (!or_point_in_quad(before[2 * i], before[2 * i + 1], road + 8 * q) &&
+                or_point_in_quad(state[4 * i], state[4 * i + 1], road + 8 * q)) {
+                flags[i] |= OR_RED_LIGHT;
+                break;
+            }
+        }
+    }
+    free(before);
+    for (int32_t i = 0; i < n_agents; ++i) {
+        if (flags[i] & (OR_COLLIDED | OR_OFFROAD | OR_RED_LIGHT)) {
             flags[i] |= OR_HALTED;
             state[4 * i + 3] = 0.0;
         }

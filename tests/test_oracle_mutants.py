@@ -105,7 +105,10 @@ MUTANTS = {
     "second agent of a pair not flagged": ("                if (j < n_agents) flags[j] |= OR_COLLIDED;\n", ""),
     "off-road needs every corner out": ("            if (!inside) {\n                flags[i] |= OR_OFFROAD;\n                break;",
                                         "            if (!inside && k == 3) {\n                flags[i] |= OR_OFFROAD;\n                break;"),
-    "halt keeps off-road agents moving": ("        if (flags[i] & (OR_COLLIDED | OR_OFFROAD)) {", "        if (flags[i] & OR_COLLIDED) {"),
+    "halt keeps off-road agents moving": ("        if (flags[i] & (OR_COLLIDED | OR_OFFROAD | OR_RED_LIGHT)) {", "        if (flags[i] & (OR_COLLIDED | OR_RED_LIGHT)) {"),
+    "red light does not halt": ("        if (flags[i] & (OR_COLLIDED | OR_OFFROAD | OR_RED_LIGHT)) {", "        if (flags[i] & (OR_COLLIDED | OR_OFFROAD)) {"),
+    "red-light halt on leaving": ("            if (!or_point_in_quad(before[2 * i], before[2 * i + 1], road + 8 * q) &&\n                or_point_in_quad(state[4 * i], state[4 * i + 1], road + 8 * q)) {", "            if (or_point_in_quad(before[2 * i], before[2 * i + 1], road + 8 * q) &&\n                !or_point_in_quad(state[4 * i], state[4 * i + 1], road + 8 * q)) {"),
+    "red-light halt for any state": ("            if (sig_state[s] != 0) continue;\n            int32_t q = 0;\n            while (q < n_road && !or_point_in_quad(sph[4 * s], sph[4 * s + 1], road + 8 * q)) ++q;\n            if (q == n_road) continue;\n            if (!or_point_in_quad(before", "            int32_t q = 0;\n            while (q < n_road && !or_point_in_quad(sph[4 * s], sph[4 * s + 1], road + 8 * q)) ++q;\n            if (q == n_road) continue;\n            if (!or_point_in_quad(before"),
     "lane frame from the quad's last match": ("        if (!or_point_in_quad(px, py, q)) continue;", "        if (!or_point_in_quad(px, py, q) || r + 1 < n_road) continue;"),
     "lane direction normalised by x only": ("        dy /= len;\n", ""),
     "jerk ego steer scale": ("ego[9 * i + 6] = jerk ? jerk[3 * i + 2] / 0.5 : 0.0;", "ego[9 * i + 6] = jerk ? jerk[3 * i + 2] : 0.0;"),
@@ -136,6 +139,7 @@ PY_MUTANTS = {
                                             "actions[:a1 - a0], self.road(w)"),
     "initial speed from box height": ("self.state[a0:a1, 3] = bx[:, 6]",
                                       "self.state[a0:a1, 3] = bx[:, 5]"),
+    "signals ignored by the step": ("jk,\n                       sph=sp, sph_state=ss)", "jk)"),
 }
 ALL = sorted(MUTANTS) + sorted("py: " + k for k in PY_MUTANTS)
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")

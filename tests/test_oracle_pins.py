@@ -1504,6 +1504,68 @@ def test_red_light_violation_term():
     assert r_of(-0.5, 0.5, [0], fl_before=4 | 1) == 0.0  # halted agents earn nothing
 
 
+def test_red_light_violator_is_halted():
+    """App. A "Other Details": a red-light violation halts the agent in place like a
+    collision or an off-road departure.  An agent whose centre enters, during the step, the
+    road quad under a red signal gets the red-light flag (16) and the halt flag (4), speed
+    0, and keeps its post-move pose; later steps leave it there whatever the action.  Green,
+    amber and off signals, staying inside, leaving, and a signal over no road halt
+    nothing; both dynamics halt."""
+    road = np.array([rect_quad(-100.0, 0.0, -3.5, 3.5), rect_quad(0.0, 100.0, -3.5, 3.5)],
+                    np.float32)
+    over_b = [[50.0, 0.0, 5.0, 0.4]]
+
+    def run(x0, yaw, state, sph=over_b, jerk=None, flags0=0, steps=1, accel=0.0):
+        boxes = np.array([[x0, -1.75, yaw, 4.5, 1.9, 1.5]], np.float64)
+        st = np.array([[x0, -1.75, yaw, 15.0]], np.float64)
+        fl = np.array([flags0], np.uint8)
+        for _ in range(steps):
+            boxes[0, 0:3] = st[0, 0:3]
+            oracle.step_world(boxes, st, fl, np.array([[accel, 0.0]], np.float32), road,
+                              jerk=jerk, sph=sph, sph_state=state)
+        return st[0].copy(), int(fl[0])
+
+    s1, f1 = run(-1.0, 0.0, [0])
+    assert f1 == 16 | 4 and s1[3] == 0.0
+    assert s1[0] == pytest.approx(0.5, abs=1e-12) and s1[1] == -1.75   # moved, then halted
+    s3, f3 = run(-1.0, 0.0, [0], steps=3, accel=2.0)                      # stays put
+    assert f3 == 16 | 4 and np.array_equal(s3, s1)
+    for st in ([1], [2], [3]):
+        s, f = run(-1.0, 0.0, st)
+        assert f == 0 and s[3] == 15.0 and s[0] == pytest.approx(0.5, abs=1e-12)
+    assert run(0.5, 0.0, [0])[1] == 0                                     # already inside
+    s, f = run(1.0, math.pi, [0])                                         # leaving B for A
+    assert f == 0 and s[0] == pytest.approx(-0.5, abs=1e-12)
+    assert run(-1.5, 0.0, [0])[1] == 16 | 4                              # lands on the edge
+    assert run(-1.0, 0.0, [0], sph=[[50.0, 40.0, 5.0, 0.4]])[1] == 0     # over no road
+    assert run(-1.0, 0.0, [0], flags0=4)[1] == 4                          # halted: no move
+    # the signal controls the quad of smallest index under it: over A, entering A halts
+    assert run(1.0, math.pi, [0], sph=[[-50.0, 0.0, 5.0, 0.4]])[1] == 16 | 4
+    s, f = run(-1.0, 0.0, [0], jerk=np.zeros((1, 3)))
+    assert f == 16 | 4 and s[3] == 0.0
+
+
+def test_batch_driver_halts_red_light_violators_per_world():
+    """The batch driver hands each world its own signals to the step: two identical worlds
+    whose one agent crosses into the quad under a signal, red in world 1 and green in world
+    0; only world 1's agent is halted with the red-light flag."""
+    import worldgen as wg
+    road = np.array([rect_quad(-100.0, 0.0, -3.5, 3.5), rect_quad(0.0, 100.0, -3.5, 3.5)] * 2,
+                    np.float32)
+    box = [-1.0, -1.75, 0.0, 4.5, 1.9, 1.5, 15.0]
+    worlds = wg.Worlds(np.array([0, 1, 2], np.int32), np.array([1, 1], np.int32),
+                       np.array([box, box], np.float32), np.array([0, 2, 4], np.int32), road,
+                       np.array([0, 0, 0], np.int32), np.zeros((0, 8), np.float32),
+                       np.array([0, 1, 2], np.int32),
+                       np.array([[50.0, 0.0, 5.0, 0.4]] * 2, np.float32),
+                       np.array([2, 0], np.uint8))
+    sim = oracle.Sim(worlds)
+    sim.step(np.zeros((2, 2), np.float32))
+    assert list(sim.flags) == [0, 16 | 4]
+    assert sim.state[0, 3] == 15.0 and sim.state[1, 3] == 0.0
+    assert sim.state[0, 0] == pytest.approx(0.5, abs=1e-6) and sim.state[1, 0] == sim.state[0, 0]
+
+
 def test_episode_end_returns_worlds_to_their_start():
     """A world's agents are back at the descriptor's poses and speeds, with only the done
     flag, exactly every episode_steps steps; other steps keep moving."""
