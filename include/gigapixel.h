@@ -51,7 +51,8 @@ enum { GP_KEY_F32 = 0, GP_KEY_F16 = 1 };
 enum { GP_OUT_CLASS_U8 = 0, GP_OUT_ONEHOT_BF16 = 1, GP_OUT_RGB_U8 = 2 };
 /* Per-agent flag bits (latched for the lifetime of the handle or until gp_set_state). */
 enum { GP_FLAG_COLLIDED = 1, GP_FLAG_OFFROAD = 2, GP_FLAG_HALTED = 4,
-       GP_FLAG_DONE = 8 /* set for one step: the world's episode ended and it was reset */ };
+       GP_FLAG_DONE = 8, /* set for one step: the world's episode ended and it was reset */
+       GP_FLAG_RED_LIGHT = 16 /* the agent ran a red light (App. A "Other Details") */ };
 /* Device status bits (sticky until gp_clear_status). */
 enum {
     GP_DEV_NONFINITE_STATE = 1u << 0, /* an agent's state became NaN/inf */
@@ -202,11 +203,16 @@ typedef struct gp_config {
                                      0.25 0.25 0.25); shaded like every surface */
 } gp_config;
 
-/* Fill `cfg` with the defaults above. */
+/* Fill `cfg` with the defaults above.  The paper fixes only dt = 0.1 s (App. A "Action
+ * Space and Dynamics") and the reward weights' inference column (App. A, Table "Reward
+ * terms"); every other default is this library's reading. */
 gp_status gp_default_config(gp_config *cfg);
 
 /*
- * Create a batch of worlds on CUDA device `device`.  Copies the descriptor, builds the
+ * Create a batch of worlds on CUDA device `device`: each world is the paper's simulator
+ * state S_t = (A_t, M, L_t) -- agent bounding boxes, static map geometry (road planes and
+ * lane-line strips) and traffic-light states (Sec. 3.1 "Gigapixel"), rendered as cuboids,
+ * planes and spheres (App. A "High-Throughput Batched Rendering").  Copies the descriptor, builds the
  * device-side world layout (culling clusters, off-road grid, work list), optionally runs
  * the autotuner, and returns a handle in *out.  Synchronous.  Limits: GP_MAX_BOXES boxes,
  * GP_MAX_QUADS quads per world; with GP_KEY_F16 a world holds at most 65535 primitive ids.
@@ -216,14 +222,18 @@ gp_status gp_default_config(gp_config *cfg);
 gp_status gp_create_worlds(const gp_world_desc *desc, const gp_config *cfg, int device,
                            gp_handle **out);
 
-/* Release every device and host resource of the handle.  NULL is accepted. */
+/* Release every device and host resource of the handle.  NULL is accepted.  The paper has
+ * no counterpart (resource management of this library). */
 gp_status gp_destroy(gp_handle *h);
 
 /*
- * Advance every world by one step (App. A): kinematic bicycle (wheelbase 0.6 L) for each
- * non-halted agent, then footprint collisions among all box pairs that contain an agent,
- * then the off-road test (a footprint corner outside every road quad), then halt: flagged
- * agents get v = 0 and ignore later actions but stay in the scene.
+ * Advance every world by one step (App. A "Action Space and Dynamics", "Other Details"):
+ * kinematic bicycle (wheelbase 0.6 L) for each non-halted agent, then footprint collisions
+ * among all box pairs that contain an agent, then the off-road test (a footprint corner
+ * outside every road quad), then the red-light test (the agent's centre entered, during
+ * the step, the road quad of smallest index under a red signal's centre), then halt: an
+ * agent flagged by any of the three gets v = 0 and ignores later actions but stays in the
+ * scene.
  *   actions_dev  float [n_agents][2] device: acceleration (m/s^2), steering angle (rad);
  *                agents ordered by world, then by agent index within the world.
  *                With GP_DYN_JERK: longitudinal and lateral jerk (m/s^3) of the
@@ -275,6 +285,8 @@ gp_status gp_step_trace(gp_handle *h, const float *actions_dev, void *out_dev,
 /*
  * Per-world path: step or render one world only (one launch each), writing the world's
  * slice of the same tensors (actions/out/depth point at the start of the FULL arrays).
+ * The paper has no counterpart: it is the plain one-world-at-a-time baseline against which
+ * the batched launch of App. A "High-Throughput Batched Rendering" is measured.
  */
 gp_status gp_step_world(gp_handle *h, int32_t world, const float *actions_dev, void *stream);
 gp_status gp_render_world(gp_handle *h, int32_t world, void *out_dev, void *depth_dev,
@@ -283,7 +295,9 @@ gp_status gp_render_world(gp_handle *h, int32_t world, void *out_dev, void *dept
 /*
  * Agent state: state[n_agents][4] = x, y, yaw, v (float) and flags[n_agents] (uint8).
  * on_host = 1: host pointers (the call synchronises the stream); 0: device pointers.
- * gp_set_state also forks/resumes a simulation (e.g. teacher rollouts from a snapshot);
+ * gp_set_state also forks/resumes a simulation: the paper rolls the teacher out in a
+ * parallel simulator instance initialised at the current state S (Sec. 3.2 "Pixel-based
+ * student training"; App. B.2: a forked copy of the simulator, horizon 4 s);
  * it zeroes the jerk dynamics' actuator state (restore it with gp_set_dynamics after) and
  * leaves the per-world episode step counters alone (gp_reset_worlds restarts them).
  */
@@ -292,7 +306,9 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
                        void *stream);
 
 /*
- * Episode reset: the agents of every world w with mask[w] != 0 (every world if mask is
+ * Episode reset (App. A "Other Details": an episode runs for up to 20 s and then ends;
+ * the scenario's initial states start the next one): the agents
+ * of every world w with mask[w] != 0 (every world if mask is
  * NULL) return to their initial pose and speed from gp_create_worlds, with clear flags and
  * zero previous-step accelerations and actuator state, and the world's episode step
  * counter restarts; other worlds are untouched.
@@ -302,6 +318,7 @@ gp_status gp_set_state(gp_handle *h, const float *state, const uint8_t *flags, i
 gp_status gp_reset_worlds(gp_handle *h, const uint8_t *mask, int on_host, void *stream);
 
 /*
+ * The paper has no counterpart (instrumentation of this library).
  * Render counters out[GP_STAT_COUNT] (host, uint64) summed since create or the last reset
  * (reset != 0 clears them after reading).  Synchronises the device.  GP_ESTATE unless
  * gp_config.stats = 1.
@@ -337,7 +354,7 @@ gp_status gp_set_dynamics(gp_handle *h, const float *dyn, int on_host, void *str
  */
 gp_status gp_set_signal_states(gp_handle *h, const uint8_t *state, int on_host, void *stream);
 
-/* Sizes of a handle. */
+/* Sizes of a handle (no counterpart in the paper). */
 typedef struct gp_info {
     int32_t n_worlds, n_agents, n_boxes, n_views, width, height, n_cams;
     int32_t key_precision, output;
@@ -404,7 +421,8 @@ gp_status gp_get_reward_weights(gp_handle *h, float *weights, int on_host, void 
 gp_status gp_observe_vec(gp_handle *h, float *agents_dev, float *roads_dev, float *signals_dev,
                          void *stream);
 
-/* Read (synchronously) / clear the device status word; set bits for tests. */
+/* Read (synchronously) / clear the device status word; set bits for tests.  The paper has
+ * no counterpart: this is this library's device-side error reporting. */
 gp_status gp_get_status(gp_handle *h, uint32_t *bits);
 gp_status gp_clear_status(gp_handle *h);
 gp_status gp_debug_inject_status(gp_handle *h, uint32_t bits);
@@ -421,6 +439,8 @@ gp_status gp_debug_stall_pipeline(gp_handle *h, void *out_dev, void *depth_dev, 
                                   void *stream);
 
 /*
+ * The paper has no counterpart: a parity aid of this library (the "identical snapped
+ * vertices" comparison with the CPU oracle).
  * Render all cameras (like gp_render) and copy the snapped triangles that camera `view`
  * rasterised to host memory: records of int32 X[3], Y[3] (1/16 pixel, y down), float d[3]
  * (n / z_view), uint32 prim, uint32 sub (fan index after clipping); 44 bytes each.  A
@@ -441,8 +461,10 @@ gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out_dev, void *de
  * synchronisation that cudaMalloc/cudaFree imply.  The paper has no counterpart; this is
  * a debugging aid of this library.
  *  - cap must be at most GP_NOALLOC_MAX_TRIS, otherwise GP_ELIMIT (nothing is launched).
- *  - The first call on a device looks up the array's device address (no allocation); make
- *    that first call before any stream capture on that device.
+ *  - The array's device address is looked up (no allocation) when a handle is created on
+ *    the device, and again at every later creation there, so it belongs to the context of
+ *    the live handles; the call itself does no set-up.  Like every handle, it does not
+ *    survive a cudaDeviceReset: create a new handle after one.
  *  - All calls share the one array (the counters are cleared at the start of every call;
  *    the records keep the last call's contents): calls that overlap on the GPU, from
  *    several threads or streams, race.  Synchronous, like gp_debug_dump_tris.
@@ -451,7 +473,8 @@ gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out_dev, void *de
 gp_status gp_debug_dump_tris_noalloc(gp_handle *h, int32_t view, void *out_dev, void *depth_dev,
                                      void *host_tris, int64_t cap, int64_t *n, void *stream);
 
-/* Description of the last error on the calling thread ("" if none). */
+/* Description of the last error on the calling thread ("" if none).  No counterpart in the
+ * paper. */
 const char *gp_last_error(void);
 
 #ifdef __cplusplus

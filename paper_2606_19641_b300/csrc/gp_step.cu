@@ -10,8 +10,10 @@
 //      four box axes, strict overlap (touching is no collision);
 //   3. off-road: an agent whose footprint has a corner outside every road quad (boundary
 //      counts as inside); candidate quads come from a per-world uniform grid;
-//   4. halt: collided or off-road agents are latched halted with v = 0.  Halted agents keep
-//      their pose and stay in the scene as obstacles.
+//   4. red light: an agent whose centre enters, during the step, the road quad controlled
+//      by a red signal (the quad of smallest index under the signal's centre) is flagged;
+//   5. halt: collided, off-road or red-light agents are latched halted with v = 0.  Halted
+//      agents keep their pose and stay in the scene as obstacles.
 // All arithmetic is FP32 with full-precision libm (no fast-math).
 #include "gp_internal.h"
 
@@ -144,14 +146,27 @@ __device__ __forceinline__ float2 jerk_actuate(float2 jerk, float v, float L, fl
     return make_float2(a_lon, steer);
 }
 
+// Red-light violation of one step: the centre moved from outside to inside the road quad
+// controlled by a red signal of the world (signal states are read modulo 4).
+__device__ bool entered_red(const StepParams &p, const WorldInfo &wi, float px0, float py0,
+                            float px, float py) {
+    for (int s = 0; s < wi.n_sig; ++s) {
+        const int q = p.sig_quad[wi.sig_begin + s];
+        if (q < 0 || (p.sig_state[wi.sig_begin + s] & 3) != GP_SIGNAL_RED) continue;
+        const float4 g0 = p.road_geo[2 * q], g1 = p.road_geo[2 * q + 1];
+        if (!in_quad(px0, py0, g0, g1) && in_quad(px, py, g0, g1)) return true;
+    }
+    return false;
+}
+
 // Reward terms of one agent's step (App. A reward table; inference weights by default) and
 // its ego state.  Accelerations are the bicycle's increments of the step (speed before any
-// halt); an agent halted before the step earns 0.  The traffic-light term charges an agent
-// whose centre enters, during the step, the road quad controlled by a red signal (the quad
-// of smallest index under the signal's centre); the goal term is 0.
-__device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, float px0, float py0,
-                             float px, float py, float yaw, float v_after, float v0, float2 act,
-                             float L, float W, unsigned int fl0, unsigned int fl1) {
+// halt); an agent halted before the step earns 0.  The traffic-light term charges the
+// step's red-light violation (`ran_red`, charged once however many red signals it crossed);
+// the goal term is 0.
+__device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, float px, float py,
+                             float yaw, float v_after, float v0, float2 act, float L, float W,
+                             unsigned int fl0, unsigned int fl1, bool ran_red) {
     const float *w = p.weights + 10 * a;
     float a_lon = 0.f, a_lat = 0.f, r = 0.f;
     if (!(fl0 & GP_FLAG_HALTED)) {
@@ -178,16 +193,7 @@ __device__ void agent_reward(const StepParams &p, const WorldInfo &wi, int a, fl
         if (fabsf(vn) > 0.f || a_lon != 0.f || a_lat != 0.f) r -= w[7] * p.dt;
         if (vn < 0.f) r -= w[8] * p.dt;
         if (fabsf(vn) > p.vlim) r -= w[9];
-        // red-light violation: the centre enters a red signal's road quad during the step
-        for (int s = 0; s < wi.n_sig; ++s) {
-            const int q = p.sig_quad[wi.sig_begin + s];
-            if (q < 0 || (p.sig_state[wi.sig_begin + s] & 3) != GP_SIGNAL_RED) continue;
-            const float4 g0 = p.road_geo[2 * q], g1 = p.road_geo[2 * q + 1];
-            if (!in_quad(px0, py0, g0, g1) && in_quad(px, py, g0, g1)) {
-                r -= w[6];
-                break;
-            }
-        }
+        if (ran_red) r -= w[6];
     }
     p.acc[a] = make_float2(a_lon, a_lat);
     p.reward[a] = r;
@@ -223,7 +229,7 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
             pose = p.box_pose[wi.box_begin + tid];
             dim = p.box_dim[wi.box_begin + tid];
         }
-        const float x0 = pose.x, y0 = pose.y;  // centre before the step (red-light term)
+        const float x0 = pose.x, y0 = pose.y;  // centre before the step (red-light test)
         if (tid < wi.n_agents) {
             const int a = wi.agent_begin + tid;
             fl = p.flags[a] & ~GP_FLAG_DONE;  // the done flag lasts one step
@@ -318,7 +324,10 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
         if (tid < na) {
             const int a = wi.agent_begin + tid;
             fl |= sflag[tid];
-            if (fl & (GP_FLAG_COLLIDED | GP_FLAG_OFFROAD)) {
+            // a halted agent did not move, so it cannot have entered a quad
+            const bool ran_red = !(fl0 & GP_FLAG_HALTED) && entered_red(p, wi, x0, y0, pose.x, pose.y);
+            if (ran_red) fl |= GP_FLAG_RED_LIGHT;
+            if (fl & (GP_FLAG_COLLIDED | GP_FLAG_OFFROAD | GP_FLAG_RED_LIGHT)) {
                 fl |= GP_FLAG_HALTED;
                 v = 0.f;
             }
@@ -326,8 +335,8 @@ __global__ void __launch_bounds__(kMaxBoxes) step_kernel(StepParams p) {
             p.speed[a] = v;
             p.flags[a] = (uint8_t)fl;
             if (p.rewards)
-                agent_reward(p, wi, a, x0, y0, pose.x, pose.y, pose.z, v, v0, act, dim.x, dim.y, fl0,
-                             fl);
+                agent_reward(p, wi, a, pose.x, pose.y, pose.z, v, v0, act, dim.x, dim.y, fl0, fl,
+                             ran_red);
         }
         if (p.episode_steps > 0) {
             // end of the world's episode: its agents return to their initial state (the

@@ -105,6 +105,69 @@ def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
         assert n_halted > 0  # random steering does drive some agents off the road
 
 
+@pytest.mark.parametrize("name,n_worlds,steps", [("uniform", 4, 15), ("ragged", 6, 12)])
+def test_red_light_halt_matches_oracle(name, n_worlds, steps):
+    """App. A "Other Details": a red-light violation halts the agent like a collision or an
+    off-road departure.  32 red signals per world hang over the agents' roads; every step
+    from the GPU's own FP32 state is compared with one oracle step: pose and speed within
+    FP32 rounding, flags identical (including the red-light bit 16), rewards as the
+    oracle's; violators stop at once and stay where they stopped."""
+    import torch
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
+    wg.add_signals(worlds, 32, wl.seed, height=5.0)
+    worlds.signal_state[:] = 0
+    sim, cfg = sim_for(worlds, wl, rewards=1)
+    off = worlds.agent_offsets()
+    na = worlds.n_agents
+    dims = np.zeros((na, 2), np.float64)
+    for w in range(worlds.n_worlds):
+        b0 = int(worlds.box_off[w])
+        a0, a1 = int(off[w]), int(off[w + 1])
+        dims[a0:a1] = worlds.boxes[b0:b0 + (a1 - a0), 3:5]
+    weights = np.tile(np.array(oracle.REWARD_WEIGHTS, np.float32), (na, 1))
+    acc = np.zeros((na, 2), np.float64)
+    red = np.zeros(na, bool)
+    stopped_at = {}
+    for k in range(steps):
+        st0, fl0 = sim.get_state()
+        osim = oracle.Sim(worlds)
+        osim.set_state(st0.astype(np.float64), fl0)
+        act_t, act = torch_actions(worlds, k, wl.seed)
+        sim.step(act_t)
+        osim.step(act)
+        st1, fl1 = sim.get_state()
+        r, _ = sim.rewards()
+        torch.cuda.synchronize()
+        r = r.cpu().numpy()
+        assert np.array_equal(fl1, osim.flags), "flags differ at step %d" % k
+        assert np.allclose(st1[:, 0:2], osim.state[:, 0:2], atol=2e-4, rtol=0)
+        assert np.allclose(st1[:, 3], osim.state[:, 3], atol=2e-5)
+        new = (fl1 & 16).astype(bool) & ~(fl0 & 16).astype(bool)
+        assert np.all(fl1[new] & 4) and np.all(st1[new, 3] == 0.0)
+        for i in np.flatnonzero(new):
+            stopped_at[i] = st1[i, 0:3].copy()
+        for i, pose in stopped_at.items():
+            assert np.array_equal(st1[i, 0:3], pose), "agent %d moved after its red-light halt" % i
+        red |= new
+        for w in range(worlds.n_worlds):
+            a0, a1 = int(off[w]), int(off[w + 1])
+            road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
+            s0, s1 = int(worlds.signal_off[w]), int(worlds.signal_off[w + 1])
+            acc_w = np.ascontiguousarray(acc[a0:a1])
+            rr, _ = oracle.rewards_world(st0[a0:a1], fl0[a0:a1], st1[a0:a1], fl1[a0:a1],
+                                         act[a0:a1], dims[a0:a1], acc_w, weights[a0:a1], road,
+                                         sph=worlds.signal[s0:s1],
+                                         sph_state=worlds.signal_state[s0:s1])
+            acc[a0:a1] = acc_w
+            # the red-light term is charged exactly on the steps that set the flag
+            tl = np.abs(rr - r[a0:a1]) <= 1e-4 + 1e-4 * np.abs(rr) + weights[a0:a1, 2]
+            assert np.all(tl)
+    print("red-light halts: %d of %d agents" % (int(red.sum()), na))
+    assert red.sum() > 0
+    assert sim.status() == 0
+
+
 # ---------------------------------------------------------------------------------------
 # T2 / T3 / T4 rendering
 # ---------------------------------------------------------------------------------------
@@ -395,6 +458,17 @@ def test_status_word_injection_and_nonfinite_state():
     with pytest.raises(gp.GigapixelError) as e:
         sim.step(act)
     assert e.value.status == gp.binding.GP_EDEVICE
+    # the debug entry points refuse to launch on a sticky status too
+    import ctypes
+    out, depth = sim.alloc_outputs()
+    n = ctypes.c_int64(-7)
+    tris = np.zeros(64, gp.binding.TRI_DTYPE)
+    L, h = gp.lib(), sim._h
+    assert L.gp_debug_stall_pipeline(h, out.data_ptr(), None, 20_000_000, None) == gp.binding.GP_EDEVICE
+    for entry in (L.gp_debug_dump_tris, L.gp_debug_dump_tris_noalloc):
+        assert entry(h, 0, out.data_ptr(), depth.data_ptr(), tris.ctypes.data, 64, ctypes.byref(n),
+                     None) == gp.binding.GP_EDEVICE
+    assert n.value == -7
     sim.clear_status()
     sim.step(act)
     assert sim.status() == 0
@@ -649,6 +723,18 @@ def test_library_refuses_unreachable_pointers():
     assert L.gp_step_trace(h, hp, out.data_ptr(), None, None) == gp.binding.GP_EINVAL
     assert "pageable host memory" in L.gp_last_error().decode()
     assert L.gp_observe_vec(h, hp, None, None, None) == gp.binding.GP_EINVAL
+    # the debug entry points run the same checks before their launch
+    import ctypes
+    n = ctypes.c_int64(-7)
+    tris = np.zeros(64, gp.binding.TRI_DTYPE)
+    assert L.gp_debug_stall_pipeline(h, hp, None, 20_000_000, None) == gp.binding.GP_EINVAL
+    assert L.gp_debug_stall_pipeline(h, out.data_ptr(), hp, 20_000_000, None) == gp.binding.GP_EINVAL
+    for entry in (L.gp_debug_dump_tris, L.gp_debug_dump_tris_noalloc):
+        assert entry(h, 0, hp, None, tris.ctypes.data, 64, ctypes.byref(n), None) == gp.binding.GP_EINVAL
+        assert entry(h, 0, out.data_ptr(), hp, tris.ctypes.data, 64, ctypes.byref(n), None) == \
+            gp.binding.GP_EINVAL
+        assert "pageable host memory" in L.gp_last_error().decode()
+    assert n.value == -7  # refused before anything was written
     sim.step_render(act, out, depth)
     torch.cuda.synchronize()
     assert sim.status() == 0
