@@ -661,6 +661,45 @@ void release_all(gp_handle *h) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Scratch of the triangle dump that allocates nothing (gp_debug_dump_tris_noalloc).
+// ---------------------------------------------------------------------------------------
+
+// Fixed scratch of the allocation-free dump: bytes [0, 4) work counter, [4, 8) record
+// count, records from byte 256.  One copy per device, alive until the process exits.
+static __device__ __align__(256) unsigned char gp_noalloc_scratch[256 + GP_NOALLOC_MAX_TRIS * sizeof(DumpTri)];
+
+namespace {
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kNoAllocDevices] = {};
+
+// Set-up, with `device` current: look up the device address of the scratch array (the
+// host-side name of the array is not a device address; the lookup allocates nothing).
+// Done by gp_create_worlds for its device, and again at every later creation on that
+// device, so the address is that of the context the live handles were created in (a
+// cudaDeviceReset ends that context and every handle made before it).
+gp_status noalloc_setup(int device) {
+    if (device < 0 || device >= kNoAllocDevices) return GP_OK;  // no allocation-free dump there
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, gp_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(GP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    g_noalloc_addr[device] = (unsigned char *)p;
+    return GP_OK;
+}
+
+// The address found by the last set-up on `device`, or null.
+unsigned char *noalloc_scratch(int device) {
+    if (device < 0 || device >= kNoAllocDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    return g_noalloc_addr[device];
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *gp_last_error(void) { return g_err.c_str(); }
@@ -1051,6 +1090,11 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     if (render_configure(smem_limit(device) - 1024) != cudaSuccess) {
         gp_destroy(h);
         return fail(GP_ECUDA, "cannot configure render kernel shared memory");
+    }
+    st = noalloc_setup(device);
+    if (st != GP_OK) {
+        gp_destroy(h);
+        return st;
     }
     h->shape = default_shape(h);
     if (h->shape.blocks == 0) {
@@ -1477,6 +1521,9 @@ gp_status gp_debug_stall_pipeline(gp_handle *h, void *out, void *depth, int64_t 
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
     CK(cudaSetDevice(h->device));
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    st = check_reach(h, nullptr, out, depth);
+    if (st != GP_OK) return st;
     Shape s = h->shape;  // same bands as the handle's work list
     s.prod_warps = std::max(1, s.threads / 128);
     if (!finish_shape(h, s)) {
@@ -1501,6 +1548,9 @@ gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out, void *depth,
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
     CK(cudaSetDevice(h->device));
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    st = check_reach(h, nullptr, out, depth);
+    if (st != GP_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t want = (size_t)std::max<int64_t>(std::min<int64_t>(cap, 1 << 24), 1);
     if (h->dump.n < want) {
@@ -1525,38 +1575,6 @@ gp_status gp_debug_dump_tris(gp_handle *h, int32_t view, void *out, void *depth,
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------------------
-// Triangle dump that allocates nothing (gp_debug_dump_tris_noalloc).
-// ---------------------------------------------------------------------------------------
-
-// Fixed scratch of the allocation-free dump: bytes [0, 4) work counter, [4, 8) record
-// count, records from byte 256.  One copy per device, alive until the process exits.
-static __device__ __align__(256) unsigned char gp_noalloc_scratch[256 + GP_NOALLOC_MAX_TRIS * sizeof(DumpTri)];
-
-namespace {
-
-constexpr int kNoAllocDevices = 64;
-std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_addr[kNoAllocDevices] = {};
-
-// Device address of the scratch array on `device` (which must be current).  Looked up once
-// per device; the host-side name of the array is not a device address.
-gp_status noalloc_scratch(int device, unsigned char **addr) {
-    if (device < 0 || device >= kNoAllocDevices) return fail(GP_EINVAL, "device index too large");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, gp_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(GP_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_noalloc_addr[device] = (unsigned char *)p;
-    }
-    *addr = g_noalloc_addr[device];
-    return GP_OK;
-}
-
-}  // namespace
-
 extern "C" gp_status gp_debug_dump_tris_noalloc(gp_handle *h, int32_t view, void *out,
                                                 void *depth, void *host_tris, int64_t cap,
                                                 int64_t *n, void *stream) {
@@ -1569,9 +1587,12 @@ extern "C" gp_status gp_debug_dump_tris_noalloc(gp_handle *h, int32_t view, void
     gp_status st = check_out(out, depth);
     if (st != GP_OK) return st;
     CK(cudaSetDevice(h->device));
-    unsigned char *scratch = nullptr;
-    st = noalloc_scratch(h->device, &scratch);
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    st = check_reach(h, nullptr, out, depth);
     if (st != GP_OK) return st;
+    // set up when the handle was created on this device (no lookup or allocation here)
+    unsigned char *scratch = noalloc_scratch(h->device);
+    if (!scratch) return fail(GP_ESTATE, "no allocation-free scratch on this device");
     cudaStream_t s = (cudaStream_t)stream;
     int *counters = (int *)scratch;
     // the work counter and the record count must start at zero; the records need no clearing
