@@ -318,42 +318,44 @@ __device__ __forceinline__ int tri_items(uint32_t s) {
 // empty if lo > hi afterwards).  Edge k runs from vertex a = k to b = k + 1; its function
 // at pixel centre (16 i + 8, py) is E = A (16 i + 8 - X_a) + B (py - Y_a) - bias with
 // A = Y_a - Y_b, B = X_b - X_a, and bias 0 on a top or left edge, else 1 (top-left fill
-// rule); the pixel is covered if E >= 0 on all three edges.
+// rule); the pixel is covered if E >= 0 on all three edges.  An edge with A > 0 bounds the
+// span from below (smallest i with E >= 0), one with A < 0 from above; the latter is the
+// former in the mirrored frame i -> -i, X_a -> 16 - X_a, so every edge runs the same
+// instructions (no divergence between the lanes of a warp).  The crossing is estimated in
+// float (within one pixel wherever it matters) and fixed by one exact integer check on each
+// side.  A horizontal edge (A = 0) keeps or empties the whole row.
 __device__ __forceinline__ void row_span(const TriRec &T, int row, int &lo, int &hi) {
     const int py = 16 * row + 8;
+    int vx[3], vy[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int xa = vtx_x(T.xy[k]), ya = vtx_y(T.xy[k]);
-        const int xb = vtx_x(T.xy[(k + 1) % 3]), yb = vtx_y(T.xy[(k + 1) % 3]);
-        const int A = ya - yb, B = xb - xa;
-        const bool top_left = (A == 0 && B > 0) || A > 0;
-        const int R = (int)wrap_mul_add(B, py - ya, top_left ? 0u : 0xFFFFFFFFu);
-        if (A == 0) {
-            if (R < 0) hi = lo - 1;
-            continue;
-        }
-        // E(i) = A (16 i + 8 - X_a) + R ; the edge crosses at i* = (X_a - 8 - R / A) / 16.
-        // The float estimate is within one pixel wherever it matters; one exact integer
-        // check on each side fixes it.
-        const float q = ((float)(xa - 8) - __fdividef((float)R, (float)A)) * 0.0625f;
-        if (A > 0) {  // lower bound: smallest i with E(i) >= 0
-            int i = __float2int_ru(fminf(fmaxf(q, -1e6f), 1e6f));
-            i = min(max(i, lo), hi + 1);
-            if (i > lo && (int)wrap_mul_add(A, 16 * (i - 1) + 8 - xa, (unsigned int)R) >= 0)
-                --i;
-            else if (i <= hi && (int)wrap_mul_add(A, 16 * i + 8 - xa, (unsigned int)R) < 0)
-                ++i;
-            lo = i;
-        } else {  // upper bound: largest i with E(i) >= 0
-            int i = __float2int_rd(fminf(fmaxf(q, -1e6f), 1e6f));
-            i = min(max(i, lo - 1), hi);
-            if (i < hi && (int)wrap_mul_add(A, 16 * (i + 1) + 8 - xa, (unsigned int)R) >= 0)
-                ++i;
-            else if (i >= lo && (int)wrap_mul_add(A, 16 * i + 8 - xa, (unsigned int)R) < 0)
-                --i;
-            hi = i;
-        }
+        vx[k] = vtx_x(T.xy[k]);
+        vy[k] = vtx_y(T.xy[k]);
     }
+    int L = lo, U = hi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int xa = vx[k], ya = vy[k], xb = vx[(k + 1) % 3], yb = vy[(k + 1) % 3];
+        const int A = ya - yb, B = xb - xa;
+        const bool top_left = A > 0 || (A == 0 && B > 0);
+        const int R = (int)wrap_mul_add(B, py - ya, top_left ? 0u : 0xFFFFFFFFu);
+        const bool up = A < 0;
+        const int Am = up ? -A : A;
+        const int xm = up ? 16 - xa : xa;
+        const int lm = up ? -U : L, hm = up ? -L : U;
+        // smallest i in [lm, hm + 1] with Am (16 i + 8 - xm) + R >= 0
+        const float q = ((float)(xm - 8) - __fdividef((float)R, (float)Am)) * 0.0625f;
+        int c = __float2int_ru(fminf(fmaxf(q, -1e6f), 1e6f));
+        c = min(max(c, lm), hm + 1);
+        const int e = (int)wrap_mul_add(Am, 16 * c + 8 - xm, (unsigned int)R);  // E at c
+        const int em = e - 16 * Am;                                            // E at c - 1
+        c = (c > lm && em >= 0) ? c - 1 : ((c <= hm && e < 0) ? c + 1 : c);
+        if (A == 0) c = R >= 0 ? lm : hm + 1;
+        if (up) U = min(U, -c);
+        else L = max(L, c);
+    }
+    lo = L;
+    hi = U;
 }
 
 // Depth test of one fragment: the key's maximum wins per pixel -- FP32 mode one 64-bit key
