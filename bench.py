@@ -107,29 +107,77 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(worlds, wl, seconds, rank_seed_step=0):
-    """Time the CPU oracle on a bounded sample: step a world and render its cameras, one
-    world after another, until `seconds` of work is done.  Returns (agent-steps/s, what)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(job):
+    """One host core's share of the CPU baseline: from t_start, for `seconds`, step one of
+    its worlds with the oracle and render every agent's camera, world after world."""
+    worlds_list, wl, seconds, t_start, step = job
     import oracle
     cam = oracle.CamConfig(wl.width, wl.height, math.radians(wl.hfov_deg), wl.cam_height)
-    t0 = time.perf_counter()
-    done_agents = 0
+    sims = [oracle.Sim(one) for one in worlds_list]
+    while time.time() < t_start:
+        time.sleep(0.001)
+    t_end = t_start + seconds
+    done = 0
     w = 0
-    while True:
-        one = worlds.world(w % worlds.n_worlds)
-        sim = oracle.Sim(one)
-        act = wg.actions(wl.seed, rank_seed_step, one.n_agents)
-        sim.step(act)
-        for a in range(one.n_agents):
+    while time.time() < t_end:
+        sim = sims[w % len(sims)]
+        sim.step(wg.actions(wl.seed, step + w // len(sims), sim.w.n_agents))
+        for a in range(sim.w.n_agents):
             sim.render(cam, 0, a, 0.0)
-            done_agents += 1
-            if time.perf_counter() - t0 > seconds:
+            done += 1
+            if time.time() >= t_end:
                 break
         w += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    el = time.perf_counter() - t0
-    return done_agents / el, el, done_agents
+    return done, time.time() - t_start
+
+
+class OracleSampler:
+    """The CPU oracle, as it stands, timed on a bounded sample of a workload on every host
+    core: one spawned process per core (the bench process already holds a CUDA context),
+    each stepping worlds of its own and rendering their cameras for a fixed wall time."""
+
+    def __init__(self, worlds, wl, cores=None):
+        import concurrent.futures
+        import multiprocessing
+        self.wl = wl
+        self.cores = cores or host_cores()
+        per = [[worlds.world(w % worlds.n_worlds) for w in range(j, j + 2 * self.cores, self.cores)]
+               for j in range(self.cores)]
+        self.per = per
+        self.pool = concurrent.futures.ProcessPoolExecutor(
+            self.cores, mp_context=multiprocessing.get_context("spawn"))
+        # start every worker (imports, oracle library load) before the first timed sample
+        list(self.pool.map(_oracle_worker, [([p[0]], wl, 0.0, 0.0, 0) for p in per]))
+
+    def sample(self, seconds, step=0):
+        """(agent-steps/s over all cores, wall seconds, agent cameras done)."""
+        t_start = time.time() + 0.5
+        res = list(self.pool.map(_oracle_worker,
+                                 [(p, self.wl, seconds, t_start, step) for p in self.per]))
+        done = sum(r[0] for r in res)
+        wall = max(r[1] for r in res)
+        return done / wall, wall, done
+
+    def close(self):
+        self.pool.shutdown()
 
 
 def rank_workload(wl, rank):
@@ -155,31 +203,110 @@ def job_rate(total_agents, steps, max_ms):
     return total_agents * steps / (max_ms / 1e3)
 
 
+def accuracy_vs_oracle(sample):
+    """Pixel-mismatch fraction and depth error of sampled GPU views against the CPU oracle's
+    FP64 pipeline rendered from the same FP32 state: against the oracle in the path's own
+    key precision (parity), and against its FP32-key image (the precision's error)."""
+    import oracle
+    worlds, wl, cfg = sample["worlds"], sample["wl"], sample["cfg"]
+    o = oracle.Sim(worlds)
+    o.set_state(sample["state"].astype(np.float64), sample["flags"])
+    cam = oracle.CamConfig(int(cfg.width), int(cfg.height), float(np.float32(cfg.hfov)),
+                           float(np.float32(cfg.cam_height)), float(np.float32(cfg.near_plane)),
+                           float(np.float32(cfg.lane_line_z)))
+    off = worlds.agent_offsets()
+    f16 = bool(cfg.key_precision)
+    onehot = int(cfg.output) == 1
+    hot = None
+    if onehot:
+        hot = [int(oracle.f32_to_bf16_bits(np.float32((1 - np.float32(m)) / np.float32(sd)))[0])
+               for m, sd in zip(cfg.norm_mean, cfg.norm_std)]
+    mis_same = mis_f32 = total = 0
+    rel, rel16 = [], []
+    for k, v in enumerate(sample["views"]):
+        agent, c = divmod(int(v), int(cfg.n_cams))
+        w = int(np.searchsorted(off, agent, side="right") - 1)
+        yaw = float(np.float32(cfg.cam_yaw[c]))
+        g = sample["out"][k].numpy()
+        if onehot:
+            g16 = g.view(np.uint16)
+            gcls = np.zeros(g16.shape[1:], np.uint8)
+            for ch in range(4):
+                gcls[g16[ch] == hot[ch]] = ch
+        else:
+            gcls = g
+        gd = sample["depth"][k].numpy()
+        gdepth = (gd.view(np.uint16).view(np.float16) if f16 else gd.view(np.float32)).astype(np.float64)
+        ref32 = o.render(cam, w, agent - int(off[w]), yaw, False)
+        ref = o.render(cam, w, agent - int(off[w]), yaw, True) if f16 else ref32
+
+        def cls_of(img):
+            return np.where(img.cls == 4, 3, img.cls) if onehot else img.cls
+        mis_same += int((gcls != cls_of(ref)).sum())
+        mis_f32 += int((gcls != cls_of(ref32)).sum())
+        total += gcls.size
+        both = (gcls > 0) & (gcls == cls_of(ref32))
+        e = ref32.depth.astype(np.float64)
+        if both.any():
+            rel.append(np.abs(gdepth[both] - e[both]) / np.maximum(e[both], 1e-12))
+        if f16:
+            same = (gcls > 0) & (gcls == cls_of(ref))
+            e16 = ref.depth.view(np.float16).astype(np.float64)
+            if same.any():
+                rel16.append(np.abs(gdepth[same] - e16[same]) / np.maximum(e16[same], 1e-12))
+    r = np.concatenate(rel) if rel else np.zeros(1)
+    out = {"views": int(len(sample["views"])), "pixels": int(total),
+           "class_mismatch_frac_vs_oracle_same_precision": mis_same / max(total, 1),
+           "class_mismatch_frac_vs_oracle_fp32_key": mis_f32 / max(total, 1),
+           "depth_rel_err_vs_oracle_fp32_depth": {"max": float(r.max()), "p99": float(np.quantile(r, 0.99)),
+                                                  "mean": float(r.mean())}}
+    if f16:
+        r16 = np.concatenate(rel16) if rel16 else np.zeros(1)
+        out["depth_rel_err_vs_oracle_fp16_key"] = {"max": float(r16.max()), "mean": float(r16.mean())}
+    return out
+
+
+def algorithmic_bytes(sim, worlds, wl, with_depth=True):
+    """The method's bytes per render launch (SURVEY-style accounting of the hot path): the
+    images written, plus the world read once -- 32 B per road segment (stored as its
+    parameters), about 40 B per agent (pose, size, speed, flags) and 28 B per static box."""
+    n_w = worlds.n_worlds
+    segs = int(wg.workload_counts(wl)[2][:n_w].sum())
+    n_agents = int(worlds.n_agents)
+    static = int(len(worlds.boxes)) - n_agents
+    depth = sim.info.depth_bytes if with_depth else 0
+    return sim.info.out_bytes + depth + 32 * segs + 40 * n_agents + 28 * static
+
+
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, on this machine's host cores."""
+    """Reference arm: the CPU oracle as it stands, on all of this machine's host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = WORKLOAD
-    worlds = wg.make_workload(wl, n_worlds=4)
-    per_step = float(os.environ.get("GP_REF_STEP_SECONDS", "5"))
-    for _ in range(args.warmup):
-        oracle_sample(worlds, wl, min(per_step, 1.0))
-    rates, secs, agents = [], 0.0, 0
+    sampler = OracleSampler(wg.make_workload(wl, n_worlds=64), wl)
+    # each step is a bounded sample; the whole run stays within a few minutes
+    per_step = float(os.environ.get("GP_REF_STEP_SECONDS",
+                                    str(min(5.0, max(0.5, 150.0 / (args.steps + args.warmup))))))
+    for k in range(args.warmup):
+        sampler.sample(min(per_step, 1.0), k)
+    secs, agents = 0.0, 0
     for k in range(args.steps):
-        r, el, n = oracle_sample(worlds, wl, per_step, k)
-        rates.append(r)
+        r, el, n = sampler.sample(per_step, args.warmup + k)
         secs += el
         agents += n
+    sampler.close()
     value = agents / secs
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_desc(wl, wl.n_worlds)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: worlds of the workload stepped and their cameras "
-                                   "rendered one after another for %.0f s" % per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sampler.cores, "kind": "oracle",
+                         "cpu": cpu_model(),
+                         "sample": "each step: on every host core (one process each), worlds of "
+                                   "the workload stepped and their cameras rendered one after "
+                                   "another for %.2f s" % per_step},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -206,6 +333,49 @@ def profiled_traffic(shape, kernel="render_kernel"):
     return int(m.group(1))
 
 
+PROFILE_CONFIGS = {
+    # name: (workload, config overrides)
+    "uniform": ("uniform", dict()),
+    "uniform_precision": ("uniform", dict(key_precision=1, output=1)),
+    "ragged_precision_128x128": ("ragged", dict(key_precision=1, output=1)),
+    "ragged_precision_256x144": ("ragged_precision", dict()),
+}
+
+
+def run_profile(args):
+    """One configuration's render, alone: --warmup then --steps direct render calls after
+    one step; prints the mean render time (not a bench line)."""
+    import torch
+    from paper_2606_19641_b300 import Simulator, build, config_for
+    build.build()
+    name, _, nw = args.profile.partition(":")
+    wl_name, kw = PROFILE_CONFIGS[name]
+    wl = wg.WORKLOADS[wl_name]
+    worlds = wg.make_workload(wl, n_worlds=int(nw) if nw else None)
+    shape = dict(autotune=1)
+    if args.shape:
+        rows, threads, cap = (int(v) for v in args.shape.split(","))
+        shape = dict(band_rows=rows, threads=threads, tri_capacity=cap)
+    sim = Simulator(worlds, config_for(wl, **shape, **kw))
+    out, depth = sim.alloc_outputs(depth=False)
+    sim.step(torch.from_numpy(wg.actions(wl.seed, 0, worlds.n_agents)).cuda())
+    for _ in range(args.warmup):
+        sim.render(out, depth)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        sim.render(out, depth)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"profile": name, "worlds": worlds.n_worlds, "cameras": sim.n_views,
+                      "render_ms": ms, "algorithmic_bytes": algorithmic_bytes(sim, worlds, wl, False),
+                      "shape": [sim.info.band_rows, sim.info.threads, sim.info.tri_capacity,
+                                sim.info.producer_warps]}), flush=True)
+    sim.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,8 +386,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--backend", default="raster", choices=["raster", "trace"],
                     help="renderer of the timed step: the rasteriser (default) or the ray tracer")
-    ap.add_argument("--sweep", action="store_true",
-                    help="also time the 3-camera resolution sweep 64..512 (extra minutes)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 3-camera resolution sweep 64..512 of both paths")
+    ap.add_argument("--profile", default="",
+                    help="profiling helper: NAME[:WORLDS] renders only that configuration "
+                         "(uniform, uniform_precision, ragged_precision_128x128, "
+                         "ragged_precision_256x144), --warmup then --steps direct render "
+                         "calls, and prints their mean time; for ncu captures of a reduced batch")
     ap.add_argument("--shape", default="",
                     help="pin the render launch shape ROWS,THREADS,TRI_CAP instead of autotuning "
                          "(for profiler captures that must skip a known number of launches)")
@@ -226,6 +401,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
 
     import torch
     import torch.distributed as dist
@@ -310,8 +487,7 @@ def main():
     render_ms = statistics.mean(b.elapsed_time(c) for a, b, c in evr)
     stepk_ms = statistics.mean(a.elapsed_time(b) for a, b, c in evr)
     out_bytes = sim.info.out_bytes + sim.info.depth_bytes
-    geo_bytes = 36 * (len(worlds.road) + len(worlds.line)) + 32 * len(worlds.boxes)
-    algo_bytes = out_bytes + geo_bytes
+    algo_bytes = algorithmic_bytes(sim, worlds, wl_rank)
     peak, peak_kind = peaks()
     achieved = algo_bytes / (render_ms / 1e3) / 1e9
     shape_s = "%d,%d,%d" % (sim.info.band_rows, sim.info.threads, sim.info.tri_capacity)
@@ -352,9 +528,29 @@ def main():
 
     extras = {}
 
-    def graph_rate(sim2, worlds2, wl2, steps):
+    # GPU images of sampled views for the accuracy check of the CPU leg (the oracle renders
+    # the same views from the same FP32 state after every GPU timing is done)
+    accuracy_samples = {}
+
+    def keep_sample(key, sim2, worlds2, wl2, n_views=64):
+        o2, d2 = sim2.alloc_outputs(depth=True)
+        sim2.render(o2, d2)
+        torch.cuda.synchronize()
+        views = np.unique(np.linspace(0, sim2.n_views - 1, n_views).round().astype(np.int64))
+        st, fl = sim2.get_state()
+        idx = torch.from_numpy(views).cuda()
+
+        def bits(t):  # raw bits (numpy has no bfloat16)
+            return t.view(torch.int16) if t.element_size() == 2 else (
+                t.view(torch.int32) if t.element_size() == 4 else t)
+        accuracy_samples[key] = dict(
+            worlds=worlds2, wl=wl2, cfg=sim2.config, views=views, state=st, flags=fl,
+            out=bits(o2[idx]).cpu(), depth=bits(d2[idx]).cpu())
+        del o2, d2
+
+    def graph_rate(sim2, worlds2, wl2, steps, depth=False):
         """agent-steps/s and render roofline of graph replays for another configuration."""
-        o2, d2 = sim2.alloc_outputs(depth=False)
+        o2, d2 = sim2.alloc_outputs(depth=depth)
         a2 = [torch.from_numpy(wg.actions(wl2.seed, k, sim2.n_agents)).cuda() for k in range(steps + 3)]
         for k in range(3):
             sim2.step_render(a2[k], o2, d2)
@@ -376,16 +572,19 @@ def main():
         e1.record(stream)
         barrier()
         rms = e0.elapsed_time(e1) / steps
-        rb = sim2.info.out_bytes + 36 * (len(worlds2.road) + len(worlds2.line)) + 32 * len(worlds2.boxes)
+        rb = algorithmic_bytes(sim2, worlds2, wl2, with_depth=depth)
         agents2 = reduce_over_ranks(sim2.n_agents, "sum", world, "cuda")
+        del o2, d2
         return {"agent_steps_per_s": job_rate(agents2, 1, ms), "ms_per_step": ms,
                 "render_kernel_ms": rms, "render_gbs": rb / (rms / 1e3) / 1e9,
                 "render_frac_of_measured_hbm": rb / (rms / 1e3) / 1e9 / peaks()[0],
                 "cameras": sim2.n_views, "band_rows": sim2.info.band_rows,
                 "threads": sim2.info.threads, "tri_capacity": sim2.info.tri_capacity,
-                "planes_written": "the output tensor only (no depth plane)"}
+                "planes_written": ("the output tensor and the depth plane" if depth
+                                   else "the output tensor only (no depth plane)")}
 
     if not args.no_extras:
+        keep_sample("uniform_fp32_u8_class", sim, worlds, wl_rank)
         # plain per-world path: one step launch and one render launch per world, no graph
         pw_steps = 5
         barrier()
@@ -408,6 +607,7 @@ def main():
         sim_p = Simulator(worlds, config_for(wl_rank, key_precision=1, output=1, autotune=1),
                           device=local)
         extras["precision_path"] = graph_rate(sim_p, worlds, wl_rank, 20)
+        keep_sample("uniform_precision_bf16_f16key", sim_p, worlds, wl_rank)
         extras["precision_path"]["output"] = "bf16 NCHW one-hot (4 channels), f16 reversed-Z keys"
         extras["precision_path"]["speedup_vs_per_world_path"] = (
             extras["precision_path"]["agent_steps_per_s"] / extras["per_world_path"]["agent_steps_per_s"])
@@ -465,6 +665,7 @@ def main():
         worlds_r = wg.make_workload(wl_r)
         sim_r = Simulator(worlds_r, config_for(wl_r, autotune=1), device=local)
         extras["ragged_precision_256x144"] = graph_rate(sim_r, worlds_r, wl_r, 5)
+        keep_sample("ragged_precision_256x144", sim_r, worlds_r, wl_r)
         extras["ragged_precision_256x144"]["workload"] = wl_r.name
         sim_r.close()
         # the ragged batch at 128x128 on the precision path (FP16 key, BF16 one-hot NCHW)
@@ -473,9 +674,9 @@ def main():
         sim_c = Simulator(worlds_c, config_for(wl_c, autotune=1, key_precision=1, output=1),
                           device=local)
         extras["ragged_precision_128x128"] = graph_rate(sim_c, worlds_c, wl_c, 5)
+        keep_sample("ragged_precision_128x128", sim_c, worlds_c, wl_c)
         extras["ragged_precision_128x128"]["workload"] = wl_c.name + ", f16 key, bf16 one-hot"
         sim_c.close()
-        del worlds_c
         # the paper's observation rig: 4 cameras (0, +-60, 180 deg) at 434x252, shaded RGB
         wl_g = rank_workload(wg.WORKLOADS["paper_rig_434x252"], rank)
         worlds_g = wg.make_workload(wl_g)
@@ -487,27 +688,43 @@ def main():
             (extras["paper_rig_434x252_rgb"]["ms_per_step"] / 1e3) / 1e6)
         sim_g.close()
 
-    if args.sweep and not args.no_extras:
-        # resolution sweep: 3 cameras (0, +-60 deg), 64 boxes, 1000 segments per world
-        # (about three minutes with the autotuner at every size, so only on request)
+    if not args.no_sweep and not args.no_extras:
+        # resolution sweep: 3 cameras (0, +-60 deg), 64 boxes, 1000 segments per world; the
+        # batched precision path (f16 keys, bf16 one-hot) against the plain FP32 path (u8 class
+        # + FP32 depth), square sizes 64..512, default launch shapes (no autotuning)
         wl_s0 = rank_workload(wg.WORKLOADS["sweep"], rank)
         worlds_s = wg.make_workload(wl_s0)
         sweep = {}
         for res in (64, 128, 256, 512):
             wl_s = dataclasses.replace(wl_s0, width=res, height=res)
-            sim_s = Simulator(worlds_s, config_for(wl_s, autotune=1), device=local)
-            r = graph_rate(sim_s, worlds_s, wl_s, 5)
-            r["mpix_per_s"] = r["cameras"] * res * res / (r["ms_per_step"] / 1e3) / 1e6
-            sweep["%dx%d" % (res, res)] = r
-            sim_s.close()
-        extras["sweep_3cam_class_u8"] = sweep
+            row = {}
+            for path, kw, dep in (("plain_fp32_u8_class_f32_depth", dict(key_precision=0, output=0), True),
+                                  ("precision_f16_key_bf16_onehot", dict(key_precision=1, output=1), False)):
+                sim_s = Simulator(worlds_s, config_for(wl_s, **kw), device=local)
+                r = graph_rate(sim_s, worlds_s, wl_s, 3, depth=dep)
+                r["mpix_per_s"] = r["cameras"] * res * res / (r["ms_per_step"] / 1e3) / 1e6
+                row[path] = r
+                sim_s.close()
+            row["precision_speedup"] = (row["precision_f16_key_bf16_onehot"]["agent_steps_per_s"] /
+                                        row["plain_fp32_u8_class_f32_depth"]["agent_steps_per_s"])
+            sweep["%dx%d" % (res, res)] = row
+        extras["sweep_3cam"] = sweep
 
+    # --- CPU leg: the oracle on this machine's host cores, after all GPU timing ---
     cpu = None
     if rank == 0:
-        rate, el, n = oracle_sample(worlds, wl_rank, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d cameras (world step + one 128x128 render each) in %.1f s, "
-                         "single thread" % (n, el)}
+        sampler = OracleSampler(wg.make_workload(wl_rank, n_worlds=min(worlds.n_worlds, 64)), wl_rank)
+        rate, el, n = sampler.sample(args.cpu_seconds)
+        sampler.close()
+        cpu = {"value": rate, "unit": UNIT, "cores": sampler.cores, "kind": "oracle",
+               "cpu": cpu_model(),
+               "sample": "%d cameras (world step + one %dx%d render each) in %.1f s of wall time "
+                         "on %d host cores, one process per core" % (
+                             n, wl.width, wl.height, el, sampler.cores)}
+        # the same oracle on the sampled GPU views of each configuration (from the GPU's state)
+        acc = {k: accuracy_vs_oracle(v) for k, v in accuracy_samples.items()}
+        if acc:
+            extras["accuracy_vs_fp64_oracle"] = acc
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -4,7 +4,7 @@ one (gp_debug_dump_tris), called through the C ABI.
 The allocation-free variant exists for callers that cannot allocate device memory at the
 point of the call (a caching allocator already holding the free HBM, or a loop that cannot
 take the synchronisation of cudaMalloc/cudaFree); its scratch is one fixed device array
-shared by all calls.  This file sorts last so that a run that stops at the first failure
+shared by all calls, whose address is looked up when a handle is created.  This file sorts last so that a run that stops at the first failure
 has already run every other test.
 """
 import ctypes
@@ -32,17 +32,20 @@ def _sorted(t):
     return np.sort(t.view(np.dtype((np.void, t.dtype.itemsize))))
 
 
-def test_noalloc_dump_matches_allocating_dump_on_consecutive_calls():
+@pytest.mark.parametrize("name,n_worlds", [("uniform", 2), ("ragged", 6)])
+def test_noalloc_dump_matches_allocating_dump_on_consecutive_calls(name, n_worlds):
+    """Two calls in a row (and a third repeating the first view) give the allocating dump's
+    records and images; the ragged batch runs the handle's work list of uneven worlds."""
     import torch
-    wl = wg.WORKLOADS["uniform"]
-    worlds = wg.make_workload(wl, n_worlds=2)
+    wl = wg.WORKLOADS[name]
+    worlds = wg.make_workload(wl, n_worlds=n_worlds)
     sim, cfg = sim_for(worlds, wl)
     for k in range(2):
         sim.step(torch.from_numpy(wg.actions(wl.seed, k, worlds.n_agents)).cuda())
     out_a, dep_a = sim.alloc_outputs()
     out_b, dep_b = sim.alloc_outputs()
     cap = 16384
-    views = (3, 40, 3)  # two different views in a row, then the first one again
+    views = (3, min(40, sim.n_views - 1), 3)  # two views in a row, then the first again
     refs = {v: _dump("gp_debug_dump_tris", sim, v, out_a, dep_a, cap) for v in set(views)}
     torch.cuda.synchronize()
     for v in views:
@@ -52,7 +55,33 @@ def test_noalloc_dump_matches_allocating_dump_on_consecutive_calls():
         assert np.array_equal(_sorted(got), _sorted(ref))
         torch.cuda.synchronize()
         assert torch.equal(out_a, out_b)
-        assert torch.equal(dep_a.view(torch.int32), dep_b.view(torch.int32))
+        if dep_a.dtype == torch.float32:
+            assert torch.equal(dep_a.view(torch.int32), dep_b.view(torch.int32))
+        else:
+            assert torch.equal(dep_a.view(torch.int16), dep_b.view(torch.int16))
+
+
+def test_noalloc_dump_counts_every_record_beyond_cap():
+    """With 0 < cap < n, *n still counts every record produced while only cap of them are
+    copied, and those are records of the full dump."""
+    import torch
+    wl = wg.WORKLOADS["uniform"]
+    worlds = wg.make_workload(wl, n_worlds=2)
+    sim, cfg = sim_for(worlds, wl)
+    for k in range(2):
+        sim.step(torch.from_numpy(wg.actions(wl.seed, k, worlds.n_agents)).cuda())
+    out, dep = sim.alloc_outputs()
+    # the busiest of a few views, so that a third of its records is still many
+    dumps = {v: _dump("gp_debug_dump_tris", sim, v, out, dep, 16384) for v in (3, 5, 20, 40)}
+    view = max(dumps, key=lambda v: dumps[v][1])
+    full, n_full = dumps[view]
+    assert n_full > 100
+    cap = n_full // 3
+    got, n = _dump("gp_debug_dump_tris_noalloc", sim, view, out, dep, cap)
+    torch.cuda.synchronize()
+    assert n == n_full and len(got) == cap
+    rows = set(_sorted(full).tolist())
+    assert all(r in rows for r in _sorted(got).tolist())
 
 
 def test_noalloc_dump_rejects_capacity_beyond_its_scratch():
