@@ -24,9 +24,11 @@
 //      in shared memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or
 //      (binary16 depth << 16 | ~prim) in FP16 mode; the nearest surface wins, ties go to
 //      the smaller primitive id;
-//   4. encode: keys become class ids (uint8) + depth, or a normalised one-hot BF16 NCHW
-//      tensor; the band is one contiguous range of every output plane, written with 16-byte
-//      streaming stores.
+//   4. encode: keys become class ids (uint8) + depth, a normalised one-hot BF16 NCHW
+//      tensor, or shaded RGB; the band is one contiguous range of every output plane, written
+//      with coalesced streaming stores: per lane 16 B of FP32 depth, 4 B of class ids (or of
+//      each RGB channel), and with FP16 keys 16 B per one-hot channel and of binary16 depth
+//      (8 pixels per lane when the width is a multiple of 8; else 8 B for 4 pixels).
 // A pipelined variant splits the block into producer warps (steps 1-2) and consumer warps
 // (steps 3-4) that hand double-buffered triangle batches to each other.
 // The depth plane d = d0 + a (X - X0) + b (Y - Y0) and its per-pixel evaluation follow a
@@ -1100,13 +1102,45 @@ __device__ void encode_f32(const RenderParams &p, const Cam &cm, unsigned long l
     }
 }
 
-// FP16 mode: one key per pixel, binary16 depth bits above the inverted primitive id.
+// FP16 mode: one key per pixel, binary16 depth bits above the inverted primitive id.  With
+// the one-hot output and a width that is a multiple of 8, a lane takes eight pixels, so each
+// channel (and the depth plane) is written with one 16-byte store per lane.
 __device__ void encode_f16(const RenderParams &p, const Cam &cm, unsigned int *keys, int view,
                            const Group &g) {
     const int band_px = (cm.by1 - cm.by0 + 1) * p.W;
     const long long slot = p.view_mod ? (view % p.view_mod) : view;
     const long long plane = (long long)p.H * p.W;
     const long long row0 = (long long)cm.by0 * p.W;
+    if (p.out_mode == GP_OUT_ONEHOT_BF16 && (p.W & 7) == 0) {
+        for (int b = 8 * g.tid; b < band_px; b += 8 * g.nt) {
+            const uint4 ka = *(const uint4 *)(keys + b);
+            const uint4 kb = *(const uint4 *)(keys + b + 4);
+            *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
+            *(uint4 *)(keys + b + 4) = make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t k[8] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const uint32_t c = class_of_low(k[q] & 0xFFFFu, 0xFFFFu, cm);
+                o[q] = c == 4u ? 3u : c;  // signals share the object channel 3 with the boxes
+            }
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = (uint32_t)p.onehot[ch][o[2 * q] == (uint32_t)ch] |
+                           ((uint32_t)p.onehot[ch][o[2 * q + 1] == (uint32_t)ch] << 16);
+                __stcs((uint4 *)((uint16_t *)p.out + (slot * 4 + ch) * plane + row0 + b),
+                       make_uint4(w[0], w[1], w[2], w[3]));
+            }
+            if (p.depth)
+                __stcs((uint4 *)((uint16_t *)p.depth + slot * plane + row0 + b),
+                       make_uint4((k[0] >> 16) | (k[1] & 0xFFFF0000u), (k[2] >> 16) | (k[3] & 0xFFFF0000u),
+                                  (k[4] >> 16) | (k[5] & 0xFFFF0000u), (k[6] >> 16) | (k[7] & 0xFFFF0000u)));
+        }
+        return;
+    }
     for (int b = 4 * g.tid; b < band_px; b += 4 * g.nt) {
         const uint4 k = *(const uint4 *)(keys + b);
         *(uint4 *)(keys + b) = make_uint4(0u, 0u, 0u, 0u);
