@@ -127,19 +127,24 @@ def test_step_matches_oracle_from_same_state(name, n_worlds, steps):
         assert n_halted > 0  # random steering does drive some agents off the road
 
 
-@pytest.mark.parametrize("name,n_worlds,steps", [("uniform", 4, 15), ("ragged", 6, 12)])
-def test_red_light_halt_matches_oracle(name, n_worlds, steps):
+@pytest.mark.parametrize("name,n_worlds,steps,jerk", [("uniform", 4, 15, False), ("ragged", 6, 12, False),
+                                                      ("uniform", 4, 12, True)],
+                         ids=["uniform", "ragged", "uniform-jerk"])
+def test_red_light_halt_matches_oracle(name, n_worlds, steps, jerk):
     """App. A "Other Details": a red-light violation halts the agent like a collision or an
     off-road departure.  32 red signals per world hang over the agents' roads; every step
-    from the GPU's own FP32 state is compared with one oracle step: pose and speed within
-    FP32 rounding, flags identical (including the red-light bit 16), rewards as the
-    oracle's; violators stop at once and stay where they stopped."""
+    from the GPU's own FP32 state (and, under the jerk dynamics, actuator state) is compared
+    with one oracle step: pose and speed within FP32 rounding, flags identical (including
+    the red-light bit 16), rewards as the oracle's (direct control); violators stop at once
+    and stay where they stopped."""
     import torch
+    import paper_2606_19641_b300 as gp
     wl = wg.WORKLOADS[name]
     worlds = wg.make_workload(wl, n_worlds=n_worlds)
     wg.add_signals(worlds, 32, wl.seed, height=5.0)
     worlds.signal_state[:] = 0
-    sim, cfg = sim_for(worlds, wl, rewards=1)
+    extra = dict(dynamics=gp.DYN_JERK) if jerk else {}
+    sim, cfg = sim_for(worlds, wl, rewards=1, **extra)
     off = worlds.agent_offsets()
     na = worlds.n_agents
     dims = np.zeros((na, 2), np.float64)
@@ -153,12 +158,20 @@ def test_red_light_halt_matches_oracle(name, n_worlds, steps):
     stopped_at = {}
     for k in range(steps):
         st0, fl0 = sim.get_state()
-        osim = oracle.Sim(worlds)
-        osim.set_state(st0.astype(np.float64), fl0)
-        act_t, act = torch_actions(worlds, k, wl.seed)
+        if jerk:
+            osim = oracle.Sim(worlds, jerk_dynamics=True)
+            osim.set_state(st0.astype(np.float64), fl0, sim.get_dynamics().astype(np.float64))
+            act = _jerk_actions(na, k, wl.seed)
+            act_t = torch.from_numpy(act).cuda()
+        else:
+            osim = oracle.Sim(worlds)
+            osim.set_state(st0.astype(np.float64), fl0)
+            act_t, act = torch_actions(worlds, k, wl.seed)
         sim.step(act_t)
         osim.step(act)
         st1, fl1 = sim.get_state()
+        if jerk:
+            assert np.allclose(sim.get_dynamics(), osim.jerk, atol=2e-5, rtol=0)
         r, _ = sim.rewards()
         torch.cuda.synchronize()
         r = r.cpu().numpy()
@@ -172,7 +185,7 @@ def test_red_light_halt_matches_oracle(name, n_worlds, steps):
         for i, pose in stopped_at.items():
             assert np.array_equal(st1[i, 0:3], pose), "agent %d moved after its red-light halt" % i
         red |= new
-        for w in range(worlds.n_worlds):
+        for w in range(0 if jerk else worlds.n_worlds):  # jerk rewards: their own test
             a0, a1 = int(off[w]), int(off[w + 1])
             road = worlds.road[int(worlds.road_off[w]):int(worlds.road_off[w + 1])]
             s0, s1 = int(worlds.signal_off[w]), int(worlds.signal_off[w + 1])
