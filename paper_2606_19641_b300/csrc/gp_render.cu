@@ -1419,17 +1419,33 @@ __global__ void __launch_bounds__(128, 14) trace_kernel(RenderParams p) {
     __syncthreads();
     if (px0 >= plane) return;
     const uint32_t full = p.key_f16 ? 0xFFFFu : 0xFFFFFFFFu;
-    uint32_t c[4], low[4];
-    float d[4];
-#pragma unroll
+    // the four pixels one after another in a rolled loop (one copy of the tracing code: the
+    // unrolled kernel stalled on instruction fetch), their results gathered in scalars
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll 1
     for (int k = 0; k < 4; ++k) {
         const int pix = px0 + k, j = pix / p.W, i = pix - j * p.W;
         uint32_t prim;
         float t;
-        c[k] = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, blist, nbk, ts, prim, t);
-        low[k] = c[k] ? full - prim : 0u;
-        d[k] = c[k] ? __fdiv_rn(p.near_plane, t) : 0.f;
+        const uint32_t ck = (uint32_t)trace_pixel(p, cm, wi, i, j, tb, blist, nbk, ts, prim, t);
+        const uint32_t lk = ck ? full - prim : 0u;
+        const float dk = ck ? __fdiv_rn(p.near_plane, t) : 0.f;
+        c0 = k == 0 ? ck : c0;
+        c1 = k == 1 ? ck : c1;
+        c2 = k == 2 ? ck : c2;
+        c3 = k == 3 ? ck : c3;
+        l0 = k == 0 ? lk : l0;
+        l1 = k == 1 ? lk : l1;
+        l2 = k == 2 ? lk : l2;
+        l3 = k == 3 ? lk : l3;
+        d0 = k == 0 ? dk : d0;
+        d1 = k == 1 ? dk : d1;
+        d2 = k == 2 ? dk : d2;
+        d3 = k == 3 ? dk : d3;
     }
+    const uint32_t c[4] = {c0, c1, c2, c3}, low[4] = {l0, l1, l2, l3};
+    const float d[4] = {d0, d1, d2, d3};
     const long long slot = view;
     store_classes(p, cm, slot, plane, px0, c, low, full);
     if (p.depth) {
