@@ -308,6 +308,7 @@ RenderParams render_params(gp_handle *h, void *out, void *depth) {
     }
     p.sig = h->sig.p;
     p.sig_state = h->sig_state.p;
+    p.has_signals = h->n_signals > 0;
     p.out = out;
     p.depth = depth;
     p.view_mod = 0;

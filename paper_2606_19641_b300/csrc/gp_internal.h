@@ -136,6 +136,7 @@ struct RenderParams {
     float sig_colour[4][3];   // RGB output: signal colours by state
     const float4 *sig;        // signal spheres: x, y, z, r
     const uint8_t *sig_state; // their states
+    int has_signals;          // some world of the batch has signal spheres
     void *out;
     void *depth;
     int view_mod;            // 0, or write view v at slot v % view_mod (tuning scratch)

@@ -1335,6 +1335,11 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
 // 14 blocks of 128 threads per SM caps the kernel at 32 registers: the latency of its grid
 // and quad loads hides better with more resident warps than it loses to a few spills
 // (A/B: 2.59 -> 2.38 ms per launch on the uniform batch).
+// PAIRS: the four pixels are traced two at a time (interleaved, for instruction-level
+// parallelism) -- used when no world has signal spheres; with spheres the larger tracing
+// code runs one pixel at a time, which stalls less on instruction fetch (A/B on B300:
+// uniform 2.31 -> 2.13 ms with pairs; the 210 x 126 rig with signals 19.9 -> 21.1 ms).
+template <bool PAIRS>
 __global__ void __launch_bounds__(128, 14) trace_kernel(RenderParams p) {
     __shared__ TraceBox tb[kMaxBoxes];
     __shared__ float4 ts[kMaxSignals];
@@ -1419,11 +1424,11 @@ __global__ void __launch_bounds__(128, 14) trace_kernel(RenderParams p) {
     __syncthreads();
     if (px0 >= plane) return;
     const uint32_t full = p.key_f16 ? 0xFFFFu : 0xFFFFFFFFu;
-    // the four pixels one after another in a rolled loop (one copy of the tracing code: the
+    // the four pixels in a rolled loop (one or two copies of the tracing code: the fully
     // unrolled kernel stalled on instruction fetch), their results gathered in scalars
     uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
     float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
-#pragma unroll 1
+#pragma unroll(PAIRS ? 2 : 1)
     for (int k = 0; k < 4; ++k) {
         const int pix = px0 + k, j = pix / p.W, i = pix - j * p.W;
         uint32_t prim;
@@ -1885,7 +1890,9 @@ cudaError_t launch_trace(const RenderParams &p, int n_views, cudaStream_t s) {
     for (int v0 = 0; v0 < n_views; v0 += 65535) {
         RenderParams q = p;
         q.trace_view0 = v0;
-        trace_kernel<<<dim3(bx, (unsigned)std::min(65535, n_views - v0)), 128, 0, s>>>(q);
+        const dim3 grid(bx, (unsigned)std::min(65535, n_views - v0));
+        if (p.has_signals) trace_kernel<false><<<grid, 128, 0, s>>>(q);
+        else trace_kernel<true><<<grid, 128, 0, s>>>(q);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
