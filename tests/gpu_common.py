@@ -199,7 +199,7 @@ def check_views(sim, cfg, worlds, views, out, depth, t2=True, t4=True):
     cam = cam_config(cfg)
     W, H = int(cfg.width), int(cfg.height)
     S = dict(views=0, pixels=0, covered=0, o_vis=0, g_vis=0, matched=0, exact=0, worst=0,
-             missing=0, extra=0, differing=0, recut=0, mismatch=0, explained=0, bound=0.0)
+             missing=0, extra=0, differing=0, recut=0, mismatch=0, explained=0, ties=0, bound=0.0)
     derr = []
     for v in views:
         g = dedupe(sim.dump_tris(v, out, depth))
@@ -293,6 +293,21 @@ def check_views(sim, cfg, worlds, views, out, depth, t2=True, t4=True):
                 S["bound"] += tri_perimeter_px(t) + 3.0
         S["mismatch"] += int(mis.sum())
         S["explained"] += int((mis & band).sum())
+        # the rest should be near-ties in depth between two surfaces (a box's base on the
+        # road plane, a lane line far away): both pipelines cover the pixel, at depths
+        # within the per-vertex n / z rounding of FP32 against FP64 (or one binary16 step)
+        rest = mis & ~band & (gcls > 0) & (ocls > 0)
+        if rest.any() and depth is not None:
+            if int(cfg.key_precision) == 0:
+                gz = gd.view(np.float32).astype(np.float64)
+                oz = ref.depth.astype(np.float64)
+                tol = 1e-5
+            else:
+                gz = gd.view(np.float16).astype(np.float64)
+                oz = ref.depth.view(np.float16).astype(np.float64)
+                tol = 2.0 ** -9
+            tie = rest & (np.abs(gz - oz) <= tol * np.maximum(np.abs(oz), 1e-12))
+            S["ties"] += int(tie.sum())
         if depth is not None:
             both = (gcls > 0) & (gcls == ocls)
             if int(cfg.key_precision) == 0:
@@ -312,11 +327,11 @@ def assert_views(S, label, min_covered=0.2):
     d = S["depth_rel_err"]
     print("%s: %d views; T2 %d oracle / %d GPU visible triangles, %d matched (%d exact, worst "
           "%d units), %d missing, %d extra, %d differing, %d recut; T4 %d class mismatches of %d pixels "
-          "(%.2e), %d within a pixel of a differing triangle's boundary, bound %.0f; depth rel "
+          "(%.2e), %d within a pixel of a differing triangle's boundary, %d depth near-ties, bound %.0f; depth rel "
           "err p99 %.2e max %.2e" % (
               label, S["views"], S["o_vis"], S["g_vis"], S["matched"], S["exact"], S["worst"],
               S["missing"], S["extra"], S["differing"], S["recut"], S["mismatch"], S["pixels"],
-              S["mismatch"] / max(S["pixels"], 1), S["explained"], S["bound"],
+              S["mismatch"] / max(S["pixels"], 1), S["explained"], S["ties"], S["bound"],
               np.percentile(d, 99), d.max()))
     assert S["covered"] > min_covered * S["pixels"]
     assert S["missing"] <= 0.002 * S["o_vis"] + 2 and S["extra"] <= 0.002 * S["g_vis"] + 2
