@@ -267,7 +267,7 @@ def accuracy_vs_oracle(sample):
 
 
 def algorithmic_bytes(sim, worlds, wl, with_depth=True):
-    """The method's bytes per render launch (SURVEY-style accounting of the hot path): the
+    """The method's bytes per render launch (the hot path's own accounting): the
     images written, plus the world read once -- 32 B per road segment (stored as its
     parameters), about 40 B per agent (pose, size, speed, flags) and 28 B per static box."""
     n_w = worlds.n_worlds
