@@ -6,7 +6,8 @@ the first call does, and raises if it was not built.
 """
 from .binding import (Config, GigapixelError, Simulator, default_config, lib, load_library,
                       KEY_F16, KEY_F32, OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8, FLAG_COLLIDED,
-                      FLAG_HALTED, FLAG_OFFROAD, FLAG_DONE, TRI_DTYPE, DYN_DIRECT, DYN_JERK, EGO_DIM,
+                      FLAG_HALTED, FLAG_OFFROAD, FLAG_DONE, FLAG_RED_LIGHT, TRI_DTYPE, DYN_DIRECT,
+                      DYN_JERK, EGO_DIM,
                       JERK_ACTIONS)
 
 

@@ -20,7 +20,7 @@ KEY_F32, KEY_F16 = 0, 1
 OUT_CLASS_U8, OUT_ONEHOT_BF16, OUT_RGB_U8 = 0, 1, 2
 CLASS_SIGNAL = 4
 SIGNAL_RED, SIGNAL_AMBER, SIGNAL_GREEN, SIGNAL_OFF = 0, 1, 2, 3
-FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED, FLAG_DONE = 1, 2, 4, 8
+FLAG_COLLIDED, FLAG_OFFROAD, FLAG_HALTED, FLAG_DONE, FLAG_RED_LIGHT = 1, 2, 4, 8, 16
 DEV_NONFINITE_STATE, DEV_CLIP_OVERFLOW, DEV_PIPELINE_TIMEOUT, DEV_INJECTED = 1, 2, 4, 1 << 31
 MAX_CAMS = 8
 DYN_DIRECT, DYN_JERK = 0, 1

@@ -356,6 +356,53 @@ def test_edge_case_worlds():
     assert fl[1] == 0                      # on its road
 
 
+@pytest.mark.parametrize("precision", [False, True], ids=["f32", "f16"])
+def test_maximum_sizes(precision):
+    """The documented limits at once: a world of GP_MAX_BOXES = 128 boxes that are all
+    agents, GP_MAX_CAMS = 8 cameras per agent (every 45 deg), 2000 road segments (20 300
+    quads, 42 136 primitive ids: within the FP16 key's 16-bit ids), and a second world of
+    100 agents among 128 boxes.  One step against the oracle (all 128 x 128 box pairs), then
+    T3, T2 and T4 on every camera of four agents, and the ray tracer on some views."""
+    import math
+    import torch
+    import paper_2606_19641_b300 as gp
+    worlds = wg.make_worlds(2, [128, 100], [128, 128], [2000, 1500], seed=77)
+    wl = wg.WORKLOADS["tiny"]
+    extra = dict(key_precision=gp.KEY_F16) if precision else {}
+    sim, cfg = sim_for(worlds, wl, width=64, height=64,
+                       cam_yaw=[math.radians(45.0 * k) for k in range(8)], **extra)
+    assert sim.n_views == 8 * 228
+    st0, fl0 = sim.get_state()
+    osim = oracle.Sim(worlds)
+    osim.set_state(st0.astype(np.float64), fl0)
+    act_t, act = torch_actions(worlds, 0, 4242)
+    sim.step(act_t)
+    osim.step(act)
+    st1, fl1 = sim.get_state()
+    assert np.allclose(st1[:, 0:2], osim.state[:, 0:2], atol=2e-4, rtol=0)
+    assert np.array_equal(fl1, osim.flags)
+    out, depth = sim.alloc_outputs()
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    views = sorted(8 * a + c for a in (0, 63, 127, 200) for c in range(8))
+    S = check_views(sim, cfg, worlds, views, out, depth)
+    assert_views(S, "maximum sizes %s" % ("f16" if precision else "f32"), min_covered=0.05)
+    if not precision:
+        sim.trace(out, depth)
+        torch.cuda.synchronize()
+        o2 = oracle_sim(worlds, sim)
+        cam = cam_config(cfg)
+        bad = total = 0
+        for v in views[::4]:
+            w, a, c = view_loc(worlds, cfg, v)
+            tr = o2.trace(cam, w, a, float(np.float32(cfg.cam_yaw[c])))
+            g = out[v].cpu().numpy()
+            bad += int((g != tr.cls).sum())
+            total += g.size
+        assert bad <= 1e-3 * total
+
+
 # ---------------------------------------------------------------------------------------
 # Paths, state and status
 # ---------------------------------------------------------------------------------------
