@@ -176,7 +176,7 @@ def tri_perimeter_px(t):
     return float(sum(np.hypot(X[(k + 1) % 3] - X[k], Y[(k + 1) % 3] - Y[k]) for k in range(3)))
 
 
-def check_views(sim, cfg, worlds, views, out, depth, t2=True, t4=True):
+def check_views(sim, cfg, worlds, views, out, depth, t2=True, t4=True, t3=True):
     """Per view, from one triangle dump of the GPU:
       T3  the raster rule on the GPU's own snapped triangles gives bit-identical planes;
       T2  (both directions) every triangle covering a pixel centre in one pipeline has a
@@ -203,13 +203,14 @@ def check_views(sim, cfg, worlds, views, out, depth, t2=True, t4=True):
     derr = []
     for v in views:
         g = dedupe(sim.dump_tris(v, out, depth))
-        # T3
+        # T3 (class or one-hot outputs; the RGB tests check their planes themselves)
         img = oracle_raster_of(worlds, cfg, v, g)
         go, gd = gpu_view(cfg, out, depth, v)
-        eo, ed = expected_planes(cfg, img)
-        assert np.array_equal(go, eo), "view %d: class/one-hot differs from the raster rule" % v
-        if depth is not None:
-            assert np.array_equal(gd, ed), "view %d: depth bits differ from the raster rule" % v
+        if t3:
+            eo, ed = expected_planes(cfg, img)
+            assert np.array_equal(go, eo), "view %d: class/one-hot differs from the raster rule" % v
+            if depth is not None:
+                assert np.array_equal(gd, ed), "view %d: depth bits differ from the raster rule" % v
         S["covered"] += int((img.cls > 0).sum())
         S["views"] += 1
         S["pixels"] += W * H

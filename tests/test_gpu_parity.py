@@ -705,6 +705,10 @@ def test_paper_rig_rgb(size, key):
     assert frac < 1e-3
     # every class colour appears, shaded boxes differ by face
     assert int(out[:, 2].float().mean()) > 0
+    # the rig's geometry (four cameras, signal spheres) against the FP64 oracle, both ways
+    S = check_views(sim, cfg, worlds, views, out, depth, t3=False, t4=False)
+    assert_views(S, "paper rig %s %s T2" % (name, key), min_covered=0.05)
+    assert S["o_vis"] > 500
 
 
 def test_binding_checks_tensor_layouts():
