@@ -409,9 +409,14 @@ def test_maximum_sizes(precision):
 
 @pytest.mark.parametrize("shape", [dict(), dict(producer_warps=2)], ids=["default", "pipelined"])
 def test_graph_and_per_world_paths_match_direct_calls(shape):
+    """Direct calls, the step + render graph and the one-world-at-a-time path give identical
+    images and states; 16 red signals per world over the roads make the red-light halts run
+    on every path."""
     import torch
     wl = wg.WORKLOADS["ragged"]
     worlds = wg.make_workload(wl, n_worlds=6)
+    wg.add_signals(worlds, 16, wl.seed, height=5.0)
+    worlds.signal_state[:] = 0
     a, cfg = sim_for(worlds, wl, **shape)
     b, _ = sim_for(worlds, wl, **shape)
     c, _ = sim_for(worlds, wl, **shape)
@@ -436,6 +441,7 @@ def test_graph_and_per_world_paths_match_direct_calls(shape):
     sc, fc = c.get_state()
     assert np.array_equal(sa, sb) and np.array_equal(sa, sc)
     assert np.array_equal(fa, fb) and np.array_equal(fa, fc)
+    assert (fa & 16).any()  # some agent ran a red light and was halted on every path
 
 
 def test_state_roundtrip_and_fork():
