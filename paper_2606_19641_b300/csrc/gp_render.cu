@@ -60,6 +60,18 @@ static_assert(sizeof(TriRec) == 32, "TriRec layout");
 static_assert(kMaxBandRows <= 128, "(j0 - by0) and (j1 - j0) have 7 bits each");
 static_assert(kMaxBandRows * GP_MAX_WIDTH <= 65536, "a band's key index fits 16 bits");
 
+// A warp's non-empty spans, compacted (one 640-byte table per warp): the key index and the
+// pixel offset of fragment f of the warp's concatenated spans are kb + f and gb + 16 f for
+// the span holding f, which ends before fragment `end`.
+struct __align__(16) FragEnt {
+    uint32_t w0;     // kb + kKbBias (bits 0..16) | end (bits 17..31)
+    int gb;          // pixel-centre offset (1/16 px) from vertex 0 of fragment 0 along this row
+    float a, inner;  // depth plane along the row
+};
+constexpr int kKbBias = 1 << 14;  // kb = kofs - start > -2^14: a wave holds <= 2^14 fragments
+static_assert(32 * GP_MAX_WIDTH <= (1 << 14), "a wave's fragment count fits 15 bits");
+constexpr int kFragTabBytes = 32 * (sizeof(FragEnt) + 4);  // entries + inverted ids, per warp
+
 __device__ __forceinline__ int span_i0(uint32_t s) { return (int)(s & 511u); }
 __device__ __forceinline__ int span_i1(uint32_t s) { return (int)((s >> 9) & 511u); }
 __device__ __forceinline__ int span_j0(uint32_t s) { return (int)((s >> 18) & 127u); }  // band-relative
@@ -78,7 +90,7 @@ struct Cam {
 };
 
 struct Smem {
-    size_t keys, tris, rowoff, map, clipscratch, vq0, vpre, vnq, visbox, vissig, clipq, total;
+    size_t keys, tris, rowoff, map, ftab, clipscratch, vq0, vpre, vnq, visbox, vissig, clipq, total;
 };
 
 // Traffic-signal polyhedron (4 latitude bands x 8 longitude sectors, vertices on the
@@ -120,6 +132,8 @@ __host__ __device__ inline Smem smem_layout(int W, int band_rows, int key_f16, i
     s.map = o;
     o += (size_t)raster_threads * kItemsPerThread * 2;
     o = align_up(o, 16);
+    s.ftab = o;  // the raster warps' span tables (FP16 keys only)
+    if (key_f16) o += (size_t)(raster_threads / 32) * kFragTabBytes;
     // per clipping warp: 4 jobs x 8 vertices x 3 floats; shares space with the raster
     // bookkeeping unless both sides run at once (pipelined kernel)
     s.clipscratch = prod_warps ? o : shared_base;
@@ -385,22 +399,24 @@ __device__ __forceinline__ void depth_test(void *keys, int ko, int g, float a, f
 
 // Relative cost of one cooperative round (32 fragments) against one per-lane iteration:
 // 64-bit key updates favour the cooperative walk.
-constexpr int kCoopCostF32 = 1, kCoopCostF16 = 3;
+constexpr int kCoopCostF32 = 1;
 
-// Depth resolution of a warp's spans (warp-uniform call).  Lane k brings a span of `cnt`
-// pixels starting at key index `kofs`, whose first pixel centre lies gx0 (1/16 px) right of
-// the triangle's vertex 0.  If the spans are even, each lane walks its own span; if a few
-// long spans dominate, the warp scans the counts and walks the concatenated fragments 32 at
-// a time, each lane finding its span by binary search over the prefix sums, so the cost
-// follows the number of fragments rather than the longest span.
-template <bool F32>
-__device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float a, float inner,
-                                               uint32_t low, void *keys) {
+// Depth resolution of a warp's spans with FP32 keys (warp-uniform call).  Lane k brings a
+// span of `cnt` pixels starting at key index `kofs`, whose first pixel centre lies gx0
+// (1/16 px) right of the triangle's vertex 0.  If the spans are even, each lane walks its
+// own span; if a few long spans dominate, the warp scans the counts and walks the
+// concatenated fragments 32 at a time, each lane finding its span by binary search over the
+// prefix sums, so the cost follows the number of fragments rather than the longest span.
+// Consecutive lanes take consecutive fragments, so the 64-bit key atomics of a round land
+// on adjacent keys (distinct banks); this walk needs no shared table, which the FP32 key
+// buffer leaves no room for.
+__device__ __forceinline__ void warp_fragments_coop(int cnt, int kofs, int gx0, float a,
+                                                    float inner, uint32_t low, void *keys) {
     const int lane = threadIdx.x & 31;
     const int maxc = __reduce_max_sync(0xffffffffu, cnt);
     const int total = __reduce_add_sync(0xffffffffu, cnt);
-    if (maxc <= ((total + 31) >> 5) * (F32 ? kCoopCostF32 : kCoopCostF16)) {
-        for (int t = 0; t < cnt; ++t) depth_test<F32>(keys, kofs + t, gx0 + 16 * t, a, inner, low);
+    if (maxc <= ((total + 31) >> 5) * kCoopCostF32) {
+        for (int t = 0; t < cnt; ++t) depth_test<true>(keys, kofs + t, gx0 + 16 * t, a, inner, low);
         return;
     }
     int incl = cnt;
@@ -441,9 +457,9 @@ __device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float
         const uint32_t lA = __shfl_sync(0xffffffffu, low, oA);
         const uint32_t lB = __shfl_sync(0xffffffffu, low, oB);
         // fA < total here
-        depth_test<F32>(keys, (kgA & 0xFFFF) + tA, (kgA >> 16) + 16 * tA, aA, iA, lA);
+        depth_test<true>(keys, (kgA & 0xFFFF) + tA, (kgA >> 16) + 16 * tA, aA, iA, lA);
         if (fB < total)
-            depth_test<F32>(keys, (kgB & 0xFFFF) + tB, (kgB >> 16) + 16 * tB, aB, iB, lB);
+            depth_test<true>(keys, (kgB & 0xFFFF) + tB, (kgB >> 16) + 16 * tB, aB, iB, lB);
     }
     if (f0 < total) {
         const int f = f0 + lane;
@@ -461,8 +477,65 @@ __device__ __forceinline__ void warp_fragments(int cnt, int kofs, int gx0, float
         const float fa = __shfl_sync(0xffffffffu, a, o);
         const float fi = __shfl_sync(0xffffffffu, inner, o);
         const uint32_t lw = __shfl_sync(0xffffffffu, low, o);
-        if (f < total) depth_test<F32>(keys, (kgo & 0xFFFF) + t, (kgo >> 16) + 16 * t, fa, fi, lw);
+        if (f < total) depth_test<true>(keys, (kgo & 0xFFFF) + t, (kgo >> 16) + 16 * t, fa, fi, lw);
     }
+}
+
+// Depth resolution of a warp's spans with FP16 keys (warp-uniform call), arguments as for
+// warp_fragments_coop plus the warp's span table.  The warp concatenates its spans (prefix
+// sums) and cuts the fragments into 32 runs of equal, odd length, one per lane: each lane
+// walks its run pixel by pixel and moves to the next span from the table when it crosses
+// one, so the cost follows the number of fragments, not the longest span, with no search
+// per fragment.  The odd run length puts the lanes that share one long span on different
+// shared-memory banks at every step.
+__device__ __forceinline__ void warp_fragments_runs(int cnt, int kofs, int gx0, float a,
+                                                    float inner, uint32_t low, void *keys,
+                                                    FragEnt *ent, uint32_t *lows) {
+    const int lane = threadIdx.x & 31;
+    const unsigned int nz = __ballot_sync(0xffffffffu, cnt > 0);
+    if (!nz) return;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (cnt > 0) {
+        const int k = __popc(nz & ((1u << lane) - 1u));
+        const int start = incl - cnt;
+        ent[k] = FragEnt{(uint32_t)(kofs - start + kKbBias) | ((uint32_t)incl << 17), gx0 - 16 * start,
+                         a, inner};
+        lows[k] = low;
+    }
+    __syncwarp();
+    const int L = ((total + 31) >> 5) | 1;
+    int f = lane * L;
+    // the lane holding fragment f: the number of inclusive prefixes <= f (f < total)
+    int o = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, o + st - 1);
+        if (v <= f) o += st;
+    }
+    if (f < total) {
+        const int fe = min(f + L, total);
+        int k = __popc(nz & ((1u << o) - 1u));
+        FragEnt e = ent[k];
+        uint32_t lw = lows[k];
+        int end = (int)(e.w0 >> 17), kb = (int)(e.w0 & 0x1FFFFu) - kKbBias;
+        for (; f < fe; ++f) {
+            if (f == end) {
+                ++k;
+                e = ent[k];
+                lw = lows[k];
+                end = (int)(e.w0 >> 17);
+                kb = (int)(e.w0 & 0x1FFFFu) - kKbBias;
+            }
+            depth_test<false>(keys, kb + f, e.gb + 16 * f, e.a, e.inner, lw);
+        }
+    }
+    __syncwarp();  // the next wave rewrites the table
 }
 
 // Warp-aggregated append: returns this lane's slot (valid where keep is true).
@@ -556,7 +629,8 @@ struct Shared {
 // threads of group g call; ends with a group barrier).
 template <bool F32, bool ST>
 __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys, TriRec *tris,
-                      int *rowoff, unsigned short *map, int *s_warp, const Group &g) {
+                      int *rowoff, unsigned short *map, unsigned char *ftab, int *s_warp,
+                      const Group &g) {
     n = min(n, p.tri_cap);
     const int tid = g.tid, nt = g.nt;
     // row counts -> exclusive scan (each thread owns a contiguous slice of triangles)
@@ -609,8 +683,13 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
         }
         g.sync();
         // Consecutive items (the rows of one triangle) go to different warps, so a large
-        // triangle is spread over the block instead of holding up one warp.
-        const int nw = nt >> 5, mine = (tid & 31) * nw + (tid >> 5);
+        // triangle is spread over the block instead of holding up one warp.  The warp order
+        // is rotated per group of lanes so that a warp's 32 reads of the map fall on distinct
+        // banks (lane l reads entry l nw + its rotated warp index).
+        const int nw = nt >> 5, lane = tid & 31;
+        const int mine = lane * nw + ((tid >> 5) + 2 * ((lane * nw) >> 6)) % nw;
+        FragEnt *ent = (FragEnt *)(ftab + (size_t)(tid >> 5) * kFragTabBytes);
+        uint32_t *lows = (uint32_t *)(ent + 32);
         for (int ib = 0; ib < len; ib += nt) {  // warp-uniform trip count
             const int i = ib + mine;
             int cnt = 0, kofs = 0, gx0 = 0;
@@ -640,7 +719,8 @@ __device__ void flush(const RenderParams &p, int by0, int by1, int n, void *keys
                 if ((tid & 31) == 0 && fr)
                     atomicAdd(&p.stats[GP_STAT_FRAGMENTS], (unsigned long long)fr);
             }
-            warp_fragments<F32>(cnt, kofs, gx0, a, inner, low, keys);
+            if (F32) warp_fragments_coop(cnt, kofs, gx0, a, inner, low, keys);
+            else warp_fragments_runs(cnt, kofs, gx0, a, inner, low, keys, ent, lows);
         }
         g.sync();
     }
@@ -1683,6 +1763,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     TriRec *tris = (TriRec *)(smem + L.tris);
     int *rowoff = (int *)(smem + L.rowoff);
     unsigned short *map = (unsigned short *)(smem + L.map);
+    unsigned char *ftab = smem + L.ftab;
     SetupMem m{tris, (uint32_t *)(smem + L.clipq), (float *)(smem + L.clipscratch),
                (int *)(smem + L.vq0), (int *)(smem + L.vpre), smem + L.vnq,
                smem + L.visbox, smem + L.vissig};
@@ -1694,7 +1775,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     int view = 0;
     auto emit = [&](bool last) -> TriRec * {
         const int n = sh.resv;
-        if (n > 0) flush<F32, ST>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, s_warp, g);
+        if (n > 0) flush<F32, ST>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, ftab, s_warp, g);
         if (g.tid == 0) sh.resv = 0;
         g.sync();
         if (last) {  // 3. encode and store the band
@@ -1851,6 +1932,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
         const Group g{(int)threadIdx.x - nprod, ncons, 2};
         int *rowoff = (int *)(smem + L.rowoff);
         unsigned short *map = (unsigned short *)(smem + L.map);
+        unsigned char *ftab = smem + L.ftab;
         for (int s = 0;; ++s) {
             const int b = s & 1;
             // a flag per batch parity: a thread already waiting for batch s + 1 cannot change
@@ -1863,7 +1945,7 @@ __global__ void __launch_bounds__(1024, 1) render_kernel_ws(RenderParams p) {
             if (mt.flags & kBatchEnd) break;
             if (mt.n > 0)
                 flush<F32, ST>(p, mt.by0, mt.by1, mt.n, keys, tris0 + (size_t)b * p.tri_cap, rowoff,
-                           map, s_warp, g);
+                               map, ftab, s_warp, g);
             mbar_arrive(&bars[2 + b]);  // release: this thread is done reading buffer b
             if (mt.flags & kBatchLast) {
                 Cam cm;
