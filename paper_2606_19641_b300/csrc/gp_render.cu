@@ -1610,12 +1610,16 @@ struct SetupMem {
 template <bool ST, class Emit>
 __device__ bool produce_item(const RenderParams &p, const Cam &cm, const WorldInfo &wi, int view,
                              Shared &sh, SetupMem &m, const Group &g, Emit &emit) {
-    // 1. cull clusters and boxes against the band frustum
-    for (int base = 0; base < wi.n_cl; base += g.nt) {
+    // 1. cull clusters and boxes against the band frustum.  The clusters hold only ground
+    //    quads; when the ground lies below the eye, each of their vertices (clipped ones
+    //    too) projects below the horizon (snapped Y >= 8 H), so a band whose pixel-centre
+    //    rows all lie above it (by1 < H / 2) can show none of them.
+    const int n_cl = (cm.by1 < (p.H >> 1) && fmaxf(0.f, p.line_z) < p.cam_h) ? 0 : wi.n_cl;
+    for (int base = 0; base < n_cl; base += g.nt) {
         const int c = base + g.tid;
         bool keep = false;
         Cluster cl{};
-        if (c < wi.n_cl) {
+        if (c < n_cl) {
             cl = p.clusters[wi.cl_begin + c];
             keep = aabb_visible(p, cm, cl.cx, cl.cy, cl.hx, cl.hy, cl.zlo, cl.zhi);
         }
