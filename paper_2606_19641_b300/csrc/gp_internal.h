@@ -31,6 +31,9 @@ struct WorldInfo {
     int lcell_begin;             // a finer grid over lane-line quads (same origin)
     int lgnx, lgny;
     float lginv;
+    int rcell_begin;             // a finer grid over road quads for the ray tracer (same origin)
+    int rgnx, rgny;
+    float rginv;
     int scell_begin;             // the same grid listing each road/line segment once, in the
                                  // cell of its centre-line midpoint (ids: road r, n_road + line l)
     int gnx, gny;
@@ -144,7 +147,7 @@ struct RenderParams {
 
     // ray tracing: ground quads in original order and their per-world grids
     const float4 *road_geo, *line_geo;
-    const int *cell_off, *cell_quads, *lcell_off, *lcell_quads;
+    const int *cell_off, *cell_quads, *lcell_off, *lcell_quads, *rcell_off, *rcell_quads;
     int trace_view0;         // first view of a ray-tracing launch
 
     int tri_cap;             // triangles per raster batch

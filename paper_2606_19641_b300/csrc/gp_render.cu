@@ -1360,8 +1360,8 @@ __device__ int trace_pixel(const RenderParams &p, const Cam &cm, const WorldInfo
         }
         const float tr = -oz / dz;
         if (!line_hit && tr >= p.near_plane && tr < best) {
-            const int q = ground_quad(wi, cm.px + tr * dx, cm.py + tr * dy, p.cell_off,
-                                      p.cell_quads, wi.cell_begin, wi.ginv, wi.gnx, wi.gny,
+            const int q = ground_quad(wi, cm.px + tr * dx, cm.py + tr * dy, p.rcell_off,
+                                      p.rcell_quads, wi.rcell_begin, wi.rginv, wi.rgnx, wi.rgny,
                                       p.road_geo);
             if (q >= 0) {
                 best = tr;
