@@ -843,47 +843,58 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         // x-extent of the quad within the row's y-band.  A point that passes the kernels'
         // FP32 containment test lies within rounding (far below 1 mm) of the quad, and their
         // cell index floor((p - origin) * ginv) is monotone in p, so it finds the quad.
+        // Built in two passes over the quads (count per cell, then fill at the scanned
+        // offsets), each cell's list in increasing quad index.
         auto build_cells = [&](const float *quads, int n, int index_base, float ginv, int gnx,
                                int gny, std::vector<int> &off, std::vector<int> &list) {
-            std::vector<std::vector<int>> cells((size_t)gnx * gny);
             const double eps = 1e-3, cell = 1.0 / ginv;
-            for (int r = 0; r < n; ++r) {
-                const float *q = quads + 8 * (size_t)r;
-                double qy0 = q[1], qy1 = q[1];
-                for (int k = 1; k < 4; ++k) {
-                    qy0 = std::min(qy0, (double)q[2 * k + 1]);
-                    qy1 = std::max(qy1, (double)q[2 * k + 1]);
-                }
-                const int cy0 = std::max(0, (int)std::floor(((float)(qy0 - eps) - by0) * ginv));
-                const int cy1 = std::min(gny - 1, (int)std::floor(((float)(qy1 + eps) - by0) * ginv));
-                for (int cy = cy0; cy <= cy1; ++cy) {
-                    const double ya = by0 + cy * cell - eps, yb = by0 + (cy + 1) * cell + eps;
-                    double xa = INFINITY, xb = -INFINITY;
-                    for (int k = 0; k < 4; ++k) {
-                        const double x0 = q[2 * k], y0 = q[2 * k + 1];
-                        const double x1 = q[(2 * k + 2) % 8], y1 = q[(2 * k + 3) % 8];
-                        if (y0 >= ya && y0 <= yb) {
-                            xa = std::min(xa, x0);
-                            xb = std::max(xb, x0);
-                        }
-                        for (const double yc : {ya, yb})
-                            if ((y0 - yc) * (y1 - yc) < 0.0) {
-                                const double x = x0 + (x1 - x0) * (yc - y0) / (y1 - y0);
-                                xa = std::min(xa, x);
-                                xb = std::max(xb, x);
-                            }
+            // calls row(r, cy, cx0, cx1) for every row of cells quad r overlaps
+            auto visit = [&](auto &&row) {
+                for (int r = 0; r < n; ++r) {
+                    const float *q = quads + 8 * (size_t)r;
+                    double qy0 = q[1], qy1 = q[1];
+                    for (int k = 1; k < 4; ++k) {
+                        qy0 = std::min(qy0, (double)q[2 * k + 1]);
+                        qy1 = std::max(qy1, (double)q[2 * k + 1]);
                     }
-                    if (!(xa <= xb)) continue;  // the quad misses this row's band
-                    const int cx0 = std::max(0, (int)std::floor(((float)(xa - eps) - bx0) * ginv));
-                    const int cx1 = std::min(gnx - 1, (int)std::floor(((float)(xb + eps) - bx0) * ginv));
-                    for (int cx = cx0; cx <= cx1; ++cx)
-                        cells[(size_t)cy * gnx + cx].push_back(index_base + r);
+                    const int cy0 = std::max(0, (int)std::floor(((float)(qy0 - eps) - by0) * ginv));
+                    const int cy1 = std::min(gny - 1, (int)std::floor(((float)(qy1 + eps) - by0) * ginv));
+                    for (int cy = cy0; cy <= cy1; ++cy) {
+                        const double ya = by0 + cy * cell - eps, yb = by0 + (cy + 1) * cell + eps;
+                        double xa = INFINITY, xb = -INFINITY;
+                        for (int k = 0; k < 4; ++k) {
+                            const double x0 = q[2 * k], y0 = q[2 * k + 1];
+                            const double x1 = q[(2 * k + 2) % 8], y1 = q[(2 * k + 3) % 8];
+                            if (y0 >= ya && y0 <= yb) {
+                                xa = std::min(xa, x0);
+                                xb = std::max(xb, x0);
+                            }
+                            for (const double yc : {ya, yb})
+                                if ((y0 - yc) * (y1 - yc) < 0.0) {
+                                    const double x = x0 + (x1 - x0) * (yc - y0) / (y1 - y0);
+                                    xa = std::min(xa, x);
+                                    xb = std::max(xb, x);
+                                }
+                        }
+                        if (!(xa <= xb)) continue;  // the quad misses this row's band
+                        const int cx0 = std::max(0, (int)std::floor(((float)(xa - eps) - bx0) * ginv));
+                        const int cx1 = std::min(gnx - 1, (int)std::floor(((float)(xb + eps) - bx0) * ginv));
+                        row(r, cy, cx0, cx1);
+                    }
                 }
-            }
-            for (auto &cl : cells) {
-                list.insert(list.end(), cl.begin(), cl.end());
-                off.push_back((int)list.size());
-            }
+            };
+            const size_t nc = (size_t)gnx * gny, base = list.size();
+            std::vector<int> pos(nc + 1, 0);
+            visit([&](int, int cy, int cx0, int cx1) {
+                for (int cx = cx0; cx <= cx1; ++cx) ++pos[(size_t)cy * gnx + cx + 1];
+            });
+            for (size_t c = 0; c < nc; ++c) pos[c + 1] += pos[c];
+            list.resize(base + (size_t)pos[nc]);
+            for (size_t c = 0; c < nc; ++c) off.push_back((int)(base + (size_t)pos[c + 1]));
+            visit([&](int r, int cy, int cx0, int cx1) {
+                for (int cx = cx0; cx <= cx1; ++cx)
+                    list[base + (size_t)pos[(size_t)cy * gnx + cx]++] = index_base + r;
+            });
         };
         wi.cell_begin = (int)cell_off.size() - 1;
         build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.ginv, wi.gnx, wi.gny, cell_off,
