@@ -12,6 +12,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -790,6 +791,72 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     std::vector<int> cell_off(1, 0), cell_quads, lcell_off(1, 0), lcell_quads, rcell_off(1, 0),
         rcell_quads, seg_off(1, 0),
         seg_list;
+    // The ground grids of every world (8 m off-road grid, 1 m lane-line grid, the tracer's
+    // road grid): queued by the world loop below, built in parallel after it and appended in
+    // world order.
+    struct GridJob {
+        int grid, w;
+        const float *quads;
+        int n, index_base;
+        float ginv;
+        int gnx, gny;
+        float bx0, by0;
+    };
+    std::vector<GridJob> grid_jobs;
+    // Built in two passes over the quads (count per cell, then fill at the scanned
+    // offsets), each cell's list in increasing quad index.
+    auto build_cells = [](const float *quads, int n, int index_base, float ginv, int gnx,
+                          int gny, float bx0, float by0, std::vector<int> &off,
+                          std::vector<int> &list) {
+        const double eps = 1e-3, cell = 1.0 / ginv;
+        // calls row(r, cy, cx0, cx1) for every row of cells quad r overlaps
+        auto visit = [&](auto &&row) {
+            for (int r = 0; r < n; ++r) {
+                const float *q = quads + 8 * (size_t)r;
+                double qy0 = q[1], qy1 = q[1];
+                for (int k = 1; k < 4; ++k) {
+                    qy0 = std::min(qy0, (double)q[2 * k + 1]);
+                    qy1 = std::max(qy1, (double)q[2 * k + 1]);
+                }
+                const int cy0 = std::max(0, (int)std::floor(((float)(qy0 - eps) - by0) * ginv));
+                const int cy1 = std::min(gny - 1, (int)std::floor(((float)(qy1 + eps) - by0) * ginv));
+                for (int cy = cy0; cy <= cy1; ++cy) {
+                    const double ya = by0 + cy * cell - eps, yb = by0 + (cy + 1) * cell + eps;
+                    double xa = INFINITY, xb = -INFINITY;
+                    for (int k = 0; k < 4; ++k) {
+                        const double x0 = q[2 * k], y0 = q[2 * k + 1];
+                        const double x1 = q[(2 * k + 2) % 8], y1 = q[(2 * k + 3) % 8];
+                        if (y0 >= ya && y0 <= yb) {
+                            xa = std::min(xa, x0);
+                            xb = std::max(xb, x0);
+                        }
+                        for (const double yc : {ya, yb})
+                            if ((y0 - yc) * (y1 - yc) < 0.0) {
+                                const double x = x0 + (x1 - x0) * (yc - y0) / (y1 - y0);
+                                xa = std::min(xa, x);
+                                xb = std::max(xb, x);
+                            }
+                    }
+                    if (!(xa <= xb)) continue;  // the quad misses this row's band
+                    const int cx0 = std::max(0, (int)std::floor(((float)(xa - eps) - bx0) * ginv));
+                    const int cx1 = std::min(gnx - 1, (int)std::floor(((float)(xb + eps) - bx0) * ginv));
+                    row(r, cy, cx0, cx1);
+                }
+            }
+        };
+        const size_t nc = (size_t)gnx * gny, base = list.size();
+        std::vector<int> pos(nc + 1, 0);
+        visit([&](int, int cy, int cx0, int cx1) {
+            for (int cx = cx0; cx <= cx1; ++cx) ++pos[(size_t)cy * gnx + cx + 1];
+        });
+        for (size_t c = 0; c < nc; ++c) pos[c + 1] += pos[c];
+        list.resize(base + (size_t)pos[nc]);
+        for (size_t c = 0; c < nc; ++c) off.push_back((int)(base + (size_t)pos[c + 1]));
+        visit([&](int r, int cy, int cx0, int cx1) {
+            for (int cx = cx0; cx <= cx1; ++cx)
+                list[base + (size_t)pos[(size_t)cy * gnx + cx]++] = index_base + r;
+        });
+    };
     h->worlds_h.resize(nw);
     for (int w = 0; w < nw; ++w) {
         WorldInfo wi{};
@@ -843,62 +910,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
         // x-extent of the quad within the row's y-band.  A point that passes the kernels'
         // FP32 containment test lies within rounding (far below 1 mm) of the quad, and their
         // cell index floor((p - origin) * ginv) is monotone in p, so it finds the quad.
-        // Built in two passes over the quads (count per cell, then fill at the scanned
-        // offsets), each cell's list in increasing quad index.
-        auto build_cells = [&](const float *quads, int n, int index_base, float ginv, int gnx,
-                               int gny, std::vector<int> &off, std::vector<int> &list) {
-            const double eps = 1e-3, cell = 1.0 / ginv;
-            // calls row(r, cy, cx0, cx1) for every row of cells quad r overlaps
-            auto visit = [&](auto &&row) {
-                for (int r = 0; r < n; ++r) {
-                    const float *q = quads + 8 * (size_t)r;
-                    double qy0 = q[1], qy1 = q[1];
-                    for (int k = 1; k < 4; ++k) {
-                        qy0 = std::min(qy0, (double)q[2 * k + 1]);
-                        qy1 = std::max(qy1, (double)q[2 * k + 1]);
-                    }
-                    const int cy0 = std::max(0, (int)std::floor(((float)(qy0 - eps) - by0) * ginv));
-                    const int cy1 = std::min(gny - 1, (int)std::floor(((float)(qy1 + eps) - by0) * ginv));
-                    for (int cy = cy0; cy <= cy1; ++cy) {
-                        const double ya = by0 + cy * cell - eps, yb = by0 + (cy + 1) * cell + eps;
-                        double xa = INFINITY, xb = -INFINITY;
-                        for (int k = 0; k < 4; ++k) {
-                            const double x0 = q[2 * k], y0 = q[2 * k + 1];
-                            const double x1 = q[(2 * k + 2) % 8], y1 = q[(2 * k + 3) % 8];
-                            if (y0 >= ya && y0 <= yb) {
-                                xa = std::min(xa, x0);
-                                xb = std::max(xb, x0);
-                            }
-                            for (const double yc : {ya, yb})
-                                if ((y0 - yc) * (y1 - yc) < 0.0) {
-                                    const double x = x0 + (x1 - x0) * (yc - y0) / (y1 - y0);
-                                    xa = std::min(xa, x);
-                                    xb = std::max(xb, x);
-                                }
-                        }
-                        if (!(xa <= xb)) continue;  // the quad misses this row's band
-                        const int cx0 = std::max(0, (int)std::floor(((float)(xa - eps) - bx0) * ginv));
-                        const int cx1 = std::min(gnx - 1, (int)std::floor(((float)(xb + eps) - bx0) * ginv));
-                        row(r, cy, cx0, cx1);
-                    }
-                }
-            };
-            const size_t nc = (size_t)gnx * gny, base = list.size();
-            std::vector<int> pos(nc + 1, 0);
-            visit([&](int, int cy, int cx0, int cx1) {
-                for (int cx = cx0; cx <= cx1; ++cx) ++pos[(size_t)cy * gnx + cx + 1];
-            });
-            for (size_t c = 0; c < nc; ++c) pos[c + 1] += pos[c];
-            list.resize(base + (size_t)pos[nc]);
-            for (size_t c = 0; c < nc; ++c) off.push_back((int)(base + (size_t)pos[c + 1]));
-            visit([&](int r, int cy, int cx0, int cx1) {
-                for (int cx = cx0; cx <= cx1; ++cx)
-                    list[base + (size_t)pos[(size_t)cy * gnx + cx]++] = index_base + r;
-            });
-        };
-        wi.cell_begin = (int)cell_off.size() - 1;
-        build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.ginv, wi.gnx, wi.gny, cell_off,
-                    cell_quads);
+        grid_jobs.push_back(GridJob{0, w, d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.ginv,
+                                    wi.gnx, wi.gny, bx0, by0});
         // lane-line strips are thin: a finer grid (1 m cells, at most 256 per side) keeps
         // their per-cell lists short for the ray tracer's lookups
         {
@@ -907,9 +920,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
             wi.lgnx = std::max(1, (int)std::ceil((bx1 - bx0) / lcs) + 1);
             wi.lgny = std::max(1, (int)std::ceil((by1 - by0) / lcs) + 1);
         }
-        wi.lcell_begin = (int)lcell_off.size() - 1;
-        build_cells(d->line + 8 * (size_t)l0, nl, wi.line_begin, wi.lginv, wi.lgnx, wi.lgny,
-                    lcell_off, lcell_quads);
+        grid_jobs.push_back(GridJob{1, w, d->line + 8 * (size_t)l0, nl, wi.line_begin, wi.lginv,
+                                    wi.lgnx, wi.lgny, bx0, by0});
         // the road quads again on a finer grid for the ray tracer, whose lookup scans a cell's
         // list up to the first quad holding the point: the overlapping roads of these worlds
         // put about a dozen quads in an 8 m cell (kTraceRoadCell cells, at most 256 a side);
@@ -921,9 +933,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
             wi.rgnx = std::max(1, (int)std::ceil((bx1 - bx0) / rcs) + 1);
             wi.rgny = std::max(1, (int)std::ceil((by1 - by0) / rcs) + 1);
         }
-        wi.rcell_begin = (int)rcell_off.size() - 1;
-        build_cells(d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.rginv, wi.rgnx, wi.rgny,
-                    rcell_off, rcell_quads);
+        grid_jobs.push_back(GridJob{2, w, d->road + 8 * (size_t)r0, nr, wi.road_begin, wi.rginv,
+                                    wi.rgnx, wi.rgny, bx0, by0});
         // each road/line segment once, in the cell of its centre-line midpoint (the same
         // FP32 expressions as the observation kernel's, so both agree on the cell)
         {
@@ -1011,6 +1022,38 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
             }
         }
         h->worlds_h[w] = wi;
+    }
+    {
+        // the queued grids on the host's cores, then appended in world order
+        const size_t nj = grid_jobs.size();
+        std::vector<std::vector<int>> joff(nj), jlist(nj);
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const size_t nt = std::min<size_t>(std::min(hw, 32u), std::max<size_t>(nj, 1));
+        auto work = [&](size_t t) {
+            for (size_t j = t; j < nj; j += nt) {
+                const GridJob &g = grid_jobs[j];
+                build_cells(g.quads, g.n, g.index_base, g.ginv, g.gnx, g.gny, g.bx0, g.by0,
+                            joff[j], jlist[j]);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < nt; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+        std::vector<int> *offs[3] = {&cell_off, &lcell_off, &rcell_off};
+        std::vector<int> *lists[3] = {&cell_quads, &lcell_quads, &rcell_quads};
+        for (size_t j = 0; j < nj; ++j) {
+            const GridJob &g = grid_jobs[j];
+            std::vector<int> &off = *offs[g.grid], &list = *lists[g.grid];
+            WorldInfo &wi = h->worlds_h[g.w];
+            (g.grid == 0 ? wi.cell_begin : (g.grid == 1 ? wi.lcell_begin : wi.rcell_begin)) =
+                (int)off.size() - 1;
+            const int base = (int)list.size();
+            for (const int e : joff[j]) off.push_back(base + e);
+            list.insert(list.end(), jlist[j].begin(), jlist[j].end());
+            std::vector<int>().swap(joff[j]);
+            std::vector<int>().swap(jlist[j]);
+        }
     }
     h->n_agents = (int)agent_world.size();
     h->n_boxes = nbox;
