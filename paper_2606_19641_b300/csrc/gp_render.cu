@@ -19,9 +19,11 @@
 //   3. raster: kept triangles are expanded into (triangle, row) items, dealt out so that
 //      one triangle's rows land in different warps; each item computes the exact covered
 //      span of its row from the integer edge functions (top-left fill rule); a warp then
-//      walks its spans' pixels -- each lane its own span when the spans are even, 32
-//      fragments at a time when a few long spans dominate -- and resolves depth per pixel
-//      in shared memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or
+//      walks its spans' pixels -- with FP32 keys each lane its own span when the spans are
+//      even, else 32 fragments at a time found by binary search over the spans' prefix
+//      sums; with FP16 keys each lane one odd-length run of the concatenated fragments, the
+//      spans' parameters read from a per-warp table -- and resolves depth per pixel in
+//      shared memory with atomicMax on a key: (FP32 depth bits << 32 | ~prim), or
 //      (binary16 depth << 16 | ~prim) in FP16 mode; the nearest surface wins, ties go to
 //      the smaller primitive id;
 //   4. encode: keys become class ids (uint8) + depth, a normalised one-hot BF16 NCHW
