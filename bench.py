@@ -510,21 +510,29 @@ def main():
     h_flags = torch.empty((n_agents,), dtype=torch.uint8).pin_memory()
     d_state = torch.empty((n_agents, 4), dtype=torch.float32, device="cuda")
     d_flags = torch.empty((n_agents,), dtype=torch.uint8, device="cuda")
+    if not trace:  # untimed: the host call's graph (keyed on its staging buffer) is captured here
+        sim.step_render_host(h_acts[0], out, depth, h_state, h_flags, stream=stream)
+        stream.synchronize()
     barrier()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        act.copy_(h_acts[k], non_blocking=True)
-        step_render(act, out, depth)
-        sim.get_state_device(d_state, d_flags)
-        h_state.copy_(d_state, non_blocking=True)
-        h_flags.copy_(d_flags, non_blocking=True)
+        if trace:  # five calls: copy in, step + trace, state export, two copies out
+            act.copy_(h_acts[k], non_blocking=True)
+            step_render(act, out, depth)
+            sim.get_state_device(d_state, d_flags)
+            h_state.copy_(d_state, non_blocking=True)
+            h_flags.copy_(d_flags, non_blocking=True)
+        else:  # one call: gp_step_render_host
+            sim.step_render_host(h_acts[k], out, depth, h_state, h_flags, stream=stream)
         stream.synchronize()
     e2e_s = maxred(time.perf_counter() - t0)
     e2e = {"value": job_rate(total_agents, e2e_steps, 1e3 * e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": h_act.numel() * 4,
            "d2h_bytes_per_step": h_state.numel() * 4 + h_flags.numel(),
-           "note": "actions host->device and agent state/flags device->host every step; "
-                   "images stay on the GPU as a batched tensor"}
+           "note": "actions host->device and agent state/flags device->host every step "
+                   "(one gp_step_render_host call per step for the raster), the host waiting "
+                   "for each step's state; images stay on the GPU as a batched tensor; no L2 "
+                   "flush between steps (each step writes 671 MB of images, 5x the L2)"}
 
     extras = {}
 

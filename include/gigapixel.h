@@ -283,6 +283,21 @@ gp_status gp_step_trace(gp_handle *h, const float *actions_dev, void *out_dev,
                         void *depth_dev, void *stream);
 
 /*
+ * One closed-loop step for a policy that runs on the host (Sec. 3.1: actions in, the next
+ * state and the images out): copies actions_host[n_agents][2] (pinned host memory, layout
+ * as gp_step) to a library-owned device buffer, replays the gp_step_render graph on it,
+ * and copies the post-step agent state (as gp_get_state: x, y, yaw, v per agent) and flags
+ * to state_host / flags_host (pinned; either may be NULL).  The images stay on the device
+ * in out_dev / depth_dev.  One call instead of five (copy in, step+render, state export,
+ * two copies out).  Asynchronous on `stream`: synchronise it before reading state_host or
+ * flags_host, and before overwriting actions_host.  Pageable host memory is refused with
+ * GP_EINVAL (its copies would not be asynchronous).
+ */
+gp_status gp_step_render_host(gp_handle *h, const float *actions_host, void *out_dev,
+                              void *depth_dev, float *state_host, uint8_t *flags_host,
+                              void *stream);
+
+/*
  * Per-world path: step or render one world only (one launch each), writing the world's
  * slice of the same tensors (actions/out/depth point at the start of the FULL arrays).
  * The paper has no counterpart: it is the plain one-world-at-a-time baseline against which

@@ -34,7 +34,7 @@ TRI_DTYPE = np.dtype([("X", "<i4", (3,)), ("Y", "<i4", (3,)), ("d", "<f4", (3,))
                       ("prim", "<u4"), ("sub", "<u4")])
 
 EXPORTED = ("gp_default_config", "gp_create_worlds", "gp_destroy", "gp_step", "gp_render", "gp_trace",
-            "gp_step_render", "gp_step_trace", "gp_step_world", "gp_render_world", "gp_get_state",
+            "gp_step_render", "gp_step_render_host", "gp_step_trace", "gp_step_world", "gp_render_world", "gp_get_state",
             "gp_set_state", "gp_get_info", "gp_get_status", "gp_clear_status",
             "gp_get_rewards", "gp_set_reward_weights", "gp_observe_vec",
             "gp_get_dynamics", "gp_set_dynamics", "gp_set_signal_states", "gp_reset_worlds",
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "gp_render": [vp, vp, vp, vp],
         "gp_step_render": [vp, vp, vp, vp, vp],
         "gp_step_trace": [vp, vp, vp, vp, vp],
+        "gp_step_render_host": [vp, vp, vp, vp, vp, vp, vp],
         "gp_step_world": [vp, i32, vp, vp],
         "gp_render_world": [vp, i32, vp, vp, vp],
         "gp_get_state": [vp, vp, vp, ctypes.c_int, vp],
@@ -290,6 +291,25 @@ class Simulator:
                                  % (name, t.numel(), tuple(t.shape), numel))
         return t.data_ptr()
 
+    def _host(self, t, dtype, numel: int, name: str) -> int:
+        """Address of a pinned host tensor the library will copy from or to, after checking
+        its dtype, element count and contiguity (the library refuses pageable memory)."""
+        import torch
+        if t is None:
+            return 0
+        if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+            raise GigapixelError(GP_EINVAL, "%s: expected a pinned CPU tensor" % name)
+        if not t.is_pinned():
+            raise GigapixelError(GP_EINVAL, "%s: CPU tensor is not pinned" % name)
+        if t.dtype != dtype:
+            raise GigapixelError(GP_EINVAL, "%s: dtype %s, expected %s" % (name, t.dtype, dtype))
+        if not t.is_contiguous():
+            raise GigapixelError(GP_EINVAL, "%s: tensor is not contiguous" % name)
+        if t.numel() != numel:
+            raise GigapixelError(GP_EINVAL, "%s: %d elements (shape %s), expected %d"
+                                 % (name, t.numel(), tuple(t.shape), numel))
+        return t.data_ptr()
+
     def _actions(self, actions) -> int:
         import torch
         return self._dev(actions, torch.float32, 2 * self.n_agents, "actions")
@@ -319,6 +339,17 @@ class Simulator:
         a = self._actions(actions)
         o, d = self._images(out, depth)
         check(lib().gp_step_render(self._h, a, o, d, _stream(stream)))
+
+    def step_render_host(self, actions, out, depth=None, state=None, flags=None,
+                         stream=None) -> None:
+        """One closed-loop step from pinned host actions to pinned host state (asynchronous:
+        synchronise `stream` before reading state/flags or refilling actions)."""
+        import torch
+        a = self._host(actions, torch.float32, 2 * self.n_agents, "actions")
+        o, d = self._images(out, depth)
+        sp = self._host(state, torch.float32, 4 * self.n_agents, "state")
+        fp = self._host(flags, torch.uint8, self.n_agents, "flags")
+        check(lib().gp_step_render_host(self._h, a, o, d, sp, fp, _stream(stream)))
 
     def step_trace(self, actions, out, depth=None, stream=None) -> None:
         """One step then the ray-traced render, replayed from a CUDA graph."""

@@ -117,6 +117,7 @@ struct gp_handle {
     DevBuf<float> reward, ego, weights;  // per-step rewards: [n_agents], [n_agents][GP_EGO_DIM], [n_agents][10]
     DevBuf<float> jerk;                  // jerk dynamics' actuator state [n_agents][3]
     DevBuf<float2> acc;                  // previous-step accelerations
+    DevBuf<float2> act_stage;            // actions copied in by gp_step_render_host
     DevBuf<uint8_t> flag_stage, world_stage;  // host-copy staging: per agent, per world
     Shape shape;
     uint16_t onehot[4][2];
@@ -432,6 +433,21 @@ gp_status check_reach(const gp_handle *h, const void *p, const char *what) {
     return GP_OK;
 }
 
+// Is p page-locked host memory (so that a copy from or to it is asynchronous)?  Null passes.
+gp_status check_pinned(const void *p, const char *what) {
+    if (!p) return GP_OK;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GP_EINVAL, std::string(what) + ": not a pointer CUDA knows (" +
+                                   cudaGetErrorString(e) + ")");
+    }
+    if (a.type != cudaMemoryTypeHost)
+        return fail(GP_EINVAL, std::string(what) + " must be pinned (page-locked) host memory");
+    return GP_OK;
+}
+
 gp_status check_reach(const gp_handle *h, const void *actions, const void *out,
                       const void *depth) {
     gp_status st = check_reach(h, actions, "actions_dev");
@@ -667,6 +683,7 @@ void release_all(gp_handle *h) {
     h->dump.release();
     h->state_stage.release();
     h->flag_stage.release();
+    h->act_stage.release();
     h->world_stage.release();
 }
 
@@ -1151,6 +1168,8 @@ gp_status gp_create_worlds(const gp_world_desc *d, const gp_config *cfg, int dev
     UP(state_stage, stage);
     std::vector<uint8_t> fstage(std::max(1, h->n_agents), 0);
     UP(flag_stage, fstage);
+    std::vector<float2> astage(std::max(1, h->n_agents), make_float2(0.f, 0.f));
+    UP(act_stage, astage);
     std::vector<uint8_t> wstage(std::max(1, nw), 0);
     UP(world_stage, wstage);
     {
@@ -1296,6 +1315,32 @@ gp_status gp_step_render(gp_handle *h, const float *actions, void *out, void *de
                          void *stream) {
     NvtxRange range("gp_step_render");
     return step_then_render(h, actions, out, depth, stream, 0);
+}
+
+gp_status gp_step_render_host(gp_handle *h, const float *actions_host, void *out, void *depth,
+                              float *state_host, uint8_t *flags_host, void *stream) {
+    NvtxRange range("gp_step_render_host");
+    if (!h) return fail(GP_EINVAL, "null handle");
+    if (!actions_host) return fail(GP_EINVAL, "actions_host is null");
+    CK(cudaSetDevice(h->device));
+    gp_status st = check_pinned(actions_host, "actions_host");
+    if (st == GP_OK) st = check_pinned(state_host, "state_host");
+    if (st == GP_OK) st = check_pinned(flags_host, "flags_host");
+    if (st != GP_OK) return st;
+    if (h->sticky) return fail(GP_EDEVICE, "device status word has an error bit set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = h->n_agents;
+    if (n) CK(cudaMemcpyAsync(h->act_stage.p, actions_host, sizeof(float2) * n, cudaMemcpyHostToDevice, s));
+    st = step_then_render(h, (const float *)h->act_stage.p, out, depth, stream, 0);
+    if (st != GP_OK) return st;
+    if (n && (state_host || flags_host)) {
+        CK(launch_state(h->state_stage.p, h->flag_stage.p, h->box_pose.p, h->speed.p, h->flags.p,
+                        h->agent_box.p, n, 1, s));
+        if (state_host)
+            CK(cudaMemcpyAsync(state_host, h->state_stage.p, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, s));
+        if (flags_host) CK(cudaMemcpyAsync(flags_host, h->flag_stage.p, n, cudaMemcpyDeviceToHost, s));
+    }
+    return GP_OK;
 }
 
 gp_status gp_step_trace(gp_handle *h, const float *actions, void *out, void *depth,

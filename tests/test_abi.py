@@ -129,6 +129,7 @@ def test_null_handle_calls_fail_cleanly(gp):
     L = gp.lib()
     assert L.gp_step(None, None, None) == -1
     assert L.gp_render(None, None, None, None) == -1
+    assert L.gp_step_render_host(None, None, None, None, None, None, None) == -1
     assert L.gp_destroy(None) == 0
     assert L.gp_get_info(None, None) == -1
     assert L.gp_get_dynamics(None, None, 1, None) == -1

@@ -444,6 +444,48 @@ def test_graph_and_per_world_paths_match_direct_calls(shape):
     assert (fa & 16).any()  # some agent ran a red light and was halted on every path
 
 
+def test_host_step_matches_graph_path():
+    """gp_step_render_host (pinned host actions in, pinned host state out, one call) gives the
+    images and states of gp_step_render + gp_get_state on device buffers, step after step,
+    and refuses pageable host buffers before any launch."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    wl = wg.WORKLOADS["ragged"]
+    worlds = wg.make_workload(wl, n_worlds=6)
+    a, cfg = sim_for(worlds, wl)
+    b, _ = sim_for(worlds, wl)
+    oa, da = a.alloc_outputs()
+    ob, db = b.alloc_outputs()
+    n = worlds.n_agents
+    act = torch.empty((n, 2), device="cuda")
+    h_act = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    h_state = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    h_flags = torch.empty((n,), dtype=torch.uint8).pin_memory()
+    for k in range(4):
+        acts = torch_actions(worlds, k, wl.seed)[0]
+        act.copy_(acts)
+        h_act.copy_(acts.cpu())
+        a.step_render(act, oa, da)
+        b.step_render_host(h_act, ob, db, h_state, h_flags)
+        torch.cuda.synchronize()
+        assert torch.equal(oa, ob) and torch.equal(da.view(torch.int32), db.view(torch.int32))
+        sa, fa = a.get_state()
+        assert np.array_equal(sa, h_state.numpy()) and np.array_equal(fa, h_flags.numpy())
+    L, h = gp.lib(), b._h
+    page = np.zeros((n, 4), np.float32)  # pageable host memory
+    assert L.gp_step_render_host(h, page.ctypes.data, ob.data_ptr(), None, None, None,
+                                 None) == gp.binding.GP_EINVAL
+    assert L.gp_step_render_host(h, h_act.data_ptr(), ob.data_ptr(), None, page.ctypes.data,
+                                 None, None) == gp.binding.GP_EINVAL
+    assert "pinned" in L.gp_last_error().decode()
+    with pytest.raises(gp.GigapixelError):
+        b.step_render_host(act, ob, db)  # a device tensor where pinned host memory belongs
+    torch.cuda.synchronize()
+    sb, fb = b.get_state()
+    assert np.array_equal(sb, h_state.numpy())  # the refused calls stepped nothing
+    assert b.status() == 0
+
+
 def test_state_roundtrip_and_fork():
     import torch
     wl = wg.WORKLOADS["uniform"]
