@@ -357,6 +357,42 @@ def test_edge_case_worlds():
 
 
 @pytest.mark.parametrize("precision", [False, True], ids=["f32", "f16"])
+def test_full_width_spans_fill_a_wave(precision):
+    """The largest wave of the fragment walk: 32 boxes one behind the other, each front face
+    (30 m wide, 21 m tall, 5..14 m ahead, inside the guard band, its diagonal above the view)
+    covering whole 512-pixel rows, so every wave of 32 row items carries 32 full-width spans
+    (16 384 fragments: the walk's packed span fields at their limits).  Raster parity (T3)
+    on the GPU's own triangles."""
+    import torch
+    import paper_2606_19641_b300 as gp
+    n = 32
+    boxes = np.zeros((n + 1, 7), np.float32)
+    boxes[0] = [0, 0, 0, 4.5, 1.9, 1.5, 0.0]  # the agent, facing +x
+    for k in range(n):
+        boxes[k + 1] = [5.1 + 0.3 * k, 0, 0, 0.2, 30.0, 21.0, 0.0]
+    worlds = wg.Worlds(box_off=np.array([0, n + 1], np.int32), agent_count=np.array([1], np.int32),
+                       boxes=boxes, road_off=np.array([0, 0], np.int32), road=np.zeros((0, 8), np.float32),
+                       line_off=np.array([0, 0], np.int32), line=np.zeros((0, 8), np.float32))
+    wl = wg.WORKLOADS["tiny"]
+    extra = dict(key_precision=gp.KEY_F16) if precision else {}
+    sim, cfg = sim_for(worlds, wl, width=512, height=512, band_rows=16, **extra)
+    out, depth = sim.alloc_outputs()
+    sim.render(out, depth)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    assert check_t3(sim, cfg, worlds, [0], out, depth) > 300 * 512
+    o = out.cpu().numpy()[0]
+    assert (o[:300] == 3).all()  # every pixel of the upper rows shows the nearest box face
+    # the counters of the same render: every box face covers >= 282 whole rows, so the
+    # waves above row 282 are all full-width spans
+    cnt, _ = sim_for(worlds, wl, width=512, height=512, band_rows=16, stats=1, **extra)
+    cnt.render_stats(reset=True)
+    cnt.render(out, depth)
+    st = cnt.render_stats(reset=True)
+    assert st["fragments"] >= n * 282 * 512, st
+
+
+@pytest.mark.parametrize("precision", [False, True], ids=["f32", "f16"])
 def test_maximum_sizes(precision):
     """The documented limits at once: a world of GP_MAX_BOXES = 128 boxes that are all
     agents, GP_MAX_CAMS = 8 cameras per agent (every 45 deg), 2000 road segments (20 300
