@@ -1782,18 +1782,30 @@ __global__ void __launch_bounds__(1024, 1) render_kernel(RenderParams p) {
     auto emit = [&](bool last) -> TriRec * {
         const int n = sh.resv;
         if (n > 0) flush<F32, ST>(p, cm.by0, cm.by1, n, keys, tris, rowoff, map, ftab, s_warp, g);
-        if (g.tid == 0) sh.resv = 0;
+        if (g.tid == 0) {
+            sh.resv = 0;
+            // The item's last batch: fetch the next item and reset the block state now, so
+            // that after the encode each warp goes straight on to the next item's cull
+            // (which touches neither the keys nor this item's camera; the keys are written
+            // again only after that cull's barrier).
+            if (last) {
+                sh.item = p.work_counter ? atomicAdd(p.work_counter, 1) : p.n_items;
+                sh.next_unit = 0;
+                sh.npend = 0;
+                sh.nvcl = 0;
+                sh.nvbox = 0;
+                sh.nvsig = 0;
+                sh.cq_n = 0;
+            }
+        }
         g.sync();
         if (last) {  // 3. encode and store the band
             if (F32) encode_f32(p, cm, (unsigned long long *)keys, view, g);
             else encode_f16(p, cm, keys, view, g);
-            g.sync();
         }
         return tris;
     };
-    for (int iter = 0;; ++iter) {
-        const int item = next_item(p, sh, iter, g);
-        if (item >= p.n_items) break;
+    for (int item = next_item(p, sh, 0, g); item < p.n_items; item = sh.item) {
         make_cam(p, item, cm, wi, view);
         produce_item<ST>(p, cm, wi, view, sh, m, g, emit);
     }
